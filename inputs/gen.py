@@ -1,0 +1,243 @@
+"""Seeded input generators for the k.p hole eigensolve workloads.
+
+Every array is drawn from ``numpy.random.Generator(PCG64(seed))`` with
+seed = 1000 + workload index, so the oracle and the CUDA path see the same
+bytes.  Grid conventions (both sides follow them):
+
+* interior points ``ix = 0..nx-1`` sit at ``x = (ix + 1) h``; the box length
+  is ``L_x = (nx + 1) h`` (the wave function vanishes on the enclosing layer);
+* scalar fields are ``float64[nz][ny][nx]`` (x fastest), i.e. point index
+  ``p = ix + nx * (iy + ny * iz)``;
+* strain is ``float64[6][nz][ny][nx]`` with components
+  ``(xx, yy, zz, yz, xz, xy)`` of the symmetric strain tensor in the grid frame;
+* ``rot`` is 3x3, row ``a`` = grid axis ``a`` written in crystal coordinates.
+
+The potentials stand in for the paper's self-consistent gate potentials of the
+5-gate FinFET (Sec. II A-B), which are not available: a harmonic double well,
+a row of five Gaussian gate wells/barriers with a linear field, and sweeps of
+two Gaussian plunger wells.  Energies are in eV, lengths in nm, B in tesla.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+# Material presets.  "paper_tab1" is Table I of the paper (Si); "bj" is the
+# parameter set the benchmark workloads are specified with.
+MATERIALS = {
+    "bj": dict(gamma1=4.285, gamma2=0.339, gamma3=1.446, delta_so=0.044,
+               kappa=-0.42, a_v=2.38, b=-2.1, d=-4.85),
+    "paper_tab1": dict(gamma1=4.285, gamma2=0.339, gamma3=1.21, delta_so=0.044,
+                       kappa=-0.42, a_v=2.46, b=-2.35, d=-5.32),
+}
+
+ROT_IDENTITY = np.eye(3)
+# Device frame of Sec. II A: x = [110], y = [-110], z = [001].
+ROT_DEVICE = np.array([[1.0, 1.0, 0.0],
+                       [-1.0, 1.0, 0.0],
+                       [0.0, 0.0, np.sqrt(2.0)]]) / np.sqrt(2.0)
+
+# hbar^2 / (2 m0) in eV nm^2; used here only to set the harmonic stiffness
+# of the double-well potential from a level spacing hbar*omega.
+_HB2M = 0.0380998212
+
+
+@dataclass
+class Problem:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    material: dict
+    rot: np.ndarray
+    V: np.ndarray                        # float64[nz][ny][nx], eV
+    strain: Optional[np.ndarray] = None  # float64[6][nz][ny][nx] or None
+    B: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    gauge: int = 0                       # 0 symmetric (box centre), 1 Landau
+    mask: Optional[np.ndarray] = None    # uint8[nz][ny][nx], 0 = excluded
+    levers: Optional[np.ndarray] = None  # float64[n_gates][nz][ny][nx]
+    n_states: int = 8
+    block_m: int = 16
+    degree: int = 20
+    precision: int = 0                   # 0 plain fp64, 1 mixed
+    refine_sweeps: int = 2
+    tol_ev: float = 1e-9
+    seed: int = 0
+
+    @property
+    def n_points(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_unknowns(self) -> int:
+        return 6 * self.n_points
+
+    def with_(self, **kw) -> "Problem":
+        return replace(self, **kw)
+
+
+def _coords(n: int, h: float) -> np.ndarray:
+    return (np.arange(n, dtype=np.float64) + 1.0) * h
+
+
+def _mesh(nx, ny, nz, h):
+    z, y, x = np.meshgrid(_coords(nz, h), _coords(ny, h), _coords(nx, h), indexing="ij")
+    return x, y, z
+
+
+def smooth_noise(rng: np.random.Generator, shape, passes: int = 3) -> np.ndarray:
+    """i.i.d. N(0,1) smoothed by a separable [1,2,1]/4 filter, `passes` times
+    per axis (edge values replicated); unit standard deviation afterwards."""
+    a = rng.standard_normal(shape)
+    for axis in range(a.ndim):
+        for _ in range(passes):
+            pad = [(0, 0)] * a.ndim
+            pad[axis] = (1, 1)
+            b = np.pad(a, pad, mode="edge")
+            lo = [slice(None)] * a.ndim
+            mid = [slice(None)] * a.ndim
+            hi = [slice(None)] * a.ndim
+            lo[axis] = slice(0, -2)
+            mid[axis] = slice(1, -1)
+            hi[axis] = slice(2, None)
+            a = 0.25 * b[tuple(lo)] + 0.5 * b[tuple(mid)] + 0.25 * b[tuple(hi)]
+    s = a.std()
+    return a / s if s > 0 else a
+
+
+def _strain_field(rng, nz, ny, nx, max_abs=1e-3):
+    eps = np.empty((6, nz, ny, nx))
+    for c in range(6):
+        f = smooth_noise(rng, (nz, ny, nx))
+        eps[c] = f * (max_abs / np.abs(f).max())
+    return eps
+
+
+def _double_well(nx, ny, nz, h, hw=5e-3, gamma1=4.285):
+    """Harmonic double well with minima at 0.3 L_x and 0.7 L_x, level
+    spacing hw along each axis for a particle of mass m0/gamma1."""
+    x, y, z = _mesh(nx, ny, nz, h)
+    Lx, Ly, Lz = (nx + 1) * h, (ny + 1) * h, (nz + 1) * h
+    K = hw * hw / (2.0 * gamma1 * _HB2M)
+    dx2 = np.minimum((x - 0.3 * Lx) ** 2, (x - 0.7 * Lx) ** 2)
+    return 0.5 * K * (dx2 + (y - 0.5 * Ly) ** 2 + (z - 0.5 * Lz) ** 2)
+
+
+def _gate_levers(nx, ny, nz, h, n_gates=5, s_perp=6.0):
+    """Unit-amplitude Gaussian lever fields under five equally spaced gates."""
+    x, y, z = _mesh(nx, ny, nz, h)
+    Lx, Ly, Lz = (nx + 1) * h, (ny + 1) * h, (nz + 1) * h
+    sx = Lx / 20.0
+    out = np.empty((n_gates, nz, ny, nx))
+    for g in range(n_gates):
+        xg = (g + 0.5) * Lx / n_gates
+        out[g] = np.exp(-((x - xg) ** 2) / (2 * sx * sx)
+                        - ((y - 0.5 * Ly) ** 2 + (z - 0.5 * Lz) ** 2) / (2 * s_perp * s_perp))
+    return out
+
+
+def config1() -> Problem:
+    """10x8x8 grid, h = 1 nm, harmonic double well (hw = 5 meV) plus smooth
+    noise of 1 meV rms, B = 0, no strain, lowest 8 states."""
+    rng = np.random.Generator(np.random.PCG64(1000))
+    nx, ny, nz, h = 10, 8, 8, 1.0
+    V = _double_well(nx, ny, nz, h) + 1e-3 * smooth_noise(rng, (nz, ny, nx))
+    return Problem("c1_10x8x8_fp64", nx, ny, nz, h, dict(MATERIALS["bj"]), ROT_IDENTITY.copy(),
+                   V, None, np.zeros(3), 0, n_states=8, block_m=16, degree=20, seed=1000)
+
+
+def config2() -> Problem:
+    """160x48x48 FinFET-shaped grid, h = 0.5 nm (2.21M unknowns), device
+    frame, five Gaussian gate wells/barriers (+-20 meV) and a 1 mV/nm field,
+    B = 0.5 T along [110], smooth strain |eps| <= 1e-3, lowest 16 states."""
+    rng = np.random.Generator(np.random.PCG64(1001))
+    nx, ny, nz, h = 160, 48, 48, 0.5
+    x, y, z = _mesh(nx, ny, nz, h)
+    Lx, Ly, Lz = (nx + 1) * h, (ny + 1) * h, (nz + 1) * h
+    A = rng.uniform(-0.02, 0.02, size=5)
+    sx, sp = Lx / 20.0, 6.0
+    V = 1e-3 * (z - 0.5 * Lz)
+    for g in range(5):
+        xg = (g + 0.5) * Lx / 5.0
+        V = V + A[g] * np.exp(-((x - xg) ** 2) / (2 * sx * sx)
+                              - ((y - 0.5 * Ly) ** 2 + (z - 0.5 * Lz) ** 2) / (2 * sp * sp))
+    eps = _strain_field(rng, nz, ny, nx)
+    return Problem("c2_160x48x48_fp64", nx, ny, nz, h, dict(MATERIALS["bj"]), ROT_DEVICE.copy(),
+                   V, eps, np.array([0.5, 0.0, 0.0]), 0, n_states=16, block_m=24,
+                   degree=20, seed=1001)
+
+
+def config3() -> Problem:
+    """Config-1 physics, mixed precision: FP32 Chebyshev filter of degree 20
+    on a block of 24, FP64 Rayleigh-Ritz and 2 FP64 refinement sweeps."""
+    p = config1()
+    return p.with_(name="c3_10x8x8_mixed", block_m=24, degree=20, precision=1,
+                   refine_sweeps=2, seed=1002)
+
+
+def config4(count: int = 64):
+    """64 detuning sweep points on uneven grids 96..160 x 40..48 x 40..48
+    (h = 0.5 nm): two Gaussian plunger wells with depths in [-25, -10] meV,
+    the transverse harmonic confinement of config 1, 1 meV noise and B in
+    [0, 1] T along x; lowest 12 states each."""
+    rng = np.random.Generator(np.random.PCG64(1003))
+    out = []
+    h = 0.5
+    K = (5e-3) ** 2 / (2.0 * 4.285 * _HB2M)
+    for k in range(count):
+        nx = int(rng.choice(np.arange(96, 161, 8)))
+        nyz = int(rng.choice([40, 44, 48]))
+        ny = nz = nyz
+        dL, dR = rng.uniform(-0.025, -0.010, size=2)
+        b = rng.uniform(0.0, 1.0)
+        x, y, z = _mesh(nx, ny, nz, h)
+        Lx, Ly, Lz = (nx + 1) * h, (ny + 1) * h, (nz + 1) * h
+        s = 4.0
+        r2t = (y - 0.5 * Ly) ** 2 + (z - 0.5 * Lz) ** 2
+        GL = np.exp(-((x - 0.3 * Lx) ** 2 + r2t) / (2 * s * s))
+        GR = np.exp(-((x - 0.7 * Lx) ** 2 + r2t) / (2 * s * s))
+        V = dL * GL + dR * GR + 0.5 * K * r2t + 1e-3 * smooth_noise(rng, (nz, ny, nx))
+        out.append(Problem(f"c4_sweep{k:02d}_{nx}x{ny}x{nz}", nx, ny, nz, h,
+                           dict(MATERIALS["bj"]), ROT_IDENTITY.copy(), V, None,
+                           np.array([b, 0.0, 0.0]), 0, n_states=12, block_m=16,
+                           degree=20, seed=1003))
+    return out
+
+
+def config5() -> Problem:
+    """200x64x64 grid, h = 0.5 nm (4.9M unknowns), config-1 physics scaled to
+    the box, B = 0, no strain; five Gaussian gate-lever fields; lowest 8."""
+    rng = np.random.Generator(np.random.PCG64(1004))
+    nx, ny, nz, h = 200, 64, 64, 0.5
+    V = _double_well(nx, ny, nz, h) + 1e-3 * smooth_noise(rng, (nz, ny, nx))
+    return Problem("c5_200x64x64_grad", nx, ny, nz, h, dict(MATERIALS["bj"]), ROT_IDENTITY.copy(),
+                   V, None, np.zeros(3), 0, levers=_gate_levers(nx, ny, nz, h),
+                   n_states=8, block_m=16, degree=20, seed=1004)
+
+
+def small_problem(nx, ny, nz, h=1.0, seed=7, rot="identity", B=(0.0, 0.0, 0.0),
+                  gauge=0, strain=True, material="bj", mask=False, levers=0,
+                  noise_mev=1.0, n_states=8, block_m=16) -> Problem:
+    """A small seeded problem of any shape for parity tests: double well +
+    noise, optional smooth strain, optional random point mask, optional
+    Gaussian gate levers."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    V = _double_well(nx, ny, nz, h) + noise_mev * 1e-3 * smooth_noise(rng, (nz, ny, nx))
+    eps = _strain_field(rng, nz, ny, nx) if strain else None
+    R = ROT_DEVICE.copy() if rot == "device" else ROT_IDENTITY.copy()
+    msk = None
+    if mask:
+        msk = (rng.uniform(size=(nz, ny, nx)) > 0.15).astype(np.uint8)
+    lev = _gate_levers(nx, ny, nz, h, n_gates=levers, s_perp=max(1.0, 0.25 * ny * h)) if levers else None
+    return Problem(f"small_{nx}x{ny}x{nz}", nx, ny, nz, h, dict(MATERIALS[material]), R, V, eps,
+                   np.asarray(B, dtype=np.float64), gauge, mask=msk, levers=lev,
+                   n_states=n_states, block_m=block_m, seed=seed)
+
+
+def random_block(n_rows: int, m: int, seed: int) -> np.ndarray:
+    """Complex128 [n_rows][m] block with i.i.d. N(0,1) real and imaginary parts."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((n_rows, m)) + 1j * rng.standard_normal((n_rows, m))

@@ -1,0 +1,371 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against a closed form, an independently written
+textbook matrix, a physical invariant or brute force, chosen so that a
+plausible mistake (a dropped term, a wrong sign or index, a transposed
+operand) fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import eig, kp, observables
+from tests.metrics import subspace_sin_angle
+
+C = kp.HBAR2_OVER_2M0
+
+
+def _box(nx, ny, nz, h=1.0, **kw):
+    return inputs.small_problem(nx, ny, nz, h=h, **kw)
+
+
+# --------------------------------------------------------------------------
+# closed form: gamma2 = gamma3 = 0, V = 0, B = 0, no strain -> particle in a
+# box, E_k x4 (j = 3/2) and E_k + Delta x2 (j = 1/2), any Delta
+@pytest.mark.parametrize("shape,h,delta", [((5, 4, 3), 0.7, 0.044), ((6, 3, 4), 0.5, 0.3)])
+def test_box_closed_form(shape, h, delta):
+    p = _box(*shape, h=h, strain=False, noise_mev=0.0)
+    p.material.update(gamma2=0.0, gamma3=0.0, delta_so=delta)
+    p.V[:] = 0.0
+    w = eig.all_eigenvalues_dense(kp.assemble(p))
+    g1 = p.material["gamma1"]
+    ref = []
+    nx, ny, nz = shape
+    for kx in range(1, nx + 1):
+        for ky in range(1, ny + 1):
+            for kz in range(1, nz + 1):
+                E = C * g1 * sum(2 - 2 * np.cos(k * np.pi / (n + 1))
+                                 for k, n in ((kx, nx), (ky, ny), (kz, nz))) / h ** 2
+                ref += [E] * 4 + [E + delta] * 2
+    assert np.abs(w - np.sort(ref)).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# textbook 6x6 Luttinger-Kohn matrix in the |J, m_j> basis (P, Q, R, S form),
+# typed independently of the oracle's tensor construction
+def _pqrs_kinetic(K, g1, g2, g3):
+    """Luttinger P, Q, R, S with k_i k_j -> K[i, j] (crystal frame)."""
+    kx2, ky2, kz2 = K[0, 0], K[1, 1], K[2, 2]
+    P = C * g1 * (kx2 + ky2 + kz2)
+    Q = C * g2 * (kx2 + ky2 - 2 * kz2)
+    R = C * np.sqrt(3) * (-g2 * (kx2 - ky2) + 2j * g3 * K[0, 1])
+    S = C * 2 * np.sqrt(3) * g3 * (K[0, 2] - 1j * K[1, 2])
+    return P, Q, R, S
+
+
+def _pqrs_strain(e, a_v, b, d):
+    """Bir-Pikus P, Q, R, S for the strain tensor e (crystal frame)."""
+    P = -a_v * (e[0, 0] + e[1, 1] + e[2, 2])
+    Q = -0.5 * b * (e[0, 0] + e[1, 1] - 2 * e[2, 2])
+    R = 0.5 * np.sqrt(3) * b * (e[0, 0] - e[1, 1]) - 1j * d * e[0, 1]
+    S = -d * (e[0, 2] - 1j * e[1, 2])
+    return P, Q, R, S
+
+
+def _lk_textbook(P, Q, R, S, delta):
+    s2, s32, cj = np.sqrt(2), np.sqrt(1.5), np.conj
+    return np.array([
+        [P + Q, -S, R, 0, -S / s2, s2 * R],
+        [-cj(S), P - Q, 0, R, -s2 * Q, s32 * S],
+        [cj(R), 0, P - Q, S, s32 * cj(S), s2 * Q],
+        [0, cj(R), cj(S), P + Q, -s2 * cj(R), -cj(S) / s2],
+        [-cj(S) / s2, -s2 * Q, s32 * S, -s2 * R, P + delta, 0],
+        [s2 * cj(R), s32 * cj(S), s2 * Q, -S / s2, 0, P + delta]], dtype=complex)
+
+
+def _plane_wave_symbol(H, p, kvec):
+    """6x6 symbol of a periodic, translation-invariant H at wave vector k,
+    read off by applying H to the six plane waves exp(i k.r) e_b."""
+    nx, ny, nz, h = p.nx, p.ny, p.nz, p.h
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ph = np.exp(1j * h * (kvec[0] * ix + kvec[1] * iy + kvec[2] * iz)).ravel()
+    Np = nx * ny * nz
+    X = np.zeros((6 * Np, 6), dtype=complex)
+    for b in range(6):
+        X[b::6, b] = ph
+    Y = H @ X
+    return Y[0:6, :] / ph[0]
+
+
+@pytest.mark.parametrize("rot", ["identity", "device"])
+def test_bulk_symbol_matches_textbook_luttinger_kohn(rot):
+    """Periodic CSR symbol == textbook LK matrix with k_a k_b replaced by the
+    finite-difference symbols (2-2cos)/h^2 and sin sin/h^2 in the grid frame,
+    transformed to the crystal frame with the rotation."""
+    p = _box(6, 6, 6, h=0.5, strain=False, noise_mev=0.0, rot=rot)
+    p.V[:] = 0.0
+    H = kp.assemble(p, periodic=True)
+    m = p.material
+    R = p.rot
+    for j in [(1, 0, 0), (0, 0, 2), (1, 1, 1), (1, 2, 3), (2, -1, 1), (3, 3, 0)]:
+        k = 2 * np.pi * np.array(j) / (6 * p.h)
+        Ks = np.empty((3, 3))
+        for a in range(3):
+            for b in range(3):
+                Ks[a, b] = ((2 - 2 * np.cos(k[a] * p.h)) if a == b
+                            else np.sin(k[a] * p.h) * np.sin(k[b] * p.h)) / p.h ** 2
+        Kc = R.T @ Ks @ R
+        sym = _plane_wave_symbol(H, p, k)
+        assert np.abs(sym - sym.conj().T).max() < 1e-13
+        e_or = np.linalg.eigvalsh(sym)
+        e_tb = np.linalg.eigvalsh(_lk_textbook(*_pqrs_kinetic(Kc, m["gamma1"], m["gamma2"], m["gamma3"]),
+                                               m["delta_so"]))
+        assert np.abs(e_or - e_tb).max() < 1e-12
+
+
+def test_luttinger_dispersion_001_111():
+    """Delta -> infinity (projection on j = 3/2): along [001] the heavy/light
+    holes are C(g1 -+ 2 g2) k^2 and along [111] C(g1 -+ 2 g3) k^2 (with the
+    finite-difference symbols of k_a k_b)."""
+    p = _box(6, 6, 6, h=0.5, strain=False, noise_mev=0.0)
+    p.V[:] = 0.0
+    m = p.material
+    H = kp.assemble(p, periodic=True)
+    so = kp.spin_orbit_matrix(1.0)
+    w, U = np.linalg.eigh(so)
+    P32 = U[:, np.abs(w) < 1e-12]                 # j = 3/2 eigenspace, 4 dims
+    assert P32.shape[1] == 4
+    h = p.h
+    for j in (1, 2):
+        k = 2 * np.pi * j / (6 * h)
+        Kd = (2 - 2 * np.cos(k * h)) / h ** 2
+        S = np.sin(k * h) ** 2 / h ** 2
+        e = np.linalg.eigvalsh(P32.conj().T @ _plane_wave_symbol(H, p, np.array([0, 0, k])) @ P32)
+        assert np.allclose(e, np.sort([C * (m["gamma1"] - 2 * m["gamma2"]) * Kd] * 2
+                                      + [C * (m["gamma1"] + 2 * m["gamma2"]) * Kd] * 2), atol=1e-12)
+        e = np.linalg.eigvalsh(P32.conj().T @ _plane_wave_symbol(H, p, np.array([k, k, k])) @ P32)
+        hh = C * (3 * m["gamma1"] * Kd - 6 * m["gamma3"] * S)
+        lh = C * (3 * m["gamma1"] * Kd + 6 * m["gamma3"] * S)
+        assert np.allclose(e, np.sort([hh, hh, lh, lh]), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+def test_spin_orbit_spectrum():
+    w = np.linalg.eigvalsh(kp.spin_orbit_matrix(0.044))
+    assert np.allclose(w, [0, 0, 0, 0, 0.044, 0.044], atol=1e-15)
+
+
+def test_zeeman_on_j32_is_isotropic_luttinger_term():
+    """On the j = 3/2 states the Zeeman term equals 2 kappa mu_B B.J:
+    eigenvalues +-3 kappa mu_B |B| and +-kappa mu_B |B|; zero on j = 1/2 x j = 3/2
+    is not required, only the projected spectrum."""
+    kappa = -0.42
+    rng = np.random.default_rng(3)
+    w, U = np.linalg.eigh(kp.spin_orbit_matrix(1.0))
+    P32 = U[:, np.abs(w) < 1e-12]
+    for _ in range(3):
+        B = rng.standard_normal(3)
+        Z = P32.conj().T @ kp.zeeman_matrix(B, kappa) @ P32
+        e = np.linalg.eigvalsh(Z)
+        b = kp.MU_B * np.linalg.norm(B) * abs(kappa)
+        assert np.allclose(e, [-3 * b, -b, b, 3 * b], atol=1e-18)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rot,bound", [("identity", 0.0), ("device", 1e-16)])
+def test_hermitian(rot, bound):
+    """Exactly Hermitian in the crystal frame; to rounding of the rotated
+    tensor (relative to the largest entry) in the device frame."""
+    p = _box(5, 4, 3, rot=rot, B=(0.7, -0.4, 1.1))
+    H = kp.assemble(p)
+    D = (H - H.conj().T).tocoo()
+    worst = np.abs(D.data).max() if D.nnz else 0.0
+    assert worst <= bound * abs(H).max()
+
+
+def test_kramers_doubling_at_zero_field():
+    p = _box(5, 4, 4, rot="device", strain=True)
+    w = eig.all_eigenvalues_dense(kp.assemble(p))
+    assert np.abs(w[0::2] - w[1::2]).max() < 1e-12
+    assert np.min(w[2::2] - w[1:-1:2]) > 1e-9      # doublets, not quartets everywhere
+
+
+def test_gauge_invariance():
+    B = (0.9, -1.3, 2.0)
+    p0 = _box(5, 4, 4, rot="device", B=B, gauge=0)
+    p1 = p0.with_(gauge=1)
+    w0 = eig.all_eigenvalues_dense(kp.assemble(p0))
+    w1 = eig.all_eigenvalues_dense(kp.assemble(p1))
+    assert np.abs(w0 - w1).max() < 1e-12
+    # and the field does something
+    w00 = eig.all_eigenvalues_dense(kp.assemble(p0.with_(B=np.zeros(3))))
+    assert np.abs(w0 - w00).max() > 1e-5
+
+
+def test_time_reversal_B_minus_B():
+    p = _box(4, 4, 3, rot="device", B=(0.3, 0.8, -0.5))
+    w0 = eig.all_eigenvalues_dense(kp.assemble(p))
+    w1 = eig.all_eigenvalues_dense(kp.assemble(p.with_(B=-p.B)))
+    assert np.abs(w0 - w1).max() < 1e-12
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_plaquette_flux(gauge):
+    """Product of link phases around an elementary plaquette is
+    exp(-i B.n h^2 / Phi0) (Stokes), for all three plaquette orientations."""
+    B = np.array([3.0, -2.0, 5.0])
+    p = _box(4, 4, 4, h=0.8, strain=False, noise_mev=0.0, B=B, gauge=gauge)
+    p.material.update(gamma2=0.0, gamma3=0.0)   # face hops diagonal, edges zero
+    H = kp.assemble(p).tolil()
+    nx, ny = p.nx, p.ny
+
+    def idx(x, y, z):
+        return 6 * (x + nx * (y + ny * z))
+
+    for a, b in [(0, 1), (1, 2), (2, 0)]:
+        r0 = np.array([1, 1, 1])
+        ea, eb = np.eye(3, dtype=int)[a], np.eye(3, dtype=int)[b]
+        loop = [r0, r0 + ea, r0 + ea + eb, r0 + eb, r0]
+        prod = 1.0 + 0j
+        for u, v in zip(loop[:-1], loop[1:]):
+            prod *= H[idx(*u), idx(*v)]
+        n = np.cross(ea, eb)
+        flux = B @ n * p.h ** 2
+        ref = np.exp(-1j * flux / kp.PHI0)
+        assert abs(prod / abs(prod) - ref) < 1e-13
+
+
+def test_hydrostatic_strain_rigid_shift():
+    e = 3e-4
+    p = _box(4, 4, 3, rot="device", strain=False)
+    w0 = eig.all_eigenvalues_dense(kp.assemble(p))
+    eps = np.zeros((6, p.nz, p.ny, p.nx))
+    eps[0:3] = e
+    w1 = eig.all_eigenvalues_dense(kp.assemble(p.with_(strain=eps)))
+    assert np.abs(w1 - w0 - (-3 * p.material["a_v"] * e)).max() < 1e-13
+
+
+def test_isotropic_tensor_rotation_invariant():
+    p = _box(4, 3, 3, strain=False)
+    p.material.update(gamma3=p.material["gamma2"])
+    H0 = kp.assemble(p)
+    H1 = kp.assemble(p.with_(rot=inputs.ROT_DEVICE.copy()))
+    assert abs(H0 - H1).max() < 1e-13
+
+
+@pytest.mark.parametrize("rot", ["identity", "device"])
+def test_strain_and_kinetic_match_textbook_bir_pikus(rot):
+    """Bulk symbol with a uniform random strain (grid frame) == textbook
+    LK + Bir-Pikus matrix (P_e = -a_v tr e, Q_e = -b/2 (exx + eyy - 2 ezz),
+    R_e = sqrt3/2 b (exx - eyy) - i d exy, S_e = -d (exz - i eyz)) in the
+    crystal frame, at k = 0 and at finite k."""
+    p = _box(6, 6, 6, h=0.5, strain=False, noise_mev=0.0, rot=rot)
+    p.V[:] = 0.0
+    m = p.material
+    R = p.rot
+    rng = np.random.default_rng(21)
+    eg = rng.uniform(-2e-3, 2e-3, size=(3, 3))
+    eg = 0.5 * (eg + eg.T)
+    comp = [eg[0, 0], eg[1, 1], eg[2, 2], eg[1, 2], eg[0, 2], eg[0, 1]]
+    eps = np.zeros((6, 6, 6, 6))
+    for c in range(6):
+        eps[c] = comp[c]
+    H = kp.assemble(p.with_(strain=eps), periodic=True)
+    ec = R.T @ eg @ R
+    for j in [(0, 0, 0), (1, 2, 3), (2, 0, -1)]:
+        k = 2 * np.pi * np.array(j) / (6 * p.h)
+        Ks = np.empty((3, 3))
+        for a in range(3):
+            for b in range(3):
+                Ks[a, b] = ((2 - 2 * np.cos(k[a] * p.h)) if a == b
+                            else np.sin(k[a] * p.h) * np.sin(k[b] * p.h)) / p.h ** 2
+        Pk, Qk, Rk, Sk = _pqrs_kinetic(R.T @ Ks @ R, m["gamma1"], m["gamma2"], m["gamma3"])
+        Pe, Qe, Re, Se = _pqrs_strain(ec, m["a_v"], m["b"], m["d"])
+        ref = np.linalg.eigvalsh(_lk_textbook(Pk + Pe, Qk + Qe, Rk + Re, Sk + Se, m["delta_so"]))
+        got = np.linalg.eigvalsh(_plane_wave_symbol(H, p, k))
+        assert np.abs(got - ref).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+def test_mask_equals_smaller_box():
+    """Masking the outer layer of a box gives exactly the spectrum of the
+    inner box (Dirichlet walls), with the same point-wise potential."""
+    big = _box(7, 6, 5, strain=False, noise_mev=0.0)
+    inner = _box(5, 4, 3, strain=False, noise_mev=0.0)
+    rng = np.random.default_rng(5)
+    Vin = rng.uniform(-0.01, 0.01, size=(3, 4, 5))
+    Vbig = np.zeros((5, 6, 7))
+    Vbig[1:-1, 1:-1, 1:-1] = Vin
+    mask = np.zeros((5, 6, 7), dtype=np.uint8)
+    mask[1:-1, 1:-1, 1:-1] = 1
+    wb = eig.all_eigenvalues_dense(kp.assemble(big.with_(V=Vbig, mask=mask)), mask=mask)
+    wi = eig.all_eigenvalues_dense(kp.assemble(inner.with_(V=Vin)))
+    assert np.abs(wb - wi).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+def test_block_lanczos_matches_dense():
+    for p in (inputs.config1(), _box(6, 6, 6, rot="device", B=(0.4, 0.2, -0.9))):
+        H = kp.assemble(p)
+        wd, vd = eig.lowest_dense(H, 12)
+        wl, vl, res, _ = eig.lowest_block_lanczos(H, 8, return_residuals=True)
+        assert np.abs(wl - wd[:8]).max() < 1e-12
+        assert res.max() < 1e-11
+        # same invariant subspace (clusters are not cut at 8 for these cases)
+        assert subspace_sin_angle(vd[:, :8], vl) < 1e-9
+
+
+def test_dense_matches_numpy_full_diagonalisation():
+    p = _box(4, 3, 3, rot="device", B=(0.0, 0.5, 0.5))
+    H = kp.assemble(p)
+    w, v = eig.lowest_dense(H, 6)
+    wn = np.linalg.eigvalsh(H.toarray())
+    assert np.abs(w - wn[:6]).max() < 1e-13
+    r = H @ v - v * w
+    assert np.abs(r).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+def test_density_normalisation_and_pointwise():
+    p = _box(4, 3, 3)
+    H = kp.assemble(p)
+    w, v = eig.lowest_dense(H, 6)
+    wt = np.array([1.0, 0.5, 2.0, -1.0, 0.25, 3.0])
+    rho = observables.density(v, wt)
+    assert abs(rho.sum() - wt.sum()) < 1e-12
+    # brute-force pointwise loop
+    Np = p.n_points
+    ref = np.zeros(Np)
+    for i in range(6):
+        for pt in range(Np):
+            for b in range(6):
+                ref[pt] += wt[i] * abs(v[6 * pt + b, i]) ** 2
+    assert np.abs(rho - ref).max() < 1e-14
+
+
+def _doublet_loss_weights(n):
+    """Loss = (mean of doublet 1 - mean of doublet 0) + sum_{i<n} E_i as dL/dE."""
+    g = np.ones(n)
+    g[0:2] += -0.5
+    g[2:4] += 0.5
+    return g
+
+
+def test_hellmann_feynman_vs_finite_differences():
+    """dL/dV, dL/deps and dL/dalpha from HF equal central differences of the
+    dense eigenvalues (B = 0: doublet-averaged loss, well defined)."""
+    p = _box(5, 4, 3, rot="device", strain=True, levers=3)
+    n = 8
+    g = _doublet_loss_weights(n)
+
+    def loss(q):
+        w, _ = eig.lowest_dense(kp.assemble(q), n)
+        return g @ w
+
+    w, v = eig.lowest_dense(kp.assemble(p), n)
+    dV, dEps, dA = observables.hf_gradients(v, g, p.material, p.rot, p.levers)
+    rng = np.random.default_rng(11)
+    d = 1e-5
+    for _ in range(2):
+        u = rng.standard_normal(p.V.shape)
+        fd = (loss(p.with_(V=p.V + d * u)) - loss(p.with_(V=p.V - d * u))) / (2 * d)
+        assert abs(fd - dV @ u.ravel()) < 1e-8 * max(1.0, abs(fd))
+    for c in (0, 3, 5):
+        u = np.zeros_like(p.strain)
+        u[c] = rng.standard_normal(p.V.shape)
+        de = 1e-6
+        fd = (loss(p.with_(strain=p.strain + de * u)) - loss(p.with_(strain=p.strain - de * u))) / (2 * de)
+        assert abs(fd - (dEps * u.reshape(6, -1)).sum()) < 1e-6 * max(1.0, abs(fd))
+    for gi in range(3):
+        fd = (loss(p.with_(V=p.V + d * p.levers[gi])) - loss(p.with_(V=p.V - d * p.levers[gi]))) / (2 * d)
+        assert abs(fd - dA[gi]) < 1e-8 * max(1.0, abs(fd))
