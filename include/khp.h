@@ -1,0 +1,196 @@
+/*
+ * khp.h -- C ABI of the B300 k.p hole eigensolver.
+ *
+ * The library computes the lowest confined hole states of the discretised
+ * 6x6 Luttinger-Kohn k.p Hamiltonian with Bir-Pikus strain and a magnetic
+ * field, H_NI = H_LK + H_PB + V (paper Eq. 2b), written in the
+ * |X,Y,Z> x {up,down} basis as H_DKK + H_SOI + H'_PB + V (Eqs. 5-6a), on a
+ * uniform finite-difference grid with Dirichlet walls (Sec. II B), by
+ * Chebyshev-filtered subspace iteration (the Rayleigh-Chebyshev method named
+ * in Sec. II B).  All arithmetic runs in the library's CUDA kernels.
+ *
+ * Conventions (every entry point):
+ *  - grid: nx*ny*nz interior points, spacing h [nm]; point (ix,iy,iz) sits at
+ *    ((ix+1)h, (iy+1)h, (iz+1)h); the wave function vanishes outside.
+ *    Point index p = ix + nx*(iy + ny*iz).  N = 6*nx*ny*nz unknowns.
+ *  - unknown index (row) = 6*p + b with b = 3*s + o, o in {X,Y,Z} (grid
+ *    frame), s in {up, down} (spin quantised along grid z).
+ *  - blocks of vectors are ROW-MAJOR [N][m] arrays of interleaved complex
+ *    numbers (complex128 = 2 doubles, or complex64 = 2 floats where stated):
+ *    element (row, j) at offset row*m + j.  Column j is vector j.
+ *  - energies eV, lengths nm, magnetic field tesla.
+ *  - "_dev" pointers are device pointers of the current CUDA device, "_host"
+ *    pointers are host memory.  The caller owns every buffer it passes; the
+ *    library owns only the handle and its workspace.  Nothing crosses the
+ *    boundary with ownership.
+ *  - every call returns a khp_status; nothing aborts.  On error the handle
+ *    is left usable and khp_last_error() describes the failure.
+ *  - all device work of a handle is issued on the stream given at creation;
+ *    calls that return host results synchronise that stream.
+ */
+#ifndef KHP_H
+#define KHP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct khp_grid* khp_handle;
+
+typedef enum {
+    KHP_OK = 0,
+    KHP_ERR_INVALID_ARG = 1,   /* bad size, null pointer, NaN input ...       */
+    KHP_ERR_CUDA = 2,          /* a CUDA runtime call failed                    */
+    KHP_ERR_OOM = 3,           /* device allocation of the workspace failed     */
+    KHP_ERR_NOT_CONVERGED = 4, /* max_iter reached; results hold current Ritz pairs */
+    KHP_ERR_BREAKDOWN = 5,     /* Cholesky of the Gram matrix failed even shifted */
+    KHP_ERR_STATE = 6,         /* call out of order (e.g. solve before fields)  */
+    KHP_ERR_DEGENERATE = 7     /* gradient asked for a split degenerate cluster */
+} khp_status;
+
+/* Material parameters (Table I of the paper has one Si set): Luttinger
+ * gamma1..3, split-off energy delta_so [eV], isotropic magnetic kappa,
+ * deformation potentials a_v, b, d [eV]. */
+typedef struct {
+    double gamma1, gamma2, gamma3, delta_so, kappa, a_v, b, d;
+} khp_material;
+
+/* Eigensolver options.
+ *  n_states       wanted lowest states (1..block_m-1)
+ *  block_m        subspace width, even, n_states < block_m <= 64
+ *  degree         Chebyshev filter degree per outer iteration (>= 1)
+ *  max_iter       outer-iteration cap
+ *  precision      0: plain FP64 throughout;
+ *                 1: mixed: FP32 Chebyshev filter/stencil with FP64
+ *                    Cholesky and Rayleigh-Ritz until the FP32 residual
+ *                    floor, then FP64 refinement sweeps (FP64 filter + FP64
+ *                    Rayleigh-Ritz)
+ *  refine_sweeps  precision 1 only: number of FP64 sweeps; < 0 means sweep
+ *                 until every residual is below tol_ev
+ *  tol_ev         stop when ||H x_i - theta_i x_i|| <= tol_ev for i < n_states
+ *  seed           seed of the counter-based random start vectors
+ *  warm_start_dev optional complex128 [N][warm_cols] start vectors (row-major);
+ *                 remaining columns are random.  NULL for a cold start. */
+typedef struct {
+    int n_states;
+    int block_m;
+    int degree;
+    int max_iter;
+    int precision;
+    int refine_sweeps;
+    double tol_ev;
+    uint64_t seed;
+    const void* warm_start_dev;
+    int warm_cols;
+} khp_solver_opts;
+
+/* Per-solve statistics (optional output).  The filter timings come from
+ * CUDA events recorded on the handle's stream around each Chebyshev filter
+ * (the fused stencil launches only); the algorithmic counts describe one
+ * application of H to one vector at one interior grid point. */
+typedef struct {
+    int iterations;            /* outer iterations done (all precisions)       */
+    int iterations_fp32;       /* of which with the FP32 filter                */
+    int converged;             /* states with residual <= tol_ev               */
+    int shifted_cholesky;      /* times the Gram Cholesky needed a shift        */
+    long long filter_applies;  /* block stencil applications (any precision)   */
+    double max_residual;       /* max over the n_states residual norms [eV]    */
+    double lambda_upper;       /* upper spectral bound used by the filter [eV] */
+    double ms_total;           /* wall time of the call [ms]                    */
+    double ms_filter_fp64;     /* device time of the FP64 filters [ms]          */
+    double ms_filter_fp32;     /* device time of the FP32 filters [ms]          */
+    long long launches_fp64;   /* fused stencil launches inside FP64 filters    */
+    long long launches_fp32;   /* fused stencil launches inside FP32 filters    */
+    long long kernel_launches; /* all library kernel launches of the call       */
+    double point_vectors;      /* grid points x block width of one launch      */
+    double flops_per_pv;       /* sparse H x (8 flop per complex, 4 per real
+                                  nonzero) + the three-term update, per point-vector */
+    double bytes_per_pv_fp64;  /* algorithmic HBM bytes per point-vector of a
+                                  filter step: read Y_k, Y_k-1, write Y_k+1 and
+                                  the per-point field tables over the block width */
+    double bytes_per_pv_fp32;
+} khp_stats;
+
+/* Create a grid handle.
+ *  rot     3x3 row-major; row a = grid axis a in crystal coordinates (an
+ *          orthonormal matrix).  NULL = identity.  The paper's device frame
+ *          (Sec. II A) is x=[110], y=[-110], z=[001].
+ *  mask_dev optional uint8 [Np] device array, 0 = point excluded (Dirichlet
+ *          there too).  NULL = every point active.  Copied at creation.
+ *  stream  cudaStream_t (as void*) on which all work of this handle runs;
+ *          NULL = the legacy default stream.
+ * Errors: INVALID_ARG for non-positive sizes / h, non-orthonormal rot;
+ *         OOM / CUDA on allocation failure. */
+khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
+                           const khp_material* mat, const double rot[9],
+                           const uint8_t* mask_dev, void* stream);
+
+/* Set the fields of H (Eq. 2b: V_DQD and the strain entering H_PB; plus B).
+ *  V_dev       float64 [Np] hole potential energy [eV], added as +V
+ *  strain_dev  float64 [6][Np] strain tensor (xx,yy,zz,yz,xz,xy) in the grid
+ *              frame, or NULL for no strain
+ *  levers_dev  float64 [n_gates][Np] gate-lever fields Phi_g, or NULL; the
+ *              potential used is V + sum_g alpha_host[g] * Phi_g
+ *  alpha_host  float64 [n_gates] lever coefficients (NULL when n_gates = 0)
+ *  B_host      3 doubles [T] in the grid frame (NULL = zero field)
+ *  gauge       0 symmetric about the box centre, 1 Landau A=(0,Bz x-Bx z,-By x)
+ * The arrays are read during the call (stream-ordered) and not retained.
+ * Errors: INVALID_ARG for NULL V, bad gauge, n_gates < 0 or NaN/Inf in V. */
+khp_status khp_set_potential_strain_field(khp_handle h, const double* V_dev,
+                                          const double* strain_dev,
+                                          const double* levers_dev,
+                                          const double* alpha_host, int n_gates,
+                                          const double* B_host, int gauge);
+
+/* Y = H X for a block of m vectors (the matrix-free 19-point stencil).
+ *  precision 0: X_dev, Y_dev complex128 [N][m];  1: complex64 [N][m].
+ *  X and Y must not overlap.  m in 1..64 (m even for precision 1 fast path;
+ *  odd m handled too). */
+khp_status khp_apply(khp_handle h, const void* X_dev, void* Y_dev, int m, int precision);
+
+/* Lowest opts->n_states eigenpairs (Sec. II B).
+ *  evals_host  float64 [n_states], ascending
+ *  evecs_dev   complex128 [N][n_states] row-major, orthonormal columns
+ *  resid_host  optional float64 [n_states] residual norms ||H x - theta x||
+ *  stats       optional
+ * Returns NOT_CONVERGED (with the current Ritz pairs written) when max_iter
+ * is reached before every residual is <= tol_ev. */
+khp_status khp_eigensolve(khp_handle h, const khp_solver_opts* opts, double* evals_host,
+                          void* evecs_dev, double* resid_host, khp_stats* stats);
+
+/* Hole density (Sec. II B, fed to Poisson):
+ *  rho_dev[p] = sum_i w_host[i] * sum_b |psi_i(6p+b)|^2   (discrete norm)
+ *  evecs_dev complex128 [N][n] row-major.  Deterministic summation order. */
+khp_status khp_density(khp_handle h, const void* evecs_dev, int n, const double* w_host,
+                       double* rho_dev);
+
+/* Hellmann-Feynman gradients of L(E_0..E_{n-1}) given dL/dE:
+ *  dLdV_dev[p]         = sum_i g_i sum_b |psi_i(6p+b)|^2
+ *  dLdstrain_dev[c][p] = sum_i g_i psi_i(p)^dag (dH'_PB/deps_c x 1) psi_i(p)
+ *                        (NULL to skip)
+ *  dLdalpha_host[g]    = sum_p dLdV[p] * levers_dev[g][p]  (n_gates >= 0)
+ * evals_host are the eigenvalues belonging to evecs_dev; states closer than
+ * 1e-6 eV form a cluster and g must be equal inside a cluster, else
+ * KHP_ERR_DEGENERATE (the gradient of a split cluster is not defined). */
+khp_status khp_eigs_backward(khp_handle h, const void* evecs_dev, const double* evals_host,
+                             int n, const double* dLdE_host, double* dLdV_dev,
+                             double* dLdstrain_dev, const double* levers_dev, int n_gates,
+                             double* dLdalpha_host);
+
+/* Free the handle and its workspace (synchronises its stream). */
+khp_status khp_destroy(khp_handle h);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* khp_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int khp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KHP_H */

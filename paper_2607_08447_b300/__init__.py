@@ -1,0 +1,11 @@
+"""B300-native k.p hole eigensolver (the block eigensolve inside the
+Schroedinger-Poisson loop of "Simulation of exchange coupling effects in
+double quantum dot FinFET-like structures").
+
+The compute path is the C-ABI library ``libkhp.so`` (include/khp.h) built
+from ``csrc/`` for sm_103a; this package only marshals arguments.
+"""
+from ._lib import KHPError, load  # noqa: F401
+from .solver import KPEigs, KPGrid, SolveResult  # noqa: F401
+
+__all__ = ["KPGrid", "KPEigs", "SolveResult", "KHPError", "load"]

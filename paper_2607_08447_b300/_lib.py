@@ -1,0 +1,99 @@
+"""ctypes binding of the C ABI declared in include/khp.h (argument marshalling only).
+
+Every function of the header is bound under its own name.  The library is
+the in-tree ``libkhp.so`` built by ``paper_2607_08447_b300.build``; there is
+no fallback: importing this module on a machine without the built library
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkhp.so")
+
+KHP_OK = 0
+STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KHP_ERR_OOM",
+                4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
+                7: "KHP_ERR_DEGENERATE"}
+
+EXPORTED = ["khp_create_grid", "khp_set_potential_strain_field", "khp_apply", "khp_eigensolve",
+            "khp_density", "khp_eigs_backward", "khp_destroy", "khp_last_error", "khp_version"]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("gamma1", "gamma2", "gamma3", "delta_so", "kappa", "a_v", "b", "d")]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("n_states", ctypes.c_int), ("block_m", ctypes.c_int), ("degree", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("refine_sweeps", ctypes.c_int), ("tol_ev", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("warm_start_dev", ctypes.c_void_p),
+                ("warm_cols", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("iterations_fp32", ctypes.c_int),
+                ("converged", ctypes.c_int), ("shifted_cholesky", ctypes.c_int),
+                ("filter_applies", ctypes.c_longlong), ("max_residual", ctypes.c_double),
+                ("lambda_upper", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_filter_fp64", ctypes.c_double), ("ms_filter_fp32", ctypes.c_double),
+                ("launches_fp64", ctypes.c_longlong), ("launches_fp32", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong), ("point_vectors", ctypes.c_double),
+                ("flops_per_pv", ctypes.c_double), ("bytes_per_pv_fp64", ctypes.c_double),
+                ("bytes_per_pv_fp32", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KHPError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libkhp.so and declare the signatures of every exported function."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libkhp.so not built at {path}; run `python -m paper_2607_08447_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i, d, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+    lib.khp_create_grid.argtypes = [ctypes.POINTER(vp), i, i, i, d, ctypes.POINTER(Material), dp, vp, vp]
+    lib.khp_set_potential_strain_field.argtypes = [vp, vp, vp, vp, dp, i, dp, i]
+    lib.khp_apply.argtypes = [vp, vp, vp, i, i]
+    lib.khp_eigensolve.argtypes = [vp, ctypes.POINTER(SolverOpts), dp, vp, dp, ctypes.POINTER(Stats)]
+    lib.khp_density.argtypes = [vp, vp, i, dp, vp]
+    lib.khp_eigs_backward.argtypes = [vp, vp, dp, i, dp, vp, vp, vp, i, dp]
+    lib.khp_destroy.argtypes = [vp]
+    lib.khp_last_error.argtypes = []
+    lib.khp_last_error.restype = ctypes.c_char_p
+    lib.khp_version.argtypes = []
+    lib.khp_version.restype = ctypes.c_int
+    for name in EXPORTED:
+        if name not in ("khp_last_error", "khp_version"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def check(status: int, allow=()):
+    if status != KHP_OK and status not in allow:
+        raise KHPError(status, load().khp_last_error().decode())
+    return status
+
+
+def dptr(arr):
+    """ctypes double* of a contiguous float64 numpy array (or None)."""
+    if arr is None:
+        return None
+    return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

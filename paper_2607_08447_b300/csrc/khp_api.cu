@@ -1,0 +1,721 @@
+// C ABI of the k.p hole eigensolver: handle life cycle, operator
+// construction on the host (the constant 3x3 / 6x6 pieces of H_DKK, H_SOI,
+// H'_PB and the Zeeman term), and the Chebyshev-filtered subspace iteration
+// that drives the device kernels.
+//
+// Operator (paper Eqs. 2b, 5-6a; conventions where the paper is silent):
+//   H = [C sum_ab D'_ijab k_a k_b + H'_PB,ij(eps(r)) + V(r) delta_ij] x 1_spin
+//       + (Delta/3)(1 - L.sigma) + mu_B B.(gL L + 2 S)
+// with C = hbar^2/2m0, D_iiii = g1+4g2, D_iijj = g1-2g2, D_ijij = D_ijji = 3g3,
+// the Bir-Pikus tensor of the same form with l=-(a_v+2b), m=-(a_v-b),
+// n=-sqrt3 d, both rotated into the grid frame on all four indices,
+// (L_k)_ij = -i eps_kij, gL = 3 kappa - 1, k = -i grad discretised by central
+// differences on 19 points, and Peierls phases exp(-i A(mid).(r'-r)/Phi0) on
+// every link.
+//
+// Eigensolver (the Rayleigh-Chebyshev subspace iteration of Sec. II B):
+//   X <- random (or warm start);  W = H X;  Rayleigh-Ritz
+//   repeat:  Y = T_d((H - c)/e) X   (scaled three-term recurrence, fused stencil)
+//            W = H Y
+//            G = Y^H Y, S = Y^H W   (one pass)
+//            S q = theta G q        (equilibrated Cholesky of G + Jacobi, one CTA)
+//            X = Y Q, HX = W Q      (one pass, residual norms fused)
+//   until ||HX_i - theta_i X_i|| <= tol for the wanted states.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "khp_common.cuh"
+#include "khp_internal.h"
+
+using namespace khp;
+using cplx = std::complex<double>;
+
+static thread_local std::string g_err;
+
+static khp_status fail(khp_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+#define CKS(expr)                        \
+    do {                                 \
+        khp_status s_ = (expr);          \
+        if (s_ != KHP_OK) return s_;     \
+    } while (0)
+
+// ------------------------------------------------------ host operator set-up
+namespace {
+
+struct T4 {
+    double v[3][3][3][3];
+};
+
+T4 luttinger(double g1, double g2, double g3) {
+    T4 D{};
+    for (int i = 0; i < 3; ++i) {
+        D.v[i][i][i][i] = g1 + 4 * g2;
+        for (int j = 0; j < 3; ++j)
+            if (i != j) {
+                D.v[i][i][j][j] = g1 - 2 * g2;
+                D.v[i][j][i][j] = 3 * g3;
+                D.v[i][j][j][i] = 3 * g3;
+            }
+    }
+    return D;
+}
+
+T4 bir_pikus(double a_v, double b, double d) {
+    const double l = -(a_v + 2 * b), m = -(a_v - b), n = -std::sqrt(3.0) * d;
+    T4 D{};
+    for (int i = 0; i < 3; ++i) {
+        D.v[i][i][i][i] = l;
+        for (int j = 0; j < 3; ++j)
+            if (i != j) {
+                D.v[i][i][j][j] = m;
+                D.v[i][j][i][j] = n / 2;
+                D.v[i][j][j][i] = n / 2;
+            }
+    }
+    return D;
+}
+
+// D'_abcd = R_ai R_bj R_ck R_dl D_ijkl, done one index at a time
+T4 rotate(const T4& D, const double* R) {
+    T4 a{}, b{};
+    for (int p = 0; p < 3; ++p) for (int j = 0; j < 3; ++j) for (int k = 0; k < 3; ++k) for (int l = 0; l < 3; ++l) {
+        double s = 0; for (int i = 0; i < 3; ++i) s += R[p * 3 + i] * D.v[i][j][k][l]; a.v[p][j][k][l] = s; }
+    for (int p = 0; p < 3; ++p) for (int q = 0; q < 3; ++q) for (int k = 0; k < 3; ++k) for (int l = 0; l < 3; ++l) {
+        double s = 0; for (int j = 0; j < 3; ++j) s += R[q * 3 + j] * a.v[p][j][k][l]; b.v[p][q][k][l] = s; }
+    for (int p = 0; p < 3; ++p) for (int q = 0; q < 3; ++q) for (int r = 0; r < 3; ++r) for (int l = 0; l < 3; ++l) {
+        double s = 0; for (int k = 0; k < 3; ++k) s += R[r * 3 + k] * b.v[p][q][k][l]; a.v[p][q][r][l] = s; }
+    for (int p = 0; p < 3; ++p) for (int q = 0; q < 3; ++q) for (int r = 0; r < 3; ++r) for (int t = 0; t < 3; ++t) {
+        double s = 0; for (int l = 0; l < 3; ++l) s += R[t * 3 + l] * a.v[p][q][r][l]; b.v[p][q][r][t] = s; }
+    return b;
+}
+
+// 3x3 (row-major) -> symmetric storage (00, 11, 22, 12, 02, 01)
+void to_sym(const double M[3][3], double out[6]) {
+    out[0] = M[0][0];
+    out[1] = M[1][1];
+    out[2] = M[2][2];
+    out[3] = 0.5 * (M[1][2] + M[2][1]);
+    out[4] = 0.5 * (M[0][2] + M[2][0]);
+    out[5] = 0.5 * (M[0][1] + M[1][0]);
+}
+
+void build_operator(khp_grid* g) {
+    const khp_material& m = g->mat;
+    const double C = KHP_HB2M, h2 = g->h * g->h;
+    const T4 D = rotate(luttinger(m.gamma1, m.gamma2, m.gamma3), g->rot);
+    double M[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int a = 0; a < 3; ++a) s += 2.0 * C * D.v[i][j][a][a] / h2;
+            M[i][j] = s;
+        }
+    to_sym(M, g->center);
+    // faces (pairs 0..2) and edges (pairs 3..8)
+    for (int d = 0; d < 9; ++d) {
+        const int off[3] = {pair_dx(d), pair_dy(d), pair_dz(d)};
+        int ax[2], na = 0;
+        for (int a = 0; a < 3; ++a)
+            if (off[a] != 0) ax[na++] = a;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                if (na == 1) {
+                    M[i][j] = -C * D.v[i][j][ax[0]][ax[0]] / h2;
+                } else {
+                    const double sg = off[ax[0]] * off[ax[1]];
+                    M[i][j] = -C * (D.v[i][j][ax[0]][ax[1]] + D.v[i][j][ax[1]][ax[0]]) * sg / (4.0 * h2);
+                }
+            }
+        to_sym(M, g->hop[d]);
+    }
+    // strain derivative matrices per input component (xx,yy,zz,yz,xz,xy)
+    const T4 E = rotate(bir_pikus(m.a_v, m.b, m.d), g->rot);
+    const int pa[6] = {0, 1, 2, 1, 0, 0}, pb[6] = {0, 1, 2, 2, 2, 1};
+    for (int c = 0; c < 6; ++c) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                M[i][j] = pa[c] == pb[c] ? E.v[i][j][pa[c]][pa[c]]
+                                         : E.v[i][j][pa[c]][pb[c]] + E.v[i][j][pb[c]][pa[c]];
+        to_sym(M, g->De[c]);
+    }
+    // spin-orbit + Zeeman on index 3 s + o
+    cplx L[3][3][3] = {};
+    const double eps[3][3][3] = {{{0, 0, 0}, {0, 0, 1}, {0, -1, 0}},
+                                 {{0, 0, -1}, {0, 0, 0}, {1, 0, 0}},
+                                 {{0, 1, 0}, {-1, 0, 0}, {0, 0, 0}}};
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) L[k][i][j] = cplx(0.0, -eps[k][i][j]);
+    const cplx sig[3][2][2] = {{{0, 1}, {1, 0}},
+                               {{0, cplx(0, -1)}, {cplx(0, 1), 0}},
+                               {{1, 0}, {0, -1}}};
+    const double gL = 3.0 * m.kappa - 1.0;
+    for (int b1 = 0; b1 < 6; ++b1)
+        for (int b2 = 0; b2 < 6; ++b2) {
+            const int s1 = b1 / 3, o1 = b1 % 3, s2 = b2 / 3, o2 = b2 % 3;
+            cplx v = (b1 == b2) ? cplx(m.delta_so / 3.0, 0) : cplx(0, 0);
+            for (int k = 0; k < 3; ++k) {
+                v -= (m.delta_so / 3.0) * sig[k][s1][s2] * L[k][o1][o2];
+                cplx z = 0;
+                if (s1 == s2) z += gL * L[k][o1][o2];
+                if (o1 == o2) z += sig[k][s1][s2];
+                v += KHP_MU_B * g->B[k] * z;
+            }
+            g->soz_re[b1][b2] = v.real();
+            g->soz_im[b1][b2] = v.imag();
+        }
+}
+
+double sym_rowsum_max(const double s[6]) {
+    const double r0 = std::fabs(s[0]) + std::fabs(s[5]) + std::fabs(s[4]);
+    const double r1 = std::fabs(s[5]) + std::fabs(s[1]) + std::fabs(s[3]);
+    const double r2 = std::fabs(s[4]) + std::fabs(s[3]) + std::fabs(s[2]);
+    return std::max(r0, std::max(r1, r2));
+}
+
+template <typename R>
+void fill_coeffs(const khp_grid* g, Coeffs<R>& c) {
+    for (int d = 0; d < 9; ++d)
+        for (int k = 0; k < 6; ++k) c.hop[d][k] = (R)g->hop[d][k];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            c.soz_re[i][j] = (R)g->soz_re[i][j];
+            c.soz_im[i][j] = (R)g->soz_im[i][j];
+        }
+}
+
+template <typename R>
+khp_status apply_op(khp_grid* g, const cx_t<R>* x, const cx_t<R>* prev, cx_t<R>* y, int ld,
+                    int col0, int ncol, double alpha, double beta, double gamma) {
+    StencilArgs<R> a;
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.ld = ld; a.col0 = col0; a.ncol = ncol;
+    a.alpha = (R)alpha; a.beta = (R)beta; a.gamma = (R)gamma;
+    a.x = x; a.prev = prev; a.y = y;
+    if constexpr (sizeof(R) == 8) {
+        a.onsite = (const R*)g->onsite64;
+        a.phase = (const cx_t<R>*)(g->has_phase ? g->phase64 : nullptr);
+    } else {
+        a.onsite = (const R*)g->onsite32;
+        a.phase = (const cx_t<R>*)(g->has_phase ? g->phase32 : nullptr);
+    }
+    a.mask = g->mask;
+    fill_coeffs<R>(g, a.c);
+    CK(launch_stencil<R>(a, g->stream));
+    g->launches += 1;
+    return KHP_OK;
+}
+
+void free_ws(khp_grid* g) {
+    for (int i = 0; i < 4; ++i) { if (g->blk64[i]) cudaFree(g->blk64[i]); g->blk64[i] = nullptr; }
+    for (int i = 0; i < 3; ++i) { if (g->blk32[i]) cudaFree(g->blk32[i]); g->blk32[i] = nullptr; }
+    if (g->partial) cudaFree(g->partial);
+    g->partial = nullptr;
+    g->ws_m = 0;
+    g->ws_has32 = 0;
+}
+
+khp_status ensure_ws(khp_grid* g, int m, bool need32) {
+    if (g->ws_m >= m && (!need32 || g->ws_has32)) return KHP_OK;
+    const int mm = std::max(m, g->ws_m);
+    const bool w32 = need32 || g->ws_has32;
+    CK(cudaStreamSynchronize(g->stream));
+    free_ws(g);
+    for (int i = 0; i < 4; ++i) CK(cudaMalloc(&g->blk64[i], sizeof(double2) * g->n * mm));
+    if (w32)
+        for (int i = 0; i < 3; ++i) CK(cudaMalloc(&g->blk32[i], sizeof(float2) * g->n * mm));
+    const int nblk = dense_blocks(g->n);
+    g->partial_elems = std::max(gram_partial_elems(KHP_MAX_M, nblk), (size_t)nblk * KHP_MAX_GATES);
+    CK(cudaMalloc(&g->partial, sizeof(double2) * g->partial_elems));
+    g->ws_m = mm;
+    g->ws_has32 = w32;
+    return KHP_OK;
+}
+
+bool finite_all(const double* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// Algorithmic work of one filter step at one interior point for one vector:
+// the sparse product H x counted as 8 flop per complex and 4 per real
+// nonzero of the point's 6 rows, plus 10 flop per component for the
+// three-term update; bytes: Y_k, Y_k-1 read and Y_k+1 written once, and the
+// per-point field tables (on-site 3x3, link phases) shared by the m vectors.
+void op_counts(const khp_grid* g, int m, double* flops, double* b64, double* b32) {
+    double f = 0.0;
+    for (int b1 = 0; b1 < 6; ++b1)
+        for (int b2 = 0; b2 < 6; ++b2) {
+            const int s1 = b1 / 3, o1 = b1 % 3, s2 = b2 / 3, o2 = b2 % 3;
+            const bool cplx_nz = g->soz_im[b1][b2] != 0.0;
+            bool nz = g->soz_re[b1][b2] != 0.0 || cplx_nz;
+            if (s1 == s2) {
+                // centre + V (diagonal) + strain on the orbital block
+                static const int sidx[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+                const int k = sidx[o1][o2];
+                bool onz = o1 == o2 || g->center[k] != 0.0;
+                if (g->has_strain)
+                    for (int c = 0; c < 6; ++c) onz = onz || g->De[c][k] != 0.0;
+                nz = nz || onz;
+            }
+            if (nz) f += cplx_nz ? 8.0 : 4.0;
+        }
+    for (int d = 0; d < 9; ++d) {
+        const double* h = g->hop[d];
+        int nz = 0;
+        for (int k = 0; k < 3; ++k) nz += h[k] != 0.0;
+        for (int k = 3; k < 6; ++k) nz += 2 * (h[k] != 0.0);
+        // two links (+/-), two spins; complex entries when B != 0
+        f += 2.0 * 2.0 * nz * (g->has_phase ? 8.0 : 4.0);
+    }
+    f += 6 * 10.0;
+    *flops = f;
+    const double fields64 = 6 * 8.0 + (g->has_phase ? 18 * 16.0 : 0.0);
+    *b64 = 3 * 96.0 + fields64 / m;
+    *b32 = 3 * 48.0 + 0.5 * fields64 / m;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int khp_version(void) { return 100; }
+
+const char* khp_last_error(void) { return g_err.c_str(); }
+
+khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
+                           const khp_material* mat, const double rot[9], const uint8_t* mask_dev,
+                           void* stream) {
+    g_err.clear();
+    if (!out) return fail(KHP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(KHP_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (!(h_nm > 0.0) || !std::isfinite(h_nm)) return fail(KHP_ERR_INVALID_ARG, "h must be > 0");
+    if (!mat) return fail(KHP_ERR_INVALID_ARG, "material is NULL");
+    if (!finite_all(&mat->gamma1, 8)) return fail(KHP_ERR_INVALID_ARG, "material has non-finite entries");
+    const long long np = (long long)nx * ny * nz;
+    if (np > (1LL << 31) / 6) return fail(KHP_ERR_INVALID_ARG, "grid too large");
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (rot) {
+        for (int i = 0; i < 9; ++i) R[i] = rot[i];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0;
+                for (int k = 0; k < 3; ++k) s += R[a * 3 + k] * R[b * 3 + k];
+                if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-10)
+                    return fail(KHP_ERR_INVALID_ARG, "rot is not orthonormal");
+            }
+    }
+    khp_grid* g = new khp_grid();
+    std::memset(g, 0, sizeof(khp_grid));
+    g->nx = nx; g->ny = ny; g->nz = nz; g->np = np; g->n = 6 * np; g->h = h_nm;
+    g->mat = *mat;
+    std::memcpy(g->rot, R, sizeof(R));
+    g->stream = (cudaStream_t)stream;
+    cudaGetDevice(&g->device);
+    build_operator(g);
+    auto bail = [&](khp_status s) { khp_destroy(g); return s; };
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->onsite64, sizeof(double) * 6 * np)) != cudaSuccess ||
+        (e = cudaMalloc(&g->onsite32, sizeof(float) * 6 * np)) != cudaSuccess ||
+        (e = cudaMalloc(&g->dvec, sizeof(double) * 8 * KHP_MAX_M)) != cudaSuccess ||
+        (e = cudaMalloc(&g->dflag, sizeof(int) * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&g->small, sizeof(double2) * 4 * KHP_MAX_M * KHP_MAX_M)) != cudaSuccess ||
+        (e = cudaMallocHost(&g->host_pinned, sizeof(double) * 8 * KHP_MAX_M)) != cudaSuccess)
+        return bail(fail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
+                         std::string("allocation: ") + cudaGetErrorString(e)));
+    if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess || (e = cudaEventCreate(&g->ev1)) != cudaSuccess)
+        return bail(fail(KHP_ERR_CUDA, std::string("event: ") + cudaGetErrorString(e)));
+    if (mask_dev) {
+        if ((e = cudaMalloc(&g->mask, np)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(g->mask, mask_dev, np, cudaMemcpyDeviceToDevice, g->stream)) != cudaSuccess)
+            return bail(fail(KHP_ERR_CUDA, std::string("mask copy: ") + cudaGetErrorString(e)));
+    }
+    *out = g;
+    return KHP_OK;
+}
+
+khp_status khp_destroy(khp_handle g) {
+    if (!g) return KHP_OK;
+    cudaStreamSynchronize(g->stream);
+    free_ws(g);
+    if (g->onsite64) cudaFree(g->onsite64);
+    if (g->onsite32) cudaFree(g->onsite32);
+    if (g->phase64) cudaFree(g->phase64);
+    if (g->phase32) cudaFree(g->phase32);
+    if (g->mask) cudaFree(g->mask);
+    if (g->dvec) cudaFree(g->dvec);
+    if (g->dflag) cudaFree(g->dflag);
+    if (g->small) cudaFree(g->small);
+    if (g->host_pinned) cudaFreeHost(g->host_pinned);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+    return KHP_OK;
+}
+
+khp_status khp_set_potential_strain_field(khp_handle g, const double* V_dev, const double* strain_dev,
+                                          const double* levers_dev, const double* alpha_host,
+                                          int n_gates, const double* B_host, int gauge) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!V_dev) return fail(KHP_ERR_INVALID_ARG, "V is NULL");
+    if (gauge != 0 && gauge != 1) return fail(KHP_ERR_INVALID_ARG, "gauge must be 0 or 1");
+    if (n_gates < 0 || n_gates > KHP_MAX_GATES) return fail(KHP_ERR_INVALID_ARG, "n_gates out of range");
+    if (n_gates > 0 && (!levers_dev || !alpha_host))
+        return fail(KHP_ERR_INVALID_ARG, "levers and alpha required when n_gates > 0");
+    if (n_gates > 0 && !finite_all(alpha_host, n_gates)) return fail(KHP_ERR_INVALID_ARG, "alpha non-finite");
+    double B[3] = {0, 0, 0};
+    if (B_host) {
+        if (!finite_all(B_host, 3)) return fail(KHP_ERR_INVALID_ARG, "B non-finite");
+        for (int k = 0; k < 3; ++k) B[k] = B_host[k];
+    }
+    for (int k = 0; k < 3; ++k) g->B[k] = B[k];
+    g->gauge = gauge;
+    g->has_phase = (B[0] != 0.0 || B[1] != 0.0 || B[2] != 0.0);
+    build_operator(g);
+    if (g->has_phase && !g->phase64) {
+        CK(cudaMalloc(&g->phase64, sizeof(double2) * 18 * g->np));
+        CK(cudaMalloc(&g->phase32, sizeof(float2) * 18 * g->np));
+    }
+    CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
+    g->has_strain = strain_dev != nullptr;
+    CK(launch_field_setup(g, V_dev, strain_dev, n_gates ? levers_dev : nullptr, alpha_host, n_gates, g->dflag));
+    // Gershgorin upper bound of the spectrum
+    double* partial = g->dvec + 2 * KHP_MAX_M;   // 6*KHP_MAX_M doubles available
+    const int nb = 4 * KHP_MAX_M;
+    CK(launch_onsite_rowmax(g, partial, nb, g->dvec));
+    CK(cudaMemcpyAsync(g->host_pinned, g->dvec, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (bad) {
+        g->fields_set = false;
+        return fail(KHP_ERR_INVALID_ARG, "non-finite value in V, strain or levers");
+    }
+    double soz = 0;
+    for (int b = 0; b < 6; ++b) {
+        double s = 0;
+        for (int b2 = 0; b2 < 6; ++b2) s += std::hypot(g->soz_re[b][b2], g->soz_im[b][b2]);
+        soz = std::max(soz, s);
+    }
+    double hops = 0;
+    for (int d = 0; d < 9; ++d) hops += 2.0 * sym_rowsum_max(g->hop[d]);
+    g->onsite_absmax = g->host_pinned[0] + soz + hops;
+    g->fields_set = true;
+    return KHP_OK;
+}
+
+khp_status khp_apply(khp_handle g, const void* X_dev, void* Y_dev, int m, int precision) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!g->fields_set) return fail(KHP_ERR_STATE, "fields not set");
+    if (!X_dev || !Y_dev) return fail(KHP_ERR_INVALID_ARG, "X or Y is NULL");
+    if (m < 1 || m > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "m out of range 1..64");
+    if (precision == 0)
+        return apply_op<double>(g, (const double2*)X_dev, nullptr, (double2*)Y_dev, m, 0, m, 1.0, 0.0, 0.0);
+    if (precision == 1)
+        return apply_op<float>(g, (const float2*)X_dev, nullptr, (float2*)Y_dev, m, 0, m, 1.0, 0.0, 0.0);
+    return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
+}
+
+}  // extern "C"
+
+// ============================================================ eigensolver
+namespace {
+
+struct Solver {
+    khp_grid* g;
+    int m;
+    int nblk;
+    double2* G;      // [2 m m]: G then S
+    double2* Q;      // [m m]
+    double* theta;   // [m]
+    double* res;     // [m]
+
+    khp_status rr(double2* Y, double2* W) {
+        CK(launch_gram(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        CK(launch_small(G, G + m * m, m, 1, Q, theta, g->dflag, g->stream));
+        CK(launch_rotate(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
+        g->launches += 5;
+        return KHP_OK;
+    }
+    khp_status orth(double2* Y) {
+        CK(launch_gram(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        CK(launch_small(G, nullptr, m, 0, Q, nullptr, g->dflag, g->stream));
+        CK(launch_rotate(Y, nullptr, m, 0, m, Q, m, nullptr, Y, nullptr, g->n, nullptr, nblk, nullptr, g->stream));
+        g->launches += 4;
+        return KHP_OK;
+    }
+    // host copies of theta, residuals and flags (synchronises)
+    khp_status fetch(std::vector<double>& th, std::vector<double>& rs, int& flags) {
+        double* hp = g->host_pinned;
+        CK(cudaMemcpyAsync(hp, theta, sizeof(double) * m, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaMemcpyAsync(hp + m, res, sizeof(double) * m, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaMemcpyAsync(hp + 2 * m, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        th.assign(hp, hp + m);
+        rs.assign(hp + m, hp + 2 * m);
+        std::memcpy(&flags, hp + 2 * m, sizeof(int));
+        return KHP_OK;
+    }
+    template <typename R>
+    khp_status filter(cx_t<R>* buf[3], int& out_idx, int deg, double a, double b, double low) {
+        // Y1 = (sigma1/e)(H - c)X ; Y_{k+1} = (2 s_{k+1}/e)(H - c)Y_k - s_k s_{k+1} Y_{k-1}
+        const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+        const double sigma1 = e / (low - c);
+        double sigma = sigma1;
+        const double tau = 2.0 / sigma1;
+        int ix = 0, iy = 1, iz = 2;
+        CKS(apply_op<R>(g, buf[ix], nullptr, buf[iy], m, 0, m, sigma1 / e, -c * sigma1 / e, 0.0));
+        for (int k = 2; k <= deg; ++k) {
+            const double sn = 1.0 / (tau - sigma);
+            CKS(apply_op<R>(g, buf[iy], buf[ix], buf[iz], m, 0, m, 2.0 * sn / e, -2.0 * c * sn / e, -sigma * sn));
+            const int t = ix; ix = iy; iy = iz; iz = t;
+            sigma = sn;
+        }
+        out_idx = iy;
+        return KHP_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, double* evals_host,
+                                     void* evecs_dev, double* resid_host, khp_stats* stats) {
+    g_err.clear();
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!g || !opts) return fail(KHP_ERR_INVALID_ARG, "handle or opts is NULL");
+    if (!g->fields_set) return fail(KHP_ERR_STATE, "fields not set");
+    const int n = opts->n_states, m = opts->block_m;
+    if (m < 2 || m > KHP_MAX_M || (m & 1)) return fail(KHP_ERR_INVALID_ARG, "block_m must be even, 2..64");
+    if (n < 1 || n >= m) return fail(KHP_ERR_INVALID_ARG, "need 1 <= n_states < block_m");
+    if ((long long)m > g->n) return fail(KHP_ERR_INVALID_ARG, "block_m exceeds the number of unknowns");
+    if (opts->degree < 1) return fail(KHP_ERR_INVALID_ARG, "degree must be >= 1");
+    if (opts->precision != 0 && opts->precision != 1) return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
+    if (!(opts->tol_ev > 0.0)) return fail(KHP_ERR_INVALID_ARG, "tol_ev must be > 0");
+    if (!evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "evals or evecs is NULL");
+    if (opts->warm_start_dev && (opts->warm_cols < 1 || opts->warm_cols > m))
+        return fail(KHP_ERR_INVALID_ARG, "warm_cols must be in 1..block_m");
+    const bool mixed = opts->precision == 1;
+    CKS(ensure_ws(g, m, mixed));
+
+    Solver S;
+    S.g = g; S.m = m; S.nblk = dense_blocks(g->n);
+    S.G = g->small; S.Q = g->small + 2 * m * m;
+    S.theta = g->dvec; S.res = g->dvec + m;
+    const int max_iter = opts->max_iter > 0 ? opts->max_iter : 1000;
+    const double tol = opts->tol_ev;
+    const double lam_up = g->onsite_absmax;
+
+    int ib[4] = {0, 1, 2, 3};      // ib[0] = X (current Ritz vectors), ib[3] = W = H X
+    double2** B = g->blk64;
+    g->launches = 0;
+    CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
+    CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, opts->seed, g->mask, g->stream));
+    g->launches += 1;
+    if (opts->warm_start_dev)
+        CK(cudaMemcpy2DAsync(B[ib[0]], sizeof(double2) * m, opts->warm_start_dev,
+                             sizeof(double2) * opts->warm_cols, sizeof(double2) * opts->warm_cols, g->n,
+                             cudaMemcpyDeviceToDevice, g->stream));
+    CKS(S.orth(B[ib[0]]));
+    CKS(apply_op<double>(g, B[ib[0]], nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
+    CKS(S.rr(B[ib[0]], B[ib[3]]));
+    std::vector<double> th, rs;
+    int flags = 0;
+    CKS(S.fetch(th, rs, flags));
+
+    khp_stats st{};
+    st.lambda_upper = lam_up;
+    bool fp32_phase = mixed;
+    int sweeps_done = 0, stall = 0;
+    double best_fp32 = 1e300;
+    const double switch_tol = std::max(tol, 1e-6 * lam_up);
+    bool converged = false;
+    bool timed32 = false, timed64 = false;
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        if (flags & 4) return fail(KHP_ERR_BREAKDOWN, "non-finite Ritz values");
+        double rmax = 0;
+        for (int i = 0; i < n; ++i) rmax = std::max(rmax, rs[i]);
+        if (rmax <= tol) { converged = true; break; }
+        if (mixed && !fp32_phase) {
+            if (opts->refine_sweeps >= 0 && sweeps_done >= opts->refine_sweeps) break;
+        }
+        if (fp32_phase) {
+            if (rmax <= switch_tol) fp32_phase = false;
+            else {
+                if (rmax < 0.7 * best_fp32) { best_fp32 = rmax; stall = 0; }
+                else if (++stall >= 4) fp32_phase = false;
+            }
+            if (!fp32_phase && opts->refine_sweeps == 0) break;
+        }
+        if (flags & 2) {
+            // Cholesky breakdown: re-orthonormalise the current block and redo RR
+            CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+            CKS(S.orth(B[ib[0]]));
+            CKS(S.orth(B[ib[0]]));
+            CKS(apply_op<double>(g, B[ib[0]], nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
+            CKS(S.rr(B[ib[0]], B[ib[3]]));
+            CKS(S.fetch(th, rs, flags));
+            if (flags & 2) return fail(KHP_ERR_BREAKDOWN, "Gram matrix not positive definite");
+            continue;
+        }
+        st.shifted_cholesky += (flags & 1) ? 1 : 0;
+        CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+
+        // filter interval [a, b], scaling point low; limit the degree so that
+        // the filtered block stays well conditioned (amplification <= 1e4)
+        const double a = th[m - 1], low = th[0];
+        const double e = 0.5 * (lam_up - a), c = 0.5 * (lam_up + a);
+        int deg = opts->degree;
+        const double xl = std::fabs((low - c) / e);
+        if (xl > 1.0) {
+            const int dmax = (int)std::floor(std::acosh(1e4) / std::acosh(xl));
+            deg = std::max(1, std::min(deg, dmax));
+        }
+        if (!(a < lam_up) || !(low < a)) deg = 1;
+        const double aa = (a < lam_up) ? a : lam_up - 1e-3;
+        const double ll = (low < aa) ? low : aa - 1e-3 * (lam_up - aa);
+
+        double2* Y = nullptr;
+        if (fp32_phase) {
+            float2* fb[3] = {g->blk32[0], g->blk32[1], g->blk32[2]};
+            CK(launch_convert_d2f(B[ib[0]], fb[0], g->n * m, g->stream));
+            g->launches += 3;   // three conversions on this path
+            int oi = 0;
+            CK(cudaEventRecord(g->ev0, g->stream));
+            CKS(S.filter<float>(fb, oi, deg, aa, lam_up, ll));
+            CK(cudaEventRecord(g->ev1, g->stream));
+            timed32 = true;
+            st.launches_fp32 += deg;
+            // H Y in FP32 into a free FP32 buffer
+            const int fw = (oi + 1) % 3;
+            CKS(apply_op<float>(g, fb[oi], nullptr, fb[fw], m, 0, m, 1.0, 0.0, 0.0));
+            Y = B[ib[0]];
+            CK(launch_convert_f2d(fb[oi], Y, g->n * m, g->stream));
+            CK(launch_convert_f2d(fb[fw], B[ib[3]], g->n * m, g->stream));
+            st.iterations_fp32++;
+        } else {
+            double2* fb[3] = {B[ib[0]], B[ib[1]], B[ib[2]]};
+            int oi = 0;
+            CK(cudaEventRecord(g->ev0, g->stream));
+            CKS(S.filter<double>(fb, oi, deg, aa, lam_up, ll));
+            CK(cudaEventRecord(g->ev1, g->stream));
+            timed64 = true;
+            st.launches_fp64 += deg;
+            // new roles: the filter output becomes X after the RR
+            const int bo = ib[oi];
+            int others[2], k = 0;
+            for (int j = 0; j < 3; ++j)
+                if (j != oi) others[k++] = ib[j];
+            ib[0] = bo; ib[1] = others[0]; ib[2] = others[1];
+            Y = B[ib[0]];
+            CKS(apply_op<double>(g, Y, nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
+            if (mixed) sweeps_done++;
+        }
+        st.filter_applies += deg + 1;
+        CKS(S.rr(Y, B[ib[3]]));
+        CKS(S.fetch(th, rs, flags));
+        if (timed32 || timed64) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+            if (timed32) st.ms_filter_fp32 += ms;
+            else st.ms_filter_fp64 += ms;
+            timed32 = timed64 = false;
+        }
+    }
+    // final orthonormalisation of the Ritz block
+    CKS(S.orth(B[ib[0]]));
+    CK(cudaMemcpy2DAsync(evecs_dev, sizeof(double2) * n, B[ib[0]], sizeof(double2) * m, sizeof(double2) * n,
+                         g->n, cudaMemcpyDeviceToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    for (int i = 0; i < n; ++i) evals_host[i] = th[i];
+    double rmax = 0;
+    int conv = 0;
+    for (int i = 0; i < n; ++i) {
+        rmax = std::max(rmax, rs[i]);
+        conv += rs[i] <= tol;
+        if (resid_host) resid_host[i] = rs[i];
+    }
+    st.iterations = it;
+    st.converged = conv;
+    st.kernel_launches = g->launches;
+    st.point_vectors = (double)g->np * m;
+    op_counts(g, m, &st.flops_per_pv, &st.bytes_per_pv_fp64, &st.bytes_per_pv_fp32);
+    st.max_residual = rmax;
+    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = st;
+    if (!converged && !(mixed && opts->refine_sweeps >= 0 && it < max_iter))
+        return fail(KHP_ERR_NOT_CONVERGED, "max_iter reached before all residuals <= tol_ev");
+    return KHP_OK;
+}
+
+extern "C" khp_status khp_density(khp_handle g, const void* evecs_dev, int n, const double* w_host,
+                                  double* rho_dev) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!evecs_dev || !w_host || !rho_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1 || n > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "n out of range 1..64");
+    if (!finite_all(w_host, n)) return fail(KHP_ERR_INVALID_ARG, "weights non-finite");
+    CK(launch_density((const double2*)evecs_dev, g->np, n, w_host, g->mask, rho_dev, g->stream));
+    return KHP_OK;
+}
+
+extern "C" khp_status khp_eigs_backward(khp_handle g, const void* evecs_dev, const double* evals_host,
+                                        int n, const double* dLdE_host, double* dLdV_dev,
+                                        double* dLdstrain_dev, const double* levers_dev, int n_gates,
+                                        double* dLdalpha_host) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!evecs_dev || !evals_host || !dLdE_host || !dLdV_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1 || n > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "n out of range 1..64");
+    if (n_gates < 0 || n_gates > KHP_MAX_GATES) return fail(KHP_ERR_INVALID_ARG, "n_gates out of range");
+    if (n_gates > 0 && (!levers_dev || !dLdalpha_host)) return fail(KHP_ERR_INVALID_ARG, "levers/alpha output NULL");
+    if (!finite_all(dLdE_host, n) || !finite_all(evals_host, n)) return fail(KHP_ERR_INVALID_ARG, "non-finite input");
+    // dL/dE must be constant on every degenerate cluster
+    for (int i = 0; i < n;) {
+        int j = i + 1;
+        while (j < n && evals_host[j] - evals_host[j - 1] <= 1e-6) ++j;
+        for (int k = i + 1; k < j; ++k)
+            if (std::fabs(dLdE_host[k] - dLdE_host[i]) > 1e-12 * std::max(1.0, std::fabs(dLdE_host[i])))
+                return fail(KHP_ERR_DEGENERATE, "dL/dE differs inside a degenerate cluster");
+        i = j;
+    }
+    const int nblk = 2 * 148;
+    double* partial = nullptr;
+    CK(cudaMallocAsync(&partial, sizeof(double) * nblk * std::max(1, n_gates), g->stream));
+    double* dalpha = g->dvec + 6 * KHP_MAX_M;
+    khp_status s = KHP_OK;
+    cudaError_t e = launch_backward((const double2*)evecs_dev, g->np, n, dLdE_host, g->De, dLdV_dev,
+                                    dLdstrain_dev, n_gates ? levers_dev : nullptr, n_gates, partial, nblk,
+                                    dalpha, g->stream);
+    if (e == cudaSuccess && n_gates > 0) {
+        e = cudaMemcpyAsync(g->host_pinned, dalpha, sizeof(double) * n_gates, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e == cudaSuccess)
+            for (int k = 0; k < n_gates; ++k) dLdalpha_host[k] = g->host_pinned[k];
+    }
+    cudaFreeAsync(partial, g->stream);
+    if (e != cudaSuccess) s = fail(KHP_ERR_CUDA, std::string("backward: ") + cudaGetErrorString(e));
+    return s;
+}

@@ -1,0 +1,52 @@
+// Internal launchers and constants shared by the library's translation units.
+#pragma once
+
+#include "khp_common.cuh"
+
+#define KHP_MAX_GATES 16
+#define KHP_MAX_M 64
+#define KHP_PHI0 658.2119569        /* hbar / e  [T nm^2] */
+#define KHP_MU_B 5.7883818060e-5    /* Bohr magneton [eV / T] */
+#define KHP_HB2M 0.0380998212       /* hbar^2 / (2 m0) [eV nm^2] */
+
+namespace khp {
+
+// stencil.cu
+template <typename R>
+cudaError_t launch_stencil(const StencilArgs<R>& a, cudaStream_t st);
+cudaError_t launch_field_setup(khp_grid* g, const double* V, const double* strain,
+                               const double* levers, const double* alpha, int ng, int* bad);
+cudaError_t launch_onsite_rowmax(khp_grid* g, double* partial, int nblocks, double* out);
+
+// dense.cu
+int dense_blocks(long long rows);
+size_t gram_partial_elems(int m, int nblk);
+// partial[nblk][2 m m]; out[0 .. m*m) = Y^H Y, out[m*m .. 2 m*m) = Y^H W (if W)
+cudaError_t launch_gram(const double2* Y, const double2* W, long long rows, int ld, int col0,
+                        int m, double2* partial, int nblk, double2* out, cudaStream_t st);
+// X[:, col0_out + j] = sum_i Y[:, col0_in + i] Q[i][j] (and HX from W), j < mq;
+// optional residual norms ||HX_j - theta_j X_j|| / ||X_j|| into res_out[mq]
+cudaError_t launch_rotate(const double2* Y, const double2* W, int ld, int col0, int m,
+                          const double2* Q, int mq, const double* theta, double2* X, double2* HX,
+                          long long rows, double* res_partial, int nblk, double* res_out,
+                          cudaStream_t st);
+// mode 0: Q = R^-1 of the (equilibrated) Cholesky factor of G (G = R^H R)
+// mode 1: generalized Rayleigh-Ritz  S q = theta G q  ->  theta ascending,
+//         Q = R^-1 Qhat (columns G-orthonormal)
+// flags[0] |= 1 shifted Cholesky, 2 breakdown, 4 non-finite
+cudaError_t launch_small(const double2* G, const double2* S, int m, int mode, double2* Q,
+                         double* theta, int* flags, cudaStream_t st);
+cudaError_t launch_convert_d2f(const double2* src, float2* dst, long long n, cudaStream_t st);
+cudaError_t launch_convert_f2d(const float2* src, double2* dst, long long n, cudaStream_t st);
+cudaError_t launch_random_fill(double2* X, long long rows, int ld, int col0, int ncol,
+                               unsigned long long seed, const uint8_t* mask, cudaStream_t st);
+
+// observables.cu
+cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,
+                           const uint8_t* mask, double* rho, cudaStream_t st);
+cudaError_t launch_backward(const double2* psi, long long np, int n, const double* g,
+                            const double (*De)[6], double* dV, double* dEps,
+                            const double* levers, int ng, double* partial, int nblk,
+                            double* dalpha_dev, cudaStream_t st);
+
+}  // namespace khp

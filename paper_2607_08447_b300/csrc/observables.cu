@@ -1,0 +1,136 @@
+// Hole density and Hellmann-Feynman adjoint of the lowest eigenpairs.
+//   rho(p)       = sum_i w_i sum_b |psi_i(6p+b)|^2             (Sec. II B)
+//   dL/dV(p)     = sum_i g_i sum_b |psi_i(6p+b)|^2             (dH/dV(p) = 1 at p)
+//   dL/deps_c(p) = sum_i g_i sum_s psi_i(p,s)^H M_c psi_i(p,s) (M_c = dH'_PB/deps_c)
+//   dL/dalpha_g  = sum_p dL/dV(p) Phi_g(p)
+// Every sum runs in a fixed order (states outer, bands inner; points in
+// block order), so results are bitwise reproducible.
+#include "khp_common.cuh"
+#include "khp_internal.h"
+
+namespace khp {
+
+struct DensityArgs {
+    const double2* psi;
+    long long np;
+    int n;
+    double w[KHP_MAX_M];
+    double* rho;
+};
+
+__global__ void density_kernel(const DensityArgs a) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const double2* row = a.psi + p * 6 * a.n;
+    double rho = 0.0;
+    for (int i = 0; i < a.n; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            const double2 v = row[b * a.n + i];
+            s += v.x * v.x + v.y * v.y;
+        }
+        rho += a.w[i] * s;
+    }
+    a.rho[p] = rho;
+}
+
+cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,
+                           const uint8_t* /*mask*/, double* rho, cudaStream_t st) {
+    DensityArgs a;
+    a.psi = psi; a.np = np; a.n = n; a.rho = rho;
+    for (int i = 0; i < KHP_MAX_M; ++i) a.w[i] = i < n ? w[i] : 0.0;
+    density_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+struct BackArgs {
+    const double2* psi;
+    long long np;
+    int n;
+    double g[KHP_MAX_M];
+    double De[6][6];       // sym 3x3 (00,11,22,12,02,01) per strain component
+    double* dV;
+    double* dEps;          // [6][np] or null
+    const double* levers;  // [ng][np] or null
+    int ng;
+    double* partial;       // [gridDim][ng]
+};
+
+__device__ __forceinline__ double quad_sym(const double* M, const double2 x0, const double2 x1,
+                                           const double2 x2) {
+    // Re(x^H M x) for real symmetric M
+    const double d = M[0] * (x0.x * x0.x + x0.y * x0.y) + M[1] * (x1.x * x1.x + x1.y * x1.y) +
+                     M[2] * (x2.x * x2.x + x2.y * x2.y);
+    const double o = M[3] * (x1.x * x2.x + x1.y * x2.y) + M[4] * (x0.x * x2.x + x0.y * x2.y) +
+                     M[5] * (x0.x * x1.x + x0.y * x1.y);
+    return d + 2.0 * o;
+}
+
+__global__ void backward_kernel(const BackArgs a) {
+    __shared__ double red[256];
+    const long long per = (a.np + gridDim.x - 1) / gridDim.x;
+    const long long p0 = (long long)blockIdx.x * per;
+    const long long p1 = p0 + per < a.np ? p0 + per : a.np;
+    double lev[KHP_MAX_GATES];
+    for (int g = 0; g < KHP_MAX_GATES; ++g) lev[g] = 0.0;
+    for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const double2* row = a.psi + p * 6 * a.n;
+        double dv = 0.0;
+        double de[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < a.n; ++i) {
+            double2 x[6];
+#pragma unroll
+            for (int b = 0; b < 6; ++b) x[b] = row[b * a.n + i];
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < 6; ++b) s += x[b].x * x[b].x + x[b].y * x[b].y;
+            dv += a.g[i] * s;
+            if (a.dEps) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+                    de[c] += a.g[i] * (quad_sym(a.De[c], x[0], x[1], x[2]) + quad_sym(a.De[c], x[3], x[4], x[5]));
+            }
+        }
+        a.dV[p] = dv;
+        if (a.dEps)
+            for (int c = 0; c < 6; ++c) a.dEps[(long long)c * a.np + p] = de[c];
+        for (int g = 0; g < a.ng; ++g) lev[g] += dv * a.levers[(long long)g * a.np + p];
+    }
+    for (int g = 0; g < a.ng; ++g) {
+        red[threadIdx.x] = lev[g];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * a.ng + g] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void lever_finish(const double* partial, int nblk, int ng, double* out) {
+    const int g = threadIdx.x;
+    if (g >= ng) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * ng + g];
+    out[g] = s;
+}
+
+cudaError_t launch_backward(const double2* psi, long long np, int n, const double* g,
+                            const double (*De)[6], double* dV, double* dEps, const double* levers,
+                            int ng, double* partial, int nblk, double* dalpha_dev, cudaStream_t st) {
+    BackArgs a;
+    a.psi = psi; a.np = np; a.n = n;
+    for (int i = 0; i < KHP_MAX_M; ++i) a.g[i] = i < n ? g[i] : 0.0;
+    for (int c = 0; c < 6; ++c)
+        for (int k = 0; k < 6; ++k) a.De[c][k] = De[c][k];
+    a.dV = dV; a.dEps = dEps; a.levers = levers; a.ng = levers ? ng : 0; a.partial = partial;
+    backward_kernel<<<nblk, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.ng == 0) return e;
+    lever_finish<<<1, 32, 0, st>>>(partial, nblk, a.ng, dalpha_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace khp

@@ -1,0 +1,387 @@
+// Matrix-free 19-point stencil of the discretised 6x6 k.p hole Hamiltonian
+// (H_DKK + H_SOI + H'_PB + V of the paper's Eqs. 5-6a on the uniform grid of
+// Sec. II B), fused with the three-term Chebyshev recurrence, plus the
+// per-point field set-up (on-site matrices, Peierls phases) and the
+// Gershgorin upper bound of the spectrum.
+//
+// Vector blocks are row-major [6*Np][ld] interleaved complex.  One thread
+// computes one grid point for VG consecutive vectors: it loads the point's
+// 6 x VG values, the 18 neighbours' values (pairs +delta/-delta share one
+// real symmetric 3x3 orbital matrix, so the two neighbour values are summed
+// first), and writes y = alpha*(H x) + beta*x + gamma*prev.
+#include "khp_common.cuh"
+#include "khp_internal.h"
+
+namespace khp {
+
+__device__ __forceinline__ bool inr(int i, int n) { return (unsigned)i < (unsigned)n; }
+
+template <typename R, int VG>
+__device__ __forceinline__ void load_vg(cx_t<R> (&v)[VG], const cx_t<R>* p) {
+    if constexpr (VG == 2 && sizeof(R) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = mk<R>(q.x, q.y);
+        v[1] = mk<R>(q.z, q.w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VG; ++k) v[k] = __ldg(p + k);
+    }
+}
+
+template <typename R, int VG>
+__device__ __forceinline__ void store_vg(cx_t<R>* p, const cx_t<R> (&v)[VG]) {
+    if constexpr (VG == 2 && sizeof(R) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VG; ++k) p[k] = v[k];
+    }
+}
+
+// acc[s*3 + i][v] (+)= sum_j M_ij x[s*3 + j][v], M real symmetric (00,11,22,12,02,01)
+template <typename R, int VG, bool INIT>
+__device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], const cx_t<R> (&x)[6][VG]) {
+    const R m00 = M[0], m11 = M[1], m22 = M[2], m12 = M[3], m02 = M[4], m01 = M[5];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            const cx_t<R> x0 = x[3 * s][v], x1 = x[3 * s + 1][v], x2 = x[3 * s + 2][v];
+            cx_t<R> r0, r1, r2;
+            if (INIT) {
+                r0.x = m00 * x0.x; r0.y = m00 * x0.y;
+                r1.x = m01 * x0.x; r1.y = m01 * x0.y;
+                r2.x = m02 * x0.x; r2.y = m02 * x0.y;
+            } else {
+                r0 = acc[3 * s][v]; r1 = acc[3 * s + 1][v]; r2 = acc[3 * s + 2][v];
+                r0.x = fma(m00, x0.x, r0.x); r0.y = fma(m00, x0.y, r0.y);
+                r1.x = fma(m01, x0.x, r1.x); r1.y = fma(m01, x0.y, r1.y);
+                r2.x = fma(m02, x0.x, r2.x); r2.y = fma(m02, x0.y, r2.y);
+            }
+            r0.x = fma(m01, x1.x, r0.x); r0.y = fma(m01, x1.y, r0.y);
+            r0.x = fma(m02, x2.x, r0.x); r0.y = fma(m02, x2.y, r0.y);
+            r1.x = fma(m11, x1.x, r1.x); r1.y = fma(m11, x1.y, r1.y);
+            r1.x = fma(m12, x2.x, r1.x); r1.y = fma(m12, x2.y, r1.y);
+            r2.x = fma(m12, x1.x, r2.x); r2.y = fma(m12, x1.y, r2.y);
+            r2.x = fma(m22, x2.x, r2.x); r2.y = fma(m22, x2.y, r2.y);
+            acc[3 * s][v] = r0; acc[3 * s + 1][v] = r1; acc[3 * s + 2][v] = r2;
+        }
+    }
+}
+
+template <typename R, int VG, bool PHASE, bool MASK>
+__global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
+    using C = cx_t<R>;
+    const int G = a.ncol / VG;
+    const long long np = (long long)a.nx * a.ny * a.nz;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np * G) return;
+    const int g = (int)(t % G);
+    const long long p = t / G;
+    const int ix = (int)(p % a.nx);
+    const long long q = p / a.nx;
+    const int iy = (int)(q % a.ny);
+    const int iz = (int)(q / a.ny);
+    const long long ps = 6LL * a.ld;            // complex elements per point
+    const int col = a.col0 + g * VG;
+    C* yp = a.y + p * ps + col;
+
+    if (MASK && a.mask[p] == 0) {
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            C z[VG];
+#pragma unroll
+            for (int v = 0; v < VG; ++v) z[v] = mk<R>(R(0), R(0));
+            store_vg<R, VG>(yp + b * a.ld, z);
+        }
+        return;
+    }
+
+    const C* xp = a.x + p * ps + col;
+    C xs[6][VG];
+#pragma unroll
+    for (int b = 0; b < 6; ++b) load_vg<R, VG>(xs[b], xp + b * a.ld);
+
+    C acc[6][VG];
+    {
+        R o[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k] = __ldg(a.onsite + p * 6 + k);
+        sym3<R, VG, true>(acc, o, xs);
+    }
+    // spin-orbit + Zeeman: constant complex 6x6
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+#pragma unroll
+        for (int b2 = 0; b2 < 6; ++b2) {
+            const R sr = a.c.soz_re[b][b2], si = a.c.soz_im[b][b2];
+#pragma unroll
+            for (int v = 0; v < VG; ++v) {
+                acc[b][v].x = fma(sr, xs[b2][v].x, acc[b][v].x);
+                acc[b][v].x = fma(-si, xs[b2][v].y, acc[b][v].x);
+                acc[b][v].y = fma(sr, xs[b2][v].y, acc[b][v].y);
+                acc[b][v].y = fma(si, xs[b2][v].x, acc[b][v].y);
+            }
+        }
+    }
+
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+        const int dx = pair_dx(d), dy = pair_dy(d), dz = pair_dz(d);
+        const long long off = (long long)dx + (long long)a.nx * ((long long)dy + (long long)a.ny * dz);
+        bool okp = inr(ix + dx, a.nx) && inr(iy + dy, a.ny) && inr(iz + dz, a.nz);
+        bool okm = inr(ix - dx, a.nx) && inr(iy - dy, a.ny) && inr(iz - dz, a.nz);
+        if (MASK) {
+            okp = okp && a.mask[p + off] != 0;
+            okm = okm && a.mask[p - off] != 0;
+        }
+        C s[6][VG];
+#pragma unroll
+        for (int b = 0; b < 6; ++b)
+#pragma unroll
+            for (int v = 0; v < VG; ++v) s[b][v] = mk<R>(R(0), R(0));
+        if (okp) {
+            const C* np_ = xp + off * ps;
+            C ph;
+            if (PHASE) ph = __ldg(a.phase + p * 18 + 2 * d);
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+                C w[VG];
+                load_vg<R, VG>(w, np_ + b * a.ld);
+#pragma unroll
+                for (int v = 0; v < VG; ++v) s[b][v] = PHASE ? cmul(ph, w[v]) : w[v];
+            }
+        }
+        if (okm) {
+            const C* nm_ = xp - off * ps;
+            C ph;
+            if (PHASE) ph = __ldg(a.phase + p * 18 + 2 * d + 1);
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+                C w[VG];
+                load_vg<R, VG>(w, nm_ + b * a.ld);
+#pragma unroll
+                for (int v = 0; v < VG; ++v) {
+                    if (PHASE) {
+                        cfma(s[b][v], ph, w[v]);
+                    } else {
+                        s[b][v].x += w[v].x; s[b][v].y += w[v].y;
+                    }
+                }
+            }
+        }
+        R M[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) M[k] = a.c.hop[d][k];
+        sym3<R, VG, false>(acc, M, s);
+    }
+
+    // y = alpha*acc + beta*x + gamma*prev
+    const C* pp = a.prev ? a.prev + p * ps + col : nullptr;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+        C out[VG];
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            out[v].x = a.alpha * acc[b][v].x + a.beta * xs[b][v].x;
+            out[v].y = a.alpha * acc[b][v].y + a.beta * xs[b][v].y;
+        }
+        if (pp) {
+            C w[VG];
+            load_vg<R, VG>(w, pp + b * a.ld);
+#pragma unroll
+            for (int v = 0; v < VG; ++v) {
+                out[v].x = fma(a.gamma, w[v].x, out[v].x);
+                out[v].y = fma(a.gamma, w[v].y, out[v].y);
+            }
+        }
+        store_vg<R, VG>(yp + b * a.ld, out);
+    }
+}
+
+template <typename R, int VG>
+static cudaError_t launch_vg(const StencilArgs<R>& a, cudaStream_t st) {
+    const long long np = (long long)a.nx * a.ny * a.nz;
+    const long long total = np * (a.ncol / VG);
+    if (total == 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (total + threads - 1) / threads;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const bool ph = a.phase != nullptr, mk_ = a.mask != nullptr;
+    if (ph && mk_) stencil_kernel<R, VG, true, true><<<(unsigned)blocks, threads, 0, st>>>(a);
+    else if (ph) stencil_kernel<R, VG, true, false><<<(unsigned)blocks, threads, 0, st>>>(a);
+    else if (mk_) stencil_kernel<R, VG, false, true><<<(unsigned)blocks, threads, 0, st>>>(a);
+    else stencil_kernel<R, VG, false, false><<<(unsigned)blocks, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_stencil(const StencilArgs<R>& a, cudaStream_t st) {
+    if ((a.ncol % 2) == 0 && (a.col0 % 2) == 0 && (a.ld % 2) == 0) return launch_vg<R, 2>(a, st);
+    return launch_vg<R, 1>(a, st);
+}
+
+template cudaError_t launch_stencil<double>(const StencilArgs<double>&, cudaStream_t);
+template cudaError_t launch_stencil<float>(const StencilArgs<float>&, cudaStream_t);
+
+// ------------------------------------------------------------ field set-up
+struct FieldArgs {
+    int nx, ny, nz;
+    const double* V;
+    const double* strain;     // [6][np] or null
+    const double* levers;     // [ng][np] or null
+    int ng;
+    double alpha[KHP_MAX_GATES];
+    double center[6];
+    double De[6][6];          // per strain component c: sym 3x3
+    double* onsite64;
+    float* onsite32;
+    int* bad;                 // set to 1 on a non-finite input
+};
+
+__global__ void onsite_kernel(const FieldArgs a) {
+    const long long np = (long long)a.nx * a.ny * a.nz;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    double v = a.V[p];
+    for (int g = 0; g < a.ng; ++g) v += a.alpha[g] * a.levers[(long long)g * np + p];
+    double o[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o[k] = a.center[k] + (k < 3 ? v : 0.0);
+    if (a.strain) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double e = a.strain[(long long)c * np + p];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) o[k] = fma(a.De[c][k], e, o[k]);
+        }
+    }
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        finite = finite && isfinite(o[k]);
+        a.onsite64[p * 6 + k] = o[k];
+        a.onsite32[p * 6 + k] = (float)o[k];
+    }
+    if (!finite) atomicExch(a.bad, 1);
+}
+
+struct PhaseArgs {
+    int nx, ny, nz;
+    double h;
+    double B[3];
+    double c[3];      // box centre (symmetric gauge)
+    int gauge;
+    double2* phase64;
+    float2* phase32;
+};
+
+__device__ __forceinline__ void vecpot(const PhaseArgs& a, double x, double y, double z, double A[3]) {
+    if (a.gauge == 0) {
+        const double rx = x - a.c[0], ry = y - a.c[1], rz = z - a.c[2];
+        A[0] = 0.5 * (a.B[1] * rz - a.B[2] * ry);
+        A[1] = 0.5 * (a.B[2] * rx - a.B[0] * rz);
+        A[2] = 0.5 * (a.B[0] * ry - a.B[1] * rx);
+    } else {
+        A[0] = 0.0;
+        A[1] = a.B[2] * x - a.B[0] * z;
+        A[2] = -a.B[1] * x;
+    }
+}
+
+// Peierls phase of the link r -> r' : exp(-i A((r+r')/2).(r'-r) / Phi0)
+__global__ void phase_kernel(const PhaseArgs a) {
+    const long long np = (long long)a.nx * a.ny * a.nz;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int ix = (int)(p % a.nx);
+    const int iy = (int)((p / a.nx) % a.ny);
+    const int iz = (int)(p / ((long long)a.nx * a.ny));
+    const double x = (ix + 1) * a.h, y = (iy + 1) * a.h, z = (iz + 1) * a.h;
+    for (int d = 0; d < 9; ++d) {
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const double s = sgn == 0 ? 1.0 : -1.0;
+            const double dx = s * pair_dx(d) * a.h, dy = s * pair_dy(d) * a.h, dz = s * pair_dz(d) * a.h;
+            double A[3];
+            vecpot(a, x + 0.5 * dx, y + 0.5 * dy, z + 0.5 * dz, A);
+            const double theta = (A[0] * dx + A[1] * dy + A[2] * dz) / KHP_PHI0;
+            double sn, cs;
+            sincos(theta, &sn, &cs);
+            a.phase64[p * 18 + 2 * d + sgn] = make_double2(cs, -sn);
+            a.phase32[p * 18 + 2 * d + sgn] = make_float2((float)cs, (float)-sn);
+        }
+    }
+}
+
+cudaError_t launch_field_setup(khp_grid* g, const double* V, const double* strain,
+                               const double* levers, const double* alpha, int ng, int* bad) {
+    FieldArgs a;
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.V = V; a.strain = strain; a.levers = levers; a.ng = ng;
+    for (int i = 0; i < KHP_MAX_GATES; ++i) a.alpha[i] = i < ng ? alpha[i] : 0.0;
+    for (int k = 0; k < 6; ++k) a.center[k] = g->center[k];
+    for (int c = 0; c < 6; ++c)
+        for (int k = 0; k < 6; ++k) a.De[c][k] = g->De[c][k];
+    a.onsite64 = g->onsite64; a.onsite32 = g->onsite32; a.bad = bad;
+    const int threads = 256;
+    const long long blocks = (g->np + threads - 1) / threads;
+    onsite_kernel<<<(unsigned)blocks, threads, 0, g->stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !g->has_phase) return e;
+    PhaseArgs pa;
+    pa.nx = g->nx; pa.ny = g->ny; pa.nz = g->nz; pa.h = g->h;
+    for (int k = 0; k < 3; ++k) pa.B[k] = g->B[k];
+    pa.c[0] = 0.5 * (g->nx + 1) * g->h;
+    pa.c[1] = 0.5 * (g->ny + 1) * g->h;
+    pa.c[2] = 0.5 * (g->nz + 1) * g->h;
+    pa.gauge = g->gauge;
+    pa.phase64 = g->phase64; pa.phase32 = g->phase32;
+    phase_kernel<<<(unsigned)blocks, threads, 0, g->stream>>>(pa);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------- Gershgorin upper bound
+// Per point: max over orbital rows of sum_j |onsite_ij| (the rest of the
+// Gershgorin row sum is constant and added on the host side of the call).
+__global__ void onsite_rowmax_kernel(const double* onsite, long long np, const uint8_t* mask,
+                                     double* partial) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+         p += (long long)gridDim.x * blockDim.x) {
+        if (mask && mask[p] == 0) continue;
+        const double* o = onsite + p * 6;
+        const double r0 = fabs(o[0]) + fabs(o[5]) + fabs(o[4]);
+        const double r1 = fabs(o[5]) + fabs(o[1]) + fabs(o[3]);
+        const double r2 = fabs(o[4]) + fabs(o[3]) + fabs(o[2]);
+        m = fmax(m, fmax(r0, fmax(r1, r2)));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void max_reduce_kernel(const double* partial, int n, double* out) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, partial[i]);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+cudaError_t launch_onsite_rowmax(khp_grid* g, double* partial, int nblocks, double* out) {
+    onsite_rowmax_kernel<<<nblocks, 256, 0, g->stream>>>(g->onsite64, g->np, g->mask, partial);
+    max_reduce_kernel<<<1, 256, 0, g->stream>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace khp

@@ -1,0 +1,185 @@
+"""Python front end of the CUDA k.p hole eigensolver (marshalling only).
+
+`KPGrid` wraps one C-ABI handle.  Device arrays are torch CUDA tensors
+(float64, complex128 or complex64) and are passed by pointer; all
+arithmetic runs in libkhp's kernels.  `KPEigs` is a torch.autograd.Function
+whose backward is the library's Hellmann-Feynman adjoint.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_MAT_KEYS = ("gamma1", "gamma2", "gamma3", "delta_so", "kappa", "a_v", "b", "d")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, device):
+    if t is None:
+        return None
+    if not torch.is_tensor(t):
+        t = torch.as_tensor(np.ascontiguousarray(t))
+    return t.to(device=device, dtype=dtype).contiguous()
+
+
+@dataclass
+class SolveResult:
+    evals: np.ndarray          # float64 [n], ascending
+    evecs: torch.Tensor        # complex128 [N, n] on the device
+    residuals: np.ndarray      # float64 [n]
+    stats: dict
+    status: int
+
+
+class KPGrid:
+    """One grid + Hamiltonian on one CUDA device (see include/khp.h)."""
+
+    def __init__(self, nx, ny, nz, h, material, rot=None, mask=None, device="cuda", stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
+        self.np_ = self.nx * self.ny * self.nz
+        self.N = 6 * self.np_
+        mat = _lib.Material(*[float(material[k]) for k in _MAT_KEYS])
+        R = None if rot is None else np.ascontiguousarray(np.asarray(rot, dtype=np.float64).reshape(9))
+        self._mask = None if mask is None else _dev(np.asarray(mask, dtype=np.uint8).reshape(-1), torch.uint8, self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h_ = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.khp_create_grid(ctypes.byref(h_), self.nx, self.ny, self.nz, self.h,
+                                                ctypes.byref(mat), _lib.dptr(R), _ptr(self._mask),
+                                                ctypes.c_void_p(self.stream.cuda_stream)))
+        self.handle = h_
+        self.material = dict(material)
+        self.rot = R
+
+    @classmethod
+    def from_problem(cls, p, device="cuda", with_levers=True):
+        """Grid + fields from any object with the attributes nx, ny, nz, h,
+        material, rot, mask, V, strain, B, gauge and (optionally) levers."""
+        g = cls(p.nx, p.ny, p.nz, p.h, p.material, p.rot, getattr(p, "mask", None), device=device)
+        lev = getattr(p, "levers", None) if with_levers else None
+        g.set_fields(p.V, p.strain, lev, None if lev is None else np.zeros(lev.shape[0]), p.B, p.gauge)
+        return g
+
+    # ------------------------------------------------------------------
+    def set_fields(self, V, strain=None, levers=None, alpha=None, B=None, gauge=0):
+        V = _dev(V, torch.float64, self.device).reshape(-1)
+        if V.numel() != self.np_:
+            raise ValueError("V must have nx*ny*nz entries")
+        strain = _dev(strain, torch.float64, self.device)
+        if strain is not None and strain.numel() != 6 * self.np_:
+            raise ValueError("strain must have 6*nx*ny*nz entries")
+        levers = _dev(levers, torch.float64, self.device)
+        ng = 0 if levers is None else levers.numel() // self.np_
+        a = None
+        if ng:
+            a = np.ascontiguousarray(np.zeros(ng) if alpha is None else np.asarray(alpha, dtype=np.float64))
+        Bh = None if B is None else np.ascontiguousarray(np.asarray(B, dtype=np.float64))
+        _lib.check(self.lib.khp_set_potential_strain_field(self.handle, _ptr(V), _ptr(strain), _ptr(levers),
+                                                           _lib.dptr(a), ng, _lib.dptr(Bh), int(gauge)))
+        self._keep = (V, strain, levers)   # alive until the stream has consumed them
+        return self
+
+    def apply(self, X, precision=0):
+        """Y = H X for X complex128 (precision 0) or complex64 (1), shape [N, m]."""
+        dt = torch.complex128 if precision == 0 else torch.complex64
+        X = _dev(X, dt, self.device)
+        if X.dim() == 1:
+            X = X.reshape(-1, 1)
+        m = X.shape[1]
+        Y = torch.empty_like(X)
+        _lib.check(self.lib.khp_apply(self.handle, _ptr(X), _ptr(Y), m, int(precision)))
+        return Y
+
+    def eigensolve(self, n_states, block_m=None, degree=20, max_iter=0, precision=0, refine_sweeps=2,
+                   tol=1e-9, seed=1, warm_start=None, out=None, allow_not_converged=False):
+        block_m = block_m or max(n_states + 8, 16)
+        block_m += block_m % 2
+        opts = _lib.SolverOpts()
+        opts.n_states, opts.block_m, opts.degree, opts.max_iter = n_states, block_m, degree, max_iter
+        opts.precision, opts.refine_sweeps, opts.tol_ev, opts.seed = precision, refine_sweeps, tol, seed
+        ws = None
+        if warm_start is not None:
+            ws = _dev(warm_start, torch.complex128, self.device)
+            opts.warm_start_dev = ctypes.c_void_p(ws.data_ptr())
+            opts.warm_cols = ws.shape[1]
+        evals = np.zeros(n_states)
+        res = np.zeros(n_states)
+        evecs = out if out is not None else torch.empty((self.N, n_states), dtype=torch.complex128, device=self.device)
+        st = _lib.Stats()
+        status = self.lib.khp_eigensolve(self.handle, ctypes.byref(opts), _lib.dptr(evals), _ptr(evecs),
+                                         _lib.dptr(res), ctypes.byref(st))
+        _lib.check(status, allow=(4,) if allow_not_converged else ())
+        return SolveResult(evals, evecs, res, st.as_dict(), status)
+
+    def density(self, evecs, w):
+        evecs = _dev(evecs, torch.complex128, self.device)
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        rho = torch.empty(self.np_, dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.khp_density(self.handle, _ptr(evecs), evecs.shape[1], _lib.dptr(w), _ptr(rho)))
+        return rho
+
+    def backward(self, evecs, evals, dLdE, levers=None, want_strain=True):
+        evecs = _dev(evecs, torch.complex128, self.device)
+        n = evecs.shape[1]
+        ev = np.ascontiguousarray(np.asarray(evals, dtype=np.float64))
+        g = np.ascontiguousarray(np.asarray(dLdE, dtype=np.float64))
+        dV = torch.empty(self.np_, dtype=torch.float64, device=self.device)
+        dE = torch.empty(6 * self.np_, dtype=torch.float64, device=self.device) if want_strain else None
+        levers = _dev(levers, torch.float64, self.device)
+        ng = 0 if levers is None else levers.numel() // self.np_
+        da = np.zeros(max(ng, 1))
+        _lib.check(self.lib.khp_eigs_backward(self.handle, _ptr(evecs), _lib.dptr(ev), n, _lib.dptr(g), _ptr(dV),
+                                              _ptr(dE), _ptr(levers), ng, _lib.dptr(da)))
+        return dV, dE, (da[:ng] if ng else None)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.khp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KPEigs(torch.autograd.Function):
+    """Lowest eigenvalues E(V, strain, alpha) with a Hellmann-Feynman backward.
+
+    forward(V [Np], strain [6, Np], alpha [n_gates], grid, levers, solve_kw)
+      -> evals [n] (float64, on V's device)
+    backward: dL/dV = sum_i g_i |psi_i|^2, dL/dstrain, dL/dalpha = <dL/dV, Phi_g>.
+    """
+
+    @staticmethod
+    def forward(ctx, V, strain, alpha, grid, levers, B, solve_kw):
+        grid.set_fields(V.detach(), None if strain is None else strain.detach(), levers,
+                        None if alpha is None else alpha.detach().cpu().numpy(), B=B)
+        r = grid.eigensolve(**solve_kw)
+        ctx.grid, ctx.levers = grid, levers
+        ctx.evals = r.evals
+        ctx.save_for_backward(r.evecs)
+        ctx.has_strain = strain is not None
+        ctx.has_alpha = alpha is not None
+        return torch.as_tensor(r.evals, dtype=torch.float64, device=V.device)
+
+    @staticmethod
+    def backward(ctx, grad):
+        (evecs,) = ctx.saved_tensors
+        g = grad.detach().cpu().numpy()
+        dV, dE, da = ctx.grid.backward(evecs, ctx.evals, g, ctx.levers if ctx.has_alpha else None,
+                                       want_strain=ctx.has_strain)
+        dS = dE.reshape(6, -1) if ctx.has_strain else None
+        dA = torch.as_tensor(da, dtype=torch.float64) if ctx.has_alpha else None
+        return dV, dS, dA, None, None, None, None

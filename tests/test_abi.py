@@ -1,0 +1,59 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds for
+sm_103a, loads, and exports every function include/khp.h declares; host-side
+argument validation answers with the documented status codes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "khp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(khp_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_08447_b300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("khp_create_grid", "khp_set_potential_strain_field", "khp_eigensolve",
+                     "khp_density", "khp_eigs_backward", "khp_destroy", "khp_apply",
+                     "khp_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert lib.khp_version() >= 100
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2607_08447_b300 import _lib
+    assert sorted(_lib.EXPORTED) == _declared()
+
+
+def test_host_side_validation_without_device(lib):
+    from paper_2607_08447_b300 import _lib
+    h = ctypes.c_void_p()
+    mat = _lib.Material(4.285, 0.339, 1.446, 0.044, -0.42, 2.38, -2.1, -4.85)
+    # invalid sizes and spacing are rejected before any CUDA call
+    assert lib.khp_create_grid(ctypes.byref(h), 0, 4, 4, 1.0, ctypes.byref(mat), None, None, None) == 1
+    assert b"grid sizes" in lib.khp_last_error()
+    assert lib.khp_create_grid(ctypes.byref(h), 4, 4, 4, -1.0, ctypes.byref(mat), None, None, None) == 1
+    bad_rot = (ctypes.c_double * 9)(1, 0, 0, 0, 2, 0, 0, 0, 1)
+    assert lib.khp_create_grid(ctypes.byref(h), 4, 4, 4, 1.0, ctypes.byref(mat), bad_rot, None, None) == 1
+    assert b"orthonormal" in lib.khp_last_error()
+    # NULL handles
+    assert lib.khp_apply(None, None, None, 4, 0) == 1
+    assert lib.khp_eigensolve(None, None, None, None, None, None) == 1
+    assert lib.khp_destroy(None) == 0
