@@ -106,6 +106,8 @@ typedef struct {
     long long launches_fp32;   /* fused stencil launches inside FP32 filters    */
     long long kernel_launches; /* all library kernel launches of the call       */
     double point_vectors;      /* grid points x block width of one launch      */
+    double pv_fp64;            /* point-vectors processed by the FP64 filters   */
+    double pv_fp32;            /* point-vectors processed by the FP32 filters   */
     double flops_per_pv;       /* sparse H x (8 flop per complex, 4 per real
                                   nonzero) + the three-term update, per point-vector */
     double bytes_per_pv_fp64;  /* algorithmic HBM bytes per point-vector of a

@@ -43,6 +43,7 @@ class Stats(ctypes.Structure):
                 ("ms_filter_fp64", ctypes.c_double), ("ms_filter_fp32", ctypes.c_double),
                 ("launches_fp64", ctypes.c_longlong), ("launches_fp32", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("point_vectors", ctypes.c_double),
+                ("pv_fp64", ctypes.c_double), ("pv_fp32", ctypes.c_double),
                 ("flops_per_pv", ctypes.c_double), ("bytes_per_pv_fp64", ctypes.c_double),
                 ("bytes_per_pv_fp32", ctypes.c_double)]
 

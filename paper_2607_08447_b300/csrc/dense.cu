@@ -497,18 +497,27 @@ cudaError_t launch_small(const double2* G, const double2* S, int m, int mode, do
 }
 
 // ------------------------------------------------------------- utilities
-__global__ void d2f_kernel(const double2* __restrict__ s, float2* __restrict__ d, long long n) {
+// Precision conversion of columns [col0, col0 + ncol) of a row-major block.
+__global__ void d2f_kernel(const double2* __restrict__ s, float2* __restrict__ d, long long rows, int ld,
+                           int col0, int ncol) {
+    const long long n = rows * ncol;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double2 v = s[i];
-        d[i] = make_float2((float)v.x, (float)v.y);
+        const long long r = i / ncol;
+        const long long k = r * ld + col0 + (i - r * ncol);
+        const double2 v = s[k];
+        d[k] = make_float2((float)v.x, (float)v.y);
     }
 }
-__global__ void f2d_kernel(const float2* __restrict__ s, double2* __restrict__ d, long long n) {
+__global__ void f2d_kernel(const float2* __restrict__ s, double2* __restrict__ d, long long rows, int ld,
+                           int col0, int ncol) {
+    const long long n = rows * ncol;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const float2 v = s[i];
-        d[i] = make_double2((double)v.x, (double)v.y);
+        const long long r = i / ncol;
+        const long long k = r * ld + col0 + (i - r * ncol);
+        const float2 v = s[k];
+        d[k] = make_double2((double)v.x, (double)v.y);
     }
 }
 
@@ -519,12 +528,14 @@ static unsigned grid_for(long long n) {
     return (unsigned)b;
 }
 
-cudaError_t launch_convert_d2f(const double2* src, float2* dst, long long n, cudaStream_t st) {
-    d2f_kernel<<<grid_for(n), 256, 0, st>>>(src, dst, n);
+cudaError_t launch_convert_d2f(const double2* src, float2* dst, long long rows, int ld, int col0, int ncol,
+                               cudaStream_t st) {
+    d2f_kernel<<<grid_for(rows * ncol), 256, 0, st>>>(src, dst, rows, ld, col0, ncol);
     return cudaGetLastError();
 }
-cudaError_t launch_convert_f2d(const float2* src, double2* dst, long long n, cudaStream_t st) {
-    f2d_kernel<<<grid_for(n), 256, 0, st>>>(src, dst, n);
+cudaError_t launch_convert_f2d(const float2* src, double2* dst, long long rows, int ld, int col0, int ncol,
+                               cudaStream_t st) {
+    f2d_kernel<<<grid_for(rows * ncol), 256, 0, st>>>(src, dst, rows, ld, col0, ncol);
     return cudaGetLastError();
 }
 
@@ -558,6 +569,139 @@ __global__ void random_fill_kernel(double2* X, long long rows, int ld, int col0,
 cudaError_t launch_random_fill(double2* X, long long rows, int ld, int col0, int ncol,
                                unsigned long long seed, const uint8_t* mask, cudaStream_t st) {
     random_fill_kernel<<<grid_for(rows * ncol), 256, 0, st>>>(X, rows, ld, col0, ncol, seed, mask);
+    return cudaGetLastError();
+}
+
+}  // namespace khp
+
+namespace khp {
+
+// ------------------------------------------------------ Lanczos upper bound
+// Three-term Lanczos on one vector, every scalar kept on the device:
+//   w = H v_j ; alpha_j = Re v_j^H w ; w -= alpha_j v_j + beta_{j-1} v_{j-1} ;
+//   beta_j = |w| ; v_{j+1} = w / beta_j
+// The k x k tridiagonal matrix is then diagonalised by the one-CTA kernel.
+__global__ void dot_re_partial(const double2* __restrict__ a, const double2* __restrict__ b, long long n,
+                               double* __restrict__ partial) {
+    __shared__ double red[256];
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * per;
+    const long long i1 = i0 + per < n ? i0 + per : n;
+    double s = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double2 x = a[i], y = b[i];
+        s += x.x * y.x + x.y * y.y;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// out[0] = sum (mode 0) or sqrt(sum) (mode 1)
+__global__ void finish_sum(const double* __restrict__ partial, int nb, double* out, int mode) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = mode == 1 ? sqrt(red[0]) : red[0];
+}
+
+// w -= alpha v + beta vprev (vprev may be null); partial |w|^2
+__global__ void lanczos_update(double2* __restrict__ w, const double2* __restrict__ v,
+                               const double2* __restrict__ vprev, const double* __restrict__ alpha,
+                               const double* __restrict__ beta, long long n, double* __restrict__ partial) {
+    __shared__ double red[256];
+    const double al = *alpha, be = vprev ? *beta : 0.0;
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * per;
+    const long long i1 = i0 + per < n ? i0 + per : n;
+    double s = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        double2 x = w[i];
+        const double2 y = v[i];
+        x.x -= al * y.x;
+        x.y -= al * y.y;
+        if (vprev) {
+            const double2 z = vprev[i];
+            x.x -= be * z.x;
+            x.y -= be * z.y;
+        }
+        w[i] = x;
+        s += x.x * x.x + x.y * x.y;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void scale_vec(double2* __restrict__ dst, const double2* __restrict__ src,
+                          const double* __restrict__ nrm, long long n) {
+    const double inv = 1.0 / *nrm;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 x = src[i];
+        dst[i] = make_double2(x.x * inv, x.y * inv);
+    }
+}
+
+// G = I, S = tridiag(beta, alpha, beta) as complex k x k matrices
+__global__ void build_tridiag(const double* __restrict__ alpha, const double* __restrict__ beta, int k,
+                              double2* __restrict__ G, double2* __restrict__ S) {
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int i = idx / k, j = idx - i * k;
+        G[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+        double v = 0.0;
+        if (i == j) v = alpha[i];
+        else if (j == i + 1) v = beta[i];
+        else if (i == j + 1) v = beta[j];
+        S[idx] = make_double2(v, 0.0);
+    }
+}
+
+static constexpr int kLzBlocks = 296;
+
+cudaError_t lanczos_dot(const double2* a, const double2* b, long long n, double* partial, double* out,
+                        cudaStream_t st) {
+    dot_re_partial<<<kLzBlocks, 256, 0, st>>>(a, b, n, partial);
+    finish_sum<<<1, 256, 0, st>>>(partial, kLzBlocks, out, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t lanczos_orth(double2* w, const double2* v, const double2* vprev, const double* alpha,
+                         const double* beta_prev, double* beta_out, long long n, double* partial,
+                         cudaStream_t st) {
+    lanczos_update<<<kLzBlocks, 256, 0, st>>>(w, v, vprev, alpha, beta_prev, n, partial);
+    finish_sum<<<1, 256, 0, st>>>(partial, kLzBlocks, beta_out, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t lanczos_norm(const double2* v, long long n, double* partial, double* out, cudaStream_t st) {
+    dot_re_partial<<<kLzBlocks, 256, 0, st>>>(v, v, n, partial);
+    finish_sum<<<1, 256, 0, st>>>(partial, kLzBlocks, out, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t lanczos_scale(double2* dst, const double2* src, const double* nrm, long long n, cudaStream_t st) {
+    scale_vec<<<grid_for(n), 256, 0, st>>>(dst, src, nrm, n);
+    return cudaGetLastError();
+}
+
+cudaError_t lanczos_tridiag(const double* alpha, const double* beta, int k, double2* G, double2* S,
+                            cudaStream_t st) {
+    build_tridiag<<<1, 256, 0, st>>>(alpha, beta, k, G, S);
     return cudaGetLastError();
 }
 

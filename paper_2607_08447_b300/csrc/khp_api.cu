@@ -25,6 +25,8 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -36,6 +38,7 @@ using namespace khp;
 using cplx = std::complex<double>;
 
 static thread_local std::string g_err;
+static constexpr int kLzPartials = 296;
 
 static khp_status fail(khp_status s, const std::string& msg) {
     g_err = msg;
@@ -116,6 +119,16 @@ void to_sym(const double M[3][3], double out[6]) {
     out[5] = 0.5 * (M[0][1] + M[1][0]);
 }
 
+// Entries of the rotated operator pieces below 1e-14 of the largest entry
+// are rounding residue of the rotation (exact zeros of the tensor form) and
+// are set to zero, so that the stencil skips them.
+void clean_small(double* v, int n) {
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = std::max(mx, std::fabs(v[i]));
+    for (int i = 0; i < n; ++i)
+        if (std::fabs(v[i]) <= 1e-14 * mx) v[i] = 0.0;
+}
+
 void build_operator(khp_grid* g) {
     const khp_material& m = g->mat;
     const double C = KHP_HB2M, h2 = g->h * g->h;
@@ -155,6 +168,9 @@ void build_operator(khp_grid* g) {
                                          : E.v[i][j][pa[c]][pb[c]] + E.v[i][j][pb[c]][pa[c]];
         to_sym(M, g->De[c]);
     }
+    clean_small(&g->hop[0][0], 9 * 6);
+    clean_small(g->center, 6);
+    clean_small(&g->De[0][0], 6 * 6);
     // spin-orbit + Zeeman on index 3 s + o
     cplx L[3][3][3] = {};
     const double eps[3][3][3] = {{{0, 0, 0}, {0, 0, 1}, {0, -1, 0}},
@@ -190,15 +206,54 @@ double sym_rowsum_max(const double s[6]) {
     return std::max(r0, std::max(r1, r2));
 }
 
+// Stencil coefficients scaled by alpha (the kernel computes
+// alpha*H x + beta*x + gamma*prev with alpha folded in).
 template <typename R>
-void fill_coeffs(const khp_grid* g, Coeffs<R>& c) {
-    for (int d = 0; d < 9; ++d)
-        for (int k = 0; k < 6; ++k) c.hop[d][k] = (R)g->hop[d][k];
-    for (int i = 0; i < 6; ++i)
-        for (int j = 0; j < 6; ++j) {
-            c.soz_re[i][j] = (R)g->soz_re[i][j];
-            c.soz_im[i][j] = (R)g->soz_im[i][j];
+void fill_coeffs(const khp_grid* g, Coeffs<R>& c, double alpha) {
+    for (int d = 0; d < 9; ++d) {
+        c.hop_nz[d] = 0;
+        for (int k = 0; k < 6; ++k) {
+            c.hop[d][k] = (R)(alpha * g->hop[d][k]);
+            if (g->hop[d][k] != 0.0) c.hop_nz[d] |= 1u << k;
         }
+    }
+    for (int i = 0; i < 6; ++i) {
+        c.soz_nz[i] = 0;
+        for (int j = 0; j < 6; ++j) {
+            c.soz_re[i][j] = (R)(alpha * g->soz_re[i][j]);
+            c.soz_im[i][j] = (R)(alpha * g->soz_im[i][j]);
+            if (g->soz_re[i][j] != 0.0) c.soz_nz[i] |= 1u << (2 * j);
+            if (g->soz_im[i][j] != 0.0) c.soz_nz[i] |= 2u << (2 * j);
+        }
+    }
+    // on-site orbital block: centre pattern, V on the diagonal, strain
+    c.onsite_nz = 0;
+    for (int k = 0; k < 6; ++k) {
+        bool nz = k < 3 || g->center[k] != 0.0;
+        if (g->has_strain)
+            for (int cc = 0; cc < 6; ++cc) nz = nz || g->De[cc][k] != 0.0;
+        if (nz) c.onsite_nz |= 1u << k;
+    }
+    c.pair_phase = g->pair_phase;
+}
+
+// Pairs whose Peierls phase vanishes identically on the whole grid: in the
+// symmetric gauge phi_d = (r - c).(delta_d x B) / (2 Phi0) vanishes iff
+// delta_d x B = 0; in the Landau gauge A.delta = dy (Bz x - Bx z) - dz By x.
+unsigned phase_pairs(const double B[3], int gauge) {
+    unsigned m = 0;
+    for (int d = 0; d < 9; ++d) {
+        const double dx = pair_dx(d), dy = pair_dy(d), dz = pair_dz(d);
+        bool nz;
+        if (gauge == 0) {
+            const double cx = dy * B[2] - dz * B[1], cy = dz * B[0] - dx * B[2], cz = dx * B[1] - dy * B[0];
+            nz = cx != 0.0 || cy != 0.0 || cz != 0.0;
+        } else {
+            nz = (dy != 0.0 && (B[2] != 0.0 || B[0] != 0.0)) || (dz != 0.0 && B[1] != 0.0);
+        }
+        if (nz) m |= 1u << d;
+    }
+    return m;
 }
 
 template <typename R>
@@ -217,7 +272,8 @@ khp_status apply_op(khp_grid* g, const cx_t<R>* x, const cx_t<R>* prev, cx_t<R>*
         a.phase = (const cx_t<R>*)(g->has_phase ? g->phase32 : nullptr);
     }
     a.mask = g->mask;
-    fill_coeffs<R>(g, a.c);
+    a.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
+    fill_coeffs<R>(g, a.c, alpha);
     CK(launch_stencil<R>(a, g->stream));
     g->launches += 1;
     return KHP_OK;
@@ -293,6 +349,52 @@ void op_counts(const khp_grid* g, int m, double* flops, double* b64, double* b32
     *b32 = 3 * 48.0 + 0.5 * fields64 / m;
 }
 
+// Upper bound of the spectrum for the filter interval: k-step Lanczos from a
+// random vector, bound = largest Ritz value + |beta_k|, never above the
+// Gershgorin bound.  Uses the first N entries of the four workspace blocks.
+khp_status lanczos_bound(khp_grid* g, int k, unsigned long long seed, double* out, double* out_lo) {
+    double* partial = g->lz;
+    double* alpha = g->lz + kLzPartials;
+    double* beta = alpha + KHP_MAX_M;
+    double2* Wv = g->blk64[0];
+    double2* P = g->blk64[1];
+    double2* Cc = g->blk64[2];
+    double2* Nn = g->blk64[3];
+    const long long n = g->n;
+    CK(launch_random_fill(Cc, n, 1, 0, 1, seed ^ 0x5bd1e995ULL, g->mask, g->stream));
+    CK(lanczos_norm(Cc, n, partial, beta, g->stream));
+    CK(lanczos_scale(Cc, Cc, beta, n, g->stream));
+    g->launches += 4;
+    for (int j = 0; j < k; ++j) {
+        CKS(apply_op<double>(g, Cc, nullptr, Wv, 1, 0, 1, 1.0, 0.0, 0.0));
+        CK(lanczos_dot(Cc, Wv, n, partial, alpha + j, g->stream));
+        CK(lanczos_orth(Wv, Cc, j > 0 ? P : nullptr, alpha + j, beta + j, beta + j + 1, n, partial, g->stream));
+        CK(lanczos_scale(Nn, Wv, beta + j + 1, n, g->stream));
+        g->launches += 5;
+        double2* t = P; P = Cc; Cc = Nn; Nn = t;
+    }
+    double2* G = g->small;
+    double2* S = g->small + k * k;
+    double2* Q = g->small + 2 * k * k;
+    double* th = g->dvec;
+    CK(lanczos_tridiag(alpha, beta + 1, k, G, S, g->stream));
+    CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+    CK(launch_small(G, S, k, 1, Q, th, g->dflag, g->stream));
+    g->launches += 2;
+    double* hp = g->host_pinned;
+    CK(cudaMemcpyAsync(hp, th + k - 1, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(hp + 1, beta + k, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(hp + 2, th, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const double b = hp[0] + std::fabs(hp[1]);
+    *out = std::isfinite(b) ? std::min(b, g->onsite_absmax) : g->onsite_absmax;
+    // lower estimate of the spectrum (smallest Ritz value), used to cap the
+    // filter amplification and as the scaling point
+    const double lo = hp[2];
+    *out_lo = std::isfinite(lo) ? std::max(lo, -g->onsite_absmax) : -g->onsite_absmax;
+    return KHP_OK;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -340,6 +442,7 @@ khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
         (e = cudaMalloc(&g->dvec, sizeof(double) * 8 * KHP_MAX_M)) != cudaSuccess ||
         (e = cudaMalloc(&g->dflag, sizeof(int) * 8)) != cudaSuccess ||
         (e = cudaMalloc(&g->small, sizeof(double2) * 4 * KHP_MAX_M * KHP_MAX_M)) != cudaSuccess ||
+        (e = cudaMalloc(&g->lz, sizeof(double) * (kLzPartials + 4 * KHP_MAX_M))) != cudaSuccess ||
         (e = cudaMallocHost(&g->host_pinned, sizeof(double) * 8 * KHP_MAX_M)) != cudaSuccess)
         return bail(fail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
                          std::string("allocation: ") + cudaGetErrorString(e)));
@@ -366,6 +469,7 @@ khp_status khp_destroy(khp_handle g) {
     if (g->dvec) cudaFree(g->dvec);
     if (g->dflag) cudaFree(g->dflag);
     if (g->small) cudaFree(g->small);
+    if (g->lz) cudaFree(g->lz);
     if (g->host_pinned) cudaFreeHost(g->host_pinned);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -392,6 +496,8 @@ khp_status khp_set_potential_strain_field(khp_handle g, const double* V_dev, con
     for (int k = 0; k < 3; ++k) g->B[k] = B[k];
     g->gauge = gauge;
     g->has_phase = (B[0] != 0.0 || B[1] != 0.0 || B[2] != 0.0);
+    g->phase_mode = !g->has_phase ? PH_NONE : (gauge == 0 ? PH_SYM : PH_GEN);
+    g->pair_phase = g->has_phase ? phase_pairs(B, gauge) : 0u;
     build_operator(g);
     if (g->has_phase && !g->phase64) {
         CK(cudaMalloc(&g->phase64, sizeof(double2) * 18 * g->np));
@@ -422,6 +528,7 @@ khp_status khp_set_potential_strain_field(khp_handle g, const double* V_dev, con
     for (int d = 0; d < 9; ++d) hops += 2.0 * sym_rowsum_max(g->hop[d]);
     g->onsite_absmax = g->host_pinned[0] + soz + hops;
     g->fields_set = true;
+    g->bound_valid = false;
     return KHP_OK;
 }
 
@@ -479,17 +586,17 @@ struct Solver {
         return KHP_OK;
     }
     template <typename R>
-    khp_status filter(cx_t<R>* buf[3], int& out_idx, int deg, double a, double b, double low) {
+    khp_status filter(cx_t<R>* buf[3], int& out_idx, int deg, double a, double b, double low, int c0, int nc) {
         // Y1 = (sigma1/e)(H - c)X ; Y_{k+1} = (2 s_{k+1}/e)(H - c)Y_k - s_k s_{k+1} Y_{k-1}
         const double e = 0.5 * (b - a), c = 0.5 * (b + a);
         const double sigma1 = e / (low - c);
         double sigma = sigma1;
         const double tau = 2.0 / sigma1;
         int ix = 0, iy = 1, iz = 2;
-        CKS(apply_op<R>(g, buf[ix], nullptr, buf[iy], m, 0, m, sigma1 / e, -c * sigma1 / e, 0.0));
+        CKS(apply_op<R>(g, buf[ix], nullptr, buf[iy], m, c0, nc, sigma1 / e, -c * sigma1 / e, 0.0));
         for (int k = 2; k <= deg; ++k) {
             const double sn = 1.0 / (tau - sigma);
-            CKS(apply_op<R>(g, buf[iy], buf[ix], buf[iz], m, 0, m, 2.0 * sn / e, -2.0 * c * sn / e, -sigma * sn));
+            CKS(apply_op<R>(g, buf[iy], buf[ix], buf[iz], m, c0, nc, 2.0 * sn / e, -2.0 * c * sn / e, -sigma * sn));
             const int t = ix; ix = iy; iy = iz; iz = t;
             sigma = sn;
         }
@@ -525,11 +632,15 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
     S.theta = g->dvec; S.res = g->dvec + m;
     const int max_iter = opts->max_iter > 0 ? opts->max_iter : 1000;
     const double tol = opts->tol_ev;
-    const double lam_up = g->onsite_absmax;
+    g->launches = 0;
+    if (!g->bound_valid) {
+        CKS(lanczos_bound(g, std::min<long long>(40, g->n), opts->seed, &g->lambda_lanczos, &g->lambda_low));
+        g->bound_valid = true;
+    }
+    const double lam_up = g->lambda_lanczos;
 
     int ib[4] = {0, 1, 2, 3};      // ib[0] = X (current Ritz vectors), ib[3] = W = H X
     double2** B = g->blk64;
-    g->launches = 0;
     CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
     CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, opts->seed, g->mask, g->stream));
     g->launches += 1;
@@ -546,28 +657,36 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
 
     khp_stats st{};
     st.lambda_upper = lam_up;
-    bool fp32_phase = mixed;
-    int sweeps_done = 0, stall = 0;
-    double best_fp32 = 1e300;
-    const double switch_tol = std::max(tol, 1e-6 * lam_up);
-    bool converged = false;
-    bool timed32 = false, timed64 = false;
+    // phases: FP32 filter (mixed only) -> FP64 wide-window clean-up sweeps
+    // (mixed only) -> FP64 filter
+    enum { P_FP32, P_CLEAN, P_FP64 };
+    int phase = mixed ? P_FP32 : P_FP64;
+    const int clean_sweeps = mixed ? (opts->refine_sweeps < 0 ? 2 : opts->refine_sweeps) : 0;
+    int clean_done = 0, stall = 0;
+    double best = 1e300;
+    const double floor32 = 3e-8 * lam_up;    // residual floor of FP32 blocks
+    bool converged = false, timed32 = false, timed64 = false;
+    // KHP_TRACE=1 in the environment prints one line per outer iteration
+    const char* tr = std::getenv("KHP_TRACE");
+    const bool trace = tr && tr[0] == '1';
     int it = 0;
     for (; it < max_iter; ++it) {
         if (flags & 4) return fail(KHP_ERR_BREAKDOWN, "non-finite Ritz values");
         double rmax = 0;
-        for (int i = 0; i < n; ++i) rmax = std::max(rmax, rs[i]);
+        for (int i = 0; i < n; ++i) rmax = std::max(rmax, std::isnan(rs[i]) ? HUGE_VAL : rs[i]);
+        if (rmax == HUGE_VAL) return fail(KHP_ERR_BREAKDOWN, "non-finite residuals");
         if (rmax <= tol) { converged = true; break; }
-        if (mixed && !fp32_phase) {
-            if (opts->refine_sweeps >= 0 && sweeps_done >= opts->refine_sweeps) break;
-        }
-        if (fp32_phase) {
-            if (rmax <= switch_tol) fp32_phase = false;
-            else {
-                if (rmax < 0.7 * best_fp32) { best_fp32 = rmax; stall = 0; }
-                else if (++stall >= 4) fp32_phase = false;
+        if (phase == P_FP32) {
+            if (rmax < 0.7 * best) { best = rmax; stall = 0; }
+            else ++stall;
+            if (rmax <= std::max(tol, floor32) || stall >= 4) {
+                if (opts->refine_sweeps == 0) break;
+                phase = P_CLEAN;
             }
-            if (!fp32_phase && opts->refine_sweeps == 0) break;
+        }
+        if (phase == P_CLEAN && clean_done >= clean_sweeps) {
+            if (opts->refine_sweeps >= 0) break;
+            phase = P_FP64;
         }
         if (flags & 2) {
             // Cholesky breakdown: re-orthonormalise the current block and redo RR
@@ -583,46 +702,68 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
         st.shifted_cholesky += (flags & 1) ? 1 : 0;
         CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
 
-        // filter interval [a, b], scaling point low; limit the degree so that
-        // the filtered block stays well conditioned (amplification <= 1e4)
-        const double a = th[m - 1], low = th[0];
-        const double e = 0.5 * (lam_up - a), c = 0.5 * (lam_up + a);
+        // soft locking: the leading converged Ritz vectors are not filtered
+        // (they stay in the Rayleigh-Ritz block with their H x)
+        int nlock = 0;
+        while (nlock < n && rs[nlock] <= tol) ++nlock;
+        nlock &= ~1;
+        const int na = m - nlock;
+
+        // filter interval [a, b] and scaling point low; the clean-up sweeps
+        // damp everything above a point just inside the unwanted spectrum;
+        // the degree is limited so that the filtered block stays well
+        // conditioned (amplification <= 1e4)
+        double a = th[m - 1];
         int deg = opts->degree;
-        const double xl = std::fabs((low - c) / e);
-        if (xl > 1.0) {
-            const int dmax = (int)std::floor(std::acosh(1e4) / std::acosh(xl));
-            deg = std::max(1, std::min(deg, dmax));
+        if (phase == P_CLEAN) {
+            a = a + 0.005 * (lam_up - a);
+            deg *= 2;
         }
-        if (!(a < lam_up) || !(low < a)) deg = 1;
-        const double aa = (a < lam_up) ? a : lam_up - 1e-3;
-        const double ll = (low < aa) ? low : aa - 1e-3 * (lam_up - aa);
+        if (!(a < lam_up)) a = lam_up - 1e-3 * std::fabs(lam_up);
+        // scaling point: the lower spectral estimate (or the smallest Ritz
+        // value once that is lower); the degree is capped so that the
+        // amplification at the bottom of the spectrum stays <= 1e4 (filtered
+        // block well conditioned, no FP32 overflow)
+        const double lo_est = std::min(th[0], g->lambda_low);
+        const double low = (lo_est < a) ? lo_est : a - 1e-3 * (lam_up - a);
+        {
+            const double e = 0.5 * (lam_up - a), c = 0.5 * (lam_up + a);
+            const double xl = std::fabs((low - c) / e);
+            if (xl > 1.0) {
+                const int dmax = (int)std::floor(std::acosh(1e4) / std::acosh(xl));
+                deg = std::max(1, std::min(deg, dmax));
+            }
+        }
 
         double2* Y = nullptr;
-        if (fp32_phase) {
+        if (phase == P_FP32) {
             float2* fb[3] = {g->blk32[0], g->blk32[1], g->blk32[2]};
-            CK(launch_convert_d2f(B[ib[0]], fb[0], g->n * m, g->stream));
-            g->launches += 3;   // three conversions on this path
+            CK(launch_convert_d2f(B[ib[0]], fb[0], g->n, m, nlock, na, g->stream));
             int oi = 0;
             CK(cudaEventRecord(g->ev0, g->stream));
-            CKS(S.filter<float>(fb, oi, deg, aa, lam_up, ll));
+            CKS(S.filter<float>(fb, oi, deg, a, lam_up, low, nlock, na));
             CK(cudaEventRecord(g->ev1, g->stream));
             timed32 = true;
             st.launches_fp32 += deg;
-            // H Y in FP32 into a free FP32 buffer
+            // H Y in FP32 into a free FP32 buffer, both back to FP64
             const int fw = (oi + 1) % 3;
-            CKS(apply_op<float>(g, fb[oi], nullptr, fb[fw], m, 0, m, 1.0, 0.0, 0.0));
+            CKS(apply_op<float>(g, fb[oi], nullptr, fb[fw], m, nlock, na, 1.0, 0.0, 0.0));
             Y = B[ib[0]];
-            CK(launch_convert_f2d(fb[oi], Y, g->n * m, g->stream));
-            CK(launch_convert_f2d(fb[fw], B[ib[3]], g->n * m, g->stream));
+            CK(launch_convert_f2d(fb[oi], Y, g->n, m, nlock, na, g->stream));
+            CK(launch_convert_f2d(fb[fw], B[ib[3]], g->n, m, nlock, na, g->stream));
+            g->launches += 3;
             st.iterations_fp32++;
         } else {
             double2* fb[3] = {B[ib[0]], B[ib[1]], B[ib[2]]};
             int oi = 0;
             CK(cudaEventRecord(g->ev0, g->stream));
-            CKS(S.filter<double>(fb, oi, deg, aa, lam_up, ll));
+            CKS(S.filter<double>(fb, oi, deg, a, lam_up, low, nlock, na));
             CK(cudaEventRecord(g->ev1, g->stream));
             timed64 = true;
             st.launches_fp64 += deg;
+            if (oi != 0 && nlock > 0)
+                CK(cudaMemcpy2DAsync(fb[oi], sizeof(double2) * m, fb[0], sizeof(double2) * m,
+                                     sizeof(double2) * nlock, g->n, cudaMemcpyDeviceToDevice, g->stream));
             // new roles: the filter output becomes X after the RR
             const int bo = ib[oi];
             int others[2], k = 0;
@@ -630,17 +771,26 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
                 if (j != oi) others[k++] = ib[j];
             ib[0] = bo; ib[1] = others[0]; ib[2] = others[1];
             Y = B[ib[0]];
-            CKS(apply_op<double>(g, Y, nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
-            if (mixed) sweeps_done++;
+            CKS(apply_op<double>(g, Y, nullptr, B[ib[3]], m, nlock, na, 1.0, 0.0, 0.0));
+            if (phase == P_CLEAN) clean_done++;
         }
-        st.filter_applies += deg + 1;
+        st.filter_applies += (long long)(deg + 1) * na / m;
         CKS(S.rr(Y, B[ib[3]]));
         CKS(S.fetch(th, rs, flags));
+        if (trace) {
+            double rm = 0;
+            for (int i = 0; i < n; ++i) rm = std::max(rm, rs[i]);
+            std::fprintf(stderr, "khp it %d phase %d nlock %d deg %d a %.6e low %.6e rmax %.3e\n", it, phase,
+                         nlock, deg, a, low, rm);
+        }
         if (timed32 || timed64) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
             if (timed32) st.ms_filter_fp32 += ms;
             else st.ms_filter_fp64 += ms;
+            // point-vectors actually filtered, for per-launch rates
+            if (timed32) st.pv_fp32 += (double)g->np * na * deg;
+            else st.pv_fp64 += (double)g->np * na * deg;
             timed32 = timed64 = false;
         }
     }

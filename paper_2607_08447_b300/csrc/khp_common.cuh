@@ -57,13 +57,25 @@ __host__ __device__ constexpr int pair_dz(int d) {
     return d == 2 ? 1 : d == 5 ? 1 : d == 6 ? -1 : d == 7 ? 1 : d == 8 ? -1 : 0;
 }
 
-// symmetric 3x3 stored as (00, 11, 22, 12, 02, 01)
+// symmetric 3x3 stored as (00, 11, 22, 12, 02, 01); bit k of a nonzero
+// mask flags entry k as structurally nonzero (zero entries are skipped)
 template <typename R>
 struct Coeffs {
     R hop[9][6];        // neighbour-pair orbital matrices
     R soz_re[6][6];     // spin-orbit + Zeeman (constant over the grid)
     R soz_im[6][6];
+    unsigned hop_nz[9];     // 6-bit masks
+    unsigned onsite_nz;     // 6-bit mask of the on-site orbital matrix
+    unsigned soz_nz[6];     // per row: bit 2*b2 real part, bit 2*b2+1 imaginary part
+    unsigned pair_phase;    // bit d: pair d carries a Peierls phase
 };
+
+// Peierls phase storage:
+//  PH_NONE: B = 0
+//  PH_SYM:  symmetric gauge; theta(r, r+delta) = -theta(r, r-delta) = phi_d(r),
+//           table [Np][9] of (cos phi_d, sin phi_d)
+//  PH_GEN:  any gauge; table [Np][18] of exp(-i theta) per link (+delta, -delta)
+enum { PH_NONE = 0, PH_SYM = 1, PH_GEN = 2 };
 
 template <typename R>
 struct StencilArgs {
@@ -75,7 +87,8 @@ struct StencilArgs {
     const cx_t<R>* prev;    // may be null when gamma == 0
     cx_t<R>* y;
     const R* onsite;        // [Np][6] on-site orbital matrix (centre + V + strain)
-    const cx_t<R>* phase;   // [Np][18] exp(-i theta) of links +off / -off, or null
+    const cx_t<R>* phase;   // see PH_*; null when B = 0
+    int phase_mode;
     const uint8_t* mask;    // [Np] or null
     Coeffs<R> c;
 };
@@ -103,6 +116,8 @@ struct khp_grid {
     bool fields_set;
     bool has_phase;
     bool has_strain;
+    int phase_mode;        // PH_NONE / PH_SYM / PH_GEN
+    unsigned pair_phase;   // pairs with a nonzero phase
     double onsite_absmax;  // max over points of the on-site orbital row sums
 
     // device fields
@@ -123,6 +138,11 @@ struct khp_grid {
     double* dvec;          // device vectors (theta, residuals, misc)
     int* dflag;            // device status flags
     double* host_pinned;   // pinned host staging
+
+    double* lz;            // Lanczos scratch: partials, alpha, beta
+    bool bound_valid;      // lambda_lanczos matches the current fields
+    double lambda_lanczos; // Lanczos upper bound of the spectrum
+    double lambda_low;     // Lanczos lower estimate of the spectrum
 
     long long launches;    // kernel launches issued (per call accounting)
     cudaEvent_t ev0, ev1;  // filter timing

@@ -36,10 +36,23 @@ cudaError_t launch_rotate(const double2* Y, const double2* W, int ld, int col0, 
 // flags[0] |= 1 shifted Cholesky, 2 breakdown, 4 non-finite
 cudaError_t launch_small(const double2* G, const double2* S, int m, int mode, double2* Q,
                          double* theta, int* flags, cudaStream_t st);
-cudaError_t launch_convert_d2f(const double2* src, float2* dst, long long n, cudaStream_t st);
-cudaError_t launch_convert_f2d(const float2* src, double2* dst, long long n, cudaStream_t st);
+cudaError_t launch_convert_d2f(const double2* src, float2* dst, long long rows, int ld, int col0, int ncol,
+                               cudaStream_t st);
+cudaError_t launch_convert_f2d(const float2* src, double2* dst, long long rows, int ld, int col0, int ncol,
+                               cudaStream_t st);
 cudaError_t launch_random_fill(double2* X, long long rows, int ld, int col0, int ncol,
                                unsigned long long seed, const uint8_t* mask, cudaStream_t st);
+
+// Lanczos pieces (dense.cu); scalars live in device memory
+cudaError_t lanczos_dot(const double2* a, const double2* b, long long n, double* partial, double* out,
+                        cudaStream_t st);
+cudaError_t lanczos_orth(double2* w, const double2* v, const double2* vprev, const double* alpha,
+                         const double* beta_prev, double* beta_out, long long n, double* partial,
+                         cudaStream_t st);
+cudaError_t lanczos_norm(const double2* v, long long n, double* partial, double* out, cudaStream_t st);
+cudaError_t lanczos_scale(double2* dst, const double2* src, const double* nrm, long long n, cudaStream_t st);
+cudaError_t lanczos_tridiag(const double* alpha, const double* beta, int k, double2* G, double2* S,
+                            cudaStream_t st);
 
 // observables.cu
 cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,

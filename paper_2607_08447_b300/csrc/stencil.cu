@@ -38,38 +38,91 @@ __device__ __forceinline__ void store_vg(cx_t<R>* p, const cx_t<R> (&v)[VG]) {
     }
 }
 
-// acc[s*3 + i][v] (+)= sum_j M_ij x[s*3 + j][v], M real symmetric (00,11,22,12,02,01)
+// acc[s*3 + i][v] (+)= sum_j M_ij x[s*3 + j][v] for both spins, M real
+// symmetric (00,11,22,12,02,01); entries whose bit is clear in nz are
+// structurally zero and skipped (warp-uniform branches)
 template <typename R, int VG, bool INIT>
-__device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], const cx_t<R> (&x)[6][VG]) {
-    const R m00 = M[0], m11 = M[1], m22 = M[2], m12 = M[3], m02 = M[4], m01 = M[5];
+__device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], unsigned nz,
+                                     const cx_t<R> (&x)[6][VG]) {
+    if (INIT) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+        for (int b = 0; b < 6; ++b)
 #pragma unroll
-        for (int v = 0; v < VG; ++v) {
-            const cx_t<R> x0 = x[3 * s][v], x1 = x[3 * s + 1][v], x2 = x[3 * s + 2][v];
-            cx_t<R> r0, r1, r2;
-            if (INIT) {
-                r0.x = m00 * x0.x; r0.y = m00 * x0.y;
-                r1.x = m01 * x0.x; r1.y = m01 * x0.y;
-                r2.x = m02 * x0.x; r2.y = m02 * x0.y;
-            } else {
-                r0 = acc[3 * s][v]; r1 = acc[3 * s + 1][v]; r2 = acc[3 * s + 2][v];
-                r0.x = fma(m00, x0.x, r0.x); r0.y = fma(m00, x0.y, r0.y);
-                r1.x = fma(m01, x0.x, r1.x); r1.y = fma(m01, x0.y, r1.y);
-                r2.x = fma(m02, x0.x, r2.x); r2.y = fma(m02, x0.y, r2.y);
-            }
-            r0.x = fma(m01, x1.x, r0.x); r0.y = fma(m01, x1.y, r0.y);
-            r0.x = fma(m02, x2.x, r0.x); r0.y = fma(m02, x2.y, r0.y);
-            r1.x = fma(m11, x1.x, r1.x); r1.y = fma(m11, x1.y, r1.y);
-            r1.x = fma(m12, x2.x, r1.x); r1.y = fma(m12, x2.y, r1.y);
-            r2.x = fma(m12, x1.x, r2.x); r2.y = fma(m12, x1.y, r2.y);
-            r2.x = fma(m22, x2.x, r2.x); r2.y = fma(m22, x2.y, r2.y);
-            acc[3 * s][v] = r0; acc[3 * s + 1][v] = r1; acc[3 * s + 2][v] = r2;
+            for (int v = 0; v < VG; ++v) acc[b][v] = mk<R>(R(0), R(0));
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (nz & (1u << k)) {
+            const R m = M[k];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int v = 0; v < VG; ++v) {
+                    acc[3 * s + k][v].x = fma(m, x[3 * s + k][v].x, acc[3 * s + k][v].x);
+                    acc[3 * s + k][v].y = fma(m, x[3 * s + k][v].y, acc[3 * s + k][v].y);
+                }
+        }
+    }
+    // off-diagonal (i, j): 3 -> (1,2), 4 -> (0,2), 5 -> (0,1)
+#pragma unroll
+    for (int k = 3; k < 6; ++k) {
+        if (nz & (1u << k)) {
+            const int i = k == 3 ? 1 : 0;
+            const int j = k == 5 ? 1 : 2;
+            const R m = M[k];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int v = 0; v < VG; ++v) {
+                    acc[3 * s + i][v].x = fma(m, x[3 * s + j][v].x, acc[3 * s + i][v].x);
+                    acc[3 * s + i][v].y = fma(m, x[3 * s + j][v].y, acc[3 * s + i][v].y);
+                    acc[3 * s + j][v].x = fma(m, x[3 * s + i][v].x, acc[3 * s + j][v].x);
+                    acc[3 * s + j][v].y = fma(m, x[3 * s + i][v].y, acc[3 * s + j][v].y);
+                }
         }
     }
 }
 
-template <typename R, int VG, bool PHASE, bool MASK>
+// Orbitals read through a neighbour pair: orbital j is needed when some
+// nonzero entry (i, j) of the pair's symmetric 3x3 exists.
+__host__ __device__ constexpr unsigned need_of(unsigned nz) {
+    return ((nz & (1u | 16u | 32u)) ? 1u : 0u) | ((nz & (2u | 8u | 32u)) ? 2u : 0u) |
+           ((nz & (4u | 8u | 16u)) ? 4u : 0u);
+}
+
+// acc[3s+i] += (mc * u[3s+j] + i-part) for entry (i, j):
+//   PH_SYM pairs:  m * (c u - i s v)  with u = x+ + x-, v = x+ - x-
+//   other pairs:   m * u   (mc = m, ms = 0: v unused)
+template <typename R, int VG, bool SYMPH>
+__device__ __forceinline__ void pair_entry(cx_t<R> (&acc)[6][VG], int i, int j, R mc, R ms,
+                                           const cx_t<R> (&u)[6][VG], const cx_t<R> (&v)[6][VG]) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int w = 0; w < VG; ++w) {
+            cx_t<R>& A = acc[3 * sp + i][w];
+            const cx_t<R> U = u[3 * sp + j][w];
+            A.x = fma(mc, U.x, A.x);
+            A.y = fma(mc, U.y, A.y);
+            if (SYMPH) {
+                const cx_t<R> Vv = v[3 * sp + j][w];
+                A.x = fma(ms, Vv.y, A.x);
+                A.y = fma(-ms, Vv.x, A.y);
+            }
+        }
+}
+
+// y = alpha (H x) + beta x + gamma prev, with alpha folded into the
+// coefficients: on-site (alpha o + beta delta) per point, hop and spin-orbit
+// matrices pre-scaled by alpha on the host.
+// CUBIC: compile-time sparsity of the crystal frame and of frames rotated
+// about a cube axis by 45 degrees (the [110] device frame): face pairs are
+// diagonal, the edge pair in the (a, b) plane only couples orbitals a and b.
+__host__ __device__ constexpr unsigned cubic_nz(int d) {
+    return d < 3 ? 7u : (d < 5 ? 32u : (d < 7 ? 16u : 8u));
+}
+
+template <typename R, int VG, int PH, bool MASK, bool CUBIC>
 __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
     using C = cx_t<R>;
     const int G = a.ncol / VG;
@@ -98,35 +151,48 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
     }
 
     const C* xp = a.x + p * ps + col;
-    C xs[6][VG];
-#pragma unroll
-    for (int b = 0; b < 6; ++b) load_vg<R, VG>(xs[b], xp + b * a.ld);
-
     C acc[6][VG];
     {
+        C xs[6][VG];
+#pragma unroll
+        for (int b = 0; b < 6; ++b) load_vg<R, VG>(xs[b], xp + b * a.ld);
         R o[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) o[k] = __ldg(a.onsite + p * 6 + k);
-        sym3<R, VG, true>(acc, o, xs);
-    }
-    // spin-orbit + Zeeman: constant complex 6x6
+        for (int k = 0; k < 6; ++k) o[k] = a.alpha * __ldg(a.onsite + p * 6 + k);
 #pragma unroll
-    for (int b = 0; b < 6; ++b) {
+        for (int k = 0; k < 3; ++k) o[k] += a.beta;
+        sym3<R, VG, true>(acc, o, a.c.onsite_nz | 7u, xs);
+        // spin-orbit + Zeeman (alpha-scaled): constant complex 6x6, zero parts skipped
 #pragma unroll
-        for (int b2 = 0; b2 < 6; ++b2) {
-            const R sr = a.c.soz_re[b][b2], si = a.c.soz_im[b][b2];
+        for (int b = 0; b < 6; ++b) {
+            const unsigned rowm = a.c.soz_nz[b];
 #pragma unroll
-            for (int v = 0; v < VG; ++v) {
-                acc[b][v].x = fma(sr, xs[b2][v].x, acc[b][v].x);
-                acc[b][v].x = fma(-si, xs[b2][v].y, acc[b][v].x);
-                acc[b][v].y = fma(sr, xs[b2][v].y, acc[b][v].y);
-                acc[b][v].y = fma(si, xs[b2][v].x, acc[b][v].y);
+            for (int b2 = 0; b2 < 6; ++b2) {
+                if (rowm & (1u << (2 * b2))) {
+                    const R sr = a.c.soz_re[b][b2];
+#pragma unroll
+                    for (int v = 0; v < VG; ++v) {
+                        acc[b][v].x = fma(sr, xs[b2][v].x, acc[b][v].x);
+                        acc[b][v].y = fma(sr, xs[b2][v].y, acc[b][v].y);
+                    }
+                }
+                if (rowm & (2u << (2 * b2))) {
+                    const R si = a.c.soz_im[b][b2];
+#pragma unroll
+                    for (int v = 0; v < VG; ++v) {
+                        acc[b][v].x = fma(-si, xs[b2][v].y, acc[b][v].x);
+                        acc[b][v].y = fma(si, xs[b2][v].x, acc[b][v].y);
+                    }
+                }
             }
         }
     }
 
 #pragma unroll
     for (int d = 0; d < 9; ++d) {
+        const unsigned nzd = CUBIC ? cubic_nz(d) : a.c.hop_nz[d];
+        if (nzd == 0) continue;
+        const unsigned need = need_of(nzd);
         const int dx = pair_dx(d), dy = pair_dy(d), dz = pair_dz(d);
         const long long off = (long long)dx + (long long)a.nx * ((long long)dy + (long long)a.ny * dz);
         bool okp = inr(ix + dx, a.nx) && inr(iy + dy, a.ny) && inr(iz + dz, a.nz);
@@ -135,68 +201,122 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
             okp = okp && a.mask[p + off] != 0;
             okm = okm && a.mask[p - off] != 0;
         }
-        C s[6][VG];
+        const bool ph = PH != PH_NONE && (a.c.pair_phase & (1u << d));
+        C u[6][VG], w[6][VG];
+        if (PH == PH_GEN && ph) {
+            // general gauge: s = e1 x+ + e2 x- formed per needed component
+            const C e1 = __ldg(a.phase + p * 18 + 2 * d);
+            const C e2 = __ldg(a.phase + p * 18 + 2 * d + 1);
 #pragma unroll
-        for (int b = 0; b < 6; ++b)
+            for (int o = 0; o < 3; ++o) {
+                if (!(need & (1u << o))) continue;
 #pragma unroll
-            for (int v = 0; v < VG; ++v) s[b][v] = mk<R>(R(0), R(0));
-        if (okp) {
-            const C* np_ = xp + off * ps;
-            C ph;
-            if (PHASE) ph = __ldg(a.phase + p * 18 + 2 * d);
+                for (int sp = 0; sp < 2; ++sp) {
+                    const int b = 3 * sp + o;
+                    C xpv[VG], xmv[VG];
+                    if (okp) load_vg<R, VG>(xpv, xp + off * ps + b * a.ld);
+                    else {
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                C w[VG];
-                load_vg<R, VG>(w, np_ + b * a.ld);
+                        for (int v = 0; v < VG; ++v) xpv[v] = mk<R>(R(0), R(0));
+                    }
+                    if (okm) load_vg<R, VG>(xmv, xp - off * ps + b * a.ld);
+                    else {
 #pragma unroll
-                for (int v = 0; v < VG; ++v) s[b][v] = PHASE ? cmul(ph, w[v]) : w[v];
+                        for (int v = 0; v < VG; ++v) xmv[v] = mk<R>(R(0), R(0));
+                    }
+#pragma unroll
+                    for (int v = 0; v < VG; ++v) {
+                        u[b][v] = cmul(e1, xpv[v]);
+                        cfma(u[b][v], e2, xmv[v]);
+                    }
+                }
             }
-        }
-        if (okm) {
-            const C* nm_ = xp - off * ps;
-            C ph;
-            if (PHASE) ph = __ldg(a.phase + p * 18 + 2 * d + 1);
+        } else {
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                C w[VG];
-                load_vg<R, VG>(w, nm_ + b * a.ld);
+            for (int o = 0; o < 3; ++o) {
+                if (!(need & (1u << o))) continue;
 #pragma unroll
-                for (int v = 0; v < VG; ++v) {
-                    if (PHASE) {
-                        cfma(s[b][v], ph, w[v]);
-                    } else {
-                        s[b][v].x += w[v].x; s[b][v].y += w[v].y;
+                for (int sp = 0; sp < 2; ++sp) {
+                    const int b = 3 * sp + o;
+                    C xpv[VG], xmv[VG];
+                    if (okp) load_vg<R, VG>(xpv, xp + off * ps + b * a.ld);
+                    else {
+#pragma unroll
+                        for (int v = 0; v < VG; ++v) xpv[v] = mk<R>(R(0), R(0));
+                    }
+                    if (okm) load_vg<R, VG>(xmv, xp - off * ps + b * a.ld);
+                    else {
+#pragma unroll
+                        for (int v = 0; v < VG; ++v) xmv[v] = mk<R>(R(0), R(0));
+                    }
+#pragma unroll
+                    for (int v = 0; v < VG; ++v) {
+                        u[b][v].x = xpv[v].x + xmv[v].x;
+                        u[b][v].y = xpv[v].y + xmv[v].y;
+                        if (PH == PH_SYM && ph) {
+                            w[b][v].x = xpv[v].x - xmv[v].x;
+                            w[b][v].y = xpv[v].y - xmv[v].y;
+                        }
                     }
                 }
             }
         }
-        R M[6];
+        // fold the pair's (alpha-scaled) matrix into the phase factors
+        R cth = R(1), sth = R(0);
+        if (PH == PH_SYM && ph) {
+            const C cs = __ldg(a.phase + p * 9 + d);
+            cth = cs.x;
+            sth = cs.y;
+        }
 #pragma unroll
-        for (int k = 0; k < 6; ++k) M[k] = a.c.hop[d][k];
-        sym3<R, VG, false>(acc, M, s);
+        for (int k = 0; k < 6; ++k) {
+            if (!(nzd & (1u << k))) continue;
+            const R m = a.c.hop[d][k];
+            const int i = k < 3 ? k : (k == 3 ? 1 : 0);
+            const int j = k < 3 ? k : (k == 5 ? 1 : 2);
+            if (PH == PH_SYM && ph) {
+                const R mc = m * cth, ms = m * sth;
+                pair_entry<R, VG, true>(acc, i, j, mc, ms, u, w);
+                if (k >= 3) pair_entry<R, VG, true>(acc, j, i, mc, ms, u, w);
+            } else {
+                pair_entry<R, VG, false>(acc, i, j, m, R(0), u, w);
+                if (k >= 3) pair_entry<R, VG, false>(acc, j, i, m, R(0), u, w);
+            }
+        }
     }
 
-    // y = alpha*acc + beta*x + gamma*prev
+    // y = acc + gamma prev
     const C* pp = a.prev ? a.prev + p * ps + col : nullptr;
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
         C out[VG];
 #pragma unroll
-        for (int v = 0; v < VG; ++v) {
-            out[v].x = a.alpha * acc[b][v].x + a.beta * xs[b][v].x;
-            out[v].y = a.alpha * acc[b][v].y + a.beta * xs[b][v].y;
-        }
+        for (int v = 0; v < VG; ++v) out[v] = acc[b][v];
         if (pp) {
-            C w[VG];
-            load_vg<R, VG>(w, pp + b * a.ld);
+            C wv[VG];
+            load_vg<R, VG>(wv, pp + b * a.ld);
 #pragma unroll
             for (int v = 0; v < VG; ++v) {
-                out[v].x = fma(a.gamma, w[v].x, out[v].x);
-                out[v].y = fma(a.gamma, w[v].y, out[v].y);
+                out[v].x = fma(a.gamma, wv[v].x, out[v].x);
+                out[v].y = fma(a.gamma, wv[v].y, out[v].y);
             }
         }
         store_vg<R, VG>(yp + b * a.ld, out);
     }
+}
+
+template <typename R, int VG, int PH>
+static cudaError_t launch_ph(const StencilArgs<R>& a, unsigned blocks, cudaStream_t st) {
+    bool cubic = true;
+    for (int d = 0; d < 9; ++d) cubic = cubic && (a.c.hop_nz[d] & ~cubic_nz(d)) == 0;
+    if (a.mask) {
+        if (cubic) stencil_kernel<R, VG, PH, true, true><<<blocks, 256, 0, st>>>(a);
+        else stencil_kernel<R, VG, PH, true, false><<<blocks, 256, 0, st>>>(a);
+    } else {
+        if (cubic) stencil_kernel<R, VG, PH, false, true><<<blocks, 256, 0, st>>>(a);
+        else stencil_kernel<R, VG, PH, false, false><<<blocks, 256, 0, st>>>(a);
+    }
+    return cudaGetLastError();
 }
 
 template <typename R, int VG>
@@ -207,12 +327,10 @@ static cudaError_t launch_vg(const StencilArgs<R>& a, cudaStream_t st) {
     const int threads = 256;
     const long long blocks = (total + threads - 1) / threads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const bool ph = a.phase != nullptr, mk_ = a.mask != nullptr;
-    if (ph && mk_) stencil_kernel<R, VG, true, true><<<(unsigned)blocks, threads, 0, st>>>(a);
-    else if (ph) stencil_kernel<R, VG, true, false><<<(unsigned)blocks, threads, 0, st>>>(a);
-    else if (mk_) stencil_kernel<R, VG, false, true><<<(unsigned)blocks, threads, 0, st>>>(a);
-    else stencil_kernel<R, VG, false, false><<<(unsigned)blocks, threads, 0, st>>>(a);
-    return cudaGetLastError();
+    const int mode = a.phase ? a.phase_mode : PH_NONE;
+    if (mode == PH_SYM) return launch_ph<R, VG, PH_SYM>(a, (unsigned)blocks, st);
+    if (mode == PH_GEN) return launch_ph<R, VG, PH_GEN>(a, (unsigned)blocks, st);
+    return launch_ph<R, VG, PH_NONE>(a, (unsigned)blocks, st);
 }
 
 template <typename R>
@@ -289,7 +407,10 @@ __device__ __forceinline__ void vecpot(const PhaseArgs& a, double x, double y, d
     }
 }
 
-// Peierls phase of the link r -> r' : exp(-i A((r+r')/2).(r'-r) / Phi0)
+// Peierls phase of the link r -> r' : exp(-i A((r+r')/2).(r'-r) / Phi0).
+// Symmetric gauge (mode PH_SYM): A is linear with an antisymmetric gradient,
+// so theta(r, r+delta) = A(r).delta / Phi0 = -theta(r, r-delta); only
+// (cos, sin) of phi_d = A(r).delta_d / Phi0 is stored per pair.
 __global__ void phase_kernel(const PhaseArgs a) {
     const long long np = (long long)a.nx * a.ny * a.nz;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,6 +420,17 @@ __global__ void phase_kernel(const PhaseArgs a) {
     const int iz = (int)(p / ((long long)a.nx * a.ny));
     const double x = (ix + 1) * a.h, y = (iy + 1) * a.h, z = (iz + 1) * a.h;
     for (int d = 0; d < 9; ++d) {
+        if (a.gauge == 0) {
+            const double dx = pair_dx(d) * a.h, dy = pair_dy(d) * a.h, dz = pair_dz(d) * a.h;
+            double A[3];
+            vecpot(a, x, y, z, A);
+            const double phi = (A[0] * dx + A[1] * dy + A[2] * dz) / KHP_PHI0;
+            double sn, cs;
+            sincos(phi, &sn, &cs);
+            a.phase64[p * 9 + d] = make_double2(cs, sn);
+            a.phase32[p * 9 + d] = make_float2((float)cs, (float)sn);
+            continue;
+        }
         for (int sgn = 0; sgn < 2; ++sgn) {
             const double s = sgn == 0 ? 1.0 : -1.0;
             const double dx = s * pair_dx(d) * a.h, dy = s * pair_dy(d) * a.h, dz = s * pair_dz(d) * a.h;

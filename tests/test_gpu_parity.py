@@ -225,3 +225,16 @@ def test_error_paths(khp):
     # the handle stays usable after every error
     r = g.eigensolve(8, block_m=16, tol=1e-10)
     assert r.status == 0
+
+
+@pytest.mark.parametrize("case", [0, 2])
+def test_spectral_upper_bound_is_an_upper_bound(khp, case):
+    """The filter's upper bound (Lanczos, capped by Gershgorin) lies above
+    the largest eigenvalue of the oracle's matrix, and not absurdly far."""
+    p = _problem(CASES[case])
+    wmax = eig.all_eigenvalues_dense(kp.assemble(p), mask=p.mask)[-1]
+    g = _grid(khp, p)
+    r = g.eigensolve(4, block_m=8, degree=8, tol=1e-6, max_iter=3, allow_not_converged=True)
+    ub = r.stats["lambda_upper"]
+    assert ub >= wmax
+    assert ub <= 1.6 * wmax
