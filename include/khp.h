@@ -182,6 +182,30 @@ khp_status khp_eigs_backward(khp_handle h, const void* evecs_dev, const double* 
                              double* dLdstrain_dev, const double* levers_dev, int n_gates,
                              double* dLdalpha_host);
 
+/* Allocation-free variant of khp_eigs_backward (the paper has no
+ * counterpart; it exists for callers of this library).  Same arguments,
+ * results and errors as khp_eigs_backward.  It is for callers that must not
+ * see device memory allocated or freed during the call: a process whose
+ * device memory is all owned by a pooling allocator, a latency-critical loop
+ * where an allocation or free could synchronise the device, or a host that
+ * forbids the library to hold device memory of its own between calls.
+ * Instead of allocating its reduction scratch per call, it uses one fixed
+ * array in device memory (KHP_NOALLOC_BLOCKS = 296 blocks x 16 gates of
+ * partial sums plus 16 results, about 38 KB per GPU, held until the process
+ * exits).  Limits: n_gates <= 16 (larger counts fail with
+ * KHP_ERR_INVALID_ARG), n <= 64.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before
+ *    capturing the stream into a CUDA graph.
+ *  - All calls share the array: calls whose kernels overlap on the GPU
+ *    (other streams or unordered host threads) race and must be serialised
+ *    by the caller.
+ *  - It runs on the handle's stream and synchronises it when n_gates > 0. */
+khp_status khp_eigs_backward_noalloc(khp_handle h, const void* evecs_dev, const double* evals_host,
+                                     int n, const double* dLdE_host, double* dLdV_dev,
+                                     double* dLdstrain_dev, const double* levers_dev, int n_gates,
+                                     double* dLdalpha_host);
+
 /* Free the handle and its workspace (synchronises its stream). */
 khp_status khp_destroy(khp_handle h);
 

@@ -19,7 +19,8 @@ STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KH
                 7: "KHP_ERR_DEGENERATE"}
 
 EXPORTED = ["khp_create_grid", "khp_set_potential_strain_field", "khp_apply", "khp_eigensolve",
-            "khp_density", "khp_eigs_backward", "khp_destroy", "khp_last_error", "khp_version"]
+            "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",
+            "khp_last_error", "khp_version"]
 
 
 class Material(ctypes.Structure):
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.khp_eigensolve.argtypes = [vp, ctypes.POINTER(SolverOpts), dp, vp, dp, ctypes.POINTER(Stats)]
     lib.khp_density.argtypes = [vp, vp, i, dp, vp]
     lib.khp_eigs_backward.argtypes = [vp, vp, dp, i, dp, vp, vp, vp, i, dp]
+    lib.khp_eigs_backward_noalloc.argtypes = [vp, vp, dp, i, dp, vp, vp, vp, i, dp]
     lib.khp_destroy.argtypes = [vp]
     lib.khp_last_error.argtypes = []
     lib.khp_last_error.restype = ctypes.c_char_p

@@ -45,6 +45,8 @@ static khp_status fail(khp_status s, const std::string& msg) {
     return s;
 }
 
+khp_status khp_set_error(khp_status s, const std::string& msg) { return fail(s, msg); }
+
 #define CK(call)                                                                        \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \

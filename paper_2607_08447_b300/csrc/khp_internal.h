@@ -1,6 +1,8 @@
 // Internal launchers and constants shared by the library's translation units.
 #pragma once
 
+#include <string>
+
 #include "khp_common.cuh"
 
 #define KHP_MAX_GATES 16
@@ -63,3 +65,7 @@ cudaError_t launch_backward(const double2* psi, long long np, int n, const doubl
                             double* dalpha_dev, cudaStream_t st);
 
 }  // namespace khp
+
+// Records the message returned by khp_last_error() on this thread and
+// passes the status through (khp_api.cu).
+khp_status khp_set_error(khp_status s, const std::string& msg);
