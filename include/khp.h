@@ -114,6 +114,10 @@ typedef struct {
                                   filter step: read Y_k, Y_k-1, write Y_k+1 and
                                   the per-point field tables over the block width */
     double bytes_per_pv_fp32;
+    int block_m;               /* block width used (after autotuning)          */
+    int batch_rounds;          /* batched call: lock-step rounds executed      */
+    int batch_graphs;          /* batched call: CUDA graphs instantiated       */
+    double autotune_ms;        /* batched call: time spent in autotune trials  */
 } khp_stats;
 
 /* Create a grid handle.
@@ -162,6 +166,33 @@ khp_status khp_apply(khp_handle h, const void* X_dev, void* Y_dev, int m, int pr
  * is reached before every residual is <= tol_ev. */
 khp_status khp_eigensolve(khp_handle h, const khp_solver_opts* opts, double* evals_host,
                           void* evecs_dev, double* resid_host, khp_stats* stats);
+
+/* Flags of khp_eigensolve_batched. */
+#define KHP_BATCH_GRAPH 1      /* capture every round of the batch into one CUDA graph */
+#define KHP_BATCH_AUTOTUNE 2   /* choose block_m by timed trial solves (opts->block_m ignored) */
+
+/* Solve `count` independent problems (a gate-voltage / detuning sweep,
+ * Sec. II C: the single-particle problem is re-solved for every detuning
+ * point; grids may differ in size).  Every problem runs the same algorithm as
+ * khp_eigensolve with the same options; the problems advance in lock-step
+ * rounds (one outer iteration each, converged problems drop out), each
+ * problem on its own internal stream so their kernels overlap.
+ *  hs         count distinct handles on one device, fields set
+ *  evals_host float64 [count][n_states]
+ *  evecs_dev  count device pointers, each complex128 [N_i][n_states]
+ *  resid_host optional float64 [count][n_states]
+ *  stats      optional [count]
+ *  flags      KHP_BATCH_GRAPH: every round is captured from a master stream
+ *             (fork/join over the problems' streams) into one CUDA graph and
+ *             launched once; the executable graph is updated in place when
+ *             the round's topology is unchanged.
+ *             KHP_BATCH_AUTOTUNE: block_m is chosen among n+4, n+8, n+12 by
+ *             timed trial solves of the smallest problem.
+ * Warm starts are not accepted here.  Returns NOT_CONVERGED if any problem
+ * hit max_iter (all results are still written). */
+khp_status khp_eigensolve_batched(const khp_handle* hs, int count, const khp_solver_opts* opts,
+                                  double* evals_host, void* const* evecs_dev, double* resid_host,
+                                  khp_stats* stats, int flags);
 
 /* Hole density (Sec. II B, fed to Poisson):
  *  rho_dev[p] = sum_i w_host[i] * sum_b |psi_i(6p+b)|^2   (discrete norm)

@@ -6,6 +6,6 @@ The compute path is the C-ABI library ``libkhp.so`` (include/khp.h) built
 from ``csrc/`` for sm_103a; this package only marshals arguments.
 """
 from ._lib import KHPError, load  # noqa: F401
-from .solver import KPEigs, KPGrid, SolveResult  # noqa: F401
+from .solver import KPEigs, KPGrid, SolveResult, solve_batched  # noqa: F401
 
-__all__ = ["KPGrid", "KPEigs", "SolveResult", "KHPError", "load"]
+__all__ = ["KPGrid", "KPEigs", "SolveResult", "solve_batched", "KHPError", "load"]

@@ -14,11 +14,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkhp.so")
 
 KHP_OK = 0
+KHP_BATCH_GRAPH = 1
+KHP_BATCH_AUTOTUNE = 2
 STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KHP_ERR_OOM",
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}
 
 EXPORTED = ["khp_create_grid", "khp_set_potential_strain_field", "khp_apply", "khp_eigensolve",
+            "khp_eigensolve_batched",
             "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",
             "khp_last_error", "khp_version"]
 
@@ -46,7 +49,9 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("point_vectors", ctypes.c_double),
                 ("pv_fp64", ctypes.c_double), ("pv_fp32", ctypes.c_double),
                 ("flops_per_pv", ctypes.c_double), ("bytes_per_pv_fp64", ctypes.c_double),
-                ("bytes_per_pv_fp32", ctypes.c_double)]
+                ("bytes_per_pv_fp32", ctypes.c_double), ("block_m", ctypes.c_int),
+                ("batch_rounds", ctypes.c_int), ("batch_graphs", ctypes.c_int),
+                ("autotune_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,6 +79,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.khp_set_potential_strain_field.argtypes = [vp, vp, vp, vp, dp, i, dp, i]
     lib.khp_apply.argtypes = [vp, vp, vp, i, i]
     lib.khp_eigensolve.argtypes = [vp, ctypes.POINTER(SolverOpts), dp, vp, dp, ctypes.POINTER(Stats)]
+    lib.khp_eigensolve_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(SolverOpts), dp,
+                                           ctypes.POINTER(vp), dp, ctypes.POINTER(Stats), i]
     lib.khp_density.argtypes = [vp, vp, i, dp, vp]
     lib.khp_eigs_backward.argtypes = [vp, vp, dp, i, dp, vp, vp, vp, i, dp]
     lib.khp_eigs_backward_noalloc.argtypes = [vp, vp, dp, i, dp, vp, vp, vp, i, dp]

@@ -575,17 +575,20 @@ struct Solver {
         g->launches += 4;
         return KHP_OK;
     }
-    // host copies of theta, residuals and flags (synchronises)
-    khp_status fetch(std::vector<double>& th, std::vector<double>& rs, int& flags) {
+    // copies of theta, residuals and flags into pinned memory (async)
+    khp_status copy_out() {
         double* hp = g->host_pinned;
         CK(cudaMemcpyAsync(hp, theta, sizeof(double) * m, cudaMemcpyDeviceToHost, g->stream));
         CK(cudaMemcpyAsync(hp + m, res, sizeof(double) * m, cudaMemcpyDeviceToHost, g->stream));
         CK(cudaMemcpyAsync(hp + 2 * m, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-        CK(cudaStreamSynchronize(g->stream));
+        return KHP_OK;
+    }
+    // after the stream is synchronised
+    void read_out(std::vector<double>& th, std::vector<double>& rs, int& flags) const {
+        const double* hp = g->host_pinned;
         th.assign(hp, hp + m);
         rs.assign(hp + m, hp + 2 * m);
         std::memcpy(&flags, hp + 2 * m, sizeof(int));
-        return KHP_OK;
     }
     template <typename R>
     khp_status filter(cx_t<R>* buf[3], int& out_idx, int deg, double a, double b, double low, int c0, int nc) {
@@ -609,114 +612,154 @@ struct Solver {
 
 }  // namespace
 
-extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, double* evals_host,
-                                     void* evecs_dev, double* resid_host, khp_stats* stats) {
-    g_err.clear();
-    const auto t0 = std::chrono::steady_clock::now();
-    if (!g || !opts) return fail(KHP_ERR_INVALID_ARG, "handle or opts is NULL");
-    if (!g->fields_set) return fail(KHP_ERR_STATE, "fields not set");
-    const int n = opts->n_states, m = opts->block_m;
-    if (m < 2 || m > KHP_MAX_M || (m & 1)) return fail(KHP_ERR_INVALID_ARG, "block_m must be even, 2..64");
-    if (n < 1 || n >= m) return fail(KHP_ERR_INVALID_ARG, "need 1 <= n_states < block_m");
-    if ((long long)m > g->n) return fail(KHP_ERR_INVALID_ARG, "block_m exceeds the number of unknowns");
-    if (opts->degree < 1) return fail(KHP_ERR_INVALID_ARG, "degree must be >= 1");
-    if (opts->precision != 0 && opts->precision != 1) return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
-    if (!(opts->tol_ev > 0.0)) return fail(KHP_ERR_INVALID_ARG, "tol_ev must be > 0");
-    if (!evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "evals or evecs is NULL");
-    if (opts->warm_start_dev && (opts->warm_cols < 1 || opts->warm_cols > m))
-        return fail(KHP_ERR_INVALID_ARG, "warm_cols must be in 1..block_m");
-    const bool mixed = opts->precision == 1;
-    CKS(ensure_ws(g, m, mixed));
+namespace {
 
+// One eigensolve as a resumable state machine, so that a single call and
+// the batched call drive the same code:
+//   begin()  -> [sync] absorb() -> loop { decide(); issue(); [sync] absorb(); } -> end()
+// decide() takes the host decisions (convergence, phase, locking, filter
+// interval and degree); issue() only enqueues device work on the handle's
+// stream (it may be captured into a CUDA graph); absorb() reads back the Ritz
+// values, residuals and flags that issue() copied to pinned memory.
+struct Solve {
+    khp_grid* g = nullptr;
+    khp_solver_opts o{};
     Solver S;
-    S.g = g; S.m = m; S.nblk = dense_blocks(g->n);
-    S.G = g->small; S.Q = g->small + 2 * m * m;
-    S.theta = g->dvec; S.res = g->dvec + m;
-    const int max_iter = opts->max_iter > 0 ? opts->max_iter : 1000;
-    const double tol = opts->tol_ev;
-    g->launches = 0;
-    if (!g->bound_valid) {
-        CKS(lanczos_bound(g, std::min<long long>(40, g->n), opts->seed, &g->lambda_lanczos, &g->lambda_low));
-        g->bound_valid = true;
-    }
-    const double lam_up = g->lambda_lanczos;
-
+    int n = 0, m = 0;
+    bool mixed = false;
+    int max_iter = 0;
+    double tol = 0, lam_up = 0;
     int ib[4] = {0, 1, 2, 3};      // ib[0] = X (current Ritz vectors), ib[3] = W = H X
-    double2** B = g->blk64;
-    CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
-    CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, opts->seed, g->mask, g->stream));
-    g->launches += 1;
-    if (opts->warm_start_dev)
-        CK(cudaMemcpy2DAsync(B[ib[0]], sizeof(double2) * m, opts->warm_start_dev,
-                             sizeof(double2) * opts->warm_cols, sizeof(double2) * opts->warm_cols, g->n,
-                             cudaMemcpyDeviceToDevice, g->stream));
-    CKS(S.orth(B[ib[0]]));
-    CKS(apply_op<double>(g, B[ib[0]], nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
-    CKS(S.rr(B[ib[0]], B[ib[3]]));
     std::vector<double> th, rs;
     int flags = 0;
-    CKS(S.fetch(th, rs, flags));
-
     khp_stats st{};
-    st.lambda_upper = lam_up;
-    // phases: FP32 filter (mixed only) -> FP64 wide-window clean-up sweeps
-    // (mixed only) -> FP64 filter
     enum { P_FP32, P_CLEAN, P_FP64 };
-    int phase = mixed ? P_FP32 : P_FP64;
-    const int clean_sweeps = mixed ? (opts->refine_sweeps < 0 ? 2 : opts->refine_sweeps) : 0;
-    int clean_done = 0, stall = 0;
-    double best = 1e300;
-    const double floor32 = 3e-8 * lam_up;    // residual floor of FP32 blocks
-    bool converged = false, timed32 = false, timed64 = false;
-    // KHP_TRACE=1 in the environment prints one line per outer iteration
-    const char* tr = std::getenv("KHP_TRACE");
-    const bool trace = tr && tr[0] == '1';
+    int phase = P_FP64, clean_sweeps = 0, clean_done = 0, stall = 0;
+    double best = 1e300, floor32 = 0;
+    bool converged = false, finished = false, timing = true, trace = false;
+    bool timed32 = false, timed64 = false, recover = false;
     int it = 0;
-    for (; it < max_iter; ++it) {
+    // decisions for the next issue()
+    int nlock = 0, na = 0, deg = 0;
+    double a = 0, low = 0;
+    std::chrono::steady_clock::time_point t0;
+
+    static khp_status validate(khp_grid* g, const khp_solver_opts* opts) {
+        if (!g || !opts) return fail(KHP_ERR_INVALID_ARG, "handle or opts is NULL");
+        if (!g->fields_set) return fail(KHP_ERR_STATE, "fields not set");
+        const int n = opts->n_states, m = opts->block_m;
+        if (m < 2 || m > KHP_MAX_M || (m & 1)) return fail(KHP_ERR_INVALID_ARG, "block_m must be even, 2..64");
+        if (n < 1 || n >= m) return fail(KHP_ERR_INVALID_ARG, "need 1 <= n_states < block_m");
+        if ((long long)m > g->n) return fail(KHP_ERR_INVALID_ARG, "block_m exceeds the number of unknowns");
+        if (opts->degree < 1) return fail(KHP_ERR_INVALID_ARG, "degree must be >= 1");
+        if (opts->precision != 0 && opts->precision != 1)
+            return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
+        if (!(opts->tol_ev > 0.0)) return fail(KHP_ERR_INVALID_ARG, "tol_ev must be > 0");
+        if (opts->warm_start_dev && (opts->warm_cols < 1 || opts->warm_cols > m))
+            return fail(KHP_ERR_INVALID_ARG, "warm_cols must be in 1..block_m");
+        return KHP_OK;
+    }
+
+    khp_status begin(khp_grid* grid, const khp_solver_opts* opts) {
+        t0 = std::chrono::steady_clock::now();
+        g = grid;
+        o = *opts;
+        n = o.n_states;
+        m = o.block_m;
+        mixed = o.precision == 1;
+        CKS(ensure_ws(g, m, mixed));
+        S.g = g; S.m = m; S.nblk = dense_blocks(g->n);
+        S.G = g->small; S.Q = g->small + 2 * m * m;
+        S.theta = g->dvec; S.res = g->dvec + m;
+        max_iter = o.max_iter > 0 ? o.max_iter : 1000;
+        tol = o.tol_ev;
+        g->launches = 0;
+        if (!g->bound_valid) {
+            CKS(lanczos_bound(g, std::min<long long>(40, g->n), o.seed, &g->lambda_lanczos, &g->lambda_low));
+            g->bound_valid = true;
+        }
+        lam_up = g->lambda_lanczos;
+        st = khp_stats{};
+        st.lambda_upper = lam_up;
+        phase = mixed ? P_FP32 : P_FP64;
+        clean_sweeps = mixed ? (o.refine_sweeps < 0 ? 2 : o.refine_sweeps) : 0;
+        floor32 = 3e-8 * lam_up;    // residual floor of FP32 blocks
+        // KHP_TRACE=1 in the environment prints one line per outer iteration
+        const char* tr = std::getenv("KHP_TRACE");
+        trace = tr && tr[0] == '1';
+        double2** B = g->blk64;
+        CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
+        CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, o.seed, g->mask, g->stream));
+        g->launches += 1;
+        if (o.warm_start_dev)
+            CK(cudaMemcpy2DAsync(B[ib[0]], sizeof(double2) * m, o.warm_start_dev, sizeof(double2) * o.warm_cols,
+                                 sizeof(double2) * o.warm_cols, g->n, cudaMemcpyDeviceToDevice, g->stream));
+        CKS(S.orth(B[ib[0]]));
+        CKS(apply_op<double>(g, B[ib[0]], nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
+        CKS(S.rr(B[ib[0]], B[ib[3]]));
+        CKS(S.copy_out());
+        return KHP_OK;
+    }
+
+    // after the stream has been synchronised
+    khp_status absorb() {
+        S.read_out(th, rs, flags);
+        if (timed32 || timed64) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+            if (timed32) st.ms_filter_fp32 += ms;
+            else st.ms_filter_fp64 += ms;
+        }
+        if (timed32) st.pv_fp32 += (double)g->np * na * deg;
+        if (timed64) st.pv_fp64 += (double)g->np * na * deg;
+        timed32 = timed64 = false;
+        if (trace && it > 0) {
+            double rm = 0;
+            for (int i = 0; i < n; ++i) rm = std::max(rm, rs[i]);
+            std::fprintf(stderr, "khp it %d phase %d nlock %d deg %d a %.6e low %.6e rmax %.3e\n", it - 1,
+                         phase, nlock, deg, a, low, rm);
+        }
+        return KHP_OK;
+    }
+
+    // host decisions; sets finished when the solve is over
+    khp_status decide() {
+        recover = false;
         if (flags & 4) return fail(KHP_ERR_BREAKDOWN, "non-finite Ritz values");
         double rmax = 0;
         for (int i = 0; i < n; ++i) rmax = std::max(rmax, std::isnan(rs[i]) ? HUGE_VAL : rs[i]);
         if (rmax == HUGE_VAL) return fail(KHP_ERR_BREAKDOWN, "non-finite residuals");
-        if (rmax <= tol) { converged = true; break; }
+        if (rmax <= tol) { converged = finished = true; return KHP_OK; }
+        if (it >= max_iter) { finished = true; return KHP_OK; }
         if (phase == P_FP32) {
             if (rmax < 0.7 * best) { best = rmax; stall = 0; }
             else ++stall;
             if (rmax <= std::max(tol, floor32) || stall >= 4) {
-                if (opts->refine_sweeps == 0) break;
+                if (o.refine_sweeps == 0) { finished = true; return KHP_OK; }
                 phase = P_CLEAN;
             }
         }
         if (phase == P_CLEAN && clean_done >= clean_sweeps) {
-            if (opts->refine_sweeps >= 0) break;
+            if (o.refine_sweeps >= 0) { finished = true; return KHP_OK; }
             phase = P_FP64;
         }
         if (flags & 2) {
-            // Cholesky breakdown: re-orthonormalise the current block and redo RR
-            CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
-            CKS(S.orth(B[ib[0]]));
-            CKS(S.orth(B[ib[0]]));
-            CKS(apply_op<double>(g, B[ib[0]], nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
-            CKS(S.rr(B[ib[0]], B[ib[3]]));
-            CKS(S.fetch(th, rs, flags));
-            if (flags & 2) return fail(KHP_ERR_BREAKDOWN, "Gram matrix not positive definite");
-            continue;
+            recover = true;   // Cholesky breakdown: re-orthonormalise and redo RR
+            return KHP_OK;
         }
         st.shifted_cholesky += (flags & 1) ? 1 : 0;
-        CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
 
         // soft locking: the leading converged Ritz vectors are not filtered
         // (they stay in the Rayleigh-Ritz block with their H x)
-        int nlock = 0;
+        nlock = 0;
         while (nlock < n && rs[nlock] <= tol) ++nlock;
         nlock &= ~1;
-        const int na = m - nlock;
+        na = m - nlock;
 
         // filter interval [a, b] and scaling point low; the clean-up sweeps
-        // damp everything above a point just inside the unwanted spectrum;
-        // the degree is limited so that the filtered block stays well
-        // conditioned (amplification <= 1e4)
-        double a = th[m - 1];
-        int deg = opts->degree;
+        // damp everything above a point just inside the unwanted spectrum
+        a = th[m - 1];
+        deg = o.degree;
         if (phase == P_CLEAN) {
             a = a + 0.005 * (lam_up - a);
             deg *= 2;
@@ -727,24 +770,36 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
         // amplification at the bottom of the spectrum stays <= 1e4 (filtered
         // block well conditioned, no FP32 overflow)
         const double lo_est = std::min(th[0], g->lambda_low);
-        const double low = (lo_est < a) ? lo_est : a - 1e-3 * (lam_up - a);
-        {
-            const double e = 0.5 * (lam_up - a), c = 0.5 * (lam_up + a);
-            const double xl = std::fabs((low - c) / e);
-            if (xl > 1.0) {
-                const int dmax = (int)std::floor(std::acosh(1e4) / std::acosh(xl));
-                deg = std::max(1, std::min(deg, dmax));
-            }
+        low = (lo_est < a) ? lo_est : a - 1e-3 * (lam_up - a);
+        const double e = 0.5 * (lam_up - a), c = 0.5 * (lam_up + a);
+        const double xl = std::fabs((low - c) / e);
+        if (xl > 1.0) {
+            const int dmax = (int)std::floor(std::acosh(1e4) / std::acosh(xl));
+            deg = std::max(1, std::min(deg, dmax));
         }
+        return KHP_OK;
+    }
 
+    // enqueue one outer iteration (no host synchronisation)
+    khp_status issue() {
+        double2** B = g->blk64;
+        CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+        if (recover) {
+            CKS(S.orth(B[ib[0]]));
+            CKS(S.orth(B[ib[0]]));
+            CKS(apply_op<double>(g, B[ib[0]], nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
+            CKS(S.rr(B[ib[0]], B[ib[3]]));
+            CKS(S.copy_out());
+            return KHP_OK;
+        }
         double2* Y = nullptr;
         if (phase == P_FP32) {
             float2* fb[3] = {g->blk32[0], g->blk32[1], g->blk32[2]};
             CK(launch_convert_d2f(B[ib[0]], fb[0], g->n, m, nlock, na, g->stream));
             int oi = 0;
-            CK(cudaEventRecord(g->ev0, g->stream));
+            if (timing) CK(cudaEventRecord(g->ev0, g->stream));
             CKS(S.filter<float>(fb, oi, deg, a, lam_up, low, nlock, na));
-            CK(cudaEventRecord(g->ev1, g->stream));
+            if (timing) CK(cudaEventRecord(g->ev1, g->stream));
             timed32 = true;
             st.launches_fp32 += deg;
             // H Y in FP32 into a free FP32 buffer, both back to FP64
@@ -758,9 +813,9 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
         } else {
             double2* fb[3] = {B[ib[0]], B[ib[1]], B[ib[2]]};
             int oi = 0;
-            CK(cudaEventRecord(g->ev0, g->stream));
+            if (timing) CK(cudaEventRecord(g->ev0, g->stream));
             CKS(S.filter<double>(fb, oi, deg, a, lam_up, low, nlock, na));
-            CK(cudaEventRecord(g->ev1, g->stream));
+            if (timing) CK(cudaEventRecord(g->ev1, g->stream));
             timed64 = true;
             st.launches_fp64 += deg;
             if (oi != 0 && nlock > 0)
@@ -778,47 +833,250 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
         }
         st.filter_applies += (long long)(deg + 1) * na / m;
         CKS(S.rr(Y, B[ib[3]]));
-        CKS(S.fetch(th, rs, flags));
-        if (trace) {
-            double rm = 0;
-            for (int i = 0; i < n; ++i) rm = std::max(rm, rs[i]);
-            std::fprintf(stderr, "khp it %d phase %d nlock %d deg %d a %.6e low %.6e rmax %.3e\n", it, phase,
-                         nlock, deg, a, low, rm);
-        }
-        if (timed32 || timed64) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
-            if (timed32) st.ms_filter_fp32 += ms;
-            else st.ms_filter_fp64 += ms;
-            // point-vectors actually filtered, for per-launch rates
-            if (timed32) st.pv_fp32 += (double)g->np * na * deg;
-            else st.pv_fp64 += (double)g->np * na * deg;
-            timed32 = timed64 = false;
-        }
+        CKS(S.copy_out());
+        if (!timing) timed32 = timed64 = false;
+        ++it;
+        return KHP_OK;
     }
-    // final orthonormalisation of the Ritz block
-    CKS(S.orth(B[ib[0]]));
-    CK(cudaMemcpy2DAsync(evecs_dev, sizeof(double2) * n, B[ib[0]], sizeof(double2) * m, sizeof(double2) * n,
-                         g->n, cudaMemcpyDeviceToDevice, g->stream));
+
+    khp_status end(double* evals_host, void* evecs_dev, double* resid_host, khp_stats* stats) {
+        double2** B = g->blk64;
+        // final orthonormalisation of the Ritz block
+        CKS(S.orth(B[ib[0]]));
+        CK(cudaMemcpy2DAsync(evecs_dev, sizeof(double2) * n, B[ib[0]], sizeof(double2) * m, sizeof(double2) * n,
+                             g->n, cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        for (int i = 0; i < n; ++i) evals_host[i] = th[i];
+        double rmax = 0;
+        int conv = 0;
+        for (int i = 0; i < n; ++i) {
+            rmax = std::max(rmax, rs[i]);
+            conv += rs[i] <= tol;
+            if (resid_host) resid_host[i] = rs[i];
+        }
+        st.iterations = it;
+        st.block_m = m;
+        st.converged = conv;
+        st.kernel_launches = g->launches;
+        st.point_vectors = (double)g->np * m;
+        op_counts(g, m, &st.flops_per_pv, &st.bytes_per_pv_fp64, &st.bytes_per_pv_fp32);
+        st.max_residual = rmax;
+        st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (stats) *stats = st;
+        if (!converged && !(mixed && o.refine_sweeps >= 0 && it < max_iter))
+            return fail(KHP_ERR_NOT_CONVERGED, "max_iter reached before all residuals <= tol_ev");
+        return KHP_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, double* evals_host,
+                                     void* evecs_dev, double* resid_host, khp_stats* stats) {
+    g_err.clear();
+    CKS(Solve::validate(g, opts));
+    if (!evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "evals or evecs is NULL");
+    Solve s;
+    CKS(s.begin(g, opts));
     CK(cudaStreamSynchronize(g->stream));
-    for (int i = 0; i < n; ++i) evals_host[i] = th[i];
-    double rmax = 0;
-    int conv = 0;
-    for (int i = 0; i < n; ++i) {
-        rmax = std::max(rmax, rs[i]);
-        conv += rs[i] <= tol;
-        if (resid_host) resid_host[i] = rs[i];
+    CKS(s.absorb());
+    for (;;) {
+        CKS(s.decide());
+        if (s.finished) break;
+        CKS(s.issue());
+        CK(cudaStreamSynchronize(g->stream));
+        CKS(s.absorb());
     }
-    st.iterations = it;
-    st.converged = conv;
-    st.kernel_launches = g->launches;
-    st.point_vectors = (double)g->np * m;
-    op_counts(g, m, &st.flops_per_pv, &st.bytes_per_pv_fp64, &st.bytes_per_pv_fp32);
-    st.max_residual = rmax;
-    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (stats) *stats = st;
-    if (!converged && !(mixed && opts->refine_sweeps >= 0 && it < max_iter))
-        return fail(KHP_ERR_NOT_CONVERGED, "max_iter reached before all residuals <= tol_ev");
+    return s.end(evals_host, evecs_dev, resid_host, stats);
+}
+
+
+// ------------------------------------------------------------- batched
+namespace {
+
+// Streams of a batch: every handle gets its own non-blocking stream for the
+// call (ordered after the handle's own stream on entry and before it on
+// exit), so the problems' kernels can overlap and the rounds can be captured.
+struct BatchStreams {
+    std::vector<khp_grid*> gs;
+    std::vector<cudaStream_t> orig, own;
+    std::vector<cudaEvent_t> ev;
+    cudaStream_t master = nullptr;
+    ~BatchStreams() {
+        for (size_t i = 0; i < gs.size(); ++i) {
+            if (own[i]) {
+                cudaEventRecord(ev[i], own[i]);
+                cudaStreamWaitEvent(orig[i], ev[i], 0);
+                gs[i]->stream = orig[i];
+                cudaStreamDestroy(own[i]);
+            }
+            if (ev[i]) cudaEventDestroy(ev[i]);
+        }
+        if (master) cudaStreamDestroy(master);
+    }
+};
+
+}  // namespace
+
+extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, const khp_solver_opts* opts,
+                                             double* evals_host, void* const* evecs_dev, double* resid_host,
+                                             khp_stats* stats, int flags) {
+    g_err.clear();
+    if (!hs || !opts || !evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
+    if (count < 1) return fail(KHP_ERR_INVALID_ARG, "count must be >= 1");
+    if (opts->warm_start_dev) return fail(KHP_ERR_INVALID_ARG, "warm starts are per problem: not in batched mode");
+    khp_solver_opts o = *opts;
+    const int n = o.n_states;
+    int dev0 = -1;
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i] || !evecs_dev[i]) return fail(KHP_ERR_INVALID_ARG, "NULL handle or evecs");
+        if (i == 0) dev0 = hs[i]->device;
+        if (hs[i]->device != dev0) return fail(KHP_ERR_INVALID_ARG, "all handles must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(KHP_ERR_INVALID_ARG, "a handle appears twice");
+        if (!hs[i]->fields_set) return fail(KHP_ERR_STATE, "fields not set");
+    }
+    if ((flags & KHP_BATCH_AUTOTUNE) == 0) CKS(Solve::validate(hs[0], &o));
+    const bool graph = (flags & KHP_BATCH_GRAPH) != 0;
+
+    BatchStreams bs;
+    bs.gs.assign(hs, hs + count);
+    bs.orig.resize(count);
+    bs.own.assign(count, nullptr);
+    bs.ev.assign(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+        khp_grid* g = hs[i];
+        bs.orig[i] = g->stream;
+        CK(cudaEventCreateWithFlags(&bs.ev[i], cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&bs.own[i], cudaStreamNonBlocking));
+        CK(cudaEventRecord(bs.ev[i], g->stream));
+        CK(cudaStreamWaitEvent(bs.own[i], bs.ev[i], 0));
+        g->stream = bs.own[i];
+    }
+    CK(cudaStreamCreateWithFlags(&bs.master, cudaStreamNonBlocking));
+
+    // autotuner: block width chosen by timed trial solves of the smallest
+    // problem (its best trial is kept as its answer)
+    int tuned_from = -1;
+    double tune_ms = 0.0;
+    if (flags & KHP_BATCH_AUTOTUNE) {
+        int small = 0;
+        for (int i = 1; i < count; ++i)
+            if (hs[i]->n < hs[small]->n) small = i;
+        double best = 1e300;
+        int best_m = 0;
+        for (int cand = 0; cand < 3; ++cand) {
+            khp_solver_opts t = o;
+            t.block_m = std::min(KHP_MAX_M, ((n + 4 * (cand + 1)) + 1) & ~1);
+            if (t.block_m <= n) continue;
+            CKS(Solve::validate(hs[small], &t));
+            const auto ta = std::chrono::steady_clock::now();
+            khp_stats ts{};
+            khp_status r = khp_eigensolve(hs[small], &t, evals_host + (size_t)small * n, evecs_dev[small],
+                                          resid_host ? resid_host + (size_t)small * n : nullptr, &ts);
+            if (r != KHP_OK && r != KHP_ERR_NOT_CONVERGED) return r;
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
+            tune_ms += ms;
+            if (r == KHP_OK && ms < best) {
+                best = ms;
+                best_m = t.block_m;
+                if (stats) stats[small] = ts;
+            }
+        }
+        if (best_m == 0) return fail(KHP_ERR_NOT_CONVERGED, "autotuner: no candidate block width converged");
+        o.block_m = best_m;
+        tuned_from = small;
+        // the tuned problem is re-solved with the chosen width so that every
+        // answer comes from the same configuration
+    }
+    for (int i = 0; i < count; ++i) CKS(Solve::validate(hs[i], &o));
+
+    std::vector<Solve> S(count);
+    for (int i = 0; i < count; ++i) {
+        S[i].timing = !graph;
+        CKS(S[i].begin(hs[i], &o));
+    }
+    for (int i = 0; i < count; ++i) {
+        CK(cudaStreamSynchronize(hs[i]->stream));
+        CKS(S[i].absorb());
+    }
+    std::vector<cudaEvent_t> join(count, nullptr);
+    cudaEvent_t fork = nullptr;
+    struct EvGuard {
+        std::vector<cudaEvent_t>* j; cudaEvent_t* f;
+        ~EvGuard() { for (auto e : *j) if (e) cudaEventDestroy(e); if (*f) cudaEventDestroy(*f); }
+    } evg{&join, &fork};
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int i = 0; i < count; ++i) CK(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+    cudaGraphExec_t exec = nullptr;
+    struct ExecGuard { cudaGraphExec_t* e; ~ExecGuard() { if (*e) cudaGraphExecDestroy(*e); } } xg{&exec};
+    int rounds = 0, graphs_built = 0;
+    for (;;) {
+        std::vector<int> act;
+        for (int i = 0; i < count; ++i) {
+            if (S[i].finished) continue;
+            CKS(S[i].decide());
+            if (!S[i].finished) act.push_back(i);
+        }
+        if (act.empty()) break;
+        if (graph) {
+            // one CUDA graph per round: fork every active problem's iteration
+            // from the master stream onto its own stream and join back
+            CK(cudaStreamBeginCapture(bs.master, cudaStreamCaptureModeThreadLocal));
+            khp_status cs = KHP_OK;
+            cudaError_t ce = cudaEventRecord(fork, bs.master);
+            for (int i : act) {
+                if (ce != cudaSuccess || cs != KHP_OK) break;
+                ce = cudaStreamWaitEvent(hs[i]->stream, fork, 0);
+                if (ce == cudaSuccess) cs = S[i].issue();
+                if (ce == cudaSuccess && cs == KHP_OK) ce = cudaEventRecord(join[i], hs[i]->stream);
+                if (ce == cudaSuccess && cs == KHP_OK) ce = cudaStreamWaitEvent(bs.master, join[i], 0);
+            }
+            cudaGraph_t gr = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(bs.master, &gr);
+            if (cs != KHP_OK) { if (gr) cudaGraphDestroy(gr); return cs; }
+            if (ce != cudaSuccess || ee != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                return fail(KHP_ERR_CUDA, std::string("graph capture: ") +
+                                              cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+            }
+            bool updated = false;
+            if (exec) {
+                cudaGraphExecUpdateResultInfo info;
+                updated = cudaGraphExecUpdate(exec, gr, &info) == cudaSuccess;
+                if (!updated) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(exec);
+                    exec = nullptr;
+                }
+            }
+            if (!updated) {
+                const cudaError_t ie = cudaGraphInstantiate(&exec, gr, 0);
+                if (ie != cudaSuccess) { cudaGraphDestroy(gr); exec = nullptr; CK(ie); }
+                graphs_built++;
+            }
+            cudaGraphDestroy(gr);
+            CK(cudaGraphLaunch(exec, bs.master));
+            CK(cudaStreamSynchronize(bs.master));
+        } else {
+            for (int i : act) CKS(S[i].issue());
+            for (int i : act) CK(cudaStreamSynchronize(hs[i]->stream));
+        }
+        for (int i : act) CKS(S[i].absorb());
+        rounds++;
+    }
+    khp_status worst = KHP_OK;
+    for (int i = 0; i < count; ++i) {
+        khp_stats st{};
+        const khp_status r = S[i].end(evals_host + (size_t)i * n, evecs_dev[i],
+                                      resid_host ? resid_host + (size_t)i * n : nullptr, &st);
+        st.batch_rounds = rounds;
+        st.batch_graphs = graphs_built;
+        st.autotune_ms = (i == tuned_from) ? tune_ms : 0.0;
+        if (stats) stats[i] = st;
+        if (r != KHP_OK && worst == KHP_OK) worst = r;
+    }
+    if (worst != KHP_OK) return fail(worst, "at least one problem did not converge");
     return KHP_OK;
 }
 

@@ -154,6 +154,30 @@ class KPGrid:
             pass
 
 
+def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precision=0, refine_sweeps=-1,
+                  tol=1e-9, seed=1, graph=True, autotune=False, allow_not_converged=False):
+    """Solve every grid's lowest states in one khp_eigensolve_batched call
+    (lock-step rounds, optionally one CUDA graph per round and an autotuned
+    block width).  Returns a list of SolveResult."""
+    lib = _lib.load()
+    count = len(grids)
+    opts = _lib.SolverOpts()
+    bm = block_m or max(n_states + 8, 16)
+    opts.n_states, opts.block_m, opts.degree, opts.max_iter = n_states, bm + bm % 2, degree, max_iter
+    opts.precision, opts.refine_sweeps, opts.tol_ev, opts.seed = precision, refine_sweeps, tol, seed
+    hs = (ctypes.c_void_p * count)(*[g.handle.value for g in grids])
+    outs = [torch.empty((g.N, n_states), dtype=torch.complex128, device=g.device) for g in grids]
+    ptrs = (ctypes.c_void_p * count)(*[o.data_ptr() for o in outs])
+    evals = np.zeros((count, n_states))
+    res = np.zeros((count, n_states))
+    st = (_lib.Stats * count)()
+    flags = (_lib.KHP_BATCH_GRAPH if graph else 0) | (_lib.KHP_BATCH_AUTOTUNE if autotune else 0)
+    status = lib.khp_eigensolve_batched(hs, count, ctypes.byref(opts), _lib.dptr(evals), ptrs,
+                                        _lib.dptr(res), st, flags)
+    _lib.check(status, allow=(4,) if allow_not_converged else ())
+    return [SolveResult(evals[i].copy(), outs[i], res[i].copy(), st[i].as_dict(), status) for i in range(count)]
+
+
 class KPEigs(torch.autograd.Function):
     """Lowest eigenvalues E(V, strain, alpha) with a Hellmann-Feynman backward.
 
