@@ -66,10 +66,17 @@ typedef struct {
  *  precision      0: plain FP64 throughout;
  *                 1: mixed: FP32 Chebyshev filter/stencil with FP64
  *                    Cholesky and Rayleigh-Ritz until the FP32 residual
- *                    floor, then FP64 refinement sweeps (FP64 filter + FP64
- *                    Rayleigh-Ritz)
- *  refine_sweeps  precision 1 only: number of FP64 sweeps; < 0 means sweep
- *                 until every residual is below tol_ev
+ *                    floor, then FP64 refinement sweeps (wide-window FP64
+ *                    clean-up sweeps, then FP64 filter + Rayleigh-Ritz);
+ *                 2: defect-corrected FP32: the filtered block is written as
+ *                    Y = X p(Theta) + Z with p(Theta) the FP64 scalar
+ *                    recurrence at the Ritz values and Z driven by the FP64
+ *                    residual H X - X Theta; every filter apply runs in FP32
+ *                    on Z, H Y and Rayleigh-Ritz in FP64.  Reaches the
+ *                    plain-FP64 accuracy (tested to 1e-10 eV).
+ *  refine_sweeps  precision 1 only: number of FP64 clean-up sweeps; < 0 means
+ *                 one clean-up sweep, then FP64 sweeps until every residual is
+ *                 below tol_ev
  *  tol_ev         stop when ||H x_i - theta_i x_i|| <= tol_ev for i < n_states
  *  seed           seed of the counter-based random start vectors
  *  warm_start_dev optional complex128 [N][warm_cols] start vectors (row-major);

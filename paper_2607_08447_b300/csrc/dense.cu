@@ -706,3 +706,88 @@ cudaError_t lanczos_tridiag(const double* alpha, const double* beta, int k, doub
 }
 
 }  // namespace khp
+
+namespace khp {
+
+// ------------------------------------------- defect-corrected FP32 filter
+// For Ritz pairs (theta_c, x_c) with residual r_c = H x_c - theta_c x_c, the
+// filtered block is Y_k = X diag(D_k) + Z_k, D_k the scalar recurrence at the
+// Ritz values and Z_{k+1} = alpha_k (H - c) Z_k + gamma_k Z_{k-1} + alpha_k R D_k.
+// These kernels form R (and Z_1 = alpha_0 R) in FP32 from the FP64 pair, and
+// recombine Y = X D + Z in FP64 (W = H Y then comes from one FP64 apply:
+// forming H Z in FP32 would cap the accuracy near 1e-9 eV).
+struct DcResidualArgs {
+    const double2* X;
+    const double2* HX;
+    float2* R;
+    float2* Z1;
+    long long rows;
+    int ld, col0, ncol;
+    double theta[64];
+    double alpha0;
+};
+
+__global__ void dc_residual_kernel(const DcResidualArgs a) {
+    const long long n = a.rows * a.ncol;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / a.ncol;
+        const int c = a.col0 + (int)(i - r * a.ncol);
+        const long long k = r * a.ld + c;
+        const double2 x = a.X[k], hx = a.HX[k];
+        const double th = a.theta[c];
+        const double rx = hx.x - th * x.x, ry = hx.y - th * x.y;
+        a.R[k] = make_float2((float)rx, (float)ry);
+        a.Z1[k] = make_float2((float)(a.alpha0 * rx), (float)(a.alpha0 * ry));
+    }
+}
+
+struct DcCombineArgs {
+    const double2* X;
+    const double2* HX;
+    const float2* Z;
+    double2* Y;
+    double2* W;
+    long long rows;
+    int ld, zcol0;   // columns >= zcol0 carry Z; W is written for columns < zcol0 only
+    double D[64];
+};
+
+__global__ void dc_combine_kernel(const DcCombineArgs a) {
+    const long long n = a.rows * a.ld;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % a.ld);
+        const double2 x = a.X[i];
+        if (c >= a.zcol0) {
+            const double d = a.D[c];
+            const float2 z = a.Z[i];
+            a.Y[i] = make_double2(fma(d, x.x, (double)z.x), fma(d, x.y, (double)z.y));
+        } else {
+            a.Y[i] = x;          // locked column: unchanged, with its H x
+            a.W[i] = a.HX[i];
+        }
+    }
+}
+
+cudaError_t launch_dc_residual(const double2* X, const double2* HX, float2* R, float2* Z1, long long rows,
+                               int ld, int col0, int ncol, const double* theta, double alpha0,
+                               cudaStream_t st) {
+    DcResidualArgs a;
+    a.X = X; a.HX = HX; a.R = R; a.Z1 = Z1; a.rows = rows; a.ld = ld; a.col0 = col0; a.ncol = ncol;
+    for (int c = 0; c < 64; ++c) a.theta[c] = c < ld ? theta[c] : 0.0;
+    a.alpha0 = alpha0;
+    dc_residual_kernel<<<grid_for(rows * ncol), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dc_combine(const double2* X, const double2* HX, const float2* Z, double2* Y, double2* W,
+                              long long rows, int ld, int zcol0, const double* D, cudaStream_t st) {
+    DcCombineArgs a;
+    a.X = X; a.HX = HX; a.Z = Z; a.Y = Y; a.W = W; a.rows = rows; a.ld = ld; a.zcol0 = zcol0;
+    for (int c = 0; c < 64; ++c) a.D[c] = c < ld ? D[c] : 0.0;
+    dc_combine_kernel<<<grid_for(rows * ld), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace khp

@@ -275,6 +275,7 @@ khp_status apply_op(khp_grid* g, const cx_t<R>* x, const cx_t<R>* prev, cx_t<R>*
     }
     a.mask = g->mask;
     a.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
+    a.src = nullptr;
     fill_coeffs<R>(g, a.c, alpha);
     CK(launch_stencil<R>(a, g->stream));
     g->launches += 1;
@@ -283,7 +284,7 @@ khp_status apply_op(khp_grid* g, const cx_t<R>* x, const cx_t<R>* prev, cx_t<R>*
 
 void free_ws(khp_grid* g) {
     for (int i = 0; i < 4; ++i) { if (g->blk64[i]) cudaFree(g->blk64[i]); g->blk64[i] = nullptr; }
-    for (int i = 0; i < 3; ++i) { if (g->blk32[i]) cudaFree(g->blk32[i]); g->blk32[i] = nullptr; }
+    for (int i = 0; i < 4; ++i) { if (g->blk32[i]) cudaFree(g->blk32[i]); g->blk32[i] = nullptr; }
     if (g->partial) cudaFree(g->partial);
     g->partial = nullptr;
     g->ws_m = 0;
@@ -298,7 +299,7 @@ khp_status ensure_ws(khp_grid* g, int m, bool need32) {
     free_ws(g);
     for (int i = 0; i < 4; ++i) CK(cudaMalloc(&g->blk64[i], sizeof(double2) * g->n * mm));
     if (w32)
-        for (int i = 0; i < 3; ++i) CK(cudaMalloc(&g->blk32[i], sizeof(float2) * g->n * mm));
+        for (int i = 0; i < 4; ++i) CK(cudaMalloc(&g->blk32[i], sizeof(float2) * g->n * mm));
     const int nblk = dense_blocks(g->n);
     g->partial_elems = std::max(gram_partial_elems(KHP_MAX_M, nblk), (size_t)nblk * KHP_MAX_GATES);
     CK(cudaMalloc(&g->partial, sizeof(double2) * g->partial_elems));
@@ -633,10 +634,10 @@ struct Solve {
     std::vector<double> th, rs;
     int flags = 0;
     khp_stats st{};
-    enum { P_FP32, P_CLEAN, P_FP64 };
+    enum { P_FP32, P_CLEAN, P_FP64, P_DC };
     int phase = P_FP64, clean_sweeps = 0, clean_done = 0, stall = 0;
     double best = 1e300, floor32 = 0;
-    bool converged = false, finished = false, timing = true, trace = false;
+    bool converged = false, finished = false, timing = true, trace = false, dc = false;
     bool timed32 = false, timed64 = false, recover = false;
     int it = 0;
     // decisions for the next issue()
@@ -652,8 +653,8 @@ struct Solve {
         if (n < 1 || n >= m) return fail(KHP_ERR_INVALID_ARG, "need 1 <= n_states < block_m");
         if ((long long)m > g->n) return fail(KHP_ERR_INVALID_ARG, "block_m exceeds the number of unknowns");
         if (opts->degree < 1) return fail(KHP_ERR_INVALID_ARG, "degree must be >= 1");
-        if (opts->precision != 0 && opts->precision != 1)
-            return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
+        if (opts->precision < 0 || opts->precision > 2)
+            return fail(KHP_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
         if (!(opts->tol_ev > 0.0)) return fail(KHP_ERR_INVALID_ARG, "tol_ev must be > 0");
         if (opts->warm_start_dev && (opts->warm_cols < 1 || opts->warm_cols > m))
             return fail(KHP_ERR_INVALID_ARG, "warm_cols must be in 1..block_m");
@@ -667,7 +668,11 @@ struct Solve {
         n = o.n_states;
         m = o.block_m;
         mixed = o.precision == 1;
-        CKS(ensure_ws(g, m, mixed));
+        dc = o.precision == 2;
+        CKS(ensure_ws(g, m, mixed || dc));
+        if (std::getenv("KHP_TRACE") && std::getenv("KHP_TRACE")[0] == '1')
+            std::fprintf(stderr, "khp begin: workspace ready after %.1f ms\n",
+                         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
         S.g = g; S.m = m; S.nblk = dense_blocks(g->n);
         S.G = g->small; S.Q = g->small + 2 * m * m;
         S.theta = g->dvec; S.res = g->dvec + m;
@@ -681,9 +686,10 @@ struct Solve {
         lam_up = g->lambda_lanczos;
         st = khp_stats{};
         st.lambda_upper = lam_up;
-        phase = mixed ? P_FP32 : P_FP64;
-        clean_sweeps = mixed ? (o.refine_sweeps < 0 ? 2 : o.refine_sweeps) : 0;
-        floor32 = 3e-8 * lam_up;    // residual floor of FP32 blocks
+        phase = mixed ? P_FP32 : (dc ? P_DC : P_FP64);
+        clean_sweeps = mixed ? (o.refine_sweeps < 0 ? 1 : o.refine_sweeps) : 0;
+        // residual floor of FP32 blocks (measured on B300: ~2.5e-7 x lambda_max)
+        floor32 = 3e-7 * lam_up;
         // KHP_TRACE=1 in the environment prints one line per outer iteration
         const char* tr = std::getenv("KHP_TRACE");
         trace = tr && tr[0] == '1';
@@ -710,14 +716,15 @@ struct Solve {
             if (timed32) st.ms_filter_fp32 += ms;
             else st.ms_filter_fp64 += ms;
         }
-        if (timed32) st.pv_fp32 += (double)g->np * na * deg;
+        if (timed32) st.pv_fp32 += (double)g->np * na * (phase == P_DC ? deg - 1 : deg);
         if (timed64) st.pv_fp64 += (double)g->np * na * deg;
         timed32 = timed64 = false;
         if (trace && it > 0) {
             double rm = 0;
             for (int i = 0; i < n; ++i) rm = std::max(rm, rs[i]);
-            std::fprintf(stderr, "khp it %d phase %d nlock %d deg %d a %.6e low %.6e rmax %.3e\n", it - 1,
-                         phase, nlock, deg, a, low, rm);
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            std::fprintf(stderr, "khp it %d phase %d nlock %d deg %d a %.6e low %.6e rmax %.3e t %.1f ms\n", it - 1,
+                         phase, nlock, deg, a, low, rm, ms);
         }
         return KHP_OK;
     }
@@ -732,9 +739,11 @@ struct Solve {
         if (rmax <= tol) { converged = finished = true; return KHP_OK; }
         if (it >= max_iter) { finished = true; return KHP_OK; }
         if (phase == P_FP32) {
+            // leave the FP32 phase at its floor, or when the residual stops
+            // falling (two iterations without a 30 % gain below 1e-3 eV)
             if (rmax < 0.7 * best) { best = rmax; stall = 0; }
-            else ++stall;
-            if (rmax <= std::max(tol, floor32) || stall >= 4) {
+            else if (rmax < 1e-3) ++stall;
+            if (rmax <= std::max(tol, floor32) || stall >= 2) {
                 if (o.refine_sweeps == 0) { finished = true; return KHP_OK; }
                 phase = P_CLEAN;
             }
@@ -763,6 +772,8 @@ struct Solve {
         if (phase == P_CLEAN) {
             a = a + 0.005 * (lam_up - a);
             deg *= 2;
+        } else if (phase == P_FP32) {
+            deg *= 2;   // cheap FP32 applies: fewer FP64 projections per apply
         }
         if (!(a < lam_up)) a = lam_up - 1e-3 * std::fabs(lam_up);
         // scaling point: the lower spectral estimate (or the smallest Ritz
@@ -793,7 +804,10 @@ struct Solve {
             return KHP_OK;
         }
         double2* Y = nullptr;
-        if (phase == P_FP32) {
+        if (phase == P_DC) {
+            CKS(issue_dc());
+            Y = B[ib[0]];
+        } else if (phase == P_FP32) {
             float2* fb[3] = {g->blk32[0], g->blk32[1], g->blk32[2]};
             CK(launch_convert_d2f(B[ib[0]], fb[0], g->n, m, nlock, na, g->stream));
             int oi = 0;
@@ -836,6 +850,67 @@ struct Solve {
         CKS(S.copy_out());
         if (!timing) timed32 = timed64 = false;
         ++it;
+        return KHP_OK;
+    }
+
+    // Defect-corrected FP32 filter: Y = X diag(D_d) + Z_d with the scalar
+    // Chebyshev recurrence D_k at the Ritz values (FP64, host) and the
+    // correction Z_k driven by the FP64 residual R = HX - X Theta (FP32 on
+    // the device).  The d - 1 filter applies are FP32; the FP32 rounding acts
+    // on Z, which shrinks with the residual.  W = H Y is one FP64 apply.
+    khp_status issue_dc() {
+        double2** B = g->blk64;
+        float2* R32 = g->blk32[3];
+        float2* zb[3] = {g->blk32[0], g->blk32[1], g->blk32[2]};
+        const double e = 0.5 * (lam_up - a), cm = 0.5 * (lam_up + a);
+        const double sigma1 = e / (low - cm);
+        const double tau = 2.0 / sigma1;
+        std::vector<double> Dprev(m, 1.0), Dcur(m, 1.0), Dnext(m, 1.0);
+        for (int c = nlock; c < m; ++c) Dcur[c] = (sigma1 / e) * (th[c] - cm);
+        CK(launch_dc_residual(B[ib[0]], B[ib[3]], R32, zb[0], g->n, m, nlock, na, th.data(), sigma1 / e,
+                              g->stream));
+        g->launches += 1;
+        if (timing) CK(cudaEventRecord(g->ev0, g->stream));
+        int iz = 0, ip = -1, in = 1;
+        double sigma = sigma1;
+        for (int k = 1; k < deg; ++k) {
+            const double sn = 1.0 / (tau - sigma);
+            const double al = 2.0 * sn / e, be = -2.0 * cm * sn / e, ga = -sigma * sn;
+            StencilArgs<float> sa;
+            sa.nx = g->nx; sa.ny = g->ny; sa.nz = g->nz;
+            sa.ld = m; sa.col0 = nlock; sa.ncol = na;
+            sa.alpha = (float)al; sa.beta = (float)be; sa.gamma = (float)ga;
+            sa.x = zb[iz]; sa.prev = ip >= 0 ? zb[ip] : nullptr; sa.y = zb[in];
+            sa.onsite = g->onsite32;
+            sa.phase = (const float2*)(g->has_phase ? g->phase32 : nullptr);
+            sa.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
+            sa.mask = g->mask;
+            sa.src = R32;
+            for (int c = 0; c < 64; ++c) sa.src_coef[c] = (c >= nlock && c < m) ? (float)(al * Dcur[c]) : 0.f;
+            fill_coeffs<float>(g, sa.c, al);
+            CK(launch_stencil<float>(sa, g->stream));
+            g->launches += 1;
+            for (int c = nlock; c < m; ++c) Dnext[c] = al * (th[c] - cm) * Dcur[c] + ga * Dprev[c];
+            std::swap(Dprev, Dcur);
+            std::swap(Dcur, Dnext);
+            const int free_ = (ip >= 0) ? ip : 3 - iz - in;
+            ip = iz; iz = in; in = free_;
+            sigma = sn;
+        }
+        if (timing) CK(cudaEventRecord(g->ev1, g->stream));
+        timed32 = true;
+        st.launches_fp32 += deg - 1;
+        // Y = X D + Z in FP64, then W = H Y (FP64) on the active columns
+        CK(launch_dc_combine(B[ib[0]], B[ib[3]], zb[iz], B[ib[1]], B[ib[2]], g->n, m, nlock, Dcur.data(),
+                             g->stream));
+        g->launches += 1;
+        CKS(apply_op<double>(g, B[ib[1]], nullptr, B[ib[2]], m, nlock, na, 1.0, 0.0, 0.0));
+        // roles: Y, W become the next X, HX after the Rayleigh-Ritz
+        const int x0 = ib[0], w0 = ib[3];
+        ib[0] = ib[1];
+        ib[3] = ib[2];
+        ib[1] = x0;
+        ib[2] = w0;
         return KHP_OK;
     }
 

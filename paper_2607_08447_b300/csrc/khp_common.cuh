@@ -90,6 +90,9 @@ struct StencilArgs {
     const cx_t<R>* phase;   // see PH_*; null when B = 0
     int phase_mode;
     const uint8_t* mask;    // [Np] or null
+    // optional source term: y += src_coef[col] * src (defect-corrected filter)
+    const cx_t<R>* src;     // same layout as y, or null
+    R src_coef[64];
     Coeffs<R> c;
 };
 
@@ -130,7 +133,7 @@ struct khp_grid {
     // workspace (grown on demand)
     int ws_m;
     double2* blk64[4];     // FP64 blocks [n][ws_m]
-    float2* blk32[3];      // FP32 blocks [n][ws_m]
+    float2* blk32[4];      // FP32 blocks [n][ws_m]
     int ws_has32;
     double2* partial;      // reduction partials
     size_t partial_elems;

@@ -56,6 +56,13 @@ cudaError_t lanczos_scale(double2* dst, const double2* src, const double* nrm, l
 cudaError_t lanczos_tridiag(const double* alpha, const double* beta, int k, double2* G, double2* S,
                             cudaStream_t st);
 
+// defect-corrected FP32 filter (dense.cu)
+cudaError_t launch_dc_residual(const double2* X, const double2* HX, float2* R, float2* Z1, long long rows,
+                               int ld, int col0, int ncol, const double* theta, double alpha0,
+                               cudaStream_t st);
+cudaError_t launch_dc_combine(const double2* X, const double2* HX, const float2* Z, double2* Y, double2* W,
+                              long long rows, int ld, int zcol0, const double* D, cudaStream_t st);
+
 // observables.cu
 cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,
                            const uint8_t* mask, double* rho, cudaStream_t st);

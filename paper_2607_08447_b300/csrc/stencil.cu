@@ -122,7 +122,7 @@ __host__ __device__ constexpr unsigned cubic_nz(int d) {
     return d < 3 ? 7u : (d < 5 ? 32u : (d < 7 ? 16u : 8u));
 }
 
-template <typename R, int VG, int PH, bool MASK, bool CUBIC>
+template <typename R, int VG, int PH, bool MASK, bool CUBIC, bool SRC = false>
 __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
     using C = cx_t<R>;
     const int G = a.ncol / VG;
@@ -285,8 +285,13 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
         }
     }
 
-    // y = acc + gamma prev
+    // y = acc + gamma prev (+ src_coef[col] src)
     const C* pp = a.prev ? a.prev + p * ps + col : nullptr;
+    R sc[VG];
+    if (SRC) {
+#pragma unroll
+        for (int v = 0; v < VG; ++v) sc[v] = a.src_coef[col + v];
+    }
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
         C out[VG];
@@ -301,6 +306,15 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
                 out[v].y = fma(a.gamma, wv[v].y, out[v].y);
             }
         }
+        if (SRC) {
+            C sv[VG];
+            load_vg<R, VG>(sv, a.src + p * ps + col + b * a.ld);
+#pragma unroll
+            for (int v = 0; v < VG; ++v) {
+                out[v].x = fma(sc[v], sv[v].x, out[v].x);
+                out[v].y = fma(sc[v], sv[v].y, out[v].y);
+            }
+        }
         store_vg<R, VG>(yp + b * a.ld, out);
     }
 }
@@ -309,6 +323,21 @@ template <typename R, int VG, int PH>
 static cudaError_t launch_ph(const StencilArgs<R>& a, unsigned blocks, cudaStream_t st) {
     bool cubic = true;
     for (int d = 0; d < 9; ++d) cubic = cubic && (a.c.hop_nz[d] & ~cubic_nz(d)) == 0;
+    if constexpr (sizeof(R) == 4) {
+        if (a.src) {
+            // defect-corrected FP32 filter steps
+            if (a.mask) {
+                if (cubic) stencil_kernel<R, VG, PH, true, true, true><<<blocks, 256, 0, st>>>(a);
+                else stencil_kernel<R, VG, PH, true, false, true><<<blocks, 256, 0, st>>>(a);
+            } else {
+                if (cubic) stencil_kernel<R, VG, PH, false, true, true><<<blocks, 256, 0, st>>>(a);
+                else stencil_kernel<R, VG, PH, false, false, true><<<blocks, 256, 0, st>>>(a);
+            }
+            return cudaGetLastError();
+        }
+    } else {
+        if (a.src) return cudaErrorNotSupported;
+    }
     if (a.mask) {
         if (cubic) stencil_kernel<R, VG, PH, true, true><<<blocks, 256, 0, st>>>(a);
         else stencil_kernel<R, VG, PH, true, false><<<blocks, 256, 0, st>>>(a);

@@ -63,12 +63,14 @@ def test_c2_residuals_through_oracle_csr(c2):
     assert bound <= 1e-6, bound
 
 
-def test_c2_mixed_precision_matches_plain(c2):
+@pytest.mark.parametrize("kw", [dict(degree=80, precision=1, refine_sweeps=-1),
+                                dict(degree=200, precision=2)])
+def test_c2_mixed_precision_matches_plain(c2, kw):
     p, g, r = c2
-    rm = g.eigensolve(**dict(SOLVE, degree=80, precision=1, refine_sweeps=-1))
-    assert rm.stats["iterations_fp32"] >= 1
+    rm = g.eigensolve(**dict(SOLVE, **kw))
+    assert rm.stats["launches_fp32"] >= 1
     assert np.abs(rm.evals - r.evals).max() <= 1e-10
     U, Vm = r.evecs, rm.evecs
     R = Vm - U @ (U.conj().T @ Vm)
     sin_max = torch.linalg.matrix_norm(R, ord=2).item()
-    assert sin_max <= 1e-6, sin_max
+    assert sin_max <= 1e-7, sin_max

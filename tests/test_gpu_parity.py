@@ -238,3 +238,14 @@ def test_spectral_upper_bound_is_an_upper_bound(khp, case):
     ub = r.stats["lambda_upper"]
     assert ub >= wmax
     assert ub <= 1.6 * wmax
+
+
+@pytest.mark.parametrize("which", ["c1", 1, 2, 3])
+def test_eigensolve_defect_corrected_fp32(khp, which):
+    """precision 2: every filter apply in FP32 (defect-corrected by the FP64
+    residual), FP64 projections; must reach the plain FP64 accuracy."""
+    p = inputs.config1() if which == "c1" else _problem(CASES[which], seed=9)
+    g = _grid(khp, p)
+    r = g.eigensolve(8, block_m=16, degree=20, precision=2, tol=1e-10, seed=4)
+    assert r.stats["launches_fp64"] == 0 and r.stats["launches_fp32"] > 0
+    _check_solution(p, r, 8, 1e-10, 1e-7)
