@@ -122,8 +122,8 @@ __host__ __device__ constexpr unsigned cubic_nz(int d) {
     return d < 3 ? 7u : (d < 5 ? 32u : (d < 7 ? 16u : 8u));
 }
 
-template <typename R, int VG, int PH, bool MASK, bool CUBIC, bool SRC = false>
-__global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
+template <typename R, int VG, int PH, bool MASK, bool CUBIC, bool SRC = false, int LD = 0, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R> a) {
     using C = cx_t<R>;
     const int G = a.ncol / VG;
     const long long np = (long long)a.nx * a.ny * a.nz;
@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
     const long long q = p / a.nx;
     const int iy = (int)(q % a.ny);
     const int iz = (int)(q / a.ny);
-    const long long ps = 6LL * a.ld;            // complex elements per point
+    const int ld = LD ? LD : a.ld;              // complex elements per row (compile-time when LD > 0)
+    const long long ps = 6LL * ld;              // complex elements per point
     const int col = a.col0 + g * VG;
     C* yp = a.y + p * ps + col;
 
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
             C z[VG];
 #pragma unroll
             for (int v = 0; v < VG; ++v) z[v] = mk<R>(R(0), R(0));
-            store_vg<R, VG>(yp + b * a.ld, z);
+            store_vg<R, VG>(yp + b * ld, z);
         }
         return;
     }
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
     {
         C xs[6][VG];
 #pragma unroll
-        for (int b = 0; b < 6; ++b) load_vg<R, VG>(xs[b], xp + b * a.ld);
+        for (int b = 0; b < 6; ++b) load_vg<R, VG>(xs[b], xp + b * ld);
         R o[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) o[k] = a.alpha * __ldg(a.onsite + p * 6 + k);
@@ -202,6 +203,8 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
             okm = okm && a.mask[p - off] != 0;
         }
         const bool ph = PH != PH_NONE && (a.c.pair_phase & (1u << d));
+        const C* xpp = xp + off * ps;
+        const C* xpm = xp - off * ps;
         C u[6][VG], w[6][VG];
         if (PH == PH_GEN && ph) {
             // general gauge: s = e1 x+ + e2 x- formed per needed component
@@ -214,12 +217,12 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
                 for (int sp = 0; sp < 2; ++sp) {
                     const int b = 3 * sp + o;
                     C xpv[VG], xmv[VG];
-                    if (okp) load_vg<R, VG>(xpv, xp + off * ps + b * a.ld);
+                    if (okp) load_vg<R, VG>(xpv, xpp + b * ld);
                     else {
 #pragma unroll
                         for (int v = 0; v < VG; ++v) xpv[v] = mk<R>(R(0), R(0));
                     }
-                    if (okm) load_vg<R, VG>(xmv, xp - off * ps + b * a.ld);
+                    if (okm) load_vg<R, VG>(xmv, xpm + b * ld);
                     else {
 #pragma unroll
                         for (int v = 0; v < VG; ++v) xmv[v] = mk<R>(R(0), R(0));
@@ -239,12 +242,12 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
                 for (int sp = 0; sp < 2; ++sp) {
                     const int b = 3 * sp + o;
                     C xpv[VG], xmv[VG];
-                    if (okp) load_vg<R, VG>(xpv, xp + off * ps + b * a.ld);
+                    if (okp) load_vg<R, VG>(xpv, xpp + b * ld);
                     else {
 #pragma unroll
                         for (int v = 0; v < VG; ++v) xpv[v] = mk<R>(R(0), R(0));
                     }
-                    if (okm) load_vg<R, VG>(xmv, xp - off * ps + b * a.ld);
+                    if (okm) load_vg<R, VG>(xmv, xpm + b * ld);
                     else {
 #pragma unroll
                         for (int v = 0; v < VG; ++v) xmv[v] = mk<R>(R(0), R(0));
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
         for (int v = 0; v < VG; ++v) out[v] = acc[b][v];
         if (pp) {
             C wv[VG];
-            load_vg<R, VG>(wv, pp + b * a.ld);
+            load_vg<R, VG>(wv, pp + b * ld);
 #pragma unroll
             for (int v = 0; v < VG; ++v) {
                 out[v].x = fma(a.gamma, wv[v].x, out[v].x);
@@ -308,14 +311,14 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<R> a) {
         }
         if (SRC) {
             C sv[VG];
-            load_vg<R, VG>(sv, a.src + p * ps + col + b * a.ld);
+            load_vg<R, VG>(sv, a.src + p * ps + col + b * ld);
 #pragma unroll
             for (int v = 0; v < VG; ++v) {
                 out[v].x = fma(sc[v], sv[v].x, out[v].x);
                 out[v].y = fma(sc[v], sv[v].y, out[v].y);
             }
         }
-        store_vg<R, VG>(yp + b * a.ld, out);
+        store_vg<R, VG>(yp + b * ld, out);
     }
 }
 
@@ -323,6 +326,26 @@ template <typename R, int VG, int PH>
 static cudaError_t launch_ph(const StencilArgs<R>& a, unsigned blocks, cudaStream_t st) {
     bool cubic = true;
     for (int d = 0; d < 9; ++d) cubic = cubic && (a.c.hop_nz[d] & ~cubic_nz(d)) == 0;
+    if constexpr (VG == 2) {
+        if (cubic && !a.mask) {
+            // hot path: row length known at compile time (immediate band offsets)
+#define KHP_LD_CASE(L)                                                                               \
+            if (a.ld == L) {                                                                         \
+                if constexpr (sizeof(R) == 4) {                                                      \
+                    if (a.src) stencil_kernel<R, VG, PH, false, true, true, L, 2><<<blocks, 256, 0, st>>>(a); \
+                    else stencil_kernel<R, VG, PH, false, true, false, L, 2><<<blocks, 256, 0, st>>>(a);      \
+                } else {                                                                             \
+                    if (a.src) return cudaErrorNotSupported;                                         \
+                    stencil_kernel<R, VG, PH, false, true, false, L, 1><<<blocks, 256, 0, st>>>(a);  \
+                }                                                                                    \
+                return cudaGetLastError();                                                           \
+            }
+            KHP_LD_CASE(16)
+            KHP_LD_CASE(24)
+            KHP_LD_CASE(32)
+#undef KHP_LD_CASE
+        }
+    }
     if constexpr (sizeof(R) == 4) {
         if (a.src) {
             // defect-corrected FP32 filter steps
