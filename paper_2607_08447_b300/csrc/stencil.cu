@@ -196,15 +196,20 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
         const unsigned need = need_of(nzd);
         const int dx = pair_dx(d), dy = pair_dy(d), dz = pair_dz(d);
         const long long off = (long long)dx + (long long)a.nx * ((long long)dy + (long long)a.ny * dz);
-        bool okp = inr(ix + dx, a.nx) && inr(iy + dy, a.ny) && inr(iz + dz, a.nz);
-        bool okm = inr(ix - dx, a.nx) && inr(iy - dy, a.ny) && inr(iz - dz, a.nz);
+        const bool inp = inr(ix + dx, a.nx) && inr(iy + dy, a.ny) && inr(iz + dz, a.nz);
+        const bool inm = inr(ix - dx, a.nx) && inr(iy - dy, a.ny) && inr(iz - dz, a.nz);
+        // neighbour addresses are clamped to this point's own row when the
+        // neighbour lies outside the grid, so that every address formed is
+        // inside the block even if a load is issued ahead of its predicate
+        const long long offp = inp ? off : 0, offm = inm ? off : 0;
+        bool okp = inp, okm = inm;
         if (MASK) {
-            okp = okp && a.mask[p + off] != 0;
-            okm = okm && a.mask[p - off] != 0;
+            okp = okp && a.mask[p + offp] != 0;
+            okm = okm && a.mask[p - offm] != 0;
         }
         const bool ph = PH != PH_NONE && (a.c.pair_phase & (1u << d));
-        const C* xpp = xp + off * ps;
-        const C* xpm = xp - off * ps;
+        const C* xpp = xp + offp * ps;
+        const C* xpm = xp - offm * ps;
         C u[6][VG], w[6][VG];
         if (PH == PH_GEN && ph) {
             // general gauge: s = e1 x+ + e2 x- formed per needed component
