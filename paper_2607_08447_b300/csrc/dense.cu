@@ -26,6 +26,16 @@ int dense_blocks(long long rows) {
 size_t gram_partial_elems(int m, int nblk) { return (size_t)nblk * 2 * m * m; }
 
 // ------------------------------------------------------------------ Gram
+// G = Y^H Y and S = Y^H W are Hermitian (S because W = H Y with H Hermitian),
+// so only their upper triangles are accumulated (packed row by row,
+// mt = m(m+1)/2 entries each); the reduction writes both triangles.
+__device__ __forceinline__ void packed_ij(int k, int m, int& i, int& j) {
+    int row = 0, len = m;
+    while (k >= len) { k -= len; ++row; --len; }
+    i = row;
+    j = row + k;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kThreads) gram_kernel(const double2* __restrict__ Y,
                                                        const double2* __restrict__ W, long long rows,
@@ -36,8 +46,8 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const double2* __restric
     double2* Ys = sm;
     double2* Ws = sm + TR * m;
     const int tid = threadIdx.x;
-    const int mm = m * m;
-    const int E = (W ? 2 : 1) * mm;
+    const int mt = m * (m + 1) / 2;
+    const int E = (W ? 2 : 1) * mt;
     const long long per = (rows + gridDim.x - 1) / gridDim.x;
     const long long r0 = (long long)blockIdx.x * per;
     const long long r1 = r0 + per < rows ? r0 + per : rows;
@@ -49,10 +59,10 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const double2* __restric
     for (int k = 0; k < K; ++k) {
         acc[k] = make_double2(0.0, 0.0);
         const int e = tid + k * kThreads;
-        const int rem = e % mm;
-        ia[k] = e < E ? rem / m : -1;
-        jb[k] = rem % m;
-        sw[k] = e >= mm;
+        ia[k] = -1;
+        jb[k] = 0;
+        sw[k] = e >= mt;
+        if (e < E) packed_ij(e % mt, m, ia[k], jb[k]);
     }
     for (long long rb = r0; rb < r1; rb += TR) {
         const int nr = (int)((r1 - rb) < TR ? (r1 - rb) : TR);
@@ -83,33 +93,46 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const double2* __restric
     }
 }
 
-__global__ void sum_partials_c(const double2* __restrict__ partial, int nblk, int E,
-                               double2* __restrict__ out) {
+// sums the packed partials in block order and writes the full Hermitian
+// matrices: out[0 .. m*m) = G, out[m*m .. 2 m*m) = S
+__global__ void sum_partials_herm(const double2* __restrict__ partial, int nblk, int m, int nmat,
+                                  double2* __restrict__ out) {
+    const int mt = m * (m + 1) / 2;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
+    if (e >= nmat * mt) return;
+    const int E = nmat * mt;
     double2 s = make_double2(0.0, 0.0);
     for (int b = 0; b < nblk; ++b) {
         const double2 v = partial[(size_t)b * E + e];
         s.x += v.x;
         s.y += v.y;
     }
-    out[e] = s;
+    const int which = e / mt;
+    int i, j;
+    packed_ij(e - which * mt, m, i, j);
+    double2* o = out + (size_t)which * m * m;
+    if (i == j) {
+        o[i * m + i] = make_double2(s.x, 0.0);
+    } else {
+        o[i * m + j] = s;
+        o[j * m + i] = make_double2(s.x, -s.y);
+    }
 }
 
 cudaError_t launch_gram(const double2* Y, const double2* W, long long rows, int ld, int col0, int m,
                         double2* partial, int nblk, double2* out, cudaStream_t st) {
-    const int E = (W ? 2 : 1) * m * m;
+    const int nmat = W ? 2 : 1;
+    const int E = nmat * m * (m + 1) / 2;
     const int K = (E + kThreads - 1) / kThreads;
     const size_t smem = 2ull * 16 * m * sizeof(double2);
     if (K <= 1) gram_kernel<1><<<nblk, kThreads, smem, st>>>(Y, W, rows, ld, col0, m, partial);
     else if (K <= 2) gram_kernel<2><<<nblk, kThreads, smem, st>>>(Y, W, rows, ld, col0, m, partial);
     else if (K <= 4) gram_kernel<4><<<nblk, kThreads, smem, st>>>(Y, W, rows, ld, col0, m, partial);
     else if (K <= 8) gram_kernel<8><<<nblk, kThreads, smem, st>>>(Y, W, rows, ld, col0, m, partial);
-    else if (K <= 16) gram_kernel<16><<<nblk, kThreads, smem, st>>>(Y, W, rows, ld, col0, m, partial);
-    else gram_kernel<32><<<nblk, kThreads, smem, st>>>(Y, W, rows, ld, col0, m, partial);
+    else gram_kernel<16><<<nblk, kThreads, smem, st>>>(Y, W, rows, ld, col0, m, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    sum_partials_c<<<(E + 255) / 256, 256, 0, st>>>(partial, nblk, E, out);
+    sum_partials_herm<<<(E + 255) / 256, 256, 0, st>>>(partial, nblk, m, nmat, out);
     return cudaGetLastError();
 }
 
