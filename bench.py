@@ -49,7 +49,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["plain", "mixed"], default=None,
+    ap.add_argument("--profile", choices=["plain", "mixed", "dc"], default=None,
                     help="one short C2 solve (6 outer iterations) for profiler captures; prints its stats")
     return ap.parse_args()
 
@@ -336,7 +336,10 @@ def run_profile(args):
     import paper_2607_08447_b300 as khp
     p = inputs.config2()
     g = khp.KPGrid.from_problem(p)
-    kw = dict(SOLVE_KW, max_iter=6, precision=1 if args.profile == "mixed" else 0, refine_sweeps=0)
+    prec = {"plain": 0, "mixed": 1, "dc": 2}[args.profile]
+    kw = dict(SOLVE_KW, max_iter=6, precision=prec, refine_sweeps=0)
+    if prec == 2:
+        kw["degree"] = MIXED_DEGREE
     r = g.eigensolve(**kw, allow_not_converged=True)
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "stats": r.stats}), flush=True)
