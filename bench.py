@@ -38,6 +38,11 @@ WORKLOAD = "c2: 160x48x48 grid h=0.5nm (2.21M unknowns), FP64, lowest 16 of bloc
 SOLVE_KW = dict(n_states=16, block_m=24, degree=120, precision=0, tol=1e-10, seed=1, max_iter=600)
 MIXED_DEGREE = 200   # defect-corrected FP32 filter (precision 2)
 CROP = (32, 12, 12)
+# DRAM bytes per point-vector of the FP64 fused stencil launch, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum = 2.524 GB + 0.830 GB over
+# 24 x 368640 point-vectors; profiles/stencil_fp64_c2.md).  Valid for the
+# kernel version profiled there; set to None when the kernel changes.
+NCU_TRAFFIC_FP64_PER_PV = (2.523636e9 + 0.8295552e9) / (24 * 368640)
 
 
 def _args():
@@ -257,7 +262,9 @@ def run_ours(args, rank, world, local_rank):
     achieved_tf = flops_launch / (t64 * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "stencil_kernel<double> (fused Chebyshev step)",
                 "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / fp64_peak, "traffic": None,
+                "frac": achieved_tf / fp64_peak,
+                "traffic": (NCU_TRAFFIC_FP64_PER_PV * pv_launch if NCU_TRAFFIC_FP64_PER_PV else None),
+                "traffic_note": "ncu DRAM bytes of a full-width launch scaled to this run's mean launch width",
                 "peak_source": "FP64 peak measured in this run: cuBLAS DGEMM 8192^3 (burst)",
                 "algorithmic_flops_per_launch": flops_launch, "ms_per_launch": t64,
                 "point_vectors_per_launch": pv_launch,
