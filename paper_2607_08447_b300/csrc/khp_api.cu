@@ -355,7 +355,7 @@ void op_counts(const khp_grid* g, int m, double* flops, double* b64, double* b32
 // Upper bound of the spectrum for the filter interval: k-step Lanczos from a
 // random vector, bound = largest Ritz value + |beta_k|, never above the
 // Gershgorin bound.  Uses the first N entries of the four workspace blocks.
-khp_status lanczos_bound(khp_grid* g, int k, unsigned long long seed, double* out, double* out_lo) {
+khp_status lanczos_issue(khp_grid* g, int k, unsigned long long seed) {
     double* partial = g->lz;
     double* alpha = g->lz + kLzPartials;
     double* beta = alpha + KHP_MAX_M;
@@ -388,14 +388,18 @@ khp_status lanczos_bound(khp_grid* g, int k, unsigned long long seed, double* ou
     CK(cudaMemcpyAsync(hp, th + k - 1, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaMemcpyAsync(hp + 1, beta + k, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaMemcpyAsync(hp + 2, th, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
+    return KHP_OK;
+}
+
+// after the stream is synchronised: bounds from the pinned copies
+void lanczos_finish(khp_grid* g, double* out, double* out_lo) {
+    const double* hp = g->host_pinned;
     const double b = hp[0] + std::fabs(hp[1]);
     *out = std::isfinite(b) ? std::min(b, g->onsite_absmax) : g->onsite_absmax;
     // lower estimate of the spectrum (smallest Ritz value), used to cap the
     // filter amplification and as the scaling point
     const double lo = hp[2];
     *out_lo = std::isfinite(lo) ? std::max(lo, -g->onsite_absmax) : -g->onsite_absmax;
-    return KHP_OK;
 }
 
 }  // namespace
@@ -638,7 +642,7 @@ struct Solve {
     int phase = P_FP64, clean_sweeps = 0, clean_done = 0, stall = 0;
     double best = 1e300, floor32 = 0;
     bool converged = false, finished = false, timing = true, trace = false, dc = false;
-    bool timed32 = false, timed64 = false, recover = false;
+    bool timed32 = false, timed64 = false, recover = false, need_bound = false;
     int it = 0;
     // decisions for the next issue()
     int nlock = 0, na = 0, deg = 0;
@@ -661,7 +665,9 @@ struct Solve {
         return KHP_OK;
     }
 
-    khp_status begin(khp_grid* grid, const khp_solver_opts* opts) {
+    // stage a: workspace and (when the fields changed) the Lanczos bound,
+    // issued on the handle's stream; the caller synchronises before begin_b
+    khp_status begin_a(khp_grid* grid, const khp_solver_opts* opts) {
         t0 = std::chrono::steady_clock::now();
         g = grid;
         o = *opts;
@@ -670,19 +676,24 @@ struct Solve {
         mixed = o.precision == 1;
         dc = o.precision == 2;
         CKS(ensure_ws(g, m, mixed || dc));
-        if (std::getenv("KHP_TRACE") && std::getenv("KHP_TRACE")[0] == '1')
-            std::fprintf(stderr, "khp begin: workspace ready after %.1f ms\n",
-                         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+        g->launches = 0;
+        need_bound = !g->bound_valid;
+        if (need_bound) CKS(lanczos_issue(g, (int)std::min<long long>(40, g->n), o.seed));
+        return KHP_OK;
+    }
+
+    // stage b: random / warm start, orthonormalisation and the first
+    // Rayleigh-Ritz, issued; the caller synchronises before absorb
+    khp_status begin_b() {
+        if (need_bound) {
+            lanczos_finish(g, &g->lambda_lanczos, &g->lambda_low);
+            g->bound_valid = true;
+        }
         S.g = g; S.m = m; S.nblk = dense_blocks(g->n);
         S.G = g->small; S.Q = g->small + 2 * m * m;
         S.theta = g->dvec; S.res = g->dvec + m;
         max_iter = o.max_iter > 0 ? o.max_iter : 1000;
         tol = o.tol_ev;
-        g->launches = 0;
-        if (!g->bound_valid) {
-            CKS(lanczos_bound(g, std::min<long long>(40, g->n), o.seed, &g->lambda_lanczos, &g->lambda_low));
-            g->bound_valid = true;
-        }
         lam_up = g->lambda_lanczos;
         st = khp_stats{};
         st.lambda_upper = lam_up;
@@ -952,7 +963,9 @@ extern "C" khp_status khp_eigensolve(khp_handle g, const khp_solver_opts* opts, 
     CKS(Solve::validate(g, opts));
     if (!evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "evals or evecs is NULL");
     Solve s;
-    CKS(s.begin(g, opts));
+    CKS(s.begin_a(g, opts));
+    CK(cudaStreamSynchronize(g->stream));
+    CKS(s.begin_b());
     CK(cudaStreamSynchronize(g->stream));
     CKS(s.absorb());
     for (;;) {
@@ -1067,10 +1080,13 @@ extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, co
     for (int i = 0; i < count; ++i) CKS(Solve::validate(hs[i], &o));
 
     std::vector<Solve> S(count);
+    // the set-up of all problems overlaps: Lanczos bounds, then first RR
     for (int i = 0; i < count; ++i) {
         S[i].timing = !graph;
-        CKS(S[i].begin(hs[i], &o));
+        CKS(S[i].begin_a(hs[i], &o));
     }
+    for (int i = 0; i < count; ++i) CK(cudaStreamSynchronize(hs[i]->stream));
+    for (int i = 0; i < count; ++i) CKS(S[i].begin_b());
     for (int i = 0; i < count; ++i) {
         CK(cudaStreamSynchronize(hs[i]->stream));
         CKS(S[i].absorb());
