@@ -80,7 +80,12 @@ typedef struct {
  *  tol_ev         stop when ||H x_i - theta_i x_i|| <= tol_ev for i < n_states
  *  seed           seed of the counter-based random start vectors
  *  warm_start_dev optional complex128 [N][warm_cols] start vectors (row-major);
- *                 remaining columns are random.  NULL for a cold start. */
+ *                 remaining columns are random.  NULL for a cold start.
+ *  projections    how the Rayleigh-Ritz contractions (Gram matrices and
+ *                 subspace rotation) run: 0 = on the tensor cores as exact
+ *                 split-digit BF16 products recombined in FP64 (FP64
+ *                 accurate; block_m <= 32, wider blocks use 1); 1 = FP64
+ *                 ALU.  Zero-initialised options select 0. */
 typedef struct {
     int n_states;
     int block_m;
@@ -92,6 +97,7 @@ typedef struct {
     uint64_t seed;
     const void* warm_start_dev;
     int warm_cols;
+    int projections;
 } khp_solver_opts;
 
 /* Per-solve statistics (optional output).  The filter timings come from
@@ -163,6 +169,24 @@ khp_status khp_set_potential_strain_field(khp_handle h, const double* V_dev,
  *  X and Y must not overlap.  m in 1..64 (m even for precision 1 fast path;
  *  odd m handled too). */
 khp_status khp_apply(khp_handle h, const void* X_dev, void* Y_dev, int m, int precision);
+
+/* The two dense contractions of the Rayleigh-Ritz step (Sec. II B), on the
+ * handle's grid length N, for a block that is not the solver's own.
+ *  khp_project: G = Y^H Y and (W_dev given) S = Y^H W, each m x m complex128
+ *    row-major in host memory; both are formed from their upper triangles as
+ *    Hermitian matrices (the solver's W is H Y).
+ *  khp_rotate: X = Y Q and (W_dev given) HX = W Q, Q m x m complex128
+ *    row-major in host memory; X may be Y and HX may be W (in place).
+ *  Y_dev, W_dev, X_dev, HX_dev: complex128 [N][m] row-major on the device.
+ *  method 0: tensor cores, exact split-digit BF16 products recombined in FP64
+ *    (m <= 32); 1: FP64 ALU.  Both synchronise the handle's stream; the
+ *    first call allocates the handle's reduction scratch.
+ * Errors: INVALID_ARG for NULL pointers, m outside 1..64, a bad method or
+ * method 0 with m > 32. */
+khp_status khp_project(khp_handle h, const void* Y_dev, const void* W_dev, int m, int method,
+                       double* G_host, double* S_host);
+khp_status khp_rotate(khp_handle h, const void* Y_dev, const void* W_dev, const double* Q_host,
+                      int m, int method, void* X_dev, void* HX_dev);
 
 /* Lowest opts->n_states eigenpairs (Sec. II B).
  *  evals_host  float64 [n_states], ascending

@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KH
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}
 
-EXPORTED = ["khp_create_grid", "khp_set_potential_strain_field", "khp_apply", "khp_eigensolve",
+EXPORTED = ["khp_create_grid", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
+            "khp_eigensolve",
             "khp_eigensolve_batched",
             "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",
             "khp_last_error", "khp_version"]
@@ -36,7 +37,7 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("tol_ev", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("warm_start_dev", ctypes.c_void_p),
-                ("warm_cols", ctypes.c_int)]
+                ("warm_cols", ctypes.c_int), ("projections", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

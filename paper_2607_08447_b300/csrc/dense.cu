@@ -119,6 +119,13 @@ __global__ void sum_partials_herm(const double2* __restrict__ partial, int nblk,
     }
 }
 
+cudaError_t launch_sum_partials_herm(const double2* partial, int nblk, int m, int nmat, double2* out,
+                                     cudaStream_t st) {
+    const int E = nmat * m * (m + 1) / 2;
+    sum_partials_herm<<<(E + 255) / 256, 256, 0, st>>>(partial, nblk, m, nmat, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gram(const double2* Y, const double2* W, long long rows, int ld, int col0, int m,
                         double2* partial, int nblk, double2* out, cudaStream_t st) {
     const int nmat = W ? 2 : 1;
@@ -210,6 +217,11 @@ __global__ void residual_finish(const double* __restrict__ partial, int nblk, in
         b += partial[(size_t)k * 2 * mq + mq + j];
     }
     out[j] = b > 0.0 ? sqrt(a / b) : 0.0;
+}
+
+cudaError_t launch_residual_finish(const double* partial, int nblk, int mq, double* out, cudaStream_t st) {
+    residual_finish<<<1, 64, 0, st>>>(partial, nblk, mq, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rotate(const double2* Y, const double2* W, int ld, int col0, int m,

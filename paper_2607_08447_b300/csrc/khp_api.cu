@@ -308,6 +308,15 @@ khp_status ensure_ws(khp_grid* g, int m, bool need32) {
     return KHP_OK;
 }
 
+// the reduction scratch alone (the projection entry points need no blocks)
+khp_status ensure_partial(khp_grid* g) {
+    if (g->partial) return KHP_OK;
+    const int nblk = dense_blocks(g->n);
+    g->partial_elems = std::max(gram_partial_elems(KHP_MAX_M, nblk), (size_t)nblk * KHP_MAX_GATES);
+    CK(cudaMalloc(&g->partial, sizeof(double2) * g->partial_elems));
+    return KHP_OK;
+}
+
 bool finite_all(const double* v, int n) {
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(v[i])) return false;
@@ -455,6 +464,8 @@ khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
                          std::string("allocation: ") + cudaGetErrorString(e)));
     if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess || (e = cudaEventCreate(&g->ev1)) != cudaSuccess)
         return bail(fail(KHP_ERR_CUDA, std::string("event: ") + cudaGetErrorString(e)));
+    if ((e = prepare_oz()) != cudaSuccess)
+        return bail(fail(KHP_ERR_CUDA, std::string("projection set-up: ") + cudaGetErrorString(e)));
     if (mask_dev) {
         if ((e = cudaMalloc(&g->mask, np)) != cudaSuccess ||
             (e = cudaMemcpyAsync(g->mask, mask_dev, np, cudaMemcpyDeviceToDevice, g->stream)) != cudaSuccess)
@@ -552,6 +563,51 @@ khp_status khp_apply(khp_handle g, const void* X_dev, void* Y_dev, int m, int pr
     return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
 }
 
+khp_status khp_project(khp_handle g, const void* Y_dev, const void* W_dev, int m, int method, double* G_host,
+                       double* S_host) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!Y_dev || !G_host || (W_dev && !S_host)) return fail(KHP_ERR_INVALID_ARG, "Y, G or S is NULL");
+    if (m < 1 || m > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "m out of range 1..64");
+    if (method != 0 && method != 1) return fail(KHP_ERR_INVALID_ARG, "method must be 0 or 1");
+    if (method == 0 && !oz_supported(m, m)) return fail(KHP_ERR_INVALID_ARG, "method 0 takes m <= 32");
+    CKS(ensure_partial(g));
+    const int nblk = dense_blocks(g->n);
+    const double2* Y = (const double2*)Y_dev;
+    const double2* W = (const double2*)W_dev;
+    if (method == 0) CK(launch_gram_oz(Y, W, g->n, m, 0, m, g->partial, nblk, g->small, g->stream));
+    else CK(launch_gram(Y, W, g->n, m, 0, m, g->partial, nblk, g->small, g->stream));
+    CK(cudaMemcpyAsync(G_host, g->small, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, g->stream));
+    if (W)
+        CK(cudaMemcpyAsync(S_host, g->small + m * m, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return KHP_OK;
+}
+
+khp_status khp_rotate(khp_handle g, const void* Y_dev, const void* W_dev, const double* Q_host, int m, int method,
+                      void* X_dev, void* HX_dev) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!Y_dev || !Q_host || !X_dev || (W_dev && !HX_dev)) return fail(KHP_ERR_INVALID_ARG, "Y, Q, X or HX is NULL");
+    if (m < 1 || m > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "m out of range 1..64");
+    if (method != 0 && method != 1) return fail(KHP_ERR_INVALID_ARG, "method must be 0 or 1");
+    if (method == 0 && !oz_supported(m, m)) return fail(KHP_ERR_INVALID_ARG, "method 0 takes m <= 32");
+    CKS(ensure_partial(g));
+    const int nblk = dense_blocks(g->n);
+    double2* Qd = g->small + 2 * m * m;
+    CK(cudaMemcpyAsync(Qd, Q_host, sizeof(double2) * m * m, cudaMemcpyHostToDevice, g->stream));
+    const double2* Y = (const double2*)Y_dev;
+    const double2* W = (const double2*)W_dev;
+    if (method == 0)
+        CK(launch_rotate_oz(Y, W, m, 0, m, Qd, m, nullptr, (double2*)X_dev, (double2*)HX_dev, g->n, nullptr, nblk,
+                            nullptr, g->stream));
+    else
+        CK(launch_rotate(Y, W, m, 0, m, Qd, m, nullptr, (double2*)X_dev, (double2*)HX_dev, g->n, nullptr, nblk,
+                         nullptr, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return KHP_OK;
+}
+
 }  // extern "C"
 
 // ============================================================ eigensolver
@@ -561,22 +617,31 @@ struct Solver {
     khp_grid* g;
     int m;
     int nblk;
+    bool tc = false; // Gram and rotation on the tensor cores (split-digit, FP64 accurate)
     double2* G;      // [2 m m]: G then S
     double2* Q;      // [m m]
     double* theta;   // [m]
     double* res;     // [m]
 
     khp_status rr(double2* Y, double2* W) {
-        CK(launch_gram(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        if (tc) CK(launch_gram_oz(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        else CK(launch_gram(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
         CK(launch_small(G, G + m * m, m, 1, Q, theta, g->dflag, g->stream));
-        CK(launch_rotate(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
+        if (tc)
+            CK(launch_rotate_oz(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
+        else
+            CK(launch_rotate(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
         g->launches += 5;
         return KHP_OK;
     }
     khp_status orth(double2* Y) {
-        CK(launch_gram(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        if (tc) CK(launch_gram_oz(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        else CK(launch_gram(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->stream));
         CK(launch_small(G, nullptr, m, 0, Q, nullptr, g->dflag, g->stream));
-        CK(launch_rotate(Y, nullptr, m, 0, m, Q, m, nullptr, Y, nullptr, g->n, nullptr, nblk, nullptr, g->stream));
+        if (tc)
+            CK(launch_rotate_oz(Y, nullptr, m, 0, m, Q, m, nullptr, Y, nullptr, g->n, nullptr, nblk, nullptr, g->stream));
+        else
+            CK(launch_rotate(Y, nullptr, m, 0, m, Q, m, nullptr, Y, nullptr, g->n, nullptr, nblk, nullptr, g->stream));
         g->launches += 4;
         return KHP_OK;
     }
@@ -662,6 +727,8 @@ struct Solve {
         if (!(opts->tol_ev > 0.0)) return fail(KHP_ERR_INVALID_ARG, "tol_ev must be > 0");
         if (opts->warm_start_dev && (opts->warm_cols < 1 || opts->warm_cols > m))
             return fail(KHP_ERR_INVALID_ARG, "warm_cols must be in 1..block_m");
+        if (opts->projections < 0 || opts->projections > 1)
+            return fail(KHP_ERR_INVALID_ARG, "projections must be 0 (tensor cores) or 1 (FP64 ALU)");
         return KHP_OK;
     }
 
@@ -690,6 +757,7 @@ struct Solve {
             g->bound_valid = true;
         }
         S.g = g; S.m = m; S.nblk = dense_blocks(g->n);
+        S.tc = o.projections == 0 && oz_supported(m, m);
         S.G = g->small; S.Q = g->small + 2 * m * m;
         S.theta = g->dvec; S.res = g->dvec + m;
         max_iter = o.max_iter > 0 ? o.max_iter : 1000;

@@ -32,6 +32,23 @@ cudaError_t launch_rotate(const double2* Y, const double2* W, int ld, int col0, 
                           const double2* Q, int mq, const double* theta, double2* X, double2* HX,
                           long long rows, double* res_partial, int nblk, double* res_out,
                           cudaStream_t st);
+// reducers shared with the tensor-core projections
+cudaError_t launch_sum_partials_herm(const double2* partial, int nblk, int m, int nmat, double2* out,
+                                     cudaStream_t st);
+cudaError_t launch_residual_finish(const double* partial, int nblk, int mq, double* out, cudaStream_t st);
+
+// ozaki.cu: the same Gram and rotation contractions (same arguments and
+// outputs) as exact split-digit BF16 products on the tensor cores, FP64
+// accurate; m, mq <= 32 (oz_supported).  prepare_oz() opts the kernels into
+// their shared memory (per device, outside stream capture).
+bool oz_supported(int m, int mq);
+cudaError_t prepare_oz();
+cudaError_t launch_gram_oz(const double2* Y, const double2* W, long long rows, int ld, int col0, int m,
+                           double2* partial, int nblk, double2* out, cudaStream_t st);
+cudaError_t launch_rotate_oz(const double2* Y, const double2* W, int ld, int col0, int m, const double2* Q,
+                             int mq, const double* theta, double2* X, double2* HX, long long rows,
+                             double* res_partial, int nblk, double* res_out, cudaStream_t st);
+
 // mode 0: Q = R^-1 of the (equilibrated) Cholesky factor of G (G = R^H R)
 // mode 1: generalized Rayleigh-Ritz  S q = theta G q  ->  theta ascending,
 //         Q = R^-1 Qhat (columns G-orthonormal)

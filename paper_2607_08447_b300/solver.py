@@ -100,13 +100,40 @@ class KPGrid:
         _lib.check(self.lib.khp_apply(self.handle, _ptr(X), _ptr(Y), m, int(precision)))
         return Y
 
+    def project(self, Y, W=None, method=0):
+        """G = Y^H Y and S = Y^H W (Hermitian, from their upper triangles):
+        method 0 on the tensor cores (split-digit products, FP64 accurate,
+        m <= 32), 1 on the FP64 ALUs.  Returns numpy (G, S or None)."""
+        Y = _dev(Y, torch.complex128, self.device)
+        W = _dev(W, torch.complex128, self.device)
+        m = Y.shape[1]
+        G = np.zeros((m, m), dtype=np.complex128)
+        S = np.zeros((m, m), dtype=np.complex128) if W is not None else None
+        _lib.check(self.lib.khp_project(self.handle, _ptr(Y), _ptr(W), m, int(method),
+                                        G.ctypes.data_as(ctypes.c_void_p),
+                                        None if S is None else S.ctypes.data_as(ctypes.c_void_p)))
+        return G, S
+
+    def rotate(self, Y, Q, W=None, method=0, out=None, out_w=None):
+        """X = Y Q and HX = W Q (method as in project); out/out_w may be Y/W."""
+        Y = _dev(Y, torch.complex128, self.device)
+        W = _dev(W, torch.complex128, self.device)
+        m = Y.shape[1]
+        Qh = np.ascontiguousarray(np.asarray(Q, dtype=np.complex128))
+        X = out if out is not None else torch.empty_like(Y)
+        HX = (out_w if out_w is not None else torch.empty_like(W)) if W is not None else None
+        _lib.check(self.lib.khp_rotate(self.handle, _ptr(Y), _ptr(W), Qh.ctypes.data_as(ctypes.c_void_p), m,
+                                       int(method), _ptr(X), _ptr(HX)))
+        return X, HX
+
     def eigensolve(self, n_states, block_m=None, degree=20, max_iter=0, precision=0, refine_sweeps=2,
-                   tol=1e-9, seed=1, warm_start=None, out=None, allow_not_converged=False):
+                   tol=1e-9, seed=1, warm_start=None, out=None, allow_not_converged=False, projections="tensor"):
         block_m = block_m or max(n_states + 8, 16)
         block_m += block_m % 2
         opts = _lib.SolverOpts()
         opts.n_states, opts.block_m, opts.degree, opts.max_iter = n_states, block_m, degree, max_iter
         opts.precision, opts.refine_sweeps, opts.tol_ev, opts.seed = precision, refine_sweeps, tol, seed
+        opts.projections = _projections(projections)
         ws = None
         if warm_start is not None:
             ws = _dev(warm_start, torch.complex128, self.device)
@@ -154,8 +181,17 @@ class KPGrid:
             pass
 
 
+def _projections(p):
+    """'tensor' (tensor-core split-digit products, the default) or 'fp64'."""
+    if p in ("tensor", 0):
+        return 0
+    if p in ("fp64", 1):
+        return 1
+    raise ValueError("projections must be 'tensor' or 'fp64'")
+
+
 def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precision=0, refine_sweeps=-1,
-                  tol=1e-9, seed=1, graph=True, autotune=False, allow_not_converged=False):
+                  tol=1e-9, seed=1, graph=True, autotune=False, allow_not_converged=False, projections="tensor"):
     """Solve every grid's lowest states in one khp_eigensolve_batched call
     (lock-step rounds, optionally one CUDA graph per round and an autotuned
     block width).  Returns a list of SolveResult."""
@@ -165,6 +201,7 @@ def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precisio
     bm = block_m or max(n_states + 8, 16)
     opts.n_states, opts.block_m, opts.degree, opts.max_iter = n_states, bm + bm % 2, degree, max_iter
     opts.precision, opts.refine_sweeps, opts.tol_ev, opts.seed = precision, refine_sweeps, tol, seed
+    opts.projections = _projections(projections)
     hs = (ctypes.c_void_p * count)(*[g.handle.value for g in grids])
     outs = [torch.empty((g.N, n_states), dtype=torch.complex128, device=g.device) for g in grids]
     ptrs = (ctypes.c_void_p * count)(*[o.data_ptr() for o in outs])

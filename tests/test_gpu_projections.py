@@ -1,0 +1,167 @@
+"""Rayleigh-Ritz contractions on the tensor cores (split-digit BF16 products
+recombined in FP64) against FP64 references: the Gram matrices G = Y^H Y,
+S = Y^H (H Y) and the rotation X = Y Q, through the C-ABI (khp_project,
+khp_rotate), and the eigensolver with either projection path.
+
+Accuracy bar: the split keeps 49 bits below each block's exponent bound and
+accumulates exactly, so each entry must agree with an extended-precision
+reference to a few units of 2^-49 of the norm scale of that entry; FP64
+BLAS on the same data is held to the same bar.
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from oracle import kp
+
+pytestmark = pytest.mark.gpu
+
+GRID = (37, 19, 14)      # 59,052 rows: many 64-row chunks and a ragged tail
+EPS49 = 2.0 ** -49
+
+
+def _grid(khp):
+    p = inputs.small_problem(*GRID, h=0.5, seed=21, rot="device", B=(0.3, 0.0, 0.4), gauge=0, strain=True)
+    return p, khp.KPGrid.from_problem(p)
+
+
+def _block(n, m, seed, col_scale=None, row_scale=None):
+    Y = inputs.random_block(n, m, seed=seed)
+    if col_scale is not None:
+        Y = Y * col_scale[None, :]
+    if row_scale is not None:
+        Y = Y * row_scale[:, None]
+    return Y
+
+
+def _gram_ref(Y, W):
+    """Y^H W in extended precision (numpy longdouble accumulation)."""
+    Yl = Y.real.astype(np.longdouble), Y.imag.astype(np.longdouble)
+    Wl = W.real.astype(np.longdouble), W.imag.astype(np.longdouble)
+    re = Yl[0].T @ Wl[0] + Yl[1].T @ Wl[1]
+    im = Yl[0].T @ Wl[1] - Yl[1].T @ Wl[0]
+    return re, im
+
+
+def _herm_upper(re, im):
+    """The Hermitian matrix built from the upper triangle (as the library does)."""
+    m = re.shape[0]
+    out = np.zeros((m, m), dtype=np.complex128)
+    for i in range(m):
+        for j in range(i, m):
+            out[i, j] = complex(float(re[i, j]), float(im[i, j]))
+            out[j, i] = np.conj(out[i, j]) if i != j else complex(float(re[i, i]), 0.0)
+    return out
+
+
+def _check_gram(G, Y, W):
+    re, im = _gram_ref(Y, W)
+    ref = _herm_upper(re, im)
+    ny = np.linalg.norm(Y, axis=0)
+    nw = np.linalg.norm(W, axis=0)
+    scale = np.maximum(np.outer(ny, nw), np.outer(nw, ny))
+    err = np.abs(G - ref) / np.where(scale > 0, scale, 1.0)
+    return err.max()
+
+
+@pytest.mark.parametrize("m", [1, 5, 8, 24, 32])
+def test_gram_matches_extended_precision(khp, m):
+    p, g = _grid(khp)
+    Y = _block(p.n_unknowns, m, seed=40 + m)
+    W = g.apply(torch.from_numpy(Y)).cpu().numpy()
+    for method in (0, 1):
+        G, S = g.project(Y, W, method=method)
+        assert _check_gram(G, Y, Y) <= 16 * EPS49, method
+        assert _check_gram(S, Y, W) <= 16 * EPS49, method
+        Gonly, none = g.project(Y, None, method=method)
+        assert none is None
+        assert np.array_equal(Gonly, G)
+
+
+def test_gram_column_scales_and_zero_columns(khp):
+    """Columns spread over 60 decades, one all-zero column: the per-chunk
+    column exponents keep every entry accurate relative to its own norms."""
+    p, g = _grid(khp)
+    m = 24
+    cs = 10.0 ** np.linspace(-30, 30, m)
+    cs[7] = 0.0
+    Y = _block(p.n_unknowns, m, seed=77, col_scale=cs)
+    W = g.apply(torch.from_numpy(Y)).cpu().numpy()
+    G, S = g.project(Y, W, method=0)
+    assert _check_gram(G, Y, Y) <= 16 * EPS49
+    assert _check_gram(S, Y, W) <= 16 * EPS49
+    assert np.all(G[7] == 0) and np.all(G[:, 7] == 0)
+
+
+def test_gram_propagates_nan(khp):
+    p, g = _grid(khp)
+    Y = _block(p.n_unknowns, 8, seed=5)
+    Y[1234, 3] = np.nan
+    G, _ = g.project(Y, None, method=0)
+    assert np.isnan(G[3, 3].real)
+    assert np.isfinite(G[0, 1]) and np.isfinite(G[5, 6])
+
+
+@pytest.mark.parametrize("m", [1, 5, 24, 32])
+def test_rotation_matches_extended_precision(khp, m):
+    p, g = _grid(khp)
+    rs = 10.0 ** np.random.default_rng(3).uniform(-20, 20, p.n_unknowns)
+    Y = _block(p.n_unknowns, m, seed=60 + m, row_scale=rs)
+    W = _block(p.n_unknowns, m, seed=160 + m)
+    rng = np.random.default_rng(m)
+    Q = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    Q[:, 0] *= 1e-12
+    Ql = Q.real.astype(np.longdouble), Q.imag.astype(np.longdouble)
+    for method in (0, 1):
+        X, HX = g.rotate(Y, Q, W, method=method)
+        for A, B in ((Y, X), (W, HX)):
+            Al = A.real.astype(np.longdouble), A.imag.astype(np.longdouble)
+            ref_re = Al[0] @ Ql[0] - Al[1] @ Ql[1]
+            ref_im = Al[0] @ Ql[1] + Al[1] @ Ql[0]
+            B = B.cpu().numpy()
+            scale = np.outer(np.linalg.norm(A, axis=1), np.linalg.norm(Q, axis=0))
+            scale = np.where(scale > 0, scale, 1.0)
+            err = np.maximum(np.abs(B.real - ref_re.astype(np.float64)), np.abs(B.imag - ref_im.astype(np.float64)))
+            assert (err / scale).max() <= 16 * EPS49, method
+
+
+def test_rotation_in_place(khp):
+    p, g = _grid(khp)
+    m = 24
+    Y = torch.from_numpy(_block(p.n_unknowns, m, seed=9)).cuda()
+    W = torch.from_numpy(_block(p.n_unknowns, m, seed=10)).cuda()
+    rng = np.random.default_rng(1)
+    Q = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    X_ref, HX_ref = g.rotate(Y, Q, W, method=0)
+    g.rotate(Y, Q, W, method=0, out=Y, out_w=W)
+    assert torch.equal(Y, X_ref) and torch.equal(W, HX_ref)
+
+
+@pytest.mark.parametrize("case", ["config1", "field"])
+def test_eigensolve_tensor_vs_fp64_projections(khp, case):
+    if case == "config1":
+        p = inputs.config1()
+        kw = dict(n_states=p.n_states, block_m=p.block_m, degree=p.degree)
+    else:
+        p = inputs.small_problem(12, 9, 8, h=0.5, seed=4, rot="device", B=(0.5, 0.2, 0.0), gauge=0, strain=True)
+        kw = dict(n_states=8, block_m=16, degree=16)
+    g = khp.KPGrid.from_problem(p)
+    rt = g.eigensolve(**kw, tol=1e-10, seed=2, projections="tensor")
+    rf = g.eigensolve(**kw, tol=1e-10, seed=2, projections="fp64")
+    assert rt.stats["converged"] == kw["n_states"]
+    assert np.abs(rt.evals - rf.evals).max() <= 1e-12
+    H = kp.assemble(p)
+    V = rt.evecs.cpu().numpy()
+    res = np.linalg.norm(H @ V - V * rt.evals[None, :], axis=0)
+    assert res.max() <= 1e-9
+    assert np.abs(V.conj().T @ V - np.eye(V.shape[1])).max() < 1e-12
+
+
+def test_project_rejects_bad_arguments(khp):
+    p, g = _grid(khp)
+    Y = _block(p.n_unknowns, 40, seed=1)
+    with pytest.raises(khp.KHPError):
+        g.project(Y, None, method=0)         # tensor-core path takes m <= 32
+    with pytest.raises(khp.KHPError):
+        g.project(Y[:, :8], None, method=3)
