@@ -304,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
                          "speedup_vs_fp64": (rm.stats["converged"] / (msm * 1e-3)) / (value / world),
                          "max_abs_dE_vs_fp64_ev": float(np.abs(rm.evals - evals_plain).max()),
                          "iterations_fp32": sm["iterations_fp32"], "iterations": sm["iterations"],
-                         "max_residual": sm["max_residual"], "precision": "fp32 filter (defect-corrected) + fp64 RR",
+                         "max_residual": sm["max_residual"], "precision": "fp32 filter (defect-corrected) + FP64-accurate Rayleigh-Ritz on the tensor cores",
                          "degree": MIXED_DEGREE}
         line["stencil_fp32"] = {"bound": "hbm", "kernel": "stencil_kernel<float> defect-corrected step (reads Z_k, Z_k-1, R; writes Z_k+1)",
                                 "achieved": b32 / (t32 * 1e-3) / 1e9, "peak": hbm,
@@ -312,6 +312,8 @@ def run_ours(args, rank, world, local_rank):
                                 "frac_of_nominal_8tbs": b32 / (t32 * 1e-3) / 1e9 / 8000.0,
                                 "ms_per_launch": t32, "algorithmic_bytes_per_launch": b32,
                                 "tflops": sm["flops_per_pv"] * pv32 / (t32 * 1e-3) / 1e12}
+
+    line["projections"] = _projections_bench(grid, p.n_unknowns, SOLVE_KW["block_m"], hbm, torch)
 
     # end to end through host buffers: H2D of V and strain, solve, D2H of
     # eigenvalues and eigenvectors, every step
@@ -339,6 +341,52 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line), flush=True)
     grid.close()
+
+
+def _projections_bench(grid, N, m, hbm, torch):
+    """The Rayleigh-Ritz contractions at the bench's block size: Gram
+    (G = Y^H Y, S = Y^H HY; reads 2 blocks) and rotation (X = Y Q, HX = W Q;
+    reads 2, writes 2 blocks), on the tensor cores (split-digit BF16
+    products, 28 digit pairs) and on the FP64 ALUs.  CUDA events on the
+    handle's stream around 5 calls after 2 warm-up calls."""
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    Y = torch.randn((N, m), dtype=torch.complex128, device="cuda", generator=gen)
+    W = grid.apply(Y)
+    X = torch.empty_like(Y)
+    HX = torch.empty_like(Y)
+    rng = np.random.default_rng(7)
+    Q = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    blk = N * m * 16.0
+    out = {}
+
+    def t(fn):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(grid.stream)
+        for _ in range(5):
+            fn()
+        e1.record(grid.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 5
+
+    for name, method in (("tensor", 0), ("fp64", 1)):
+        tg = t(lambda: grid.project(Y, W, method=method))
+        tr = t(lambda: grid.rotate(Y, Q, W, method=method, out=X, out_w=HX))
+        out[name] = {"gram_ms": tg, "rotate_ms": tr,
+                     "gram_gbs": 2 * blk / (tg * 1e-3) / 1e9, "rotate_gbs": 4 * blk / (tr * 1e-3) / 1e9}
+    mma_flop = 28 * 2.0 * (2 * m) ** 2 * N * 2          # per contraction pair (G and S, or X and HX)
+    tc = out["tensor"]
+    tc["gram_hbm_frac"] = tc["gram_gbs"] / hbm
+    tc["rotate_hbm_frac"] = tc["rotate_gbs"] / hbm
+    tc["gram_bf16_tflops"] = mma_flop / (tc["gram_ms"] * 1e-3) / 1e12
+    tc["rotate_bf16_tflops"] = mma_flop / (tc["rotate_ms"] * 1e-3) / 1e12
+    out["speedup_gram"] = out["fp64"]["gram_ms"] / tc["gram_ms"]
+    out["speedup_rotate"] = out["fp64"]["rotate_ms"] / tc["rotate_ms"]
+    out["note"] = ("times include the library's stream synchronisation and the m x m host copy; "
+                   "algorithmic bytes: Gram 2 blocks read, rotation 2 read + 2 written (N x m complex128)")
+    return out
 
 
 def run_profile(args):
