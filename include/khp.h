@@ -72,7 +72,8 @@ typedef struct {
  *                    Y = X p(Theta) + Z with p(Theta) the FP64 scalar
  *                    recurrence at the Ritz values and Z driven by the FP64
  *                    residual H X - X Theta; every filter apply runs in FP32
- *                    on Z, H Y and Rayleigh-Ritz in FP64.  Reaches the
+ *                    on Z, H Y in FP64 and an FP64-accurate Rayleigh-Ritz
+ *                    (see projections).  Reaches the
  *                    plain-FP64 accuracy (tested to 1e-10 eV).
  *  refine_sweeps  precision 1 only: number of FP64 clean-up sweeps; < 0 means
  *                 one clean-up sweep, then FP64 sweeps until every residual is
