@@ -39,57 +39,54 @@ namespace oz {
 
 constexpr int kS = 7;           // digits per value and levels kept
 constexpr int kMaxM = 32;       // complex columns (real width 64)
-constexpr int kChunk = 64;      // Gram rows per exponent block
-constexpr int kTile = 64;       // rotation rows per tile
+constexpr int kSub = 64;        // rows per digit tile (Gram sub-chunk, rotation tile)
+constexpr int kBlkSub = 4;      // Gram: sub-chunks per exponent block (256 rows)
 constexpr int kGramWarps = 12;
 constexpr int kRotWarps = 8;
 
 __host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
+// digit-row stride in BF16 elements: an odd number of 16-B units, so the
+// eight rows of an ldmatrix 8x8 load fall on distinct bank groups
+__host__ __device__ constexpr int dstride(int cols) { return cols + 8; }
 
 // exponent field of a double (0 for zero and subnormals, 2047 for Inf/NaN)
 __device__ __forceinline__ int efield(double v) {
     return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
 }
 
-// BF16 bit pattern of a digit of magnitude q <= 128 (exact), sign in bit 15
-__device__ __forceinline__ uint32_t bf16_digit(uint32_t q, uint32_t sgn) {
-    const float f = __uint_as_float(0x4B000000u | q) - 8388608.0f;
-    return q ? ((__float_as_uint(f) >> 16) | sgn) : 0u;
-}
+// 64 in each of the six low base-128 digit positions: adding it turns the
+// plain digits u_s of F into balanced ones, q_s = u_s - 64
+constexpr unsigned long long kBal = 0x20408102040ull;
 
-// digits of v against the block's exponent field emax (|v| < 2^(emax-1022)):
-// F = round(|v| 2^(49-E)) <= 2^49, written in balanced base 128,
-// F = sum_s q_s 128^(6-s) with |q_s| <= 64 for s >= 1 and 0 <= q_0 <= 128;
-// the digits carry the sign of v.  Balanced digits make the dropped
-// low-level products of a value with itself (the Gram diagonal) average out.
-__device__ __forceinline__ void split(double v, int emax, uint16_t (&d)[kS]) {
+// Digits of v against its block's exponent field emax (|v| < 2^(emax-1022)):
+// F = round(|v| 2^(49-E)) <= 2^49 = sum_s q_s 128^(6-s) with |q_s| <= 64
+// for s >= 1 and 0 <= q_0 <= 128; returned as the FP32 bit patterns of
+// sign(v) q_s (exact; their upper halves are the BF16 digits).  Balanced
+// digits make the dropped low-level products of a value with itself (the
+// Gram diagonal) average out.
+__device__ __forceinline__ void split_bits(double v, int emax, uint32_t (&fb)[kS]) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((b >> 52) & 0x7ff);
-    const uint32_t sgn = (uint32_t)(b >> 48) & 0x8000u;
     unsigned long long F = 0;
     if (ex != 0 && emax < 2047) {
         const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
         const int sh = emax - ex + 4;          // >= 4
         if (sh < 64) F = (mant >> sh) + ((mant >> (sh - 1)) & 1ull);
     }
-    int q[kS];
+    const unsigned long long G = F + kBal;
+    const uint32_t neg = (uint32_t)(b >> 32) & 0x80000000u;
+    // 0x4B400000 is 1.5 * 2^23: adding a small integer q to its bit pattern
+    // and subtracting the float gives q exactly
+    fb[0] = __float_as_uint(__int_as_float(0x4B400000 + (int)(G >> 42)) - 12582912.0f) ^ neg;
 #pragma unroll
-    for (int s = kS - 1; s >= 1; --s) {
-        int r = (int)(F & 127ull);
-        F >>= 7;
-        if (r >= 64) {
-            r -= 128;
-            F += 1;
-        }
-        q[s] = r;
-    }
-    q[0] = (int)F;
-#pragma unroll
-    for (int s = 0; s < kS; ++s) {
-        const uint32_t a = (uint32_t)(q[s] < 0 ? -q[s] : q[s]);
-        d[s] = (uint16_t)bf16_digit(a, q[s] < 0 ? (sgn ^ 0x8000u) : sgn);
+    for (int s = 1; s < kS; ++s) {
+        const int u = (int)((uint32_t)(G >> (7 * (6 - s))) & 127u);
+        fb[s] = __float_as_uint(__int_as_float(0x4B400000 - 64 + u) - 12582912.0f) ^ neg;
     }
 }
+
+// BF16 pair (lo at the lower address) from two FP32 bit patterns
+__device__ __forceinline__ uint32_t pack_bf16(uint32_t lo, uint32_t hi) { return __byte_perm(lo, hi, 0x7632); }
 
 // v 2^sc for |v| < 2^52, built from the bit pattern (exact)
 __device__ __forceinline__ double i2d_scaled(long long v, int sc) {
@@ -105,15 +102,24 @@ __device__ __forceinline__ double i2d_scaled(long long v, int sc) {
     return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | mant));
 }
 
+// integer value of an FP32 holding an exact integer; SMALL: |c| < 2^22
+// (magic-number conversion on the FMA/ALU pipes), else cvt
+template <bool SMALL>
+__device__ __forceinline__ long long f2ll(float c) {
+    if (SMALL) return (long long)(__float_as_int(c + 12582912.0f) - 0x4B400000);
+    return (long long)__float2int_rn(c);
+}
+
 // sum_L c[L] 2^(-7L) 2^(Ea + Eb - 14) with Ea = ea - 1022, Eb = eb - 1022
 // (ea, eb exponent fields); NaN when either block held Inf/NaN
+template <bool SMALL>
 __device__ __forceinline__ double recombine(const float (&c)[kS], int ea, int eb) {
     if (ea == 2047 || eb == 2047) return __longlong_as_double(0x7ff8000000000000ll);
     long long hi = 0, lo = 0;
 #pragma unroll
-    for (int L = 0; L < 4; ++L) hi = hi * 128 + (long long)__float2int_rn(c[L]);
+    for (int L = 0; L < 4; ++L) hi = hi * 128 + f2ll<SMALL>(c[L]);
 #pragma unroll
-    for (int L = 4; L < kS; ++L) lo = lo * 128 + (long long)__float2int_rn(c[L]);
+    for (int L = 4; L < kS; ++L) lo = lo * 128 + f2ll<SMALL>(c[L]);
     const int E = (ea - 1022) + (eb - 1022) - 14;
     // sum_L c_L 2^-7L = hi 2^-21 + lo 2^-42
     return i2d_scaled(hi, E - 21) + i2d_scaled(lo, E - 42);
@@ -127,23 +133,78 @@ __device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint3
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// four 8x8 BF16 matrices; lane l gives the address of row l % 8 of matrix l / 8
+template <bool TRANS>
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const uint16_t* p) {
+    if (TRANS)
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(su32(p)));
+    else
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(su32(p)));
+}
+// two 8x8 matrices; lanes 0..15 give the row addresses (the others are ignored
+// but must be valid)
+template <bool TRANS>
+__device__ __forceinline__ void ldsm2(uint32_t (&r)[2], const uint16_t* p) {
+    if (TRANS)
+        asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                     : "=r"(r[0]), "=r"(r[1]) : "r"(su32(p)));
+    else
+        asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                     : "=r"(r[0]), "=r"(r[1]) : "r"(su32(p)));
+}
+
+// digits of the complex pair (a, b) of one row into a natural-layout digit
+// tile D[s][row][col] (slice stride `slice`, row stride ds elements): real
+// parts at columns c, c + 1, imaginary parts at m + c, m + 1 + c (m even);
+// exponent fields of the four real columns
+__device__ __forceinline__ void store_pair(uint16_t* D, size_t slice, int ds, int row, int c, int m, double2 a,
+                                           double2 b, int ear, int ebr, int eai, int ebi) {
+    uint32_t ar[kS], br[kS], ai[kS], bi[kS];
+    split_bits(a.x, ear, ar);
+    split_bits(b.x, ebr, br);
+    split_bits(a.y, eai, ai);
+    split_bits(b.y, ebi, bi);
+    uint16_t* base = D + (size_t)row * ds;
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+        *reinterpret_cast<uint32_t*>(base + s * slice + c) = pack_bf16(ar[s], br[s]);
+        *reinterpret_cast<uint32_t*>(base + s * slice + m + c) = pack_bf16(ai[s], bi[s]);
+    }
+}
+// one complex value (m odd)
+__device__ __forceinline__ void store_one(uint16_t* D, size_t slice, int ds, int row, int c, int m, double2 a,
+                                          int er, int ei) {
+    uint32_t ar[kS], ai[kS];
+    split_bits(a.x, er, ar);
+    split_bits(a.y, ei, ai);
+    uint16_t* base = D + (size_t)row * ds;
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+        base[s * slice + c] = (uint16_t)(ar[s] >> 16);
+        base[s * slice + m + c] = (uint16_t)(ai[s] >> 16);
+    }
+}
 
 // ------------------------------------------------------------------ Gram
-// A = [Re Y | Im Y] (rows x 2m), B = [Re W | Im W]; per CTA and chunk of 64
-// rows: digits of A^T and B^T in shared memory ([slice][column][row], rows
-// contiguous, padded), D_G += A^T A and D_S += A^T B over the CTA's rows
-// (FP64 in shared memory), then the packed upper triangles of the complex
-// G_ij = D[i][j] + D[i+m][j+m] + i (D[i][j+m] - D[i+m][j]) (and S) as the
-// CTA's partial.  Warp unit = (matrix, 16-row m-tile, group of 3 n-tiles).
-constexpr int kRowStride = kChunk + 8;   // padded digit row (bank-conflict free fragments)
-
+// A = [Re Y | Im Y] (rows x 2m), B = [Re W | Im W].  A CTA walks exponent
+// blocks of 256 rows (64 when a warp must serve two output units): column
+// exponent bounds of the block first, then four 64-row sub-chunks whose
+// digits (natural layout [slice][row][column]) feed A^T A and A^T B through
+// ldmatrix.trans fragments; the level sums of the whole block stay exact in
+// FP32 (below 2^24) and are recombined once per block into FP64 running
+// sums D in shared memory.  At the end the CTA writes the packed upper
+// triangles of G_ij = D[i][j] + D[i+m][j+m] + i (D[i][j+m] - D[i+m][j])
+// (and S) as its partial.  Warp unit = (matrix, 16-row m-tile, 3 n-tiles).
 struct GramSmem {
     static size_t bytes(int m, bool w) {
         const int RP = round16(2 * m);
-        const size_t dig = (size_t)(w ? 2 : 1) * kS * RP * kRowStride * sizeof(uint16_t);
+        const size_t dig = (size_t)(w ? 2 : 1) * kS * kSub * dstride(RP) * sizeof(uint16_t);
         const size_t acc = (size_t)(w ? 2 : 1) * RP * RP * sizeof(double);
-        return dig + acc + 2 * RP * sizeof(int) * 2;
+        return dig + acc + 2 * RP * sizeof(int);
     }
 };
 
@@ -153,134 +214,171 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
     extern __shared__ __align__(16) unsigned char sm[];
     const bool hasW = W != nullptr;
     const int nmat = hasW ? 2 : 1;
-    const int R2 = 2 * m, RP = round16(R2);
-    uint16_t* Ad = reinterpret_cast<uint16_t*>(sm);                  // [kS][RP][kRowStride]
-    uint16_t* Bd = Ad + (size_t)kS * RP * kRowStride;                // same, W (if any)
-    double* D = reinterpret_cast<double*>(Bd + (hasW ? (size_t)kS * RP * kRowStride : 0));  // [nmat][RP][RP]
-    int* ea = reinterpret_cast<int*>(D + (size_t)nmat * RP * RP);    // [RP] chunk column exponents of A
+    const int R2 = 2 * m, RP = round16(R2), CS = dstride(RP);
+    const size_t slice = (size_t)kSub * CS;
+    uint16_t* Ad = reinterpret_cast<uint16_t*>(sm);                  // [kS][kSub][CS]
+    uint16_t* Bd = Ad + kS * slice;                                  // same, W (if any)
+    double* D = reinterpret_cast<double*>(Bd + (hasW ? kS * slice : 0));  // [nmat][RP][RP]
+    int* ea = reinterpret_cast<int*>(D + (size_t)nmat * RP * RP);    // [RP] block column exponents of A
     int* eb = ea + RP;                                               // [RP] of B
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = blockDim.x;
+    const int g = lane >> 2, tg = lane & 3;
 
     for (int i = tid; i < nmat * RP * RP; i += nthr) D[i] = 0.0;
     // padding columns (real index >= 2m) keep zero digits for the whole run
-    for (int i = tid; i < (hasW ? 2 : 1) * kS * RP * kRowStride; i += nthr) Ad[i] = 0;
-
-    const long long nchunks = (rows + kChunk - 1) / kChunk;
-    const long long per = (nchunks + gridDim.x - 1) / gridDim.x;
-    const long long c0 = (long long)blockIdx.x * per;
-    const long long c1 = c0 + per < nchunks ? c0 + per : nchunks;
+    for (int i = tid; i < nmat * kS * (int)slice; i += nthr) Ad[i] = 0;
 
     const int MT = RP / 16, NT = RP / 8, NG = (NT + 2) / 3;
     const int units = nmat * MT * NG;
-    const int g = lane >> 2, tg = lane & 3;
+    const int nsub = units <= kGramWarps ? kBlkSub : 1;
+    const long long BR = (long long)nsub * kSub;
+    const long long nblocks = (rows + BR - 1) / BR;
+    const long long per = (nblocks + gridDim.x - 1) / gridDim.x;
+    const long long b0 = (long long)blockIdx.x * per;
+    const long long b1 = b0 + per < nblocks ? b0 + per : nblocks;
+    const int ncp = m >> 1;                 // column pairs per row
+    const int items = ncp + (m & 1);        // + the single last column when m is odd
 
-    for (long long ch = c0; ch < c1; ++ch) {
-        const long long r0 = ch * kChunk;
-        const int nr = (int)(rows - r0 < kChunk ? rows - r0 : kChunk);
-        __syncthreads();   // previous chunk's fragments are consumed
+    float acc[kS][3][4];
+    for (long long blk = b0; blk < b1; ++blk) {
+        const long long r0 = blk * BR;
+        const int nrb = (int)(rows - r0 < BR ? rows - r0 : BR);
+        __syncthreads();   // previous block's digits and exponents are consumed
         for (int i = tid; i < 2 * RP; i += nthr) ea[i] = 0;
         __syncthreads();
-        // column exponent bounds of this chunk
-        for (int idx = tid; idx < kChunk * m; idx += nthr) {
-            const int r = idx / m, c = idx - r * m;
-            if (r < nr) {
-                const double2 y = Y[(r0 + r) * ld + col0 + c];
-                atomicMax(&ea[c], efield(y.x));
-                atomicMax(&ea[c + m], efield(y.y));
+        // column exponent bounds of the block: thread -> (column, row lane)
+        {
+            const int lanes = nthr / m;
+            const int c = tid % m, rl = tid / m;
+            if (rl < lanes) {
+                int yr = 0, yi = 0, wr = 0, wi = 0;
+                for (int r = rl; r < nrb; r += lanes) {
+                    const double2 y = Y[(r0 + r) * ld + col0 + c];
+                    yr = max(yr, efield(y.x));
+                    yi = max(yi, efield(y.y));
+                    if (hasW) {
+                        const double2 w = W[(r0 + r) * ld + col0 + c];
+                        wr = max(wr, efield(w.x));
+                        wi = max(wi, efield(w.y));
+                    }
+                }
+                atomicMax(&ea[c], yr);
+                atomicMax(&ea[c + m], yi);
                 if (hasW) {
-                    const double2 w = W[(r0 + r) * ld + col0 + c];
-                    atomicMax(&eb[c], efield(w.x));
-                    atomicMax(&eb[c + m], efield(w.y));
+                    atomicMax(&eb[c], wr);
+                    atomicMax(&eb[c + m], wi);
                 }
             }
         }
-        __syncthreads();
-        // digits, transposed: Ad[s][column][row]
-        for (int idx = tid; idx < kChunk * m; idx += nthr) {
-            const int r = idx / m, c = idx - r * m;
-            double2 y = make_double2(0.0, 0.0), w = make_double2(0.0, 0.0);
-            if (r < nr) {
-                y = Y[(r0 + r) * ld + col0 + c];
-                if (hasW) w = W[(r0 + r) * ld + col0 + c];
-            }
-            uint16_t d[kS];
-            split(y.x, ea[c], d);
-#pragma unroll
-            for (int s = 0; s < kS; ++s) Ad[((size_t)s * RP + c) * kRowStride + r] = d[s];
-            split(y.y, ea[c + m], d);
-#pragma unroll
-            for (int s = 0; s < kS; ++s) Ad[((size_t)s * RP + c + m) * kRowStride + r] = d[s];
-            if (hasW) {
-                split(w.x, eb[c], d);
-#pragma unroll
-                for (int s = 0; s < kS; ++s) Bd[((size_t)s * RP + c) * kRowStride + r] = d[s];
-                split(w.y, eb[c + m], d);
-#pragma unroll
-                for (int s = 0; s < kS; ++s) Bd[((size_t)s * RP + c + m) * kRowStride + r] = d[s];
-            }
-        }
-        __syncthreads();
-
-        for (int u = warp; u < units; u += kGramWarps) {
-            const int mat = u / (MT * NG);
-            const int mt = (u / NG) % MT;
-            const int ng = u % NG;
-            const uint16_t* Lt = Ad;                  // left operand: A^T
-            const uint16_t* Rt = mat ? Bd : Ad;       // right operand: A or B
-            const int* er = mat ? eb : ea;
-            float acc[kS][3][4];
+        if (nsub > 1) {
 #pragma unroll
             for (int L = 0; L < kS; ++L)
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc[L][q][e] = 0.f;
-#pragma unroll 1
-            for (int ks = 0; ks < kChunk / 16; ++ks) {
-                const int k0 = ks * 16 + tg * 2;
-                uint32_t a[kS][4];
-#pragma unroll
-                for (int s = 0; s < kS; ++s) {
-                    const uint16_t* base = Lt + ((size_t)s * RP + mt * 16 + g) * kRowStride + k0;
-                    a[s][0] = ld32(base);
-                    a[s][1] = ld32(base + 8 * kRowStride);
-                    a[s][2] = ld32(base + 8);
-                    a[s][3] = ld32(base + 8 * kRowStride + 8);
-                }
-#pragma unroll
-                for (int t = 0; t < kS; ++t) {
-                    uint32_t b[3][2];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const int nt = ng * 3 + q;
-                        const int n = (nt < NT ? nt : 0) * 8 + g;
-                        const uint16_t* base = Rt + ((size_t)t * RP + n) * kRowStride + k0;
-                        b[q][0] = ld32(base);
-                        b[q][1] = ld32(base + 8);
+        }
+        for (int sub = 0; sub < nsub; ++sub) {
+            const long long rs0 = r0 + (long long)sub * kSub;
+            const int nr = (int)(rows - rs0 < kSub ? (rows - rs0 > 0 ? rows - rs0 : 0) : kSub);
+            __syncthreads();   // exponents ready / previous sub-chunk's fragments consumed
+            for (int idx = tid; idx < kSub * items; idx += nthr) {
+                const int r = idx / items, k = idx - r * items;
+                const bool ok = r < nr;
+                if (k < ncp) {
+                    const int c = 2 * k;
+                    const double2* yp = Y + (rs0 + r) * ld + col0 + c;
+                    const double2 y0 = ok ? yp[0] : make_double2(0.0, 0.0);
+                    const double2 y1 = ok ? yp[1] : make_double2(0.0, 0.0);
+                    if (m & 1) {
+                        store_one(Ad, slice, CS, r, c, m, y0, ea[c], ea[c + m]);
+                        store_one(Ad, slice, CS, r, c + 1, m, y1, ea[c + 1], ea[c + 1 + m]);
+                    } else {
+                        store_pair(Ad, slice, CS, r, c, m, y0, y1, ea[c], ea[c + 1], ea[c + m], ea[c + 1 + m]);
                     }
-#pragma unroll
-                    for (int s = 0; s + t < kS; ++s)
-#pragma unroll
-                        for (int q = 0; q < 3; ++q)
-                            if (ng * 3 + q < NT) mma(acc[s + t][q], a[s], b[q][0], b[q][1]);
+                    if (hasW) {
+                        const double2* wp = W + (rs0 + r) * ld + col0 + c;
+                        const double2 w0 = ok ? wp[0] : make_double2(0.0, 0.0);
+                        const double2 w1 = ok ? wp[1] : make_double2(0.0, 0.0);
+                        if (m & 1) {
+                            store_one(Bd, slice, CS, r, c, m, w0, eb[c], eb[c + m]);
+                            store_one(Bd, slice, CS, r, c + 1, m, w1, eb[c + 1], eb[c + 1 + m]);
+                        } else {
+                            store_pair(Bd, slice, CS, r, c, m, w0, w1, eb[c], eb[c + 1], eb[c + m], eb[c + 1 + m]);
+                        }
+                    }
+                } else {
+                    const int c = m - 1;
+                    const double2 y = ok ? Y[(rs0 + r) * ld + col0 + c] : make_double2(0.0, 0.0);
+                    store_one(Ad, slice, CS, r, c, m, y, ea[c], ea[c + m]);
+                    if (hasW) {
+                        const double2 w = ok ? W[(rs0 + r) * ld + col0 + c] : make_double2(0.0, 0.0);
+                        store_one(Bd, slice, CS, r, c, m, w, eb[c], eb[c + m]);
+                    }
                 }
             }
-            // D[mat] += level sums scaled by the chunk's column exponents
-            double* Dm = D + (size_t)mat * RP * RP;
+            __syncthreads();
+
+            for (int u = warp; u < units; u += kGramWarps) {
+                const int mat = u / (MT * NG);
+                const int mt = (u / NG) % MT;
+                const int ng = u % NG;
+                const uint16_t* Rt = mat ? Bd : Ad;
+                if (nsub == 1) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int nt = ng * 3 + q;
-                if (nt >= NT) continue;
+                    for (int L = 0; L < kS; ++L)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int i = mt * 16 + g + (e >> 1) * 8;
-                    const int j = nt * 8 + tg * 2 + (e & 1);
-                    if (i >= R2 || j >= R2) continue;
-                    float c[kS];
+                        for (int q = 0; q < 3; ++q)
 #pragma unroll
-                    for (int L = 0; L < kS; ++L) c[L] = acc[L][q][e];
-                    Dm[i * RP + j] += recombine(c, ea[i], er[j]);
+                            for (int e = 0; e < 4; ++e) acc[L][q][e] = 0.f;
+                }
+                const int j8 = lane >> 3, r8 = lane & 7;
+                const int nt0 = ng * 3;
+                const int ntA = nt0 + (j8 >> 1) < NT ? nt0 + (j8 >> 1) : 0;   // x4: tiles nt0, nt0 + 1
+                const int ntB = nt0 + 2 < NT ? nt0 + 2 : 0;                   // x2: tile nt0 + 2
+#pragma unroll 1
+                for (int ks = 0; ks < kSub / 16; ++ks) {
+                    uint32_t a[kS][4];
+                    // A^T fragments from the [row][column] tile: matrix j8 = (m-block j8 & 1, k-block j8 >> 1)
+                    const uint16_t* pa = Ad + (size_t)(ks * 16 + (j8 >> 1) * 8 + r8) * CS + mt * 16 + (j8 & 1) * 8;
+#pragma unroll
+                    for (int s = 0; s < kS; ++s) ldsm4<true>(a[s], pa + s * slice);
+                    // B fragments: matrix j8 = (k-block j8 & 1, n-tile nt0 + (j8 >> 1))
+                    const uint16_t* pb = Rt + (size_t)(ks * 16 + (j8 & 1) * 8 + r8) * CS + ntA * 8;
+                    const uint16_t* pc = Rt + (size_t)(ks * 16 + (j8 & 1) * 8 + r8) * CS + ntB * 8;
+#pragma unroll
+                    for (int t = 0; t < kS; ++t) {
+                        uint32_t b01[4], b2[2];
+                        ldsm4<true>(b01, pb + t * slice);
+                        ldsm2<true>(b2, pc + t * slice);
+#pragma unroll
+                        for (int s = 0; s + t < kS; ++s) {
+                            if (nt0 < NT) mma(acc[s + t][0], a[s], b01[0], b01[1]);
+                            if (nt0 + 1 < NT) mma(acc[s + t][1], a[s], b01[2], b01[3]);
+                            if (nt0 + 2 < NT) mma(acc[s + t][2], a[s], b2[0], b2[1]);
+                        }
+                    }
+                }
+                if (nsub == 1 || sub == nsub - 1) {
+                    // D[mat] += level sums scaled by the block's column exponents
+                    double* Dm = D + (size_t)mat * RP * RP;
+                    const int* er = mat ? eb : ea;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int nt = nt0 + q;
+                        if (nt >= NT) continue;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int i = mt * 16 + g + (e >> 1) * 8;
+                            const int j = nt * 8 + tg * 2 + (e & 1);
+                            if (i >= R2 || j >= R2) continue;
+                            float c[kS];
+#pragma unroll
+                            for (int L = 0; L < kS; ++L) c[L] = acc[L][q][e];
+                            Dm[i * RP + j] += recombine<false>(c, ea[i], er[j]);
+                        }
+                    }
                 }
             }
         }
@@ -307,15 +405,14 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
 // column of Qr over its 2m entries.  A CTA walks tiles of 64 rows; warp w
 // owns m-tile w % 4 and n-group w / 4 (NTW n-tiles of 8 columns).  The
 // tile's digits are taken before any of its rows is written, so X may
-// alias Y and HX may alias W.
-constexpr int kTileStride(int RK) { return RK + 8; }
-
+// alias Y and HX may alias W.  Level sums have K = 2m <= 64 terms: below
+// 2^22, converted to integers without the cvt pipe.
 struct RotSmem {
     static size_t bytes(int m, int mq) {
-        const int RK = round16(2 * m), RN = round16(2 * mq);
-        const size_t q = (size_t)kS * RN * kTileStride(RK) * sizeof(uint16_t);
-        const size_t a = (size_t)2 * kS * kTile * kTileStride(RK) * sizeof(uint16_t);
-        return q + a + (RN + 2 * kTile) * sizeof(int) + (size_t)2 * RN * sizeof(double) * 4;
+        const int RK = round16(2 * m), RN = round16(2 * mq), TS = dstride(RK);
+        const size_t q = (size_t)kS * RN * TS * sizeof(uint16_t);
+        const size_t a = (size_t)2 * kS * kSub * TS * sizeof(uint16_t);
+        return q + a + (RN + 2 * kSub) * sizeof(int) + (size_t)4 * 2 * RN * sizeof(double);
     }
 };
 
@@ -326,22 +423,24 @@ __global__ void __launch_bounds__(kRotWarps * 32, 1)
                      double* __restrict__ res_partial) {
     extern __shared__ __align__(16) unsigned char sm[];
     const bool hasW = W != nullptr;
-    const int RK = round16(2 * m), RN = round16(2 * mq), TS = kTileStride(RK);
+    const int RK = round16(2 * m), RN = round16(2 * mq), TS = dstride(RK);
+    const size_t slice = (size_t)kSub * TS;
     uint16_t* Qd = reinterpret_cast<uint16_t*>(sm);               // [kS][RN][TS]  (Qr^T digits)
-    uint16_t* Yd = Qd + (size_t)kS * RN * TS;                      // [kS][kTile][TS]
-    uint16_t* Wd = Yd + (size_t)kS * kTile * TS;                   // [kS][kTile][TS]
-    int* fq = reinterpret_cast<int*>(Wd + (size_t)kS * kTile * TS);  // [RN] column exponents of Qr
-    int* ey = fq + RN;                                             // [kTile] row exponents of Y
-    int* ew = ey + kTile;                                          // [kTile] of W
-    double* red = reinterpret_cast<double*>(ew + kTile);           // [4][2 RN] residual partials
+    uint16_t* Yd = Qd + (size_t)kS * RN * TS;                      // [kS][kSub][TS]
+    uint16_t* Wd = Yd + kS * slice;                                // [kS][kSub][TS]
+    int* fq = reinterpret_cast<int*>(Wd + kS * slice);             // [RN] column exponents of Qr
+    int* ey = fq + RN;                                             // [kSub] row exponents of Y
+    int* ew = ey + kSub;                                           // [kSub] of W
+    double* red = reinterpret_cast<double*>(ew + kSub);            // [4][2 RN] residual partials
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = blockDim.x;
     const int g = lane >> 2, tg = lane & 3;
+    const int j8 = lane >> 3, r8 = lane & 7;
 
     // Qr digits ([t][n][k]) with per-column exponents
     for (int i = tid; i < RN; i += nthr) fq[i] = 0;
     for (int i = tid; i < kS * RN * TS; i += nthr) Qd[i] = 0;
-    for (int i = tid; i < 2 * kS * kTile * TS; i += nthr) Yd[i] = 0;
+    for (int i = tid; i < 2 * kS * (int)slice; i += nthr) Yd[i] = 0;
     __syncthreads();
     auto qr = [&](int k, int n) -> double {
         const int i = k < m ? k : k - m, j = n < mq ? n : n - mq;
@@ -356,10 +455,10 @@ __global__ void __launch_bounds__(kRotWarps * 32, 1)
     __syncthreads();
     for (int idx = tid; idx < 2 * m * 2 * mq; idx += nthr) {
         const int k = idx / (2 * mq), n = idx - k * (2 * mq);
-        uint16_t d[kS];
-        split(qr(k, n), fq[n], d);
+        uint32_t d[kS];
+        split_bits(qr(k, n), fq[n], d);
 #pragma unroll
-        for (int t = 0; t < kS; ++t) Qd[((size_t)t * RN + n) * TS + k] = d[t];
+        for (int t = 0; t < kS; ++t) Qd[((size_t)t * RN + n) * TS + k] = (uint16_t)(d[t] >> 16);
     }
 
     const int mt = warp & 3, ngrp = warp >> 2;
@@ -367,39 +466,47 @@ __global__ void __launch_bounds__(kRotWarps * 32, 1)
     double rs[NTW][2], xs[NTW][2];
 #pragma unroll
     for (int q = 0; q < NTW; ++q) rs[q][0] = rs[q][1] = xs[q][0] = xs[q][1] = 0.0;
+    const int ncp = m >> 1, items = ncp + (m & 1);
 
-    const long long ntiles = (rows + kTile - 1) / kTile;
+    const long long ntiles = (rows + kSub - 1) / kSub;
     const long long per = (ntiles + gridDim.x - 1) / gridDim.x;
     const long long t0 = (long long)blockIdx.x * per;
     const long long t1 = t0 + per < ntiles ? t0 + per : ntiles;
     for (long long tl = t0; tl < t1; ++tl) {
-        const long long r0 = tl * kTile;
-        const int nr = (int)(rows - r0 < kTile ? rows - r0 : kTile);
+        const long long r0 = tl * kSub;
+        const int nr = (int)(rows - r0 < kSub ? rows - r0 : kSub);
         __syncthreads();   // Qd ready / previous tile consumed
         // row digits: 4 threads per row, row exponent by shuffles
         {
             const int r = tid >> 2, qd = tid & 3;
+            const bool ok = r < nr;
             for (int pass = 0; pass < (hasW ? 2 : 1); ++pass) {
-                const double2* src = pass ? W : Y;
+                const double2* src = (pass ? W : Y) + (r0 + r) * ld + col0;
                 uint16_t* dst = pass ? Wd : Yd;
                 int emax = 0;
-                if (r < nr)
+                if (ok)
                     for (int c = qd; c < m; c += 4) {
-                        const double2 v = src[(r0 + r) * ld + col0 + c];
+                        const double2 v = src[c];
                         emax = max(emax, max(efield(v.x), efield(v.y)));
                     }
                 emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
                 emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
                 if (qd == 0) (pass ? ew : ey)[r] = emax;
-                for (int c = qd; c < m; c += 4) {
-                    const double2 v = r < nr ? src[(r0 + r) * ld + col0 + c] : make_double2(0.0, 0.0);
-                    uint16_t d[kS];
-                    split(v.x, emax, d);
-#pragma unroll
-                    for (int s = 0; s < kS; ++s) dst[((size_t)s * kTile + r) * TS + c] = d[s];
-                    split(v.y, emax, d);
-#pragma unroll
-                    for (int s = 0; s < kS; ++s) dst[((size_t)s * kTile + r) * TS + c + m] = d[s];
+                for (int k = qd; k < items; k += 4) {
+                    if (k < ncp) {
+                        const int c = 2 * k;
+                        const double2 v0 = ok ? src[c] : make_double2(0.0, 0.0);
+                        const double2 v1 = ok ? src[c + 1] : make_double2(0.0, 0.0);
+                        if (m & 1) {
+                            store_one(dst, slice, TS, r, c, m, v0, emax, emax);
+                            store_one(dst, slice, TS, r, c + 1, m, v1, emax, emax);
+                        } else {
+                            store_pair(dst, slice, TS, r, c, m, v0, v1, emax, emax, emax, emax);
+                        }
+                    } else {
+                        const double2 v = ok ? src[m - 1] : make_double2(0.0, 0.0);
+                        store_one(dst, slice, TS, r, m - 1, m, v, emax, emax);
+                    }
                 }
             }
         }
@@ -417,26 +524,33 @@ __global__ void __launch_bounds__(kRotWarps * 32, 1)
                     for (int e = 0; e < 4; ++e) acc[L][q][e] = 0.f;
 #pragma unroll 1
             for (int ks = 0; ks < RK / 16; ++ks) {
-                const int k0 = ks * 16 + tg * 2;
                 uint32_t a[kS][4];
+                // matrix j8 = (row block j8 & 1, k-block j8 >> 1)
+                const uint16_t* pa = Ad + (size_t)(mt * 16 + (j8 & 1) * 8 + r8) * TS + ks * 16 + (j8 >> 1) * 8;
 #pragma unroll
-                for (int s = 0; s < kS; ++s) {
-                    const uint16_t* base = Ad + ((size_t)s * kTile + mt * 16 + g) * TS + k0;
-                    a[s][0] = ld32(base);
-                    a[s][1] = ld32(base + 8 * TS);
-                    a[s][2] = ld32(base + 8);
-                    a[s][3] = ld32(base + 8 * TS + 8);
-                }
+                for (int s = 0; s < kS; ++s) ldsm4<false>(a[s], pa + s * slice);
 #pragma unroll
                 for (int t = 0; t < kS; ++t) {
                     uint32_t b[NTW][2];
 #pragma unroll
-                    for (int q = 0; q < NTW; ++q) {
-                        const int nt = ngrp * NTW + q;
-                        const int n = (nt < NT ? nt : 0) * 8 + g;
-                        const uint16_t* base = Qd + ((size_t)t * RN + n) * TS + k0;
-                        b[q][0] = ld32(base);
-                        b[q][1] = ld32(base + 8);
+                    for (int q = 0; q < NTW; q += 2) {
+                        // matrix j8 = (k-block j8 & 1, n-tile q + (j8 >> 1))
+                        const int ntq = ngrp * NTW + q + (q + 1 < NTW ? (j8 >> 1) : 0);
+                        const int nt = ntq < NT ? ntq : 0;
+                        const uint16_t* pb = Qd + ((size_t)t * RN + nt * 8 + r8) * TS + ks * 16 + (j8 & 1) * 8;
+                        if (q + 1 < NTW) {
+                            uint32_t r4[4];
+                            ldsm4<false>(r4, pb);
+                            b[q][0] = r4[0];
+                            b[q][1] = r4[1];
+                            b[q + 1][0] = r4[2];
+                            b[q + 1][1] = r4[3];
+                        } else {
+                            uint32_t r2[2];
+                            ldsm2<false>(r2, pb);
+                            b[q][0] = r2[0];
+                            b[q][1] = r2[1];
+                        }
                     }
 #pragma unroll
                     for (int s = 0; s + t < kS; ++s)
@@ -457,7 +571,7 @@ __global__ void __launch_bounds__(kRotWarps * 32, 1)
                     float c[kS];
 #pragma unroll
                     for (int L = 0; L < kS; ++L) c[L] = acc[L][q][e];
-                    const double v = recombine(c, er[r], fq[n]);
+                    const double v = recombine<true>(c, er[r], fq[n]);
                     double* o = reinterpret_cast<double*>(out + (r0 + r) * ld + col0 + (n < mq ? n : n - mq));
                     o[n < mq ? 0 : 1] = v;
                     if (pass == 0) {
@@ -536,7 +650,7 @@ cudaError_t prepare_oz() {
 cudaError_t launch_gram_oz(const double2* Y, const double2* W, long long rows, int ld, int col0, int m,
                            double2* partial, int nblk, double2* out, cudaStream_t st) {
     if (!oz_supported(m, m)) return cudaErrorInvalidValue;
-    const long long nchunks = (rows + oz::kChunk - 1) / oz::kChunk;
+    const long long nchunks = (rows + oz::kSub - 1) / oz::kSub;
     int nb = (int)std::min<long long>(std::min<long long>(nblk, oz::sm_count()), nchunks);
     if (nb < 1) nb = 1;
     const size_t smem = oz::GramSmem::bytes(m, W != nullptr);
@@ -550,7 +664,7 @@ cudaError_t launch_rotate_oz(const double2* Y, const double2* W, int ld, int col
                              const double* theta, double2* X, double2* HX, long long rows, double* res_partial,
                              int nblk, double* res_out, cudaStream_t st) {
     if (!oz_supported(m, mq)) return cudaErrorInvalidValue;
-    const long long ntiles = (rows + oz::kTile - 1) / oz::kTile;
+    const long long ntiles = (rows + oz::kSub - 1) / oz::kSub;
     int nb = (int)std::min<long long>(std::min<long long>(nblk, oz::sm_count()), ntiles);
     if (nb < 1) nb = 1;
     const bool want_res = theta && W && res_partial && res_out;
