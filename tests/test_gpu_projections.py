@@ -74,9 +74,10 @@ def test_gram_matches_extended_precision(khp, m):
         G, S = g.project(Y, W, method=method)
         assert _check_gram(G, Y, Y) <= 16 * EPS49, method
         assert _check_gram(S, Y, W) <= 16 * EPS49, method
+        # without W the kernel may pick longer exponent blocks: same accuracy bar
         Gonly, none = g.project(Y, None, method=method)
         assert none is None
-        assert np.array_equal(Gonly, G)
+        assert _check_gram(Gonly, Y, Y) <= 16 * EPS49, method
 
 
 def test_gram_column_scales_and_zero_columns(khp):
