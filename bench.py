@@ -139,6 +139,28 @@ def _fp64_peak_tflops(torch):
     return 2 * 8192 ** 3 / (best * 1e-3) / 1e12
 
 
+def _fp32_peak_tflops(torch):
+    """FP32 (non-tensor) peak of this GPU, measured: cuBLAS SGEMM 8192^3 with
+    TF32 off (best of 5)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    a = torch.randn(8192, 8192, dtype=torch.float32, device="cuda")
+    b = torch.randn(8192, 8192, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    best = 1e30
+    for _ in range(5):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        torch.matmul(a, b)
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e))
+    del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return 2 * 8192 ** 3 / (best * 1e-3) / 1e12
+
+
 def _crop(p):
     """The workload's physics on a bounded CROP-sized box (cpu baseline sample)."""
     nx, ny, nz = CROP
@@ -155,6 +177,21 @@ def _oracle_solve(q, n):
     t0 = time.perf_counter()
     w, v, res, cyc = eig.lowest_block_lanczos(H, n, tol=1e-10, return_residuals=True)
     return w, time.perf_counter() - t0
+
+
+def _arpack_baseline(q, n, full_unknowns):
+    """Second CPU baseline: SciPy eigsh (ARPACK, which='SA') on the oracle's
+    CSR matrix of the same crop; the paper compares its solver with ARPACK."""
+    from oracle import kp
+    from scipy.sparse.linalg import eigsh
+    H = kp.assemble(q).tocsr()
+    t0 = time.perf_counter()
+    eigsh(H, k=n, which="SA", tol=1e-10, return_eigenvectors=True)
+    t = time.perf_counter() - t0
+    scale = q.n_unknowns / full_unknowns
+    return {"value": n / t * scale, "unit": UNIT, "cores": os.cpu_count(), "kind": "scipy eigsh (ARPACK)",
+            "sample": (f"eigsh(k={n}, which='SA', tol=1e-10) on the oracle CSR of the {CROP[0]}x{CROP[1]}x"
+                       f"{CROP[2]} crop: {t:.2f} s, scaled by the unknowns ratio {scale:.4g}")}
 
 
 def _cpu_baseline(p, n, full_unknowns):
@@ -244,9 +281,19 @@ def run_ours(args, rank, world, local_rank):
     value = world * conv * args.steps / (ms_max * 1e-3)
     evals_plain = r.evals.copy()
 
+    # warm start: the previous solve's eigenvectors as the start block (the
+    # situation inside a Schroedinger-Poisson loop or a sweep)
+    ew0, ew1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ew0.record(stream)
+    rw = grid.eigensolve(**SOLVE_KW, warm_start=r.evecs)
+    ew1.record(stream)
+    torch.cuda.synchronize()
+    ms_warm = ew0.elapsed_time(ew1)
+
     peaks, peak_kind = _peaks()
     hbm = float(peaks["hbm_gbs"])
     fp64_peak = _fp64_peak_tflops(torch)
+    fp32_peak = _fp32_peak_tflops(torch)
 
     # dominant kernel: the fused FP64 Chebyshev stencil.  Its device time is
     # taken from CUDA events the library records on this stream around every
@@ -281,6 +328,9 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (4 x 849 MB blocks), no flush",
                        "iterations": st0["iterations"], "peaks": peak_kind},
             "roofline": roofline, "clocks": clocks,
+            "warm": {"value": rw.stats["converged"] / (ms_warm * 1e-3), "unit": UNIT, "ms_per_solve": ms_warm,
+                     "iterations": rw.stats["iterations"],
+                     "note": "warm start from the previous solve's eigenvectors (same fields)"},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
 
     # mixed precision to the same tolerance: every filter apply in FP32,
@@ -311,7 +361,10 @@ def run_ours(args, rank, world, local_rank):
                                 "unit": "GB/s", "frac": b32 / (t32 * 1e-3) / 1e9 / hbm,
                                 "frac_of_nominal_8tbs": b32 / (t32 * 1e-3) / 1e9 / 8000.0,
                                 "ms_per_launch": t32, "algorithmic_bytes_per_launch": b32,
-                                "tflops": sm["flops_per_pv"] * pv32 / (t32 * 1e-3) / 1e12}
+                                "tflops": sm["flops_per_pv"] * pv32 / (t32 * 1e-3) / 1e12,
+                                "fp32_peak_tflops": fp32_peak,
+                                "flop_frac": sm["flops_per_pv"] * pv32 / (t32 * 1e-3) / 1e12 / fp32_peak,
+                                "fp32_peak_source": "cuBLAS SGEMM 8192^3, TF32 off, measured in this run"}
 
     line["projections"] = _projections_bench(grid, p.n_unknowns, SOLVE_KW["block_m"], hbm, torch)
 
@@ -338,6 +391,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(p, n, p.n_unknowns)
+        line["cpu_baseline_arpack"] = _arpack_baseline(_crop(p), n, p.n_unknowns)
     if rank == 0:
         print(json.dumps(line), flush=True)
     grid.close()
