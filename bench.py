@@ -281,14 +281,20 @@ def run_ours(args, rank, world, local_rank):
     value = world * conv * args.steps / (ms_max * 1e-3)
     evals_plain = r.evals.copy()
 
-    # warm start: the previous solve's eigenvectors as the start block (the
-    # situation inside a Schroedinger-Poisson loop or a sweep)
+    # warm start: the previous solve's eigenvectors start the solve for a
+    # potential changed by 0.1 meV of smooth noise (one Schroedinger-Poisson
+    # update); the original fields are restored afterwards
+    lev = getattr(p, "levers", None)
+    alpha0 = None if lev is None else np.zeros(lev.shape[0])
+    dV = 1e-4 * inputs.smooth_noise(np.random.Generator(np.random.PCG64(99)), (p.nz, p.ny, p.nx))
+    grid.set_fields(p.V + dV, p.strain, lev, alpha0, p.B, p.gauge)
     ew0, ew1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ew0.record(stream)
     rw = grid.eigensolve(**SOLVE_KW, warm_start=r.evecs)
     ew1.record(stream)
     torch.cuda.synchronize()
     ms_warm = ew0.elapsed_time(ew1)
+    grid.set_fields(p.V, p.strain, lev, alpha0, p.B, p.gauge)
 
     peaks, peak_kind = _peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -330,7 +336,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "clocks": clocks,
             "warm": {"value": rw.stats["converged"] / (ms_warm * 1e-3), "unit": UNIT, "ms_per_solve": ms_warm,
                      "iterations": rw.stats["iterations"],
-                     "note": "warm start from the previous solve's eigenvectors (same fields)"},
+                     "note": "warm start from the previous solve's eigenvectors, V changed by 0.1 meV smooth noise"},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
 
     # mixed precision to the same tolerance: every filter apply in FP32,
