@@ -282,3 +282,19 @@ def assemble(prob, periodic: bool = False) -> sp.csr_matrix:
 def matvec(H, X):
     """Y = H X for a CSR H and a dense block X [N][m] (row-major)."""
     return np.asarray(H @ X)
+
+
+def assemble_h0(prob, periodic: bool = False) -> sp.csr_matrix:
+    """CSR matrix of the spin-independent single-particle Hamiltonian
+    H0 = H_DKK + V + H'_PB (Sec. II C, Eq. 6a), 3 Np x 3 Np, row index 3 p + o
+    (o = X, Y, Z).  Without spin-orbit coupling and magnetic field the 6x6
+    operator is the identity in spin times H0, so H0 is its spin-up block,
+    taken here from the 6x6 assembly with delta_so = 0 and B = 0."""
+    if np.any(np.asarray(prob.B, dtype=np.float64) != 0):
+        raise ValueError("H0 has no magnetic field: B must be zero")
+    mat = dict(prob.material)
+    mat["delta_so"] = 0.0
+    H6 = assemble(prob.with_(material=mat), periodic=periodic).tocsr()
+    Np = prob.nx * prob.ny * prob.nz
+    idx = (6 * np.arange(Np)[:, None] + np.arange(3)[None, :]).ravel()
+    return H6[idx][:, idx].tocsr()

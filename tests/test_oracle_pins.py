@@ -369,3 +369,83 @@ def test_hellmann_feynman_vs_finite_differences():
     for gi in range(3):
         fd = (loss(p.with_(V=p.V + d * p.levers[gi])) - loss(p.with_(V=p.V - d * p.levers[gi]))) / (2 * d)
         assert abs(fd - dA[gi]) < 1e-8 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------
+# the spin-independent H0 (Sec. II C, Eq. 6a): one 3x3-orbital block
+@pytest.mark.parametrize("shape,h", [((5, 4, 3), 0.7), ((6, 3, 4), 0.5)])
+def test_h0_box_closed_form(shape, h):
+    """gamma2 = gamma3 = 0, V = 0, no strain: the three orbitals decouple and
+    each is the particle in a box, so every box level appears three times."""
+    p = _box(*shape, h=h, strain=False, noise_mev=0.0)
+    p.material.update(gamma2=0.0, gamma3=0.0)
+    p.V[:] = 0.0
+    w = eig.all_eigenvalues_dense(kp.assemble_h0(p))
+    g1 = p.material["gamma1"]
+    nx, ny, nz = shape
+    ref = []
+    for kx in range(1, nx + 1):
+        for ky in range(1, ny + 1):
+            for kz in range(1, nz + 1):
+                E = C * g1 * sum(2 - 2 * np.cos(k * np.pi / (n + 1))
+                                 for k, n in ((kx, nx), (ky, ny), (kz, nz))) / h ** 2
+                ref += [E] * 3
+    assert np.abs(w - np.sort(ref)).max() < 1e-12
+
+
+def _dkk_textbook(K, g1, g2, g3):
+    """Dresselhaus-Kittel-Kip 3x3 (hole picture, crystal frame) with
+    L = g1 + 4 g2, M = g1 - 2 g2, N = 6 g3 and k_a k_b -> K[a, b]."""
+    L, M, N = g1 + 4 * g2, g1 - 2 * g2, 6 * g3
+    D = np.empty((3, 3))
+    for i in range(3):
+        D[i, i] = L * K[i, i] + M * (np.trace(K) - K[i, i])
+        for j in range(3):
+            if j != i:
+                D[i, j] = N * K[i, j]
+    return C * D
+
+
+@pytest.mark.parametrize("rot", ["identity", "device"])
+def test_h0_bulk_symbol_matches_textbook_dkk(rot):
+    """Periodic H0 applied to the three plane waves exp(i k.r) e_o gives the
+    textbook DKK matrix with the finite-difference symbols of k_a k_b."""
+    p = _box(6, 6, 6, h=0.5, strain=False, noise_mev=0.0, rot=rot)
+    p.V[:] = 0.0
+    H = kp.assemble_h0(p, periodic=True)
+    m, R = p.material, p.rot
+    iz, iy, ix = np.meshgrid(np.arange(6), np.arange(6), np.arange(6), indexing="ij")
+    for j in [(1, 0, 0), (1, 1, 1), (1, 2, 3), (2, -1, 1)]:
+        k = 2 * np.pi * np.array(j) / (6 * p.h)
+        ph = np.exp(1j * p.h * (k[0] * ix + k[1] * iy + k[2] * iz)).ravel()
+        X = np.zeros((3 * ph.size, 3), dtype=complex)
+        for o in range(3):
+            X[o::3, o] = ph
+        sym = (H @ X)[0:3, :] / ph[0]
+        Ks = np.empty((3, 3))
+        for a in range(3):
+            for b in range(3):
+                Ks[a, b] = ((2 - 2 * np.cos(k[a] * p.h)) if a == b
+                            else np.sin(k[a] * p.h) * np.sin(k[b] * p.h)) / p.h ** 2
+        Kc = R.T @ Ks @ R
+        e_or = np.linalg.eigvalsh(sym)
+        e_tb = np.linalg.eigvalsh(_dkk_textbook(Kc, m["gamma1"], m["gamma2"], m["gamma3"]))
+        assert np.abs(e_or - e_tb).max() < 1e-12
+
+
+def test_h0_is_the_spin_block_of_the_full_operator():
+    """delta_so = 0, B = 0: the 6x6 operator is 1_spin x H0 (both spin blocks
+    equal H0, no spin mixing) and H0 is real symmetric; a field is refused."""
+    p = _box(5, 4, 6, h=0.5, strain=True, rot="device")
+    p.material.update(delta_so=0.0)
+    H6 = kp.assemble(p).tocsr()
+    H0 = kp.assemble_h0(p)
+    Np = p.nx * p.ny * p.nz
+    up = (6 * np.arange(Np)[:, None] + np.arange(3)[None, :]).ravel()
+    dn = up + 3
+    assert abs(H6[up][:, up] - H0).max() == 0
+    assert abs(H6[dn][:, dn] - H0).max() == 0
+    assert abs(H6[up][:, dn]).max() == 0
+    assert abs(H0.imag).max() == 0 and abs(H0 - H0.T).max() < 1e-15 * abs(H0).max()
+    with pytest.raises(ValueError):
+        kp.assemble_h0(p.with_(B=(0.0, 0.0, 0.1)))
