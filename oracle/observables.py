@@ -21,11 +21,12 @@ from .kp import bir_pikus_tensor, rotate_tensor
 STRAIN_PAIRS = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
 
 
-def density(evecs, w):
-    """evecs: [6 Np][n] complex, w: [n] -> rho [Np]."""
+def density(evecs, w, bands=6):
+    """evecs: [bands Np][n] complex, w: [n] -> rho [Np] (bands = 6, or 3 for
+    the spin-independent H0)."""
     N, n = evecs.shape
-    P = np.abs(evecs) ** 2                         # [6 Np][n]
-    per_state = P.reshape(N // 6, 6, n).sum(axis=1)  # [Np][n]
+    P = np.abs(evecs) ** 2                         # [bands Np][n]
+    per_state = P.reshape(N // bands, bands, n).sum(axis=1)  # [Np][n]
     return per_state @ np.asarray(w, dtype=np.float64)
 
 
@@ -41,13 +42,14 @@ def strain_derivative_matrices(material, rot):
     return out
 
 
-def hf_gradients(evecs, g, material, rot, levers=None):
-    """Returns (dL/dV [Np], dL/deps [6][Np], dL/dalpha [n_gates] or None)."""
+def hf_gradients(evecs, g, material, rot, levers=None, bands=6):
+    """Returns (dL/dV [Np], dL/deps [6][Np], dL/dalpha [n_gates] or None);
+    bands = 3 for the spin-independent H0 (one spin)."""
     N, n = evecs.shape
-    Np = N // 6
+    Np = N // bands
     g = np.asarray(g, dtype=np.float64)
-    dV = density(evecs, g)
-    psi = evecs.reshape(Np, 2, 3, n)                # [p][s][o][i]
+    dV = density(evecs, g, bands)
+    psi = evecs.reshape(Np, bands // 3, 3, n)       # [p][s][o][i]
     dE = np.zeros((6, Np))
     for c, M in enumerate(strain_derivative_matrices(material, rot)):
         # sum_i g_i sum_s psi^dag M psi

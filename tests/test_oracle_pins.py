@@ -449,3 +449,39 @@ def test_h0_is_the_spin_block_of_the_full_operator():
     assert abs(H0.imag).max() == 0 and abs(H0 - H0.T).max() < 1e-15 * abs(H0).max()
     with pytest.raises(ValueError):
         kp.assemble_h0(p.with_(B=(0.0, 0.0, 0.1)))
+
+
+def test_h0_hellmann_feynman_vs_finite_differences():
+    """H0 (3 bands): dL/dV, dL/deps and dL/dalpha from the one-spin HF
+    formulas equal central differences of the dense H0 eigenvalues for
+    L = (E1 - E0) + sum_{i<6} E_i (H0 levels are not spin-degenerate)."""
+    p = _box(5, 4, 3, rot="device", strain=True, levers=2)
+    n = 6
+    g = np.ones(n)
+    g[0] -= 1.0
+    g[1] += 1.0
+
+    def loss(q):
+        w, _ = eig.lowest_dense(kp.assemble_h0(q), n)
+        return g @ w
+
+    w, v = eig.lowest_dense(kp.assemble_h0(p), n)
+    assert np.min(np.diff(w)) > 1e-6
+    dV, dEps, dA = observables.hf_gradients(v, g, p.material, p.rot, p.levers, bands=3)
+    rng = np.random.default_rng(12)
+    # close but non-degenerate levels: a step of 1e-6 keeps the O(d^2)
+    # truncation of the central difference below 1e-9
+    d = 1e-6
+    for _ in range(2):
+        u = rng.standard_normal(p.V.shape)
+        fd = (loss(p.with_(V=p.V + d * u)) - loss(p.with_(V=p.V - d * u))) / (2 * d)
+        assert abs(fd - dV @ u.ravel()) < 1e-8 * max(1.0, abs(fd))
+    for c in (0, 3, 5):
+        u = np.zeros_like(p.strain)
+        u[c] = rng.standard_normal(p.V.shape)
+        de = 1e-6
+        fd = (loss(p.with_(strain=p.strain + de * u)) - loss(p.with_(strain=p.strain - de * u))) / (2 * de)
+        assert abs(fd - (dEps * u.reshape(6, -1)).sum()) < 1e-6 * max(1.0, abs(fd))
+    for gi in range(2):
+        fd = (loss(p.with_(V=p.V + d * p.levers[gi])) - loss(p.with_(V=p.V - d * p.levers[gi]))) / (2 * d)
+        assert abs(fd - dA[gi]) < 1e-8 * max(1.0, abs(fd))
