@@ -148,6 +148,20 @@ khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
                            const khp_material* mat, const double rot[9],
                            const uint8_t* mask_dev, void* stream);
 
+/* Create a handle for the spin-independent single-particle Hamiltonian H0
+ * (Sec. II C, Eq. 6a): without spin-orbit coupling the 6x6 Hamiltonian splits
+ * into two identical 3x3 blocks (kinetic Luttinger term plus Bir-Pikus strain
+ * plus V, on the orbitals X, Y, Z), and only one is kept.  Its eigenstates
+ * form the orbital basis of the configuration-interaction step.
+ * Same arguments and errors as khp_create_grid; delta_so and kappa of the
+ * material are not used.  Every other entry point takes the handle with
+ * N = 3 Np unknowns: row index 3 p + o, o = X, Y, Z.
+ * khp_set_potential_strain_field rejects a nonzero B (INVALID_ARG): H0 has
+ * no magnetic field. */
+khp_status khp_create_grid_h0(khp_handle* out, int nx, int ny, int nz, double h_nm,
+                              const khp_material* mat, const double rot[9], const uint8_t* mask_dev,
+                              void* stream);
+
 /* Set the fields of H (Eq. 2b: V_DQD and the strain entering H_PB; plus B).
  *  V_dev       float64 [Np] hole potential energy [eV], added as +V
  *  strain_dev  float64 [6][Np] strain tensor (xx,yy,zz,yz,xz,xy) in the grid

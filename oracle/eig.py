@@ -29,7 +29,8 @@ import scipy.linalg as sla
 def _active(H, mask):
     if mask is None:
         return H, None
-    keep = np.repeat(mask.reshape(-1).astype(bool), 6)
+    bands = H.shape[0] // mask.size          # 6, or 3 for the spin-independent H0
+    keep = np.repeat(mask.reshape(-1).astype(bool), bands)
     idx = np.nonzero(keep)[0]
     return H[idx][:, idx], idx
 

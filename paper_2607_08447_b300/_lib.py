@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KH
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}
 
-EXPORTED = ["khp_create_grid", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
+EXPORTED = ["khp_create_grid", "khp_create_grid_h0", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
             "khp_eigensolve",
             "khp_eigensolve_batched",
             "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",

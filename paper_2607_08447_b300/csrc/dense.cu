@@ -583,14 +583,14 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
 }
 
 __global__ void random_fill_kernel(double2* X, long long rows, int ld, int col0, int ncol,
-                                   unsigned long long seed, const uint8_t* mask) {
+                                   unsigned long long seed, const uint8_t* mask, int bands) {
     const long long n = rows * ncol;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const long long r = i / ncol;
         const int c = (int)(i - r * ncol);
         double2 v = make_double2(0.0, 0.0);
-        if (!mask || mask[r / 6]) {
+        if (!mask || mask[r / bands]) {
             const unsigned long long h = splitmix64(seed * 0x632be59bd9b4e019ULL + (unsigned long long)(r * 64 + col0 + c));
             const double u1 = (double)(h >> 11) * (1.0 / 9007199254740992.0);
             const unsigned long long h2 = splitmix64(h);
@@ -602,8 +602,8 @@ __global__ void random_fill_kernel(double2* X, long long rows, int ld, int col0,
 }
 
 cudaError_t launch_random_fill(double2* X, long long rows, int ld, int col0, int ncol,
-                               unsigned long long seed, const uint8_t* mask, cudaStream_t st) {
-    random_fill_kernel<<<grid_for(rows * ncol), 256, 0, st>>>(X, rows, ld, col0, ncol, seed, mask);
+                               unsigned long long seed, const uint8_t* mask, cudaStream_t st, int bands) {
+    random_fill_kernel<<<grid_for(rows * ncol), 256, 0, st>>>(X, rows, ld, col0, ncol, seed, mask, bands);
     return cudaGetLastError();
 }
 

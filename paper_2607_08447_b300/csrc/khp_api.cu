@@ -196,8 +196,9 @@ void build_operator(khp_grid* g) {
                 if (o1 == o2) z += sig[k][s1][s2];
                 v += KHP_MU_B * g->B[k] * z;
             }
-            g->soz_re[b1][b2] = v.real();
-            g->soz_im[b1][b2] = v.imag();
+            // the spin-independent H0 has neither spin-orbit nor Zeeman term
+            g->soz_re[b1][b2] = g->nb == 3 ? 0.0 : v.real();
+            g->soz_im[b1][b2] = g->nb == 3 ? 0.0 : v.imag();
         }
 }
 
@@ -276,6 +277,7 @@ khp_status apply_op(khp_grid* g, const cx_t<R>* x, const cx_t<R>* prev, cx_t<R>*
     a.mask = g->mask;
     a.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
     a.src = nullptr;
+    a.nb = g->nb;
     fill_coeffs<R>(g, a.c, alpha);
     CK(launch_stencil<R>(a, g->stream));
     g->launches += 1;
@@ -330,8 +332,9 @@ bool finite_all(const double* v, int n) {
 // per-point field tables (on-site 3x3, link phases) shared by the m vectors.
 void op_counts(const khp_grid* g, int m, double* flops, double* b64, double* b32) {
     double f = 0.0;
-    for (int b1 = 0; b1 < 6; ++b1)
-        for (int b2 = 0; b2 < 6; ++b2) {
+    const int nb = g->nb;
+    for (int b1 = 0; b1 < nb; ++b1)
+        for (int b2 = 0; b2 < nb; ++b2) {
             const int s1 = b1 / 3, o1 = b1 % 3, s2 = b2 / 3, o2 = b2 % 3;
             const bool cplx_nz = g->soz_im[b1][b2] != 0.0;
             bool nz = g->soz_re[b1][b2] != 0.0 || cplx_nz;
@@ -351,14 +354,14 @@ void op_counts(const khp_grid* g, int m, double* flops, double* b64, double* b32
         int nz = 0;
         for (int k = 0; k < 3; ++k) nz += h[k] != 0.0;
         for (int k = 3; k < 6; ++k) nz += 2 * (h[k] != 0.0);
-        // two links (+/-), two spins; complex entries when B != 0
-        f += 2.0 * 2.0 * nz * (g->has_phase ? 8.0 : 4.0);
+        // two links (+/-), nb / 3 spins; complex entries when B != 0
+        f += 2.0 * (nb / 3) * nz * (g->has_phase ? 8.0 : 4.0);
     }
-    f += 6 * 10.0;
+    f += nb * 10.0;
     *flops = f;
     const double fields64 = 6 * 8.0 + (g->has_phase ? 18 * 16.0 : 0.0);
-    *b64 = 3 * 96.0 + fields64 / m;
-    *b32 = 3 * 48.0 + 0.5 * fields64 / m;
+    *b64 = 3 * 16.0 * nb + fields64 / m;
+    *b32 = 3 * 8.0 * nb + 0.5 * fields64 / m;
 }
 
 // Upper bound of the spectrum for the filter interval: k-step Lanczos from a
@@ -373,7 +376,7 @@ khp_status lanczos_issue(khp_grid* g, int k, unsigned long long seed) {
     double2* Cc = g->blk64[2];
     double2* Nn = g->blk64[3];
     const long long n = g->n;
-    CK(launch_random_fill(Cc, n, 1, 0, 1, seed ^ 0x5bd1e995ULL, g->mask, g->stream));
+    CK(launch_random_fill(Cc, n, 1, 0, 1, seed ^ 0x5bd1e995ULL, g->mask, g->stream, g->nb));
     CK(lanczos_norm(Cc, n, partial, beta, g->stream));
     CK(lanczos_scale(Cc, Cc, beta, n, g->stream));
     g->launches += 4;
@@ -420,9 +423,9 @@ int khp_version(void) { return 100; }
 
 const char* khp_last_error(void) { return g_err.c_str(); }
 
-khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
-                           const khp_material* mat, const double rot[9], const uint8_t* mask_dev,
-                           void* stream) {
+static khp_status create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
+                              const khp_material* mat, const double rot[9], const uint8_t* mask_dev,
+                              void* stream, int nb) {
     g_err.clear();
     if (!out) return fail(KHP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -445,7 +448,7 @@ khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
     }
     khp_grid* g = new khp_grid();
     std::memset(g, 0, sizeof(khp_grid));
-    g->nx = nx; g->ny = ny; g->nz = nz; g->np = np; g->n = 6 * np; g->h = h_nm;
+    g->nx = nx; g->ny = ny; g->nz = nz; g->np = np; g->nb = nb; g->n = (long long)nb * np; g->h = h_nm;
     g->mat = *mat;
     std::memcpy(g->rot, R, sizeof(R));
     g->stream = (cudaStream_t)stream;
@@ -473,6 +476,18 @@ khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
     }
     *out = g;
     return KHP_OK;
+}
+
+khp_status khp_create_grid(khp_handle* out, int nx, int ny, int nz, double h_nm,
+                           const khp_material* mat, const double rot[9], const uint8_t* mask_dev,
+                           void* stream) {
+    return create_grid(out, nx, ny, nz, h_nm, mat, rot, mask_dev, stream, 6);
+}
+
+khp_status khp_create_grid_h0(khp_handle* out, int nx, int ny, int nz, double h_nm,
+                              const khp_material* mat, const double rot[9], const uint8_t* mask_dev,
+                              void* stream) {
+    return create_grid(out, nx, ny, nz, h_nm, mat, rot, mask_dev, stream, 3);
 }
 
 khp_status khp_destroy(khp_handle g) {
@@ -510,6 +525,8 @@ khp_status khp_set_potential_strain_field(khp_handle g, const double* V_dev, con
     if (B_host) {
         if (!finite_all(B_host, 3)) return fail(KHP_ERR_INVALID_ARG, "B non-finite");
         for (int k = 0; k < 3; ++k) B[k] = B_host[k];
+        if (g->nb == 3 && (B[0] != 0.0 || B[1] != 0.0 || B[2] != 0.0))
+            return fail(KHP_ERR_INVALID_ARG, "the spin-independent H0 has no magnetic field: B must be zero");
     }
     for (int k = 0; k < 3; ++k) g->B[k] = B[k];
     g->gauge = gauge;
@@ -774,7 +791,7 @@ struct Solve {
         trace = tr && tr[0] == '1';
         double2** B = g->blk64;
         CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
-        CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, o.seed, g->mask, g->stream));
+        CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, o.seed, g->mask, g->stream, g->nb));
         g->launches += 1;
         if (o.warm_start_dev)
             CK(cudaMemcpy2DAsync(B[ib[0]], sizeof(double2) * m, o.warm_start_dev, sizeof(double2) * o.warm_cols,
@@ -965,6 +982,7 @@ struct Solve {
             sa.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
             sa.mask = g->mask;
             sa.src = R32;
+            sa.nb = g->nb;
             for (int c = 0; c < 64; ++c) sa.src_coef[c] = (c >= nlock && c < m) ? (float)(al * Dcur[c]) : 0.f;
             fill_coeffs<float>(g, sa.c, al);
             CK(launch_stencil<float>(sa, g->stream));
@@ -1246,7 +1264,7 @@ extern "C" khp_status khp_density(khp_handle g, const void* evecs_dev, int n, co
     if (!evecs_dev || !w_host || !rho_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
     if (n < 1 || n > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "n out of range 1..64");
     if (!finite_all(w_host, n)) return fail(KHP_ERR_INVALID_ARG, "weights non-finite");
-    CK(launch_density((const double2*)evecs_dev, g->np, n, w_host, g->mask, rho_dev, g->stream));
+    CK(launch_density((const double2*)evecs_dev, g->np, n, w_host, g->mask, rho_dev, g->stream, g->nb));
     return KHP_OK;
 }
 
@@ -1277,7 +1295,7 @@ extern "C" khp_status khp_eigs_backward(khp_handle g, const void* evecs_dev, con
     khp_status s = KHP_OK;
     cudaError_t e = launch_backward((const double2*)evecs_dev, g->np, n, dLdE_host, g->De, dLdV_dev,
                                     dLdstrain_dev, n_gates ? levers_dev : nullptr, n_gates, partial, nblk,
-                                    dalpha, g->stream);
+                                    dalpha, g->stream, g->nb);
     if (e == cudaSuccess && n_gates > 0) {
         e = cudaMemcpyAsync(g->host_pinned, dalpha, sizeof(double) * n_gates, cudaMemcpyDeviceToHost, g->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);

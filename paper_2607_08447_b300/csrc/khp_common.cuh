@@ -94,6 +94,7 @@ struct StencilArgs {
     const cx_t<R>* src;     // same layout as y, or null
     R src_coef[64];
     Coeffs<R> c;
+    int nb;                 // bands per point: 6, or 3 for the spin-independent H0
 };
 
 }  // namespace khp
@@ -101,8 +102,9 @@ struct StencilArgs {
 // ------------------------------------------------------------------ handle
 struct khp_grid {
     int nx, ny, nz;
+    int nb;                // bands per point: 6 (k.p with spin-orbit) or 3 (spin-independent H0)
     long long np;          // points
-    long long n;           // unknowns = 6 np
+    long long n;           // unknowns = nb np
     double h;
     khp_material mat;
     double rot[9];

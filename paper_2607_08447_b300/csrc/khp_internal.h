@@ -60,7 +60,7 @@ cudaError_t launch_convert_d2f(const double2* src, float2* dst, long long rows, 
 cudaError_t launch_convert_f2d(const float2* src, double2* dst, long long rows, int ld, int col0, int ncol,
                                cudaStream_t st);
 cudaError_t launch_random_fill(double2* X, long long rows, int ld, int col0, int ncol,
-                               unsigned long long seed, const uint8_t* mask, cudaStream_t st);
+                               unsigned long long seed, const uint8_t* mask, cudaStream_t st, int bands = 6);
 
 // Lanczos pieces (dense.cu); scalars live in device memory
 cudaError_t lanczos_dot(const double2* a, const double2* b, long long n, double* partial, double* out,
@@ -82,11 +82,11 @@ cudaError_t launch_dc_combine(const double2* X, const double2* HX, const float2*
 
 // observables.cu
 cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,
-                           const uint8_t* mask, double* rho, cudaStream_t st);
+                           const uint8_t* mask, double* rho, cudaStream_t st, int nb = 6);
 cudaError_t launch_backward(const double2* psi, long long np, int n, const double* g,
                             const double (*De)[6], double* dV, double* dEps,
                             const double* levers, int ng, double* partial, int nblk,
-                            double* dalpha_dev, cudaStream_t st);
+                            double* dalpha_dev, cudaStream_t st, int nb = 6);
 
 }  // namespace khp
 

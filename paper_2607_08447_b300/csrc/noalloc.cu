@@ -90,7 +90,7 @@ extern "C" khp_status khp_eigs_backward_noalloc(khp_handle g, const void* evecs_
         double* dalpha = scratch + KHP_NOALLOC_BLOCKS * KHP_MAX_GATES;
         e = launch_backward((const double2*)evecs_dev, g->np, n, dLdE_host, g->De, dLdV_dev, dLdstrain_dev,
                             n_gates ? levers_dev : nullptr, n_gates, partial, KHP_NOALLOC_BLOCKS, dalpha,
-                            g->stream);
+                            g->stream, g->nb);
         if (e == cudaSuccess && n_gates > 0) {
             e = cudaMemcpyAsync(dLdalpha_host, dalpha, sizeof(double) * n_gates, cudaMemcpyDeviceToHost,
                                 g->stream);

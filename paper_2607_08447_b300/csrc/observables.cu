@@ -14,6 +14,7 @@ struct DensityArgs {
     const double2* psi;
     long long np;
     int n;
+    int nb;                // bands per point (6, or 3 for the spin-independent H0)
     double w[KHP_MAX_M];
     double* rho;
 };
@@ -21,12 +22,11 @@ struct DensityArgs {
 __global__ void density_kernel(const DensityArgs a) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
-    const double2* row = a.psi + p * 6 * a.n;
+    const double2* row = a.psi + p * a.nb * a.n;
     double rho = 0.0;
     for (int i = 0; i < a.n; ++i) {
         double s = 0.0;
-#pragma unroll
-        for (int b = 0; b < 6; ++b) {
+        for (int b = 0; b < a.nb; ++b) {
             const double2 v = row[b * a.n + i];
             s += v.x * v.x + v.y * v.y;
         }
@@ -36,9 +36,9 @@ __global__ void density_kernel(const DensityArgs a) {
 }
 
 cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,
-                           const uint8_t* /*mask*/, double* rho, cudaStream_t st) {
+                           const uint8_t* /*mask*/, double* rho, cudaStream_t st, int nb) {
     DensityArgs a;
-    a.psi = psi; a.np = np; a.n = n; a.rho = rho;
+    a.psi = psi; a.np = np; a.n = n; a.nb = nb; a.rho = rho;
     for (int i = 0; i < KHP_MAX_M; ++i) a.w[i] = i < n ? w[i] : 0.0;
     density_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
@@ -48,6 +48,7 @@ struct BackArgs {
     const double2* psi;
     long long np;
     int n;
+    int nb;                // bands per point (6, or 3 for the spin-independent H0)
     double g[KHP_MAX_M];
     double De[6][6];       // sym 3x3 (00,11,22,12,02,01) per strain component
     double* dV;
@@ -75,13 +76,14 @@ __global__ void backward_kernel(const BackArgs a) {
     double lev[KHP_MAX_GATES];
     for (int g = 0; g < KHP_MAX_GATES; ++g) lev[g] = 0.0;
     for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const double2* row = a.psi + p * 6 * a.n;
+        const double2* row = a.psi + p * a.nb * a.n;
         double dv = 0.0;
         double de[6] = {0, 0, 0, 0, 0, 0};
+        const bool two = a.nb == 6;
         for (int i = 0; i < a.n; ++i) {
             double2 x[6];
 #pragma unroll
-            for (int b = 0; b < 6; ++b) x[b] = row[b * a.n + i];
+            for (int b = 0; b < 6; ++b) x[b] = (b < 3 || two) ? row[b * a.n + i] : make_double2(0.0, 0.0);
             double s = 0.0;
 #pragma unroll
             for (int b = 0; b < 6; ++b) s += x[b].x * x[b].x + x[b].y * x[b].y;
@@ -119,9 +121,9 @@ __global__ void lever_finish(const double* partial, int nblk, int ng, double* ou
 
 cudaError_t launch_backward(const double2* psi, long long np, int n, const double* g,
                             const double (*De)[6], double* dV, double* dEps, const double* levers,
-                            int ng, double* partial, int nblk, double* dalpha_dev, cudaStream_t st) {
+                            int ng, double* partial, int nblk, double* dalpha_dev, cudaStream_t st, int nb) {
     BackArgs a;
-    a.psi = psi; a.np = np; a.n = n;
+    a.psi = psi; a.np = np; a.n = n; a.nb = nb;
     for (int i = 0; i < KHP_MAX_M; ++i) a.g[i] = i < n ? g[i] : 0.0;
     for (int c = 0; c < 6; ++c)
         for (int k = 0; k < 6; ++k) a.De[c][k] = De[c][k];

@@ -38,15 +38,15 @@ __device__ __forceinline__ void store_vg(cx_t<R>* p, const cx_t<R> (&v)[VG]) {
     }
 }
 
-// acc[s*3 + i][v] (+)= sum_j M_ij x[s*3 + j][v] for both spins, M real
+// acc[s*3 + i][v] (+)= sum_j M_ij x[s*3 + j][v] for the NS spins, M real
 // symmetric (00,11,22,12,02,01); entries whose bit is clear in nz are
 // structurally zero and skipped (warp-uniform branches)
-template <typename R, int VG, bool INIT>
+template <typename R, int VG, bool INIT, int NS = 2>
 __device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], unsigned nz,
                                      const cx_t<R> (&x)[6][VG]) {
     if (INIT) {
 #pragma unroll
-        for (int b = 0; b < 6; ++b)
+        for (int b = 0; b < 3 * NS; ++b)
 #pragma unroll
             for (int v = 0; v < VG; ++v) acc[b][v] = mk<R>(R(0), R(0));
     }
@@ -55,7 +55,7 @@ __device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], uns
         if (nz & (1u << k)) {
             const R m = M[k];
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < NS; ++s)
 #pragma unroll
                 for (int v = 0; v < VG; ++v) {
                     acc[3 * s + k][v].x = fma(m, x[3 * s + k][v].x, acc[3 * s + k][v].x);
@@ -71,7 +71,7 @@ __device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], uns
             const int j = k == 5 ? 1 : 2;
             const R m = M[k];
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < NS; ++s)
 #pragma unroll
                 for (int v = 0; v < VG; ++v) {
                     acc[3 * s + i][v].x = fma(m, x[3 * s + j][v].x, acc[3 * s + i][v].x);
@@ -93,11 +93,11 @@ __host__ __device__ constexpr unsigned need_of(unsigned nz) {
 // acc[3s+i] += (mc * u[3s+j] + i-part) for entry (i, j):
 //   PH_SYM pairs:  m * (c u - i s v)  with u = x+ + x-, v = x+ - x-
 //   other pairs:   m * u   (mc = m, ms = 0: v unused)
-template <typename R, int VG, bool SYMPH>
+template <typename R, int VG, bool SYMPH, int NS = 2>
 __device__ __forceinline__ void pair_entry(cx_t<R> (&acc)[6][VG], int i, int j, R mc, R ms,
                                            const cx_t<R> (&u)[6][VG], const cx_t<R> (&v)[6][VG]) {
 #pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
+    for (int sp = 0; sp < NS; ++sp)
 #pragma unroll
         for (int w = 0; w < VG; ++w) {
             cx_t<R>& A = acc[3 * sp + i][w];
@@ -122,9 +122,12 @@ __host__ __device__ constexpr unsigned cubic_nz(int d) {
     return d < 3 ? 7u : (d < 5 ? 32u : (d < 7 ? 16u : 8u));
 }
 
-template <typename R, int VG, int PH, bool MASK, bool CUBIC, bool SRC = false, int LD = 0, int MINB = 1>
+// NB: bands per point, 6 (the spin-orbit k.p Hamiltonian) or 3 (the
+// spin-independent H0 block: one spin, no spin-orbit or Zeeman term)
+template <typename R, int VG, int PH, bool MASK, bool CUBIC, bool SRC = false, int LD = 0, int MINB = 1, int NB = 6>
 __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R> a) {
     using C = cx_t<R>;
+    constexpr int NS = NB / 3;
     const int G = a.ncol / VG;
     const long long np = (long long)a.nx * a.ny * a.nz;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,13 +139,13 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
     const int iy = (int)(q % a.ny);
     const int iz = (int)(q / a.ny);
     const int ld = LD ? LD : a.ld;              // complex elements per row (compile-time when LD > 0)
-    const long long ps = 6LL * ld;              // complex elements per point
+    const long long ps = (long long)NB * ld;              // complex elements per point
     const int col = a.col0 + g * VG;
     C* yp = a.y + p * ps + col;
 
     if (MASK && a.mask[p] == 0) {
 #pragma unroll
-        for (int b = 0; b < 6; ++b) {
+        for (int b = 0; b < NB; ++b) {
             C z[VG];
 #pragma unroll
             for (int v = 0; v < VG; ++v) z[v] = mk<R>(R(0), R(0));
@@ -156,16 +159,16 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
     {
         C xs[6][VG];
 #pragma unroll
-        for (int b = 0; b < 6; ++b) load_vg<R, VG>(xs[b], xp + b * ld);
+        for (int b = 0; b < NB; ++b) load_vg<R, VG>(xs[b], xp + b * ld);
         R o[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) o[k] = a.alpha * __ldg(a.onsite + p * 6 + k);
 #pragma unroll
         for (int k = 0; k < 3; ++k) o[k] += a.beta;
-        sym3<R, VG, true>(acc, o, a.c.onsite_nz | 7u, xs);
+        sym3<R, VG, true, NS>(acc, o, a.c.onsite_nz | 7u, xs);
         // spin-orbit + Zeeman (alpha-scaled): constant complex 6x6, zero parts skipped
 #pragma unroll
-        for (int b = 0; b < 6; ++b) {
+        for (int b = 0; b < (NB == 6 ? 6 : 0); ++b) {
             const unsigned rowm = a.c.soz_nz[b];
 #pragma unroll
             for (int b2 = 0; b2 < 6; ++b2) {
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
             for (int o = 0; o < 3; ++o) {
                 if (!(need & (1u << o))) continue;
 #pragma unroll
-                for (int sp = 0; sp < 2; ++sp) {
+                for (int sp = 0; sp < NS; ++sp) {
                     const int b = 3 * sp + o;
                     C xpv[VG], xmv[VG];
                     if (okp) load_vg<R, VG>(xpv, xpp + b * ld);
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
             for (int o = 0; o < 3; ++o) {
                 if (!(need & (1u << o))) continue;
 #pragma unroll
-                for (int sp = 0; sp < 2; ++sp) {
+                for (int sp = 0; sp < NS; ++sp) {
                     const int b = 3 * sp + o;
                     C xpv[VG], xmv[VG];
                     if (okp) load_vg<R, VG>(xpv, xpp + b * ld);
@@ -284,11 +287,11 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
             const int j = k < 3 ? k : (k == 5 ? 1 : 2);
             if (PH == PH_SYM && ph) {
                 const R mc = m * cth, ms = m * sth;
-                pair_entry<R, VG, true>(acc, i, j, mc, ms, u, w);
-                if (k >= 3) pair_entry<R, VG, true>(acc, j, i, mc, ms, u, w);
+                pair_entry<R, VG, true, NS>(acc, i, j, mc, ms, u, w);
+                if (k >= 3) pair_entry<R, VG, true, NS>(acc, j, i, mc, ms, u, w);
             } else {
-                pair_entry<R, VG, false>(acc, i, j, m, R(0), u, w);
-                if (k >= 3) pair_entry<R, VG, false>(acc, j, i, m, R(0), u, w);
+                pair_entry<R, VG, false, NS>(acc, i, j, m, R(0), u, w);
+                if (k >= 3) pair_entry<R, VG, false, NS>(acc, j, i, m, R(0), u, w);
             }
         }
     }
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
         for (int v = 0; v < VG; ++v) sc[v] = a.src_coef[col + v];
     }
 #pragma unroll
-    for (int b = 0; b < 6; ++b) {
+    for (int b = 0; b < NB; ++b) {
         C out[VG];
 #pragma unroll
         for (int v = 0; v < VG; ++v) out[v] = acc[b][v];
@@ -331,6 +334,32 @@ template <typename R, int VG, int PH>
 static cudaError_t launch_ph(const StencilArgs<R>& a, unsigned blocks, cudaStream_t st) {
     bool cubic = true;
     for (int d = 0; d < 9; ++d) cubic = cubic && (a.c.hop_nz[d] & ~cubic_nz(d)) == 0;
+    if (a.nb == 3) {
+        // spin-independent H0: no magnetic field, so no Peierls phases
+        if constexpr (PH == PH_NONE) {
+            if (a.src) {
+                if constexpr (sizeof(R) == 8) return cudaErrorNotSupported;
+                if (a.mask) {
+                    if (cubic) stencil_kernel<R, VG, PH, true, true, true, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                    else stencil_kernel<R, VG, PH, true, false, true, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                } else {
+                    if (cubic) stencil_kernel<R, VG, PH, false, true, true, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                    else stencil_kernel<R, VG, PH, false, false, true, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                }
+            } else {
+                if (a.mask) {
+                    if (cubic) stencil_kernel<R, VG, PH, true, true, false, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                    else stencil_kernel<R, VG, PH, true, false, false, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                } else {
+                    if (cubic) stencil_kernel<R, VG, PH, false, true, false, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                    else stencil_kernel<R, VG, PH, false, false, false, 0, 1, 3><<<blocks, 256, 0, st>>>(a);
+                }
+            }
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
     if constexpr (VG == 2) {
         if (cubic && !a.mask) {
             // hot path: row length known at compile time (immediate band offsets)

@@ -42,32 +42,40 @@ class SolveResult:
 class KPGrid:
     """One grid + Hamiltonian on one CUDA device (see include/khp.h)."""
 
-    def __init__(self, nx, ny, nz, h, material, rot=None, mask=None, device="cuda", stream=None):
+    def __init__(self, nx, ny, nz, h, material, rot=None, mask=None, device="cuda", stream=None, bands=6):
+        """bands = 6: the k.p hole Hamiltonian with spin-orbit coupling;
+        bands = 3: the spin-independent H0 block (no spin-orbit, B = 0)."""
+        if bands not in (6, 3):
+            raise ValueError("bands must be 6 or 3")
         self.lib = _lib.load()
         self.device = torch.device(device)
         self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
         self.np_ = self.nx * self.ny * self.nz
-        self.N = 6 * self.np_
+        self.bands = bands
+        self.N = bands * self.np_
         mat = _lib.Material(*[float(material[k]) for k in _MAT_KEYS])
         R = None if rot is None else np.ascontiguousarray(np.asarray(rot, dtype=np.float64).reshape(9))
         self._mask = None if mask is None else _dev(np.asarray(mask, dtype=np.uint8).reshape(-1), torch.uint8, self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h_ = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _lib.check(self.lib.khp_create_grid(ctypes.byref(h_), self.nx, self.ny, self.nz, self.h,
-                                                ctypes.byref(mat), _lib.dptr(R), _ptr(self._mask),
-                                                ctypes.c_void_p(self.stream.cuda_stream)))
+            create = self.lib.khp_create_grid if bands == 6 else self.lib.khp_create_grid_h0
+            _lib.check(create(ctypes.byref(h_), self.nx, self.ny, self.nz, self.h,
+                              ctypes.byref(mat), _lib.dptr(R), _ptr(self._mask),
+                              ctypes.c_void_p(self.stream.cuda_stream)))
         self.handle = h_
         self.material = dict(material)
         self.rot = R
 
     @classmethod
-    def from_problem(cls, p, device="cuda", with_levers=True):
+    def from_problem(cls, p, device="cuda", with_levers=True, bands=6):
         """Grid + fields from any object with the attributes nx, ny, nz, h,
-        material, rot, mask, V, strain, B, gauge and (optionally) levers."""
-        g = cls(p.nx, p.ny, p.nz, p.h, p.material, p.rot, getattr(p, "mask", None), device=device)
+        material, rot, mask, V, strain, B, gauge and (optionally) levers.
+        bands = 3 builds the spin-independent H0 (the field B is dropped)."""
+        g = cls(p.nx, p.ny, p.nz, p.h, p.material, p.rot, getattr(p, "mask", None), device=device, bands=bands)
         lev = getattr(p, "levers", None) if with_levers else None
-        g.set_fields(p.V, p.strain, lev, None if lev is None else np.zeros(lev.shape[0]), p.B, p.gauge)
+        B = p.B if bands == 6 else (0.0, 0.0, 0.0)
+        g.set_fields(p.V, p.strain, lev, None if lev is None else np.zeros(lev.shape[0]), B, p.gauge)
         return g
 
     # ------------------------------------------------------------------
