@@ -373,6 +373,7 @@ def run_ours(args, rank, world, local_rank):
                                 "fp32_peak_source": "cuBLAS SGEMM 8192^3, TF32 off, measured in this run"}
 
     line["projections"] = _projections_bench(grid, p.n_unknowns, SOLVE_KW["block_m"], hbm, torch)
+    line["h0"] = _h0_bench(p, dev, torch, khp)
 
     # end to end through host buffers: H2D of V and strain, solve, D2H of
     # eigenvalues and eigenvectors, every step
@@ -401,6 +402,31 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line), flush=True)
     grid.close()
+
+
+def _h0_bench(p, dev, torch, khp):
+    """The spin-independent H0 (three bands, B = 0) on the same grid and
+    fields: lowest 16 states, plain FP64 and defect-corrected FP32 filter,
+    one cold solve each after one warm-up."""
+    g = khp.KPGrid.from_problem(p, device=dev, bands=3)
+    out = {"unknowns": 3 * p.n_points}
+    for name, kw in (("fp64", dict(SOLVE_KW)), ("mixed", dict(SOLVE_KW, precision=2, degree=MIXED_DEGREE))):
+        g.eigensolve(**kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(g.stream)
+        r = g.eigensolve(**kw)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": r.stats["converged"] / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms,
+                     "iterations": r.stats["iterations"], "max_residual": r.stats["max_residual"]}
+        if name == "fp64":
+            e64 = r.evals
+        else:
+            out[name]["max_abs_dE_vs_fp64_ev"] = float(np.abs(r.evals - e64).max())
+    g.close()
+    return out
 
 
 def _projections_bench(grid, N, m, hbm, torch):
