@@ -77,6 +77,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     vp, i, d, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
     lib.khp_create_grid.argtypes = [ctypes.POINTER(vp), i, i, i, d, ctypes.POINTER(Material), dp, vp, vp]
+    lib.khp_create_grid_h0.argtypes = [ctypes.POINTER(vp), i, i, i, d, ctypes.POINTER(Material), dp, vp, vp]
+    lib.khp_project.argtypes = [vp, vp, vp, i, i, vp, vp]
+    lib.khp_rotate.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
     lib.khp_set_potential_strain_field.argtypes = [vp, vp, vp, vp, dp, i, dp, i]
     lib.khp_apply.argtypes = [vp, vp, vp, i, i]
     lib.khp_eigensolve.argtypes = [vp, ctypes.POINTER(SolverOpts), dp, vp, dp, ctypes.POINTER(Stats)]
