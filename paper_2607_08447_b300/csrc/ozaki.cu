@@ -42,7 +42,6 @@ constexpr int kMaxM = 32;       // complex columns (real width 64)
 constexpr int kSub = 64;        // rows per digit tile (Gram sub-chunk, rotation tile)
 constexpr int kBlkSub = 4;      // Gram: sub-chunks per exponent block (256 rows)
 constexpr int kGramWarps = 12;
-constexpr int kRotWarps = 8;
 
 __host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
 // digit-row stride in BF16 elements: an odd number of 16-B units, so the
@@ -403,7 +402,8 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
 // [Re X | Im X] = [Re Y | Im Y] Qr with Qr = [[Re Q, Im Q], [-Im Q, Re Q]]
 // (2m x 2mq).  Digits: per row of Y (and of W) over its 2m reals, per
 // column of Qr over its 2m entries.  A CTA walks tiles of 64 rows; warp w
-// owns m-tile w % 4 and n-group w / 4 (NTW n-tiles of 8 columns).  The
+// owns m-tile w % 4 and n-group w / 4 (NTW n-tiles of 8 columns), so the
+// CTA has 4 ceil(NT / NTW) warps.  The
 // tile's digits are taken before any of its rows is written, so X may
 // alias Y and HX may alias W.  Level sums have K = 2m <= 64 terms: below
 // 2^22, converted to integers without the cvt pipe.
@@ -416,8 +416,8 @@ struct RotSmem {
     }
 };
 
-template <int NTW>
-__global__ void __launch_bounds__(kRotWarps * 32, 1)
+template <int NTW, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
     rotate_oz_kernel(const double2* Y, const double2* W, int ld, int col0, int m, const double2* __restrict__ Q,
                      int mq, const double* __restrict__ theta, double2* X, double2* HX, long long rows,
                      double* __restrict__ res_partial) {
@@ -476,9 +476,10 @@ __global__ void __launch_bounds__(kRotWarps * 32, 1)
         const long long r0 = tl * kSub;
         const int nr = (int)(rows - r0 < kSub ? rows - r0 : kSub);
         __syncthreads();   // Qd ready / previous tile consumed
-        // row digits: 4 threads per row, row exponent by shuffles
-        {
-            const int r = tid >> 2, qd = tid & 3;
+        // row digits: 4 threads per row (the first 256 threads, or every
+        // thread twice for a 128-thread CTA), row exponent by shuffles
+        for (int rt = tid; rt < 4 * kSub; rt += nthr) {
+            const int r = rt >> 2, qd = rt & 3;
             const bool ok = r < nr;
             for (int pass = 0; pass < (hasW ? 2 : 1); ++pass) {
                 const double2* src = (pass ? W : Y) + (r0 + r) * ld + col0;
@@ -640,10 +641,8 @@ cudaError_t prepare_oz() {
     const int g = (int)oz::GramSmem::bytes(oz::kMaxM, true);
     const int r = (int)oz::RotSmem::bytes(oz::kMaxM, oz::kMaxM);
     cudaError_t e = cudaFuncSetAttribute(oz::gram_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, g);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz::rotate_oz_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, r);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz::rotate_oz_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, r);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz::rotate_oz_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, r);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz::rotate_oz_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, r);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz::rotate_oz_kernel<2, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, r);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(oz::rotate_oz_kernel<4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, r);
     return e;
 }
 
@@ -670,13 +669,15 @@ cudaError_t launch_rotate_oz(const double2* Y, const double2* W, int ld, int col
     const bool want_res = theta && W && res_partial && res_out;
     const size_t smem = oz::RotSmem::bytes(m, mq);
     const int NT = oz::round16(2 * mq) / 8;
-    const int ntw = (NT + 1) / 2;
     double* rp = want_res ? res_partial : nullptr;
     const double* th = want_res ? theta : nullptr;
-    if (ntw <= 1) oz::rotate_oz_kernel<1><<<nb, oz::kRotWarps * 32, smem, st>>>(Y, W, ld, col0, m, Q, mq, th, X, HX, rows, rp);
-    else if (ntw == 2) oz::rotate_oz_kernel<2><<<nb, oz::kRotWarps * 32, smem, st>>>(Y, W, ld, col0, m, Q, mq, th, X, HX, rows, rp);
-    else if (ntw == 3) oz::rotate_oz_kernel<3><<<nb, oz::kRotWarps * 32, smem, st>>>(Y, W, ld, col0, m, Q, mq, th, X, HX, rows, rp);
-    else oz::rotate_oz_kernel<4><<<nb, oz::kRotWarps * 32, smem, st>>>(Y, W, ld, col0, m, Q, mq, th, X, HX, rows, rp);
+    // two n-tiles per warp up to NT = 6 (4, 8 or 12 warps); four beyond
+    if (NT <= 6) {
+        const int threads = 128 * ((NT + 1) / 2);
+        oz::rotate_oz_kernel<2, 384><<<nb, threads, smem, st>>>(Y, W, ld, col0, m, Q, mq, th, X, HX, rows, rp);
+    } else {
+        oz::rotate_oz_kernel<4, 256><<<nb, 128 * ((NT + 3) / 4), smem, st>>>(Y, W, ld, col0, m, Q, mq, th, X, HX, rows, rp);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !want_res) return e;
     return launch_residual_finish(res_partial, nb, mq, res_out, st);
