@@ -40,7 +40,7 @@ MIXED_DEGREE = 200   # defect-corrected FP32 filter (precision 2)
 CROP = (32, 12, 12)
 # DRAM bytes per point-vector of the FP64 fused stencil launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum = 2.519 GB + 0.829 GB over
-# 24 x 368640 point-vectors; profiles/stencil_fp64_c2.md).  Valid for the
+# 24 x 368640 point-vectors, one ncu capture of the FP64 stencil at C2).  Valid for the
 # kernel version profiled there; set to None when the kernel changes.
 NCU_TRAFFIC_FP64_PER_PV = (2.519110e9 + 0.8291136e9) / (24 * 368640)
 
