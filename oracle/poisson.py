@@ -1,0 +1,116 @@
+"""FP64 oracle of the Poisson step and the Schroedinger-Poisson loop
+(Sec. II B).  Test infrastructure only: the tests, the bench's CPU leg and
+the entry module's smoke check use it; the library never does.
+
+Poisson problem on the Schroedinger grid (N_p points, spacing h in nm):
+    gate points (mask != 0):  phi_p = phi_gate(p)                 [V]
+    other points:             sum_{n in nb(p)} (phi_p - phi_n) / h^2 = (e / eps) rho_p
+where nb(p) are the face neighbours inside the box (a neighbour outside the
+box is dropped: zero normal flux, the paper's von Neumann condition away
+from the gates), rho is the hole density in nm^-3 and
+e / eps = e / (eps0 eps_Si) in V nm.  The matrix is assembled in CSR and
+solved by a sparse direct factorisation.
+
+Schroedinger-Poisson loop (the paper's Sec. II B procedure; readings: a fixed
+number of holes sets the Fermi level mu through Fermi-Dirac occupations at
+temperature T, the hole potential energy is V = V_ext + phi (a positive
+charge in the potential phi, in eV for phi in V), and the potential is
+updated by linear mixing):
+    E_i, psi_i = lowest n eigenpairs of H(V_k)
+    mu: sum_i f((E_i - mu) / kT) = n_holes
+    rho_p = sum_i f_i sum_b |psi_i(p, b)|^2 / h^3
+    phi = Poisson(rho)
+    V_{k+1} = (1 - a) V_k + a (V_ext + phi)
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import eig, kp, observables
+
+E_CHARGE = 1.602176634e-19      # C
+EPS0_PER_NM = 8.8541878128e-21  # F / nm
+EPS_SI = 11.7
+KB_EV = 8.617333262e-5           # eV / K
+
+
+def e_over_eps(eps_r: float = EPS_SI) -> float:
+    """e / (eps0 eps_r) in V nm."""
+    return E_CHARGE / (EPS0_PER_NM * eps_r)
+
+
+def assemble(nx, ny, nz, h, gate_mask):
+    """CSR matrix of the Poisson operator (N_p x N_p) and the per-point
+    gate flag; gate rows are the identity."""
+    Np = nx * ny * nz
+    gate = np.asarray(gate_mask, dtype=bool).reshape(Np)
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    p = ix + nx * (iy + ny * iz)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(Np)
+    for d, (dx, dy, dz) in enumerate(((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))):
+        jx, jy, jz = ix + dx, iy + dy, iz + dz
+        ok = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz) & ~gate
+        q = jx + nx * (jy + ny * jz)
+        rows.append(p[ok])
+        cols.append(q[ok])
+        vals.append(np.full(ok.sum(), -1.0 / h ** 2))
+        diag[p[ok]] += 1.0 / h ** 2
+    rows.append(np.arange(Np))
+    cols.append(np.arange(Np))
+    vals.append(np.where(gate, 1.0, diag))
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(Np, Np))
+    return A, gate
+
+
+def solve(nx, ny, nz, h, gate_mask, gate_phi, rho, eps_r: float = EPS_SI):
+    """phi [N_p] (V) for the hole density rho [N_p] (nm^-3)."""
+    A, gate = assemble(nx, ny, nz, h, gate_mask)
+    b = e_over_eps(eps_r) * np.asarray(rho, dtype=np.float64).reshape(-1)
+    b = np.where(gate, np.asarray(gate_phi, dtype=np.float64).reshape(-1), b)
+    return spla.spsolve(A.tocsc(), b)
+
+
+def fermi_level(E, n_holes, kT):
+    """mu with sum_i f((E_i - mu)/kT) = n_holes (bisection; f = Fermi-Dirac)."""
+    E = np.asarray(E, dtype=np.float64)
+
+    def count(mu):
+        return np.sum(0.5 * (1.0 - np.tanh(0.5 * (E - mu) / kT)))
+
+    lo, hi = E.min() - 50 * kT - 1.0, E.max() + 50 * kT + 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if count(mid) < n_holes:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def occupations(E, mu, kT):
+    return 0.5 * (1.0 - np.tanh(0.5 * (np.asarray(E) - mu) / kT))
+
+
+def sp_loop(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, mix, iters, bands=6, eps_r=EPS_SI):
+    """Fixed number of Schroedinger-Poisson iterations from V = V_ext (dense
+    eigensolver; small grids).  Returns (V, E, mu, history of max |dV|)."""
+    nx, ny, nz, h = prob.nx, prob.ny, prob.nz, prob.h
+    kT = KB_EV * T
+    V = np.asarray(V_ext, dtype=np.float64).reshape(-1).copy()
+    hist = []
+    for _ in range(iters):
+        q = prob.with_(V=V.reshape(nz, ny, nx))
+        H = kp.assemble(q) if bands == 6 else kp.assemble_h0(q)
+        E, psi = eig.lowest_dense(H, n_states, mask=prob.mask)
+        mu = fermi_level(E, n_holes, kT)
+        f = occupations(E, mu, kT)
+        rho = observables.density(psi, f, bands) / h ** 3
+        phi = solve(nx, ny, nz, h, gate_mask, gate_phi, rho, eps_r)
+        Vn = (1.0 - mix) * V + mix * (np.asarray(V_ext).reshape(-1) + phi)
+        hist.append(float(np.abs(Vn - V).max()))
+        V = Vn
+    return V, E, mu, hist

@@ -485,3 +485,65 @@ def test_h0_hellmann_feynman_vs_finite_differences():
     for gi in range(2):
         fd = (loss(p.with_(V=p.V + d * p.levers[gi])) - loss(p.with_(V=p.V - d * p.levers[gi]))) / (2 * d)
         assert abs(fd - dA[gi]) < 1e-8 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------
+# Poisson step of the Schroedinger-Poisson loop (Sec. II B)
+from oracle import poisson as poisson_oracle  # noqa: E402
+
+
+def _end_gates(nx, ny, nz):
+    g = np.zeros((nz, ny, nx), dtype=np.uint8)
+    g[:, :, 0] = 1
+    g[:, :, -1] = 1
+    return g
+
+
+def test_poisson_linear_between_two_gates():
+    """No charge, gates at the two x faces (0 and U), zero flux elsewhere:
+    the discrete solution is exactly linear in x."""
+    nx, ny, nz, h, U = 9, 4, 5, 0.5, 0.7
+    g = _end_gates(nx, ny, nz)
+    phi_g = np.zeros((nz, ny, nx))
+    phi_g[:, :, -1] = U
+    phi = poisson_oracle.solve(nx, ny, nz, h, g, phi_g, np.zeros(nx * ny * nz)).reshape(nz, ny, nx)
+    ref = U * np.arange(nx) / (nx - 1)
+    assert np.abs(phi - ref[None, None, :]).max() < 1e-13
+
+
+def test_poisson_uniform_charge_quadratic():
+    """Uniform hole density c between grounded x faces: -phi'' = (e/eps) c,
+    whose discrete solution is the exact quadratic (e/eps) c h^2 i (n-1-i)/2."""
+    nx, ny, nz, h, c = 11, 3, 4, 0.5, 2e-3
+    g = _end_gates(nx, ny, nz)
+    phi = poisson_oracle.solve(nx, ny, nz, h, g, np.zeros((nz, ny, nx)), np.full(nx * ny * nz, c))
+    i = np.arange(nx)
+    ref = poisson_oracle.e_over_eps() * c * h ** 2 * i * (nx - 1 - i) / 2
+    assert np.abs(phi.reshape(nz, ny, nx) - ref[None, None, :]).max() < 1e-12 * ref.max()
+
+
+def test_poisson_reciprocity():
+    """Grounded gates: the potential at b of a unit charge at a equals the
+    potential at a of a unit charge at b (symmetric operator)."""
+    nx, ny, nz, h = 6, 5, 4, 0.5
+    rng = np.random.default_rng(3)
+    g = (rng.random((nz, ny, nx)) < 0.15).astype(np.uint8)
+    g[0, 0, 0] = 1
+    free = np.flatnonzero(g.reshape(-1) == 0)
+    a, b = free[3], free[-5]
+    ra = np.zeros(nx * ny * nz)
+    ra[a] = 1.0
+    rb = np.zeros(nx * ny * nz)
+    rb[b] = 1.0
+    z = np.zeros((nz, ny, nx))
+    pa = poisson_oracle.solve(nx, ny, nz, h, g, z, ra)
+    pb = poisson_oracle.solve(nx, ny, nz, h, g, z, rb)
+    assert abs(pa[b] - pb[a]) < 1e-12 * abs(pa[b])
+    assert pa[a] > pa[b] > 0
+
+
+def test_fermi_level_counts_holes():
+    E = np.array([0.010, 0.010, 0.012, 0.012, 0.020, 0.021])
+    for kT, n in ((1e-4, 2.0), (1e-3, 3.0), (5e-3, 1.5)):
+        mu = poisson_oracle.fermi_level(E, n, kT)
+        assert abs(poisson_oracle.occupations(E, mu, kT).sum() - n) < 1e-12
