@@ -217,6 +217,41 @@ khp_status khp_eigensolve(khp_handle h, const khp_solver_opts* opts, double* eva
 #define KHP_BATCH_GRAPH 1      /* capture every round of the batch into one CUDA graph */
 #define KHP_BATCH_AUTOTUNE 2   /* choose block_m by timed trial solves (opts->block_m ignored) */
 
+/* Poisson step of the Schroedinger-Poisson loop (Sec. II B).  On the
+ * Schroedinger grid (nx, ny, nz, spacing h_nm), the potential phi [V] of the
+ * hole density rho [nm^-3] is fixed at the gate points and has zero normal
+ * flux at the box faces elsewhere:
+ *     sum over in-box face neighbours n of (phi_p - phi_n) / h^2 = (e / eps) rho_p,
+ *     eps = eps0 eps_r,  phi_p = phi_gate(p) at gates.
+ * Every connected set of free points must touch a gate.  Solved by
+ * Jacobi-preconditioned conjugate gradients on the device. */
+typedef struct khp_poisson_s* khp_poisson;
+
+/*  gate_mask_dev  uint8 [Np] device array, nonzero = gate point (copied)
+ *  gate_phi_dev   float64 [Np] device array, gate potentials [V] (read at gates, copied)
+ *  stream         cudaStream_t (as void*) for all work of this handle
+ * Errors: INVALID_ARG for bad sizes, h or eps_r <= 0, NULL arrays. */
+khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h_nm, double eps_r,
+                              const uint8_t* gate_mask_dev, const double* gate_phi_dev, void* stream);
+
+/*  rho_dev   float64 [Np] hole density [nm^-3] (device)
+ *  phi_dev   float64 [Np] (device): in = starting guess at the free points
+ *            (e.g. zeros or the previous solution), out = phi [V]
+ *  tol       stop when ||r|| <= tol ||b|| on the free points
+ *  iterations, rel_residual  optional outputs
+ * Synchronises the handle's stream.  Returns NOT_CONVERGED (phi holds the
+ * last iterate) when max_iter is reached. */
+khp_status khp_poisson_solve(khp_poisson p, const double* rho_dev, double* phi_dev, double tol, int max_iter,
+                             int* iterations, double* rel_residual);
+
+/* Potential update of the loop: V = (1 - mix) V + mix (V_ext + phi), all
+ * float64 [Np] device arrays (V_ext may be NULL), mix in (0, 1];
+ * max_change (optional, host) = max |V_new - V_old|.  Synchronises. */
+khp_status khp_sp_update(khp_poisson p, const double* V_ext_dev, const double* phi_dev, double mix, double* V_dev,
+                         double* max_change);
+
+khp_status khp_poisson_destroy(khp_poisson p);
+
 /* Solve `count` independent problems (a gate-voltage / detuning sweep,
  * Sec. II C: the single-particle problem is re-solved for every detuning
  * point; grids may differ in size).  Every problem runs the same algorithm as

@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KH
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}
 
-EXPORTED = ["khp_create_grid", "khp_create_grid_h0", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
+EXPORTED = ["khp_create_grid", "khp_create_grid_h0", "khp_poisson_create", "khp_poisson_solve", "khp_sp_update",
+            "khp_poisson_destroy", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
             "khp_eigensolve",
             "khp_eigensolve_batched",
             "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",
@@ -78,6 +79,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     vp, i, d, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
     lib.khp_create_grid.argtypes = [ctypes.POINTER(vp), i, i, i, d, ctypes.POINTER(Material), dp, vp, vp]
     lib.khp_create_grid_h0.argtypes = [ctypes.POINTER(vp), i, i, i, d, ctypes.POINTER(Material), dp, vp, vp]
+    lib.khp_poisson_create.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, vp, vp, vp]
+    lib.khp_poisson_solve.argtypes = [vp, vp, vp, d, i, ctypes.POINTER(i), dp]
+    lib.khp_sp_update.argtypes = [vp, vp, vp, d, vp, dp]
+    lib.khp_poisson_destroy.argtypes = [vp]
     lib.khp_project.argtypes = [vp, vp, vp, i, i, vp, vp]
     lib.khp_rotate.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
     lib.khp_set_potential_strain_field.argtypes = [vp, vp, vp, vp, dp, i, dp, i]

@@ -1,0 +1,396 @@
+// Poisson step of the Schroedinger-Poisson loop (Sec. II B): the potential
+// phi (V) of the hole density rho (nm^-3) on the Schroedinger grid, fixed at
+// the gate points and with zero normal flux at the box faces elsewhere:
+//     sum_{n in nb(p)} (phi_p - phi_n) / h^2 = (e / eps) rho_p      (p not a gate)
+//     phi_p = phi_gate(p)                                           (gate)
+// nb(p) = face neighbours inside the box.  The gate values move to the
+// right-hand side; the remaining operator on the free points is symmetric
+// positive definite (some gate in every connected part) and is solved by
+// conjugate gradients with the diagonal (Jacobi) preconditioner, matrix-free
+// (7-point stencil), every scalar on the device, the residual read back every
+// 16 iterations.  Reductions run in two fixed-order stages (deterministic).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "khp_common.cuh"
+#include "khp_internal.h"
+
+struct khp_poisson_s {
+    int nx, ny, nz;
+    long long np;
+    double h, eps_r, coef, h2inv;
+    cudaStream_t stream;
+    uint8_t* gate;
+    double* gphi;
+    double *x, *r, *z, *p, *Ap, *b;
+    double* partial;       // [nblk][2]
+    int nblk;
+    double* s;             // device scalars: 0 rz, 1 pAp, 2 alpha, 3 beta, 4 rr, 5 bb, 6 max change
+    double* host_pinned;   // [8]
+};
+
+namespace khp {
+namespace poisson {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ void coords(long long p, int nx, int ny, int& ix, int& iy, int& iz) {
+    ix = (int)(p % nx);
+    const long long q = p / nx;
+    iy = (int)(q % ny);
+    iz = (int)(q / ny);
+}
+
+struct Geo {
+    int nx, ny, nz;
+    long long np;
+    double h2inv;
+    const uint8_t* gate;
+};
+
+// neighbour d of p (0..5: +x, -x, +y, -y, +z, -z) or -1 outside the box
+__device__ __forceinline__ long long nbr(const Geo& g, long long p, int ix, int iy, int iz, int d) {
+    switch (d) {
+        case 0: return ix + 1 < g.nx ? p + 1 : -1;
+        case 1: return ix > 0 ? p - 1 : -1;
+        case 2: return iy + 1 < g.ny ? p + g.nx : -1;
+        case 3: return iy > 0 ? p - g.nx : -1;
+        case 4: return iz + 1 < g.nz ? p + (long long)g.nx * g.ny : -1;
+        default: return iz > 0 ? p - (long long)g.nx * g.ny : -1;
+    }
+}
+
+// block-partial sums of (a . b) and (c . d) into partial[block][0..1]
+__device__ __forceinline__ void block_sum2(double va, double vb, double* partial) {
+    __shared__ double sa[kT], sb[kT];
+    sa[threadIdx.x] = va;
+    sb[threadIdx.x] = vb;
+    __syncthreads();
+    for (int st = kT / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            sa[threadIdx.x] += sa[threadIdx.x + st];
+            sb[threadIdx.x] += sb[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sa[0];
+        partial[2 * blockIdx.x + 1] = sb[0];
+    }
+}
+
+// b = (e/eps) rho + h^-2 sum_{gate nbrs} phi_gate at free points, 0 at gates;
+// x = initial guess at free points, 0 at gates; partial: (b.b, 0)
+__global__ void rhs_kernel(const Geo g, const double* rho, const double* gphi, double coef, const double* phi_in,
+                           double* b, double* x, double* partial) {
+    double bb = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        if (g.gate[p]) {
+            b[p] = 0.0;
+            x[p] = 0.0;
+            continue;
+        }
+        int ix, iy, iz;
+        coords(p, g.nx, g.ny, ix, iy, iz);
+        double v = coef * rho[p];
+        for (int d = 0; d < 6; ++d) {
+            const long long q = nbr(g, p, ix, iy, iz, d);
+            if (q >= 0 && g.gate[q]) v += g.h2inv * gphi[q];
+        }
+        b[p] = v;
+        x[p] = phi_in ? phi_in[p] : 0.0;
+        bb += v * v;
+    }
+    block_sum2(bb, 0.0, partial);
+}
+
+// y = A x on free points (0 at gates); partial: (x.y, 0)
+__global__ void apply_kernel(const Geo g, const double* __restrict__ x, double* __restrict__ y, double* partial) {
+    double xy = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        if (g.gate[p]) {
+            y[p] = 0.0;
+            continue;
+        }
+        int ix, iy, iz;
+        coords(p, g.nx, g.ny, ix, iy, iz);
+        int deg = 0;
+        double s = 0.0;
+        for (int d = 0; d < 6; ++d) {
+            const long long q = nbr(g, p, ix, iy, iz, d);
+            if (q < 0) continue;
+            ++deg;
+            if (!g.gate[q]) s += x[q];
+        }
+        const double v = g.h2inv * (deg * x[p] - s);
+        y[p] = v;
+        xy += x[p] * v;
+    }
+    block_sum2(xy, 0.0, partial);
+}
+
+// r = b - A x (A x in y), z = r / diag, p = z; partial: (r.z, r.r)
+__global__ void init_kernel(const Geo g, const double* b, const double* Ax, double* r, double* z, double* pv,
+                            double* partial) {
+    double rz = 0.0, rr = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        if (g.gate[p]) {
+            r[p] = z[p] = pv[p] = 0.0;
+            continue;
+        }
+        int ix, iy, iz;
+        coords(p, g.nx, g.ny, ix, iy, iz);
+        int deg = 0;
+        for (int d = 0; d < 6; ++d) deg += nbr(g, p, ix, iy, iz, d) >= 0;
+        const double rv = b[p] - Ax[p];
+        const double zv = rv / (g.h2inv * (deg > 0 ? deg : 1));
+        r[p] = rv;
+        z[p] = zv;
+        pv[p] = zv;
+        rz += rv * zv;
+        rr += rv * rv;
+    }
+    block_sum2(rz, rr, partial);
+}
+
+// x += alpha p, r -= alpha Ap, z = r / diag; partial: (r.z, r.r)
+__global__ void update_kernel(const Geo g, const double* s, const double* pv, const double* Ap, double* x, double* r,
+                              double* z, double* partial) {
+    const double alpha = s[2];
+    double rz = 0.0, rr = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        if (g.gate[p]) continue;
+        int ix, iy, iz;
+        coords(p, g.nx, g.ny, ix, iy, iz);
+        int deg = 0;
+        for (int d = 0; d < 6; ++d) deg += nbr(g, p, ix, iy, iz, d) >= 0;
+        x[p] += alpha * pv[p];
+        const double rv = r[p] - alpha * Ap[p];
+        const double zv = rv / (g.h2inv * (deg > 0 ? deg : 1));
+        r[p] = rv;
+        z[p] = zv;
+        rz += rv * zv;
+        rr += rv * rv;
+    }
+    block_sum2(rz, rr, partial);
+}
+
+// p = z + beta p
+__global__ void direction_kernel(const Geo g, const double* s, const double* z, double* pv) {
+    const double beta = s[3];
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT)
+        if (!g.gate[p]) pv[p] = z[p] + beta * pv[p];
+}
+
+// one thread sums the block partials in block order; mode selects the update
+//  0: s[5] = bb                      (after rhs_kernel)
+//  1: s[0] = rz, s[4] = rr           (after init_kernel)
+//  2: s[1] = pAp, s[2] = rz / pAp    (after apply_kernel on p)
+//  3: s[3] = rz_new / rz, s[0] = rz_new, s[4] = rr   (after update_kernel)
+__global__ void finish_kernel(const double* partial, int nblk, int mode, double* s) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblk; ++k) {
+        a += partial[2 * k];
+        b += partial[2 * k + 1];
+    }
+    if (mode == 0) s[5] = a;
+    else if (mode == 1) { s[0] = a; s[4] = b; }
+    else if (mode == 2) { s[1] = a; s[2] = a != 0.0 ? s[0] / a : 0.0; }
+    else { s[3] = s[0] != 0.0 ? a / s[0] : 0.0; s[0] = a; s[4] = b; }
+}
+
+// phi = x at free points, phi_gate at gates
+__global__ void output_kernel(const Geo g, const double* x, const double* gphi, double* phi) {
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT)
+        phi[p] = g.gate[p] ? gphi[p] : x[p];
+}
+
+// V = (1 - a) V + a (V_ext + phi); partial: (max |dV|, 0)
+__global__ void mix_kernel(long long np, const double* Vext, const double* phi, double a, double* V, double* partial) {
+    __shared__ double sm[kT];
+    double mx = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
+        const double v = V[p];
+        const double vn = (1.0 - a) * v + a * ((Vext ? Vext[p] : 0.0) + phi[p]);
+        V[p] = vn;
+        mx = fmax(mx, fabs(vn - v));
+    }
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int st = kT / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[2 * blockIdx.x] = sm[0];
+}
+
+__global__ void max_finish_kernel(const double* partial, int nblk, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double m = 0.0;
+    for (int k = 0; k < nblk; ++k) m = fmax(m, partial[2 * k]);
+    *out = m;
+}
+
+__global__ void copy_gate_values_kernel(long long np, const uint8_t* gate, const double* src, double* gphi) {
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT)
+        gphi[p] = gate[p] ? src[p] : 0.0;
+}
+
+}  // namespace poisson
+}  // namespace khp
+
+// ------------------------------------------------------------------ C ABI
+namespace {
+
+using khp::poisson::kT;
+
+khp_status pfail(khp_status s, const std::string& m) { return khp_set_error(s, m); }
+
+#define PCK(call)                                                                           \
+    do {                                                                                    \
+        const cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) return pfail(KHP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+khp::poisson::Geo geo(const khp_poisson_s* P) {
+    khp::poisson::Geo g;
+    g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.np = P->np; g.h2inv = P->h2inv; g.gate = P->gate;
+    return g;
+}
+
+void free_all(khp_poisson_s* P) {
+    double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s};
+    for (double* b : bufs)
+        if (b) cudaFree(b);
+    if (P->gate) cudaFree(P->gate);
+    if (P->host_pinned) cudaFreeHost(P->host_pinned);
+}
+
+}  // namespace
+
+extern "C" {
+
+khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h_nm, double eps_r,
+                              const uint8_t* gate_mask_dev, const double* gate_phi_dev, void* stream) {
+    khp_set_error(KHP_OK, "");
+    if (!out) return pfail(KHP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return pfail(KHP_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (!(h_nm > 0.0) || !std::isfinite(h_nm)) return pfail(KHP_ERR_INVALID_ARG, "h must be > 0");
+    if (!(eps_r > 0.0) || !std::isfinite(eps_r)) return pfail(KHP_ERR_INVALID_ARG, "eps_r must be > 0");
+    if (!gate_mask_dev || !gate_phi_dev) return pfail(KHP_ERR_INVALID_ARG, "gate mask or gate potential is NULL");
+    const long long np = (long long)nx * ny * nz;
+    if (np > (1LL << 31)) return pfail(KHP_ERR_INVALID_ARG, "grid too large");
+    khp_poisson_s* P = new khp_poisson_s();
+    std::memset(P, 0, sizeof(*P));
+    P->nx = nx; P->ny = ny; P->nz = nz; P->np = np; P->h = h_nm; P->eps_r = eps_r;
+    // e / (eps0 eps_r) in V nm
+    P->coef = 1.602176634e-19 / (8.8541878128e-21 * eps_r);
+    P->h2inv = 1.0 / (h_nm * h_nm);
+    P->stream = (cudaStream_t)stream;
+    P->nblk = (int)std::min<long long>((np + kT - 1) / kT, 1184);
+    cudaError_t e = cudaSuccess;
+    const size_t vb = sizeof(double) * np;
+    if ((e = cudaMalloc(&P->gate, np)) != cudaSuccess || (e = cudaMalloc(&P->gphi, vb)) != cudaSuccess ||
+        (e = cudaMalloc(&P->x, vb)) != cudaSuccess || (e = cudaMalloc(&P->r, vb)) != cudaSuccess ||
+        (e = cudaMalloc(&P->z, vb)) != cudaSuccess || (e = cudaMalloc(&P->p, vb)) != cudaSuccess ||
+        (e = cudaMalloc(&P->Ap, vb)) != cudaSuccess || (e = cudaMalloc(&P->b, vb)) != cudaSuccess ||
+        (e = cudaMalloc(&P->partial, sizeof(double) * 2 * P->nblk)) != cudaSuccess ||
+        (e = cudaMalloc(&P->s, sizeof(double) * 8)) != cudaSuccess ||
+        (e = cudaMallocHost(&P->host_pinned, sizeof(double) * 8)) != cudaSuccess) {
+        free_all(P);
+        delete P;
+        return pfail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
+                     std::string("allocation: ") + cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpyAsync(P->gate, gate_mask_dev, np, cudaMemcpyDeviceToDevice, P->stream)) != cudaSuccess) {
+        free_all(P);
+        delete P;
+        return pfail(KHP_ERR_CUDA, std::string("gate copy: ") + cudaGetErrorString(e));
+    }
+    khp::poisson::copy_gate_values_kernel<<<P->nblk, kT, 0, P->stream>>>(np, P->gate, gate_phi_dev, P->gphi);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(P->stream)) != cudaSuccess) {
+        free_all(P);
+        delete P;
+        return pfail(KHP_ERR_CUDA, std::string("gate set-up: ") + cudaGetErrorString(e));
+    }
+    *out = P;
+    return KHP_OK;
+}
+
+khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_dev, double tol, int max_iter,
+                             int* iterations, double* rel_residual) {
+    khp_set_error(KHP_OK, "");
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!rho_dev || !phi_dev) return pfail(KHP_ERR_INVALID_ARG, "rho or phi is NULL");
+    if (!(tol > 0.0) || max_iter < 1) return pfail(KHP_ERR_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+    using namespace khp::poisson;
+    const Geo g = geo(P);
+    const int nb = P->nblk;
+    cudaStream_t st = P->stream;
+    double* hp = P->host_pinned;
+    rhs_kernel<<<nb, kT, 0, st>>>(g, rho_dev, P->gphi, P->coef, phi_dev, P->b, P->x, P->partial);
+    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 0, P->s);
+    apply_kernel<<<nb, kT, 0, st>>>(g, P->x, P->Ap, P->partial);
+    init_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->z, P->p, P->partial);
+    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 1, P->s);
+    PCK(cudaGetLastError());
+    PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    const double bb = hp[5];
+    double rel = bb > 0.0 ? std::sqrt(hp[4] / bb) : std::sqrt(hp[4]);
+    int it = 0;
+    // a zero right-hand side with a zero start is already solved
+    while (rel > tol && it < max_iter) {
+        const int chunk = std::min(16, max_iter - it);
+        for (int k = 0; k < chunk; ++k) {
+            apply_kernel<<<nb, kT, 0, st>>>(g, P->p, P->Ap, P->partial);
+            finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 2, P->s);
+            update_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->z, P->partial);
+            finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 3, P->s);
+            direction_kernel<<<nb, kT, 0, st>>>(g, P->s, P->z, P->p);
+        }
+        PCK(cudaGetLastError());
+        it += chunk;
+        PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+        PCK(cudaStreamSynchronize(st));
+        rel = bb > 0.0 ? std::sqrt(hp[4] / bb) : std::sqrt(hp[4]);
+        if (!std::isfinite(rel)) return pfail(KHP_ERR_BREAKDOWN, "Poisson CG produced a non-finite residual");
+    }
+    output_kernel<<<nb, kT, 0, st>>>(g, P->x, P->gphi, phi_dev);
+    PCK(cudaGetLastError());
+    PCK(cudaStreamSynchronize(st));
+    if (iterations) *iterations = it;
+    if (rel_residual) *rel_residual = rel;
+    if (rel > tol) return pfail(KHP_ERR_NOT_CONVERGED, "Poisson CG reached max_iter");
+    return KHP_OK;
+}
+
+khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* phi_dev, double mix, double* V_dev,
+                         double* max_change) {
+    khp_set_error(KHP_OK, "");
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!phi_dev || !V_dev) return pfail(KHP_ERR_INVALID_ARG, "phi or V is NULL");
+    if (!(mix > 0.0 && mix <= 1.0)) return pfail(KHP_ERR_INVALID_ARG, "mix must be in (0, 1]");
+    using namespace khp::poisson;
+    mix_kernel<<<P->nblk, kT, 0, P->stream>>>(P->np, V_ext_dev, phi_dev, mix, V_dev, P->partial);
+    max_finish_kernel<<<1, 32, 0, P->stream>>>(P->partial, P->nblk, P->s + 6);
+    PCK(cudaGetLastError());
+    PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    PCK(cudaStreamSynchronize(P->stream));
+    if (max_change) *max_change = P->host_pinned[6];
+    return KHP_OK;
+}
+
+khp_status khp_poisson_destroy(khp_poisson P) {
+    if (!P) return KHP_OK;
+    cudaStreamSynchronize(P->stream);
+    free_all(P);
+    delete P;
+    return KHP_OK;
+}
+
+}  // extern "C"

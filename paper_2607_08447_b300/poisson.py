@@ -1,0 +1,130 @@
+"""Poisson step and Schroedinger-Poisson loop (Sec. II B) through the C ABI.
+
+`Poisson` wraps khp_poisson_create / khp_poisson_solve / khp_sp_update
+(include/khp.h).  `sp_solve` runs the self-consistent loop: the library's
+eigensolver (warm-started from the previous iteration), occupations from a
+fixed hole number at temperature T (Fermi level by bisection over the n
+eigenvalues on the host), the library's density, the library's Poisson
+solve and potential update.  All grid-sized work runs in the library.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+import torch
+
+from . import _lib
+from .solver import _dev, _ptr
+
+KB_EV = 8.617333262e-5   # eV / K
+EPS_SI = 11.7
+
+
+class Poisson:
+    """FD Poisson operator on a grid with gate (Dirichlet) points."""
+
+    def __init__(self, nx, ny, nz, h, gate_mask, gate_phi, eps_r=EPS_SI, device="cuda", stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
+        self.np_ = self.nx * self.ny * self.nz
+        self._gate = _dev(np.asarray(gate_mask, dtype=np.uint8).reshape(-1), torch.uint8, self.device)
+        self._gphi = _dev(np.asarray(gate_phi, dtype=np.float64).reshape(-1), torch.float64, self.device)
+        if self._gate.numel() != self.np_ or self._gphi.numel() != self.np_:
+            raise ValueError("gate mask and gate potential need nx*ny*nz entries")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h_ = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.khp_poisson_create(ctypes.byref(h_), self.nx, self.ny, self.nz, self.h,
+                                                   float(eps_r), _ptr(self._gate), _ptr(self._gphi),
+                                                   ctypes.c_void_p(self.stream.cuda_stream)))
+        self.handle = h_
+
+    def solve(self, rho, phi=None, tol=1e-12, max_iter=20000):
+        """phi [Np] (V) for the hole density rho [Np] (nm^-3); `phi` (if
+        given) is the starting guess and is overwritten."""
+        rho = _dev(rho, torch.float64, self.device).reshape(-1)
+        if phi is None:
+            phi = torch.zeros(self.np_, dtype=torch.float64, device=self.device)
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        _lib.check(self.lib.khp_poisson_solve(self.handle, _ptr(rho), _ptr(phi), float(tol), int(max_iter),
+                                              ctypes.byref(it), ctypes.byref(rel)))
+        self.last_iterations, self.last_residual = it.value, rel.value
+        return phi
+
+    def update(self, V, phi, mix, V_ext=None):
+        """V <- (1 - mix) V + mix (V_ext + phi) in place; returns max |dV|."""
+        ch = ctypes.c_double(0.0)
+        _lib.check(self.lib.khp_sp_update(self.handle, _ptr(V_ext), _ptr(phi), float(mix), _ptr(V),
+                                          ctypes.byref(ch)))
+        return ch.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.khp_poisson_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fermi_level(E, n_holes, kT):
+    """mu with sum_i f((E_i - mu) / kT) = n_holes (bisection, host)."""
+    E = np.asarray(E, dtype=np.float64)
+
+    def count(mu):
+        return np.sum(0.5 * (1.0 - np.tanh(0.5 * (E - mu) / kT)))
+
+    lo, hi = E.min() - 50 * kT - 1.0, E.max() + 50 * kT + 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if count(mid) < n_holes:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@dataclass
+class SPResult:
+    V: torch.Tensor
+    evals: np.ndarray
+    evecs: torch.Tensor
+    mu: float
+    history: List[float] = field(default_factory=list)
+    poisson_iterations: List[int] = field(default_factory=list)
+
+
+def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, tol_v=1e-8, strain=None,
+             B=None, gauge=0, solve_kw=None):
+    """Self-consistent loop from V = V_ext: `iters` iterations at most, or
+    until max |dV| <= tol_v.  Returns SPResult (V on the device)."""
+    kw = dict(block_m=max(n_states + 8, 16), degree=40, tol=1e-11, seed=1)
+    kw.update(solve_kw or {})
+    V_ext = _dev(V_ext, torch.float64, grid.device).reshape(-1)
+    V = V_ext.clone()
+    phi = torch.zeros_like(V)
+    kT = KB_EV * T
+    hist, piters = [], []
+    warm = None
+    for _ in range(iters):
+        grid.set_fields(V, strain, None, None, B, gauge)
+        r = grid.eigensolve(n_states, warm_start=warm, **kw)
+        warm = r.evecs
+        mu = fermi_level(r.evals, n_holes, kT)
+        f = 0.5 * (1.0 - np.tanh(0.5 * (r.evals - mu) / kT))
+        rho = grid.density(r.evecs, f / grid.h ** 3)
+        poisson.solve(rho, phi)
+        piters.append(poisson.last_iterations)
+        dv = poisson.update(V, phi, mix, V_ext)
+        hist.append(dv)
+        if dv <= tol_v:
+            break
+    return SPResult(V, r.evals, r.evecs, mu, hist, piters)

@@ -1,0 +1,89 @@
+"""Poisson step and Schroedinger-Poisson loop (Sec. II B) through the CUDA
+path against the FP64 oracle (`oracle.poisson`): the Poisson solution for
+random gates and densities, the exact linear profile between two gates, and
+the same fixed number of self-consistent iterations on both sides."""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from oracle import poisson as po
+
+pytestmark = pytest.mark.gpu
+
+
+def _end_gates(nx, ny, nz):
+    g = np.zeros((nz, ny, nx), dtype=np.uint8)
+    g[:, :, 0] = 1
+    g[:, :, -1] = 1
+    return g
+
+
+@pytest.mark.parametrize("shape", [(9, 7, 5), (33, 17, 12)])
+def test_poisson_matches_oracle(khp, shape):
+    from paper_2607_08447_b300.poisson import Poisson
+    nx, ny, nz = shape
+    h = 0.5
+    rng = np.random.default_rng(sum(shape))
+    gate = _end_gates(nx, ny, nz)
+    gate |= (rng.random((nz, ny, nx)) < 0.05).astype(np.uint8)
+    gphi = rng.uniform(-0.5, 0.8, (nz, ny, nx))
+    rho = np.abs(rng.standard_normal(nx * ny * nz)) * 1e-3
+    ref = po.solve(nx, ny, nz, h, gate, gphi, rho)
+    P = Poisson(nx, ny, nz, h, gate, gphi)
+    phi = P.solve(torch.from_numpy(rho).cuda(), tol=1e-13).cpu().numpy()
+    assert P.last_residual <= 1e-13
+    assert np.abs(phi - ref).max() <= 1e-10 * np.abs(ref).max()
+    # warm start from the solution: no iteration needed
+    phi2 = P.solve(torch.from_numpy(rho).cuda(), torch.from_numpy(phi).cuda(), tol=1e-10).cpu().numpy()
+    assert P.last_iterations <= 16
+    assert np.abs(phi2 - ref).max() <= 1e-9 * np.abs(ref).max()
+    P.close()
+
+
+def test_poisson_linear_between_gates(khp):
+    from paper_2607_08447_b300.poisson import Poisson
+    nx, ny, nz, U = 40, 6, 5, 0.9
+    gate = _end_gates(nx, ny, nz)
+    gphi = np.zeros((nz, ny, nx))
+    gphi[:, :, -1] = U
+    P = Poisson(nx, ny, nz, 0.5, gate, gphi)
+    phi = P.solve(np.zeros(nx * ny * nz), tol=1e-14).cpu().numpy().reshape(nz, ny, nx)
+    assert np.abs(phi - U * np.arange(nx)[None, None, :] / (nx - 1)).max() <= 1e-12
+    P.close()
+
+
+def test_poisson_rejects_bad_arguments(khp):
+    from paper_2607_08447_b300.poisson import Poisson
+    g = np.ones((2, 2, 2), dtype=np.uint8)
+    with pytest.raises(khp.KHPError):
+        Poisson(2, 2, 2, 0.5, g, np.zeros((2, 2, 2)), eps_r=-1.0)
+    P = Poisson(2, 2, 2, 0.5, g, np.zeros((2, 2, 2)))
+    V = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(khp.KHPError):
+        P.update(V, V, 1.5)
+    P.close()
+
+
+@pytest.mark.parametrize("bands", [6, 3])
+def test_sp_loop_matches_oracle(khp, bands):
+    """Three self-consistent iterations (2 holes, T = 1.5 K, mixing 0.3) from
+    the same start: the potential and the eigenvalues agree with the
+    oracle's loop (dense eigensolver, direct Poisson solve)."""
+    from paper_2607_08447_b300.poisson import Poisson, sp_solve
+    p = inputs.small_problem(10, 6, 6, h=0.5, seed=5, strain=True)
+    gate = _end_gates(p.nx, p.ny, p.nz)
+    gphi = np.zeros_like(p.V)
+    iters, n, nh = 3, 8, 2.0
+    V_or, E_or, mu_or, hist_or = po.sp_loop(p, p.V, gate, gphi, n, nh, 1.5, 0.3, iters, bands=bands)
+    g = khp.KPGrid.from_problem(p, bands=bands)
+    P = Poisson(p.nx, p.ny, p.nz, p.h, gate, gphi)
+    r = sp_solve(g, P, p.V, n, nh, T=1.5, mix=0.3, iters=iters, tol_v=0.0, strain=p.strain,
+                 solve_kw=dict(block_m=16, degree=16, tol=1e-12))
+    assert len(r.history) == iters
+    assert np.abs(np.array(r.history) - np.array(hist_or)).max() <= 1e-9
+    assert np.abs(r.V.cpu().numpy() - V_or).max() <= 1e-10
+    assert np.abs(r.evals - E_or).max() <= 1e-10
+    assert abs(r.mu - mu_or) <= 1e-9
+    P.close()
+    g.close()
