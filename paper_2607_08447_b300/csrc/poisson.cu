@@ -8,7 +8,8 @@
 // positive definite (some gate in every connected part) and is solved by
 // conjugate gradients with the diagonal (Jacobi) preconditioner, matrix-free
 // (7-point stencil), every scalar on the device, the residual read back every
-// 16 iterations.  Reductions run in two fixed-order stages (deterministic).
+// 16 iterations, replayed as one captured CUDA graph of 16 iterations.
+// Reductions run in two fixed-order stages (deterministic).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,6 +30,9 @@ struct khp_poisson_s {
     int nblk;
     double* s;             // device scalars: 0 rz, 1 pAp, 2 alpha, 3 beta, 4 rr, 5 bb, 6 max change
     double* host_pinned;   // [8]
+    cudaStream_t work;     // private stream: the CG chunk is captured and replayed on it
+    cudaGraphExec_t chunk; // 16 CG iterations, instantiated on first use
+    bool have_chunk;
 };
 
 namespace khp {
@@ -262,6 +266,8 @@ khp::poisson::Geo geo(const khp_poisson_s* P) {
 }
 
 void free_all(khp_poisson_s* P) {
+    if (P->have_chunk) cudaGraphExecDestroy(P->chunk);
+    if (P->work) cudaStreamDestroy(P->work);
     double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s};
     for (double* b : bufs)
         if (b) cudaFree(b);
@@ -300,7 +306,8 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
         (e = cudaMalloc(&P->Ap, vb)) != cudaSuccess || (e = cudaMalloc(&P->b, vb)) != cudaSuccess ||
         (e = cudaMalloc(&P->partial, sizeof(double) * 2 * P->nblk)) != cudaSuccess ||
         (e = cudaMalloc(&P->s, sizeof(double) * 8)) != cudaSuccess ||
-        (e = cudaMallocHost(&P->host_pinned, sizeof(double) * 8)) != cudaSuccess) {
+        (e = cudaMallocHost(&P->host_pinned, sizeof(double) * 8)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&P->work, cudaStreamNonBlocking)) != cudaSuccess) {
         free_all(P);
         delete P;
         return pfail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
@@ -321,6 +328,17 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
     return KHP_OK;
 }
 
+// the 5 launches of one CG iteration
+static void cg_iteration(khp_poisson_s* P, const khp::poisson::Geo& g, cudaStream_t st) {
+    using namespace khp::poisson;
+    const int nb = P->nblk;
+    apply_kernel<<<nb, kT, 0, st>>>(g, P->p, P->Ap, P->partial);
+    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 2, P->s);
+    update_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->z, P->partial);
+    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 3, P->s);
+    direction_kernel<<<nb, kT, 0, st>>>(g, P->s, P->z, P->p);
+}
+
 khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_dev, double tol, int max_iter,
                              int* iterations, double* rel_residual) {
     khp_set_error(KHP_OK, "");
@@ -330,7 +348,9 @@ khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_d
     using namespace khp::poisson;
     const Geo g = geo(P);
     const int nb = P->nblk;
-    cudaStream_t st = P->stream;
+    // the caller's work (rho, phi) is complete before the private stream starts
+    PCK(cudaStreamSynchronize(P->stream));
+    cudaStream_t st = P->work;
     double* hp = P->host_pinned;
     rhs_kernel<<<nb, kT, 0, st>>>(g, rho_dev, P->gphi, P->coef, phi_dev, P->b, P->x, P->partial);
     finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 0, P->s);
@@ -346,12 +366,20 @@ khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_d
     // a zero right-hand side with a zero start is already solved
     while (rel > tol && it < max_iter) {
         const int chunk = std::min(16, max_iter - it);
-        for (int k = 0; k < chunk; ++k) {
-            apply_kernel<<<nb, kT, 0, st>>>(g, P->p, P->Ap, P->partial);
-            finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 2, P->s);
-            update_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->z, P->partial);
-            finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 3, P->s);
-            direction_kernel<<<nb, kT, 0, st>>>(g, P->s, P->z, P->p);
+        if (chunk == 16) {
+            if (!P->have_chunk) {
+                cudaGraph_t graph;
+                PCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                for (int k = 0; k < 16; ++k) cg_iteration(P, g, st);
+                PCK(cudaStreamEndCapture(st, &graph));
+                const cudaError_t e = cudaGraphInstantiate(&P->chunk, graph, 0);
+                cudaGraphDestroy(graph);
+                PCK(e);
+                P->have_chunk = true;
+            }
+            PCK(cudaGraphLaunch(P->chunk, st));
+        } else {
+            for (int k = 0; k < chunk; ++k) cg_iteration(P, g, st);
         }
         PCK(cudaGetLastError());
         it += chunk;
@@ -376,11 +404,12 @@ khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* p
     if (!phi_dev || !V_dev) return pfail(KHP_ERR_INVALID_ARG, "phi or V is NULL");
     if (!(mix > 0.0 && mix <= 1.0)) return pfail(KHP_ERR_INVALID_ARG, "mix must be in (0, 1]");
     using namespace khp::poisson;
-    mix_kernel<<<P->nblk, kT, 0, P->stream>>>(P->np, V_ext_dev, phi_dev, mix, V_dev, P->partial);
-    max_finish_kernel<<<1, 32, 0, P->stream>>>(P->partial, P->nblk, P->s + 6);
-    PCK(cudaGetLastError());
-    PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
     PCK(cudaStreamSynchronize(P->stream));
+    mix_kernel<<<P->nblk, kT, 0, P->work>>>(P->np, V_ext_dev, phi_dev, mix, V_dev, P->partial);
+    max_finish_kernel<<<1, 32, 0, P->work>>>(P->partial, P->nblk, P->s + 6);
+    PCK(cudaGetLastError());
+    PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->work));
+    PCK(cudaStreamSynchronize(P->work));
     if (max_change) *max_change = P->host_pinned[6];
     return KHP_OK;
 }
@@ -388,6 +417,7 @@ khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* p
 khp_status khp_poisson_destroy(khp_poisson P) {
     if (!P) return KHP_OK;
     cudaStreamSynchronize(P->stream);
+    if (P->work) cudaStreamSynchronize(P->work);
     free_all(P);
     delete P;
     return KHP_OK;
