@@ -188,18 +188,33 @@ __global__ void direction_kernel(const Geo g, const double* s, const double* z, 
         if (!g.gate[p]) pv[p] = z[p] + beta * pv[p];
 }
 
-// one thread sums the block partials in block order; mode selects the update
+// one block sums the block partials (thread t takes partials t, t + 256, ...
+// in order, then a fixed tree), so the result does not depend on timing;
+// mode selects the update
 //  0: s[5] = bb                      (after rhs_kernel)
 //  1: s[0] = rz, s[4] = rr           (after init_kernel)
 //  2: s[1] = pAp, s[2] = rz / pAp    (after apply_kernel on p)
 //  3: s[3] = rz_new / rz, s[0] = rz_new, s[4] = rr   (after update_kernel)
-__global__ void finish_kernel(const double* partial, int nblk, int mode, double* s) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(kT) finish_kernel(const double* partial, int nblk, int mode, double* s) {
+    __shared__ double sa[kT], sb[kT];
     double a = 0.0, b = 0.0;
-    for (int k = 0; k < nblk; ++k) {
+    for (int k = threadIdx.x; k < nblk; k += kT) {
         a += partial[2 * k];
         b += partial[2 * k + 1];
     }
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int st = kT / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            sa[threadIdx.x] += sa[threadIdx.x + st];
+            sb[threadIdx.x] += sb[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    a = sa[0];
+    b = sb[0];
     if (mode == 0) s[5] = a;
     else if (mode == 1) { s[0] = a; s[4] = b; }
     else if (mode == 2) { s[1] = a; s[2] = a != 0.0 ? s[0] / a : 0.0; }
@@ -231,11 +246,17 @@ __global__ void mix_kernel(long long np, const double* Vext, const double* phi, 
     if (threadIdx.x == 0) partial[2 * blockIdx.x] = sm[0];
 }
 
-__global__ void max_finish_kernel(const double* partial, int nblk, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(kT) max_finish_kernel(const double* partial, int nblk, double* out) {
+    __shared__ double sm[kT];
     double m = 0.0;
-    for (int k = 0; k < nblk; ++k) m = fmax(m, partial[2 * k]);
-    *out = m;
+    for (int k = threadIdx.x; k < nblk; k += kT) m = fmax(m, partial[2 * k]);
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int st = kT / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
 }
 
 __global__ void copy_gate_values_kernel(long long np, const uint8_t* gate, const double* src, double* gphi) {
@@ -333,9 +354,9 @@ static void cg_iteration(khp_poisson_s* P, const khp::poisson::Geo& g, cudaStrea
     using namespace khp::poisson;
     const int nb = P->nblk;
     apply_kernel<<<nb, kT, 0, st>>>(g, P->p, P->Ap, P->partial);
-    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 2, P->s);
+    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 2, P->s);
     update_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->z, P->partial);
-    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 3, P->s);
+    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 3, P->s);
     direction_kernel<<<nb, kT, 0, st>>>(g, P->s, P->z, P->p);
 }
 
@@ -353,10 +374,10 @@ khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_d
     cudaStream_t st = P->work;
     double* hp = P->host_pinned;
     rhs_kernel<<<nb, kT, 0, st>>>(g, rho_dev, P->gphi, P->coef, phi_dev, P->b, P->x, P->partial);
-    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 0, P->s);
+    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 0, P->s);
     apply_kernel<<<nb, kT, 0, st>>>(g, P->x, P->Ap, P->partial);
     init_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->z, P->p, P->partial);
-    finish_kernel<<<1, 32, 0, st>>>(P->partial, nb, 1, P->s);
+    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 1, P->s);
     PCK(cudaGetLastError());
     PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
@@ -406,7 +427,7 @@ khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* p
     using namespace khp::poisson;
     PCK(cudaStreamSynchronize(P->stream));
     mix_kernel<<<P->nblk, kT, 0, P->work>>>(P->np, V_ext_dev, phi_dev, mix, V_dev, P->partial);
-    max_finish_kernel<<<1, 32, 0, P->work>>>(P->partial, P->nblk, P->s + 6);
+    max_finish_kernel<<<1, kT, 0, P->work>>>(P->partial, P->nblk, P->s + 6);
     PCK(cudaGetLastError());
     PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->work));
     PCK(cudaStreamSynchronize(P->work));
