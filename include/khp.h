@@ -275,6 +275,16 @@ khp_status khp_eigensolve_batched(const khp_handle* hs, int count, const khp_sol
                                   double* evals_host, void* const* evecs_dev, double* resid_host,
                                   khp_stats* stats, int flags);
 
+/* Overlap (pair) densities of n states for the Coulomb integrals of the
+ * configuration-interaction step (Sec. II C, Eqs. 13-15):
+ *     rho_jl(p) = sum_b conj(psi_j(p, b)) psi_l(p, b)  for all ordered (j, l)
+ * (per grid point, not divided by h^3).
+ *  evecs_dev  complex128 [N][n] row-major (as returned by khp_eigensolve)
+ *  rho_dev    complex128 [Np][n * n] row-major, pair index j n + l
+ * Asynchronous on the handle's stream.  Errors: INVALID_ARG for NULL
+ * pointers or n outside 1..64. */
+khp_status khp_pair_densities(khp_handle h, const void* evecs_dev, int n, void* rho_dev);
+
 /* Hole density (Sec. II B, fed to Poisson):
  *  rho_dev[p] = sum_i w_host[i] * sum_b |psi_i(6p+b)|^2   (discrete norm)
  *  evecs_dev complex128 [N][n] row-major.  Deterministic summation order. */

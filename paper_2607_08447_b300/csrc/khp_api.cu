@@ -1257,6 +1257,16 @@ extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, co
     return KHP_OK;
 }
 
+extern "C" khp_status khp_pair_densities(khp_handle g, const void* evecs_dev, int n, void* rho_dev) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!evecs_dev || !rho_dev) return fail(KHP_ERR_INVALID_ARG, "evecs or rho is NULL");
+    if (n < 1 || n > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "n out of range 1..64");
+    CK(launch_pair_density((const double2*)evecs_dev, g->np, n, g->nb, (double2*)rho_dev, g->stream));
+    g->launches += 1;
+    return KHP_OK;
+}
+
 extern "C" khp_status khp_density(khp_handle g, const void* evecs_dev, int n, const double* w_host,
                                   double* rho_dev) {
     g_err.clear();

@@ -81,6 +81,7 @@ cudaError_t launch_dc_combine(const double2* X, const double2* HX, const float2*
                               long long rows, int ld, int zcol0, const double* D, cudaStream_t st);
 
 // observables.cu
+cudaError_t launch_pair_density(const double2* psi, long long np, int n, int nb, double2* out, cudaStream_t st);
 cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,
                            const uint8_t* mask, double* rho, cudaStream_t st, int nb = 6);
 cudaError_t launch_backward(const double2* psi, long long np, int n, const double* g,

@@ -136,3 +136,36 @@ cudaError_t launch_backward(const double2* psi, long long np, int n, const doubl
 }
 
 }  // namespace khp
+
+// ---------------------------------------------------------- pair densities
+// rho_jl(p) = sum_b conj(psi_j(p, b)) psi_l(p, b) for every ordered pair
+// (j, l) (the overlap densities of the Coulomb integrals of the CI step,
+// Sec. II C, Eqs. 13-15), written as [Np][n * n] complex, pair index j n + l.
+namespace khp {
+
+__global__ void pair_density_kernel(const double2* __restrict__ psi, long long np, int n, int nb,
+                                    double2* __restrict__ out) {
+    const int npair = n * n;
+    const long long total = np * npair;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long p = t / npair;
+        const int k = (int)(t - p * npair);
+        const int j = k / n, l = k - j * n;
+        const double2* row = psi + p * nb * n;
+        double2 s = make_double2(0.0, 0.0);
+        for (int b = 0; b < nb; ++b) cfmac(s, row[b * n + j], row[b * n + l]);
+        out[t] = s;
+    }
+}
+
+cudaError_t launch_pair_density(const double2* psi, long long np, int n, int nb, double2* out, cudaStream_t st) {
+    const long long total = np * (long long)(n * n);
+    long long blocks = (total + 255) / 256;
+    if (blocks > 148 * 32) blocks = 148 * 32;
+    if (blocks < 1) blocks = 1;
+    pair_density_kernel<<<(unsigned)blocks, 256, 0, st>>>(psi, np, n, nb, out);
+    return cudaGetLastError();
+}
+
+}  // namespace khp

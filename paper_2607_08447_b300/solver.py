@@ -163,6 +163,15 @@ class KPGrid:
         _lib.check(self.lib.khp_density(self.handle, _ptr(evecs), evecs.shape[1], _lib.dptr(w), _ptr(rho)))
         return rho
 
+    def pair_densities(self, evecs):
+        """rho_jl(p) = sum_b conj(psi_j) psi_l for all ordered (j, l):
+        complex128 [Np][n * n], pair index j n + l."""
+        evecs = _dev(evecs, torch.complex128, self.device)
+        n = evecs.shape[1]
+        out = torch.empty((self.np_, n * n), dtype=torch.complex128, device=self.device)
+        _lib.check(self.lib.khp_pair_densities(self.handle, _ptr(evecs), n, _ptr(out)))
+        return out
+
     def backward(self, evecs, evals, dLdE, levers=None, want_strain=True):
         evecs = _dev(evecs, torch.complex128, self.device)
         n = evecs.shape[1]
