@@ -547,3 +547,76 @@ def test_fermi_level_counts_holes():
     for kT, n in ((1e-4, 2.0), (1e-3, 3.0), (5e-3, 1.5)):
         mu = poisson_oracle.fermi_level(E, n, kT)
         assert abs(poisson_oracle.occupations(E, mu, kT).sum() - n) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# configuration interaction (Sec. II C, Eqs. 7-15)
+from oracle import ci as ci_oracle  # noqa: E402
+
+
+def _random_integrals(n, rng):
+    """Hermitian one-body matrix on 2n spin-orbitals and a spatial two-body
+    tensor with the symmetries of a Coulomb operator (built from random
+    complex overlap densities and a symmetric positive kernel)."""
+    A = rng.standard_normal((2 * n, 2 * n)) + 1j * rng.standard_normal((2 * n, 2 * n))
+    h = A + A.conj().T
+    npnt = 7
+    phi = rng.standard_normal((npnt, n)) + 1j * rng.standard_normal((npnt, n))
+    rho = np.einsum("pi,pk->pik", phi.conj(), phi)
+    B = rng.standard_normal((npnt, npnt))
+    G = B @ B.T + npnt * np.eye(npnt)
+    J = np.einsum("pik,pq,qjl->ijkl", rho, G, rho)
+    return h, J
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_ci_slater_condon_matches_brute_force(n):
+    """The determinant-basis CI matrix equals the full two-particle
+    Hamiltonian h1 + h2 + C projected on antisymmetric product states."""
+    rng = np.random.default_rng(n)
+    h, J = _random_integrals(n, rng)
+    H, dets = ci_oracle.ci_matrix(h, J, n)
+    M = 2 * n
+    I = np.eye(M)
+    H2 = np.kron(h, I) + np.kron(I, h)
+    for a in range(M):
+        for b in range(M):
+            for c in range(M):
+                for d in range(M):
+                    if a % 2 == c % 2 and b % 2 == d % 2:
+                        H2[a * M + b, c * M + d] += J[a // 2, b // 2, c // 2, d // 2]
+    P = np.zeros((M * M, len(dets)))
+    for x, (a, b) in enumerate(dets):
+        P[a * M + b, x] = 1 / np.sqrt(2)
+        P[b * M + a, x] = -1 / np.sqrt(2)
+    assert np.abs(P.T @ H2 @ P - H).max() < 1e-12 * np.abs(H).max()
+    assert np.abs(H - H.conj().T).max() < 1e-12 * np.abs(H).max()
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_ci_spin_labels_without_spin_orbit(n):
+    """Without spin-orbit coupling S^2 commutes with H: its eigenvalues are
+    exactly 0 (n(n+1)/2 singlets) and 2 (3 n(n-1)/2 triplet states)."""
+    s2 = np.linalg.eigvalsh(ci_oracle.spin_squared(n))
+    assert np.sum(np.abs(s2) < 1e-12) == n * (n + 1) // 2
+    assert np.sum(np.abs(s2 - 2) < 1e-12) == 3 * n * (n - 1) // 2
+
+
+def test_ci_coulomb_tensor_symmetries_and_exchange_sign():
+    """Coulomb integrals of H0 orbitals through the Poisson step: particle
+    swap J[ijkl] = J[jilk], Hermiticity J[ijkl] = conj(J[klij]); without
+    spin-orbit coupling the two-hole ground state of a double well is a
+    singlet (J_ex > 0)."""
+    p = inputs.small_problem(12, 6, 6, h=0.5, seed=5, strain=False)
+    p.material.update(delta_so=0.0)
+    gate = np.zeros((p.nz, p.ny, p.nx), dtype=np.uint8)
+    gate[:, :, 0] = 1
+    gate[:, :, -1] = 1
+    E, phi = ci_oracle.h0_orbitals(p, 2)
+    J = ci_oracle.coulomb_tensor(phi, p.nx, p.ny, p.nz, p.h, gate)
+    scale = np.abs(J).max()
+    assert np.abs(J - J.transpose(1, 0, 3, 2)).max() < 1e-12 * scale
+    assert np.abs(J - J.transpose(2, 3, 0, 1).conj()).max() < 1e-12 * scale
+    w, s2, jex = ci_oracle.exchange(ci_oracle.ci_matrix(ci_oracle.one_body(E, ci_oracle.orbital_overlaps(phi), 0.0),
+                                                        J, 2)[0], 2)
+    assert s2[0] < 1e-9 and jex > 0
