@@ -200,6 +200,11 @@ khp_status khp_apply(khp_handle h, const void* X_dev, void* Y_dev, int m, int pr
  * method 0 with m > 32. */
 khp_status khp_project(khp_handle h, const void* Y_dev, const void* W_dev, int m, int method,
                        double* G_host, double* S_host);
+/* khp_project over `rows` rows instead of the handle's N (any block of
+ * complex128 [rows][m], e.g. orbital-resolved or pair-density blocks of the
+ * CI step); the handle supplies the stream and scratch. */
+khp_status khp_project_rows(khp_handle h, const void* Y_dev, const void* W_dev, long long rows, int m,
+                            int method, double* G_host, double* S_host);
 khp_status khp_rotate(khp_handle h, const void* Y_dev, const void* W_dev, const double* Q_host,
                       int m, int method, void* X_dev, void* HX_dev);
 

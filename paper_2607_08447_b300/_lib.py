@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KH
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}
 
-EXPORTED = ["khp_create_grid", "khp_pair_densities", "khp_create_grid_h0", "khp_poisson_create", "khp_poisson_solve", "khp_sp_update",
+EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_create_grid_h0", "khp_poisson_create", "khp_poisson_solve", "khp_sp_update",
             "khp_poisson_destroy", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
             "khp_eigensolve",
             "khp_eigensolve_batched",
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.khp_sp_update.argtypes = [vp, vp, vp, d, vp, dp]
     lib.khp_poisson_destroy.argtypes = [vp]
     lib.khp_project.argtypes = [vp, vp, vp, i, i, vp, vp]
+    lib.khp_project_rows.argtypes = [vp, vp, vp, ctypes.c_longlong, i, i, vp, vp]
     lib.khp_rotate.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
     lib.khp_set_potential_strain_field.argtypes = [vp, vp, vp, vp, dp, i, dp, i]
     lib.khp_apply.argtypes = [vp, vp, vp, i, i]

@@ -580,25 +580,32 @@ khp_status khp_apply(khp_handle g, const void* X_dev, void* Y_dev, int m, int pr
     return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
 }
 
-khp_status khp_project(khp_handle g, const void* Y_dev, const void* W_dev, int m, int method, double* G_host,
-                       double* S_host) {
+khp_status khp_project_rows(khp_handle g, const void* Y_dev, const void* W_dev, long long rows, int m, int method,
+                            double* G_host, double* S_host) {
     g_err.clear();
     if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (rows < 1) return fail(KHP_ERR_INVALID_ARG, "rows must be >= 1");
     if (!Y_dev || !G_host || (W_dev && !S_host)) return fail(KHP_ERR_INVALID_ARG, "Y, G or S is NULL");
     if (m < 1 || m > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "m out of range 1..64");
     if (method != 0 && method != 1) return fail(KHP_ERR_INVALID_ARG, "method must be 0 or 1");
     if (method == 0 && !oz_supported(m, m)) return fail(KHP_ERR_INVALID_ARG, "method 0 takes m <= 32");
     CKS(ensure_partial(g));
-    const int nblk = dense_blocks(g->n);
+    const int nblk = std::min(dense_blocks(rows), dense_blocks(g->n));
     const double2* Y = (const double2*)Y_dev;
     const double2* W = (const double2*)W_dev;
-    if (method == 0) CK(launch_gram_oz(Y, W, g->n, m, 0, m, g->partial, nblk, g->small, g->stream));
-    else CK(launch_gram(Y, W, g->n, m, 0, m, g->partial, nblk, g->small, g->stream));
+    if (method == 0) CK(launch_gram_oz(Y, W, rows, m, 0, m, g->partial, nblk, g->small, g->stream));
+    else CK(launch_gram(Y, W, rows, m, 0, m, g->partial, nblk, g->small, g->stream));
     CK(cudaMemcpyAsync(G_host, g->small, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, g->stream));
     if (W)
         CK(cudaMemcpyAsync(S_host, g->small + m * m, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     return KHP_OK;
+}
+
+khp_status khp_project(khp_handle g, const void* Y_dev, const void* W_dev, int m, int method, double* G_host,
+                       double* S_host) {
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    return khp_project_rows(g, Y_dev, W_dev, g->n, m, method, G_host, S_host);
 }
 
 khp_status khp_rotate(khp_handle g, const void* Y_dev, const void* W_dev, const double* Q_host, int m, int method,

@@ -108,6 +108,18 @@ class KPGrid:
         _lib.check(self.lib.khp_apply(self.handle, _ptr(X), _ptr(Y), m, int(precision)))
         return Y
 
+    def project_rows(self, Y, W=None, method=0):
+        """Y^H Y and Y^H W for any complex128 [rows][m] blocks (see project)."""
+        Y = _dev(Y, torch.complex128, self.device)
+        W = _dev(W, torch.complex128, self.device)
+        rows, m = Y.shape
+        G = np.zeros((m, m), dtype=np.complex128)
+        S = np.zeros((m, m), dtype=np.complex128) if W is not None else None
+        _lib.check(self.lib.khp_project_rows(self.handle, _ptr(Y), _ptr(W), int(rows), m, int(method),
+                                             G.ctypes.data_as(ctypes.c_void_p),
+                                             None if S is None else S.ctypes.data_as(ctypes.c_void_p)))
+        return G, S
+
     def project(self, Y, W=None, method=0):
         """G = Y^H Y and S = Y^H W (Hermitian, from their upper triangles):
         method 0 on the tensor cores (split-digit products, FP64 accurate,
