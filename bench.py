@@ -375,6 +375,7 @@ def run_ours(args, rank, world, local_rank):
     line["projections"] = _projections_bench(grid, p.n_unknowns, SOLVE_KW["block_m"], hbm, torch)
     line["h0"] = _h0_bench(p, dev, torch, khp)
     line["sp"] = _sp_bench(p, dev, torch, khp)
+    line["ci"] = _ci_bench(p, dev, torch, khp)
 
     # end to end through host buffers: H2D of V and strain, solve, D2H of
     # eigenvalues and eigenvectors, every step
@@ -461,6 +462,33 @@ def _sp_bench(p, dev, torch, khp):
            "final_max_dV_ev": r.history[-1], "poisson_cg_iterations": r.poisson_iterations,
            "poisson_ms_cold": 1e3 * tp, "poisson_cold_iterations": P.last_iterations,
            "workload": "C2 grid and fields, grounded gates on both x faces, 2 holes, T 1.5 K, mix 0.3"}
+    P.close()
+    g.close()
+    return out
+
+
+def _ci_bench(p, dev, torch, khp):
+    """Two-hole CI on the C2 grid and fields: the lowest 4 orbitals of the
+    spin-independent H0 (defect-corrected solve), 16 Coulomb potentials
+    (32 Poisson solves, grounded gates on both x faces), K = 28
+    determinants."""
+    from paper_2607_08447_b300.ci import ci_exchange
+    from paper_2607_08447_b300.poisson import Poisson
+    gate = np.zeros((p.nz, p.ny, p.nx), dtype=np.uint8)
+    gate[:, :, 0] = 1
+    gate[:, :, -1] = 1
+    g = khp.KPGrid.from_problem(p, device=dev, bands=3)
+    P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V), device=dev)
+    kw = dict(block_m=16, degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1)
+    ci_exchange(g, P, 4, p.material["delta_so"], solve_kw=kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = ci_exchange(g, P, 4, p.material["delta_so"], solve_kw=kw)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out = {"s_total": t, "determinants": len(r.energies), "exchange_ev": r.exchange,
+           "lowest_two_hole_ev": [float(x) for x in r.energies[:4]],
+           "workload": "C2 grid and fields, H0 lowest 4 orbitals, grounded gates on both x faces"}
     P.close()
     g.close()
     return out
