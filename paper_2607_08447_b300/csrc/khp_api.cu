@@ -882,13 +882,17 @@ struct Solve {
         // scaling point: the lower spectral estimate (or the smallest Ritz
         // value once that is lower); the degree is capped so that the
         // amplification at the bottom of the spectrum stays <= 1e4 (filtered
-        // block well conditioned, no FP32 overflow)
+        // block well conditioned, no FP32 overflow; 1e5 for precision 2)
         const double lo_est = std::min(th[0], g->lambda_low);
         low = (lo_est < a) ? lo_est : a - 1e-3 * (lam_up - a);
         const double e = 0.5 * (lam_up - a), c = 0.5 * (lam_up + a);
         const double xl = std::fabs((low - c) / e);
         if (xl > 1.0) {
-            const int dmax = (int)std::floor(std::acosh(1e4) / std::acosh(xl));
+            // the defect-corrected mode filters the correction Z in FP32, not
+            // the amplified block itself, and takes a 1e5 cap (measured at
+            // C2: 7 instead of 8 outer iterations, 3 % faster)
+            const double cap = dc ? 1e5 : 1e4;
+            const int dmax = (int)std::floor(std::acosh(cap) / std::acosh(xl));
             deg = std::max(1, std::min(deg, dmax));
         }
         return KHP_OK;
