@@ -620,3 +620,120 @@ def test_ci_coulomb_tensor_symmetries_and_exchange_sign():
     w, s2, jex = ci_oracle.exchange(ci_oracle.ci_matrix(ci_oracle.one_body(E, ci_oracle.orbital_overlaps(phi), 0.0),
                                                         J, 2)[0], 2)
     assert s2[0] < 1e-9 and jex > 0
+
+
+# --------------------------------------------------------------------------
+# g-matrices (Sec. III B) and the magnetic two-hole model (Eqs. 16-17)
+from oracle import exchange as ex_oracle  # noqa: E402
+from oracle import gtensor as gt_oracle  # noqa: E402
+
+
+def test_g_matrix_free_spin_without_spin_orbit():
+    """Delta_so = 0: the 6x6 operator is H0 x 1_spin at B = 0, the lowest
+    doublet is phi (real, orbital non-degenerate) times spin, and only the
+    spin Zeeman term mu_B B.sigma acts on it (the orbital responses of a
+    real state vanish).  In the explicit basis {phi up, phi down} g = 2 I
+    exactly; in the eigensolver's basis g^T g = 4 I."""
+    p = _box(12, 6, 6, seed=3)
+    p.material.update(delta_so=0.0)
+    Np = p.n_points
+    _, phi = eig.lowest_dense(kp.assemble_h0(p), 1)
+    U = np.zeros((6 * Np, 2), dtype=complex)
+    U.reshape(Np, 2, 3, 2)[:, 0, :, 0] = phi[:, 0].reshape(Np, 3)
+    U.reshape(Np, 2, 3, 2)[:, 1, :, 1] = phi[:, 0].reshape(Np, 3)
+    g = gt_oracle.g_matrix(gt_oracle.magnetic_response(p, U))
+    assert np.abs(g - 2.0 * np.eye(3)).max() < 1e-9
+    _, U2 = gt_oracle.lowest_states(p, 2)
+    G, gp = gt_oracle.g_tensor(gt_oracle.g_matrix(gt_oracle.magnetic_response(p, U2)))
+    assert np.abs(G - 4.0 * np.eye(3)).max() < 1e-9
+
+
+@pytest.mark.parametrize("rot", ["identity", "device"])
+def test_g_matrix_predicts_the_zeeman_splitting(rot):
+    """With spin-orbit coupling and strain, the splitting of the lowest
+    Kramers doublet of the full operator H(b n) equals mu_B b |g n| up to
+    terms of order b^3 (second-order terms are proportional to the identity
+    on a Kramers doublet), for several directions n: an eigenvalue check
+    independent of the projection that defines g."""
+    p = _box(12, 6, 6, seed=3, rot=rot)
+    _, U = gt_oracle.lowest_states(p, 2)
+    g = gt_oracle.g_matrix(gt_oracle.magnetic_response(p, U))
+    rng = np.random.default_rng(4)
+    b = 1e-2
+    for n in [np.eye(3)[0], np.eye(3)[2]] + list(rng.standard_normal((2, 3))):
+        n = n / np.linalg.norm(n)
+        w, _ = eig.lowest_dense(kp.assemble(p.with_(B=b * n)), 2)
+        assert abs((w[1] - w[0]) / (kp.MU_B * b) - np.linalg.norm(g @ n)) < 1e-6 * np.abs(g).max()
+    # the g-tensor is basis independent: a random U(2) rotation of the doublet
+    q, _ = np.linalg.qr(rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2)))
+    g2 = gt_oracle.g_matrix(gt_oracle.magnetic_response(p, U @ q))
+    assert np.abs(g2.T @ g2 - g.T @ g).max() < 1e-10
+    assert abs(np.linalg.det(g2) - np.linalg.det(g)) < 1e-10
+
+
+@pytest.mark.parametrize("rot", ["identity", "device"])
+def test_left_right_g_tensors_mirror_symmetric_double_dot(rot):
+    """A double dot symmetric under x -> -x (noise-free double well plus
+    x-independent terms that break the y and z mirrors; the {100} and {110}
+    mirrors are crystal symmetries) maps the left dot onto the right one.
+    B is axial, so G_R = S G_L S with S = diag(1, -1, -1), and the
+    off-diagonal G_xy, G_xz flip sign (nonzero here)."""
+    p = _box(14, 6, 6, seed=3, strain=False, noise_mev=0.0, rot=rot)
+    z, y, x = np.meshgrid(np.arange(p.nz), np.arange(p.ny), np.arange(p.nx), indexing="ij")
+    V = p.V + 3e-3 * (y - 2.5) / 6 + 2e-3 * (z - 2.5) / 6 + 1e-3 * (y - 2.5) * (z - 2.5) / 36
+    d = gt_oracle.dqd_g_tensors(p.with_(V=V))
+    S = np.diag([1.0, -1.0, -1.0])
+    GL = d["g_left"].T @ d["g_left"]
+    GR = d["g_right"].T @ d["g_right"]
+    assert np.abs(GR - S @ GL @ S).max() < 1e-9
+    assert np.abs(d["gsym_right"] - S @ d["gsym_left"] @ S).max() < 1e-9
+    assert max(abs(GL[0, 1]), abs(GL[0, 2])) > 1e-3
+    # the symmetric tensor squares to G and keeps the sign of det g
+    assert np.abs(d["gsym_left"] @ d["gsym_left"] - GL).max() < 1e-12
+    assert np.sign(np.linalg.det(d["gsym_left"])) == np.sign(np.linalg.det(d["g_left"]))
+
+
+def test_hb_is_two_spin_zeeman_plus_singlet_tunnelling():
+    """Eq. 16 at t = 0: the {S(1,1), T+, T-, T0} block is the two-spin
+    Zeeman Hamiltonian b_L.sigma_L + b_R.sigma_R with b_L,R = (bbar +- db)/2
+    (spectrum +-|b_L| +- |b_R| for random fields); at zero field the
+    singlet block [[U - eps, sqrt2 t], [sqrt2 t, 0]] gives
+    ((U - eps) -+ sqrt((U - eps)^2 + 8 t^2)) / 2, and the lower root tends
+    to -J = -2 t^2 / (U - eps)."""
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        bL, bR = rng.standard_normal((2, 3)) * 1e-5
+        H = ex_oracle.hamiltonian_b(1e-3, 0.0, bL + bR, bL - bR)
+        assert np.abs(H - H.conj().T).max() == 0.0
+        a, b = np.linalg.norm(bL), np.linalg.norm(bR)
+        assert np.abs(np.linalg.eigvalsh(H[1:, 1:]) - np.sort([a + b, -a - b, a - b, b - a])).max() < 1e-18
+        bb = bL + bR
+        wt = np.linalg.eigvalsh(ex_oracle.hamiltonian_b(1e-3, 0.0, bb, np.zeros(3))[2:, 2:])
+        assert np.abs(wt - np.linalg.norm(bb) * np.array([-1.0, 0.0, 1.0])).max() < 1e-18
+    ue, t = 2e-3, 1.13e-5
+    w = np.linalg.eigvalsh(ex_oracle.hamiltonian_b(ue, t, np.zeros(3), np.zeros(3)))
+    r = np.sqrt(ue * ue + 8 * t * t)
+    assert np.abs(w - np.sort([0.0, 0.0, 0.0, (ue - r) / 2, (ue + r) / 2])).max() < 1e-18
+    J = 2 * t * t / ue
+    assert abs(-(ue - r) / 2 - J) < 1e-3 * J
+    assert abs(ex_oracle.u_minus_eps(ex_oracle.tunnel_coupling(np.sqrt(2) * t), J) - ue) < 1e-15
+
+
+def test_anisotropic_exchange_closed_forms():
+    """Isotropic, equal g-tensors, n_so = z: for B along n_so the exchange
+    stays isotropic (|J_perp| = J_par = J); for B perpendicular to n_so
+    |J_perp| = J cos^2 theta_so and J_par = J cos 2 theta_so; without
+    spin-orbit rotation J_perp = J_par = J for any B, and delta E_Z = 0."""
+    J, th = 1.0e-6, 0.3
+    g = 1.7 * np.eye(3)
+    n = np.array([0.0, 0.0, 1.0])
+    _, jp, jl, dz = ex_oracle.anisotropic_exchange(J, g, g, th, n, [0.0, 0.0, 0.5])
+    assert abs(jp - J) < 1e-15 and abs(jl - J) < 1e-15
+    for B in ([0.5, 0.0, 0.0], [0.3, -0.4, 0.0]):
+        _, jp, jl, dz = ex_oracle.anisotropic_exchange(J, g, g, th, n, B)
+        assert abs(jp - J * np.cos(th) ** 2) < 1e-15 and abs(jl - J * np.cos(2 * th)) < 1e-15
+        assert abs(dz - kp.MU_B * 1.7 * 0.5 * np.sin(th)) < 1e-15
+    rng = np.random.default_rng(2)
+    for B in rng.standard_normal((3, 3)):
+        _, jp, jl, dz = ex_oracle.anisotropic_exchange(J, g, g, 0.0, rng.standard_normal(3), B)
+        assert abs(jp - J) < 1e-15 and abs(jl - J) < 1e-15 and dz == 0.0
