@@ -376,6 +376,7 @@ def run_ours(args, rank, world, local_rank):
     line["h0"] = _h0_bench(p, dev, torch, khp)
     line["sp"] = _sp_bench(p, dev, torch, khp)
     line["ci"] = _ci_bench(p, dev, torch, khp)
+    line["gtensor"] = _gtensor_bench(p, dev, torch, khp, line["ci"].get("exchange_ev"))
 
     # end to end through host buffers: H2D of V and strain, solve, D2H of
     # eigenvalues and eigenvectors, every step
@@ -490,6 +491,48 @@ def _ci_bench(p, dev, torch, khp):
            "lowest_two_hole_ev": [float(x) for x in r.energies[:4]],
            "workload": "C2 grid and fields, H0 lowest 4 orbitals, grounded gates on both x faces"}
     P.close()
+    g.close()
+    return out
+
+
+def _gtensor_bench(p, dev, torch, khp, j_ci):
+    """g-matrices of the bonding/anti-bonding doublets and the left/right
+    g-tensors on the C2 grid and fields (B set to 0 for the solve and
+    restored): the 4-state defect-corrected solve, then the responses
+    (6 operator applies at B = +-d e_j, 6 tensor-core projections) and the
+    position moments.  Then the host maps of Eq. 17 on a 91 x 181 grid of
+    field directions, with the CI's J and a stated spin-orbit rotation
+    (theta_so = 0.2 about y: the paper takes it from experiment)."""
+    from paper_2607_08447_b300 import exchange as ex
+    from paper_2607_08447_b300.gtensor import g_tensors
+    g = khp.KPGrid.from_problem(p, device=dev)
+    kw = dict(block_m=12, degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1)
+    g_tensors(g, solve_kw=kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = g_tensors(g, solve_kw=kw)
+    torch.cuda.synchronize()
+    t_total = time.perf_counter() - t0
+    g.set_B(np.zeros(3))
+    st = g.eigensolve(4, **kw)
+    g.set_B(p.B)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g_tensors(g, states=(st.evals, st.evecs))
+    torch.cuda.synchronize()
+    t_resp = time.perf_counter() - t0
+    out = {"s_total": t_total, "s_response_and_moments": t_resp, "delta_ev": r.delta, "tunnel_ev": r.tunnel,
+           "g_left_principal": [float(x) for x in np.sqrt(np.linalg.eigvalsh(r.g_left.T @ r.g_left))],
+           "g_right_principal": [float(x) for x in np.sqrt(np.linalg.eigvalsh(r.g_right.T @ r.g_right))],
+           "workload": "C2 grid and fields at B = 0, lowest 4 states (bonding + anti-bonding doublets), d = 0.01 T"}
+    if j_ci and j_ci > 0:
+        th, ph = np.linspace(0, np.pi, 91), np.linspace(0, 2 * np.pi, 181)
+        t0 = time.perf_counter()
+        jp, jl, dz = ex.exchange_maps(j_ci, r.gsym_left, r.gsym_right, 0.2, [0.0, 1.0, 0.0], 0.1, th, ph)
+        out["maps_ms"] = (time.perf_counter() - t0) * 1e3
+        out["u_minus_eps_ev"] = 2 * r.tunnel ** 2 / j_ci
+        out["jperp_range_ev"] = [float(jp.min()), float(jp.max())]
+        out["jpar_range_ev"] = [float(jl.min()), float(jl.max())]
     g.close()
     return out
 

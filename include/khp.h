@@ -290,6 +290,19 @@ khp_status khp_eigensolve_batched(const khp_handle* hs, int count, const khp_sol
  * pointers or n outside 1..64. */
 khp_status khp_pair_densities(khp_handle h, const void* evecs_dev, int n, void* rho_dev);
 
+/* First moments of m states about the box centre (the position operator
+ * projected on them).  The eigenvectors of the projection along the dot
+ * axis localise the bonding and anti-bonding doublets of a double dot on
+ * the left and right dots, whose g-matrices give the g-tensors of Eq. 16
+ * (Sec. III B):
+ *     D[a][i][j] = sum_p r_a(p) sum_b conj(X_i(p, b)) X_j(p, b),
+ *     r_a(p) = (i_a(p) - (n_a - 1) / 2) h   (nm),   a = x, y, z.
+ *  X_dev   complex128 [N][m] row-major on the handle's device (N = bands Np)
+ *  D_host  complex128 [3][m][m] (Hermitian), written before the call returns
+ * Synchronous on the handle's stream.  Errors: INVALID_ARG for NULL
+ * pointers or m outside 1..16. */
+khp_status khp_position_moments(khp_handle h, const void* X_dev, int m, double* D_host);
+
 /* Hole density (Sec. II B, fed to Poisson):
  *  rho_dev[p] = sum_i w_host[i] * sum_b |psi_i(6p+b)|^2   (discrete norm)
  *  evecs_dev complex128 [N][n] row-major.  Deterministic summation order. */

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KH
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}
 
-EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_create_grid_h0", "khp_poisson_create", "khp_poisson_solve", "khp_sp_update",
+EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_position_moments", "khp_create_grid_h0", "khp_poisson_create", "khp_poisson_solve", "khp_sp_update",
             "khp_poisson_destroy", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
             "khp_eigensolve",
             "khp_eigensolve_batched",
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                            ctypes.POINTER(vp), dp, ctypes.POINTER(Stats), i]
     lib.khp_density.argtypes = [vp, vp, i, dp, vp]
     lib.khp_pair_densities.argtypes = [vp, vp, i, vp]
+    lib.khp_position_moments.argtypes = [vp, vp, i, vp]
     lib.khp_eigs_backward.argtypes = [vp, vp, dp, i, dp, vp, vp, vp, i, dp]
     lib.khp_eigs_backward_noalloc.argtypes = [vp, vp, dp, i, dp, vp, vp, vp, i, dp]
     lib.khp_destroy.argtypes = [vp]

@@ -29,13 +29,6 @@ size_t gram_partial_elems(int m, int nblk) { return (size_t)nblk * 2 * m * m; }
 // G = Y^H Y and S = Y^H W are Hermitian (S because W = H Y with H Hermitian),
 // so only their upper triangles are accumulated (packed row by row,
 // mt = m(m+1)/2 entries each); the reduction writes both triangles.
-__device__ __forceinline__ void packed_ij(int k, int m, int& i, int& j) {
-    int row = 0, len = m;
-    while (k >= len) { k -= len; ++row; --len; }
-    i = row;
-    j = row + k;
-}
-
 template <int K>
 __global__ void __launch_bounds__(kThreads) gram_kernel(const double2* __restrict__ Y,
                                                        const double2* __restrict__ W, long long rows,

@@ -1278,6 +1278,20 @@ extern "C" khp_status khp_pair_densities(khp_handle g, const void* evecs_dev, in
     return KHP_OK;
 }
 
+extern "C" khp_status khp_position_moments(khp_handle g, const void* X_dev, int m, double* D_host) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!X_dev || !D_host) return fail(KHP_ERR_INVALID_ARG, "X or D is NULL");
+    if (m < 1 || m > KHP_MAX_MOMENT_M) return fail(KHP_ERR_INVALID_ARG, "m out of range 1..16");
+    CKS(ensure_partial(g));
+    CK(launch_moments((const double2*)X_dev, g->nx, g->ny, g->nz, g->nb, m, g->h, g->partial, g->partial_elems,
+                      g->small, g->stream));
+    g->launches += 2;
+    CK(cudaMemcpyAsync(D_host, g->small, sizeof(double2) * 3 * m * m, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return KHP_OK;
+}
+
 extern "C" khp_status khp_density(khp_handle g, const void* evecs_dev, int n, const double* w_host,
                                   double* rho_dev) {
     g_err.clear();

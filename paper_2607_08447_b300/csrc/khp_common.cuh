@@ -41,6 +41,15 @@ __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
     acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
 }
 
+// packed upper-triangle index k -> (i, j), i <= j, rows of an m x m matrix
+// in order: (0,0) (0,1) .. (0,m-1) (1,1) ..
+__device__ __forceinline__ void packed_ij(int k, int m, int& i, int& j) {
+    int row = 0, len = m;
+    while (k >= len) { k -= len; ++row; --len; }
+    i = row;
+    j = row + k;
+}
+
 // ------------------------------------------------------------ stencil data
 // The 9 neighbour pairs of the 19-point stencil: pair d couples a point to
 // the neighbours at +off[d] and -off[d] with the same real symmetric 3x3

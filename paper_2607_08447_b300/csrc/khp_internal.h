@@ -7,6 +7,7 @@
 
 #define KHP_MAX_GATES 16
 #define KHP_MAX_M 64
+#define KHP_MAX_MOMENT_M 16
 #define KHP_PHI0 658.2119569        /* hbar / e  [T nm^2] */
 #define KHP_MU_B 5.7883818060e-5    /* Bohr magneton [eV / T] */
 #define KHP_HB2M 0.0380998212       /* hbar^2 / (2 m0) [eV nm^2] */
@@ -82,6 +83,10 @@ cudaError_t launch_dc_combine(const double2* X, const double2* HX, const float2*
 
 // observables.cu
 cudaError_t launch_pair_density(const double2* psi, long long np, int n, int nb, double2* out, cudaStream_t st);
+// D [3][m][m] = first moments of the m states X about the box centre
+// (partial: scratch of partial_elems entries)
+cudaError_t launch_moments(const double2* X, int nx, int ny, int nz, int nb, int m, double h, double2* partial,
+                           size_t partial_elems, double2* out, cudaStream_t st);
 cudaError_t launch_density(const double2* psi, long long np, int n, const double* w,
                            const uint8_t* mask, double* rho, cudaStream_t st, int nb = 6);
 cudaError_t launch_backward(const double2* psi, long long np, int n, const double* g,

@@ -169,3 +169,75 @@ cudaError_t launch_pair_density(const double2* psi, long long np, int n, int nb,
 }
 
 }  // namespace khp
+
+// ------------------------------------------------------------------------
+// First moments of a block of states about the box centre: the position
+// operator projected on the states,
+//   D_a[i][j] = sum_p r_a(p) sum_b conj(X_i(p, b)) X_j(p, b),
+//   r_a(p) = (i_a(p) - (n_a - 1) / 2) h,   a = x, y, z,
+// whose eigenvectors along the dot axis localise the bonding and
+// anti-bonding doublets of a double dot on the left and right dots
+// (g-tensors of Sec. III B).  One thread per packed pair (i <= j) and point
+// group; a block sums its groups in group order, the blocks are summed in
+// block order (sum_partials_herm), so the result is bitwise reproducible.
+namespace khp {
+
+__global__ void __launch_bounds__(256) moments_kernel(const double2* __restrict__ X, int nx, int ny,
+                                                      long long np, int nb, int m, double h, double cx,
+                                                      double cy, double cz, double2* __restrict__ partial) {
+    extern __shared__ double2 acc_s[];   // [groups][3 mt]
+    const int mt = m * (m + 1) / 2;
+    const int groups = blockDim.x / mt;
+    const int gi = threadIdx.x / mt;
+    const int k = threadIdx.x - gi * mt;
+    if (gi < groups) {
+        int i, j;
+        packed_ij(k, m, i, j);
+        double2 ax = make_double2(0.0, 0.0), ay = ax, az = ax;
+        for (long long p = (long long)blockIdx.x * groups + gi; p < np; p += (long long)gridDim.x * groups) {
+            const double2* row = X + p * nb * m;
+            double2 q = make_double2(0.0, 0.0);
+            for (int b = 0; b < nb; ++b) cfmac(q, row[b * m + i], row[b * m + j]);
+            const long long yz = p / nx;
+            const double x = ((double)(p - yz * nx) - cx) * h;
+            const double y = ((double)(yz % ny) - cy) * h;
+            const double z = ((double)(yz / ny) - cz) * h;
+            ax.x = fma(x, q.x, ax.x); ax.y = fma(x, q.y, ax.y);
+            ay.x = fma(y, q.x, ay.x); ay.y = fma(y, q.y, ay.y);
+            az.x = fma(z, q.x, az.x); az.y = fma(z, q.y, az.y);
+        }
+        double2* a = acc_s + gi * 3 * mt;
+        a[k] = ax;
+        a[mt + k] = ay;
+        a[2 * mt + k] = az;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * mt; e += blockDim.x) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int g = 0; g < groups; ++g) {
+            const double2 v = acc_s[g * 3 * mt + e];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        partial[(size_t)blockIdx.x * 3 * mt + e] = s;
+    }
+}
+
+cudaError_t launch_moments(const double2* X, int nx, int ny, int nz, int nb, int m, double h, double2* partial,
+                           size_t partial_elems, double2* out, cudaStream_t st) {
+    const int mt = m * (m + 1) / 2;
+    const int groups = 256 / mt;
+    const long long np = (long long)nx * ny * nz;
+    long long blocks = (np + groups - 1) / groups;
+    blocks = std::min<long long>(blocks, 148 * 4);
+    blocks = std::min<long long>(blocks, (long long)(partial_elems / (3 * mt)));
+    if (blocks < 1) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double2) * groups * 3 * mt;
+    moments_kernel<<<(unsigned)blocks, 256, smem, st>>>(X, nx, ny, np, nb, m, h, 0.5 * (nx - 1),
+                                                       0.5 * (ny - 1), 0.5 * (nz - 1), partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_sum_partials_herm(partial, (int)blocks, m, 3, out, st);
+}
+
+}  // namespace khp

@@ -95,6 +95,17 @@ class KPGrid:
         _lib.check(self.lib.khp_set_potential_strain_field(self.handle, _ptr(V), _ptr(strain), _ptr(levers),
                                                            _lib.dptr(a), ng, _lib.dptr(Bh), int(gauge)))
         self._keep = (V, strain, levers)   # alive until the stream has consumed them
+        self._fields = (V, strain, levers, a, ng, int(gauge))
+        self.B = np.zeros(3) if Bh is None else Bh.copy()
+        return self
+
+    def set_B(self, B):
+        """Change only the magnetic field (the other fields as last set)."""
+        V, strain, levers, a, ng, gauge = self._fields
+        Bh = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(3))
+        _lib.check(self.lib.khp_set_potential_strain_field(self.handle, _ptr(V), _ptr(strain), _ptr(levers),
+                                                           _lib.dptr(a), ng, _lib.dptr(Bh), gauge))
+        self.B = Bh.copy()
         return self
 
     def apply(self, X, precision=0):
@@ -174,6 +185,15 @@ class KPGrid:
         rho = torch.empty(self.np_, dtype=torch.float64, device=self.device)
         _lib.check(self.lib.khp_density(self.handle, _ptr(evecs), evecs.shape[1], _lib.dptr(w), _ptr(rho)))
         return rho
+
+    def position_moments(self, X):
+        """[3][m][m] numpy: sum_p r_a(p) X(p)^H X(p), r_a the coordinate (nm)
+        about the box centre (khp_position_moments)."""
+        X = _dev(X, torch.complex128, self.device)
+        m = X.shape[1]
+        D = np.zeros((3, m, m), dtype=np.complex128)
+        _lib.check(self.lib.khp_position_moments(self.handle, _ptr(X), m, D.ctypes.data_as(ctypes.c_void_p)))
+        return D
 
     def pair_densities(self, evecs):
         """rho_jl(p) = sum_b conj(psi_j) psi_l for all ordered (j, l):
