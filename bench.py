@@ -525,7 +525,7 @@ def _gtensor_bench(p, dev, torch, khp, j_ci):
            "g_left_principal": [float(x) for x in np.sqrt(np.linalg.eigvalsh(r.g_left.T @ r.g_left))],
            "g_right_principal": [float(x) for x in np.sqrt(np.linalg.eigvalsh(r.g_right.T @ r.g_right))],
            "workload": "C2 grid and fields at B = 0, lowest 4 states (bonding + anti-bonding doublets), d = 0.01 T"}
-    if j_ci and j_ci > 0:
+    if j_ci:
         th, ph = np.linspace(0, np.pi, 91), np.linspace(0, 2 * np.pi, 181)
         t0 = time.perf_counter()
         jp, jl, dz = ex.exchange_maps(j_ci, r.gsym_left, r.gsym_right, 0.2, [0.0, 1.0, 0.0], 0.1, th, ph)
