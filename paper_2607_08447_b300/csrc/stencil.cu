@@ -156,6 +156,38 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
 
     const C* xp = a.x + p * ps + col;
     C acc[6][VG];
+    // acc starts as gamma prev (+ src_coef[col] src): these streams are
+    // loaded first, so their latency overlaps the centre and neighbour loads
+    // instead of trailing the neighbour sums
+    {
+        const C* pp = a.prev ? a.prev + p * ps + col : nullptr;
+        C pv[6][VG], sv[6][VG];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (pp) load_vg<R, VG>(pv[b], pp + b * ld);
+            if (SRC) load_vg<R, VG>(sv[b], a.src + p * ps + col + b * ld);
+        }
+        R sc[VG];
+        if (SRC) {
+#pragma unroll
+            for (int v = 0; v < VG; ++v) sc[v] = a.src_coef[col + v];
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int v = 0; v < VG; ++v) {
+                C o = mk<R>(R(0), R(0));
+                if (pp) {
+                    o.x = a.gamma * pv[b][v].x;
+                    o.y = a.gamma * pv[b][v].y;
+                }
+                if (SRC) {
+                    o.x = fma(sc[v], sv[b][v].x, o.x);
+                    o.y = fma(sc[v], sv[b][v].y, o.y);
+                }
+                acc[b][v] = o;
+            }
+    }
     {
         C xs[6][VG];
 #pragma unroll
@@ -165,7 +197,7 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
         for (int k = 0; k < 6; ++k) o[k] = a.alpha * __ldg(a.onsite + p * 6 + k);
 #pragma unroll
         for (int k = 0; k < 3; ++k) o[k] += a.beta;
-        sym3<R, VG, true, NS>(acc, o, a.c.onsite_nz | 7u, xs);
+        sym3<R, VG, false, NS>(acc, o, a.c.onsite_nz | 7u, xs);
         // spin-orbit + Zeeman (alpha-scaled): constant complex 6x6, zero parts skipped
 #pragma unroll
         for (int b = 0; b < (NB == 6 ? 6 : 0); ++b) {
@@ -296,38 +328,8 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
         }
     }
 
-    // y = acc + gamma prev (+ src_coef[col] src)
-    const C* pp = a.prev ? a.prev + p * ps + col : nullptr;
-    R sc[VG];
-    if (SRC) {
 #pragma unroll
-        for (int v = 0; v < VG; ++v) sc[v] = a.src_coef[col + v];
-    }
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        C out[VG];
-#pragma unroll
-        for (int v = 0; v < VG; ++v) out[v] = acc[b][v];
-        if (pp) {
-            C wv[VG];
-            load_vg<R, VG>(wv, pp + b * ld);
-#pragma unroll
-            for (int v = 0; v < VG; ++v) {
-                out[v].x = fma(a.gamma, wv[v].x, out[v].x);
-                out[v].y = fma(a.gamma, wv[v].y, out[v].y);
-            }
-        }
-        if (SRC) {
-            C sv[VG];
-            load_vg<R, VG>(sv, a.src + p * ps + col + b * ld);
-#pragma unroll
-            for (int v = 0; v < VG; ++v) {
-                out[v].x = fma(sc[v], sv[v].x, out[v].x);
-                out[v].y = fma(sc[v], sv[v].y, out[v].y);
-            }
-        }
-        store_vg<R, VG>(yp + b * ld, out);
-    }
+    for (int b = 0; b < NB; ++b) store_vg<R, VG>(yp + b * ld, acc[b]);
 }
 
 template <typename R, int VG, int PH>
