@@ -95,13 +95,46 @@ def occupations(E, mu, kT):
     return 0.5 * (1.0 - np.tanh(0.5 * (np.asarray(E) - mu) / kT))
 
 
-def sp_loop(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, mix, iters, bands=6, eps_r=EPS_SI):
+class Anderson:
+    """Anderson mixing (Anderson 1965; the "type II" form of Walker and Ni,
+    SIAM J. Numer. Anal. 49, 2011) for a fixed point V = G(V).  With the
+    residual F_k = G(V_k) - V_k and the differences of the last m iterates
+    and residuals, dV_i = V_{i+1} - V_i and dF_i = F_{i+1} - F_i:
+        gamma   = argmin || F_k - dF gamma ||_2
+        V_{k+1} = V_k + beta F_k - (dV + beta dF) gamma.
+    With no history (the first step) this is linear mixing with weight beta.
+    The paper says only that the loop is repeated until convergence; this
+    scheme is an addition (a reading), not the paper's."""
+
+    def __init__(self, beta, depth):
+        self.beta, self.depth = float(beta), int(depth)
+        self.V, self.F = [], []
+
+    def step(self, V, GV):
+        F = GV - V
+        self.V.append(V.copy())
+        self.F.append(F.copy())
+        m = min(self.depth, len(self.V) - 1)
+        out = V + self.beta * F
+        if m > 0:
+            dV = np.stack([self.V[-m + i] - self.V[-m - 1 + i] for i in range(m)], axis=1)
+            dF = np.stack([self.F[-m + i] - self.F[-m - 1 + i] for i in range(m)], axis=1)
+            gamma = np.linalg.lstsq(dF, F, rcond=None)[0]
+            out = out - (dV + self.beta * dF) @ gamma
+        return out
+
+
+def sp_loop(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, mix, iters, bands=6, eps_r=EPS_SI,
+            anderson_depth=0):
     """Fixed number of Schroedinger-Poisson iterations from V = V_ext (dense
-    eigensolver; small grids).  Returns (V, E, mu, history of max |dV|)."""
+    eigensolver; small grids).  Linear mixing with weight `mix`, or Anderson
+    mixing (damping `mix`) over `anderson_depth` > 0 previous iterates.
+    Returns (V, E, mu, history of max |dV|)."""
     nx, ny, nz, h = prob.nx, prob.ny, prob.nz, prob.h
     kT = KB_EV * T
     V = np.asarray(V_ext, dtype=np.float64).reshape(-1).copy()
     hist = []
+    acc = Anderson(mix, anderson_depth) if anderson_depth > 0 else None
     for _ in range(iters):
         q = prob.with_(V=V.reshape(nz, ny, nx))
         H = kp.assemble(q) if bands == 6 else kp.assemble_h0(q)
@@ -110,7 +143,8 @@ def sp_loop(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, mix, iters, 
         f = occupations(E, mu, kT)
         rho = observables.density(psi, f, bands) / h ** 3
         phi = solve(nx, ny, nz, h, gate_mask, gate_phi, rho, eps_r)
-        Vn = (1.0 - mix) * V + mix * (np.asarray(V_ext).reshape(-1) + phi)
+        GV = np.asarray(V_ext).reshape(-1) + phi
+        Vn = acc.step(V, GV) if acc is not None else (1.0 - mix) * V + mix * GV
         hist.append(float(np.abs(Vn - V).max()))
         V = Vn
     return V, E, mu, hist

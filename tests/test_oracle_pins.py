@@ -737,3 +737,38 @@ def test_anisotropic_exchange_closed_forms():
     for B in rng.standard_normal((3, 3)):
         _, jp, jl, dz = ex_oracle.anisotropic_exchange(J, g, g, 0.0, rng.standard_normal(3), B)
         assert abs(jp - J) < 1e-15 and abs(jl - J) < 1e-15 and dz == 0.0
+
+
+# --------------------------------------------------------------------------
+# Anderson mixing of the SP loop (an addition: the paper only iterates to
+# convergence)
+from oracle import poisson as po_oracle  # noqa: E402
+
+
+@pytest.mark.parametrize("beta", [1.0, 0.5])
+def test_anderson_terminates_on_linear_fixed_point(beta):
+    """On a linear map G(V) = A V + c in n dimensions, Anderson mixing with
+    unlimited depth is equivalent to GMRES on (I - A) V = c, so it reaches
+    the fixed point after at most n + 1 steps in exact arithmetic; linear
+    mixing with the same weight is still far from it."""
+    rng = np.random.default_rng(3)
+    n = 6
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(rng.uniform(-0.95, 0.95, n)) @ Q.T
+    c = rng.standard_normal(n)
+    Vstar = np.linalg.solve(np.eye(n) - A, c)
+    acc = po_oracle.Anderson(beta, depth=20)
+    V = np.zeros(n)
+    lin = np.zeros(n)
+    for _ in range(n + 2):
+        V = acc.step(V, A @ V + c)
+        lin = (1 - beta) * lin + beta * (A @ lin + c)
+    assert np.abs(V - Vstar).max() < 1e-9 * np.abs(Vstar).max()
+    assert np.abs(lin - Vstar).max() > 1e-3 * np.abs(Vstar).max()
+
+
+def test_anderson_first_step_is_linear_mixing():
+    rng = np.random.default_rng(4)
+    V, GV = rng.standard_normal(10), rng.standard_normal(10)
+    acc = po_oracle.Anderson(0.3, depth=4)
+    assert np.abs(acc.step(V, GV) - (0.7 * V + 0.3 * GV)).max() < 1e-15
