@@ -255,6 +255,28 @@ khp_status khp_poisson_solve(khp_poisson p, const double* rho_dev, double* phi_d
 khp_status khp_sp_update(khp_poisson p, const double* V_ext_dev, const double* phi_dev, double mix, double* V_dev,
                          double* max_change);
 
+/* Anderson-mixed potential update of the Schroedinger-Poisson loop (the
+ * paper repeats the loop until convergence, Sec. II B, and names no scheme;
+ * this type-II Anderson mixing is an addition).  With the residual
+ * F_k = V_ext + phi - V_k of the fixed point and the differences
+ * dV_i = V_{i+1} - V_i, dF_i = F_{i+1} - F_i of the last m = min(k, depth)
+ * calls (kept on the handle):
+ *     gamma   = argmin |F_k - dF gamma|_2   (normal equations, host, m <= 8)
+ *     V_{k+1} = V_k + beta F_k - sum_i gamma_i (dV_i + beta dF_i)
+ * The first call after khp_poisson_create, khp_sp_anderson_reset or a
+ * change of depth is the linear step V + beta F.  A singular history
+ * falls back to that step.
+ *  V_ext_dev  float64 [Np] or NULL (zero);  phi_dev float64 [Np]
+ *  V_dev      float64 [Np], updated in place
+ *  max_change max |V_{k+1} - V_k| (host)
+ * Synchronous.  Errors: INVALID_ARG (NULL, beta outside (0, 1], depth
+ * outside 1..8), OOM (history buffers: (2 depth_max + 3) Np doubles). */
+khp_status khp_sp_anderson(khp_poisson p, const double* V_ext_dev, const double* phi_dev, double beta, int depth,
+                           double* V_dev, double* max_change);
+
+/* Forget the Anderson history (start of a new self-consistent loop). */
+khp_status khp_sp_anderson_reset(khp_poisson p);
+
 khp_status khp_poisson_destroy(khp_poisson p);
 
 /* Solve `count` independent problems (a gate-voltage / detuning sweep,

@@ -126,9 +126,29 @@ def exchange(Hci, n_orb):
     return w, s2, triplet - singlet
 
 
-def ci_pipeline(prob, n_orb, gate_mask, eps_r=poisson.EPS_SI):
-    """H0 orbitals -> one- and two-body integrals -> CI energies and J."""
+def truncate_orbitals(E, e_c, T):
+    """Number of orbitals kept by the charging-energy filter (Sec. III A: a
+    Fermi-Dirac function at E_F = E_C and temperature T applied to the
+    orbital energies measured from the lowest): those whose filter value
+    1 / (1 + exp((E_i - E_0 - E_C) / kT)) is at least 1/2."""
+    kT = poisson.KB_EV * T
+    n = 0
+    for e in E:
+        x = (e - E[0] - e_c) / kT
+        w = 0.0 if x > 700 else 1.0 / (1.0 + np.exp(x))
+        if w >= 0.5:
+            n += 1
+    return n
+
+
+def ci_pipeline(prob, n_orb, gate_mask, eps_r=poisson.EPS_SI, e_c=None, T_c=1.0):
+    """H0 orbitals -> one- and two-body integrals -> CI energies and J.
+    With e_c, the lowest n_orb orbitals are filtered by truncate_orbitals."""
     E, phi = h0_orbitals(prob, n_orb)
+    if e_c is not None:
+        k = truncate_orbitals(E, e_c, T_c)
+        E, phi = E[:k], phi[:, :k]
+        n_orb = k
     O = orbital_overlaps(phi)
     h = one_body(E, O, prob.material["delta_so"])
     J = coulomb_tensor(phi, prob.nx, prob.ny, prob.nz, prob.h, gate_mask, eps_r)

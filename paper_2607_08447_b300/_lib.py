@@ -25,7 +25,7 @@ EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_po
             "khp_eigensolve",
             "khp_eigensolve_batched",
             "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",
-            "khp_last_error", "khp_version"]
+            "khp_last_error", "khp_version", "khp_sp_anderson", "khp_sp_anderson_reset"]
 
 
 class Material(ctypes.Structure):
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.khp_poisson_create.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, vp, vp, vp]
     lib.khp_poisson_solve.argtypes = [vp, vp, vp, d, i, ctypes.POINTER(i), dp]
     lib.khp_sp_update.argtypes = [vp, vp, vp, d, vp, dp]
+    lib.khp_sp_anderson.argtypes = [vp, vp, vp, d, i, vp, dp]
+    lib.khp_sp_anderson_reset.argtypes = [vp]
     lib.khp_poisson_destroy.argtypes = [vp]
     lib.khp_project.argtypes = [vp, vp, vp, i, i, vp, vp]
     lib.khp_project_rows.argtypes = [vp, vp, vp, ctypes.c_longlong, i, i, vp, vp]

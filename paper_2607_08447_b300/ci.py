@@ -101,10 +101,20 @@ class CIResult:
     coulomb: np.ndarray         # spatial Coulomb integrals J[i, j, k, l] (eV)
 
 
-def ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=None, method=0):
+def kept_orbitals(E, e_c, T):
+    """How many orbitals pass the charging-energy filter: a Fermi-Dirac
+    function at E_C and temperature T of E_i - E_0, kept where >= 1/2."""
+    kT = 8.617333262e-5 * T
+    x = np.clip((np.asarray(E) - E[0] - e_c) / kT, -700.0, 700.0)
+    return int(np.count_nonzero(1.0 / (1.0 + np.exp(x)) >= 0.5))
+
+
+def ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=None, method=0, e_c=None, T_c=1.0):
     """Two-hole CI on the lowest n_orb orbitals of the spin-independent H0
     handle `grid` (fields set), Coulomb potentials from `poisson` (grounded
-    gates).  Returns CIResult."""
+    gates).  With e_c (eV), n_orb is the most orbitals solved for and the
+    CI keeps those within the charging energy (kept_orbitals, temperature
+    T_c in K).  Returns CIResult."""
     if getattr(grid, "bands", 6) != 3:
         raise ValueError("the CI basis comes from the spin-independent H0 (bands = 3)")
     n = int(n_orb)
@@ -114,6 +124,11 @@ def ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=None, method=0):
     kw.update(solve_kw or {})
     r = grid.eigensolve(n, **kw)
     E, psi = r.evals, r.evecs
+    if e_c is not None:
+        n = kept_orbitals(E, e_c, T_c)
+        if n < 1:
+            raise ValueError("no orbital within the charging energy")
+        E, psi = E[:n], psi[:, :n].contiguous()
     Np = grid.np_
     m_ov = 0 if (method == 0 and 3 * n <= 32) else 1
     m_cb = 0 if (method == 0 and n * n <= 32) else 1

@@ -33,6 +33,13 @@ struct khp_poisson_s {
     cudaStream_t work;     // private stream: the CG chunk is captured and replayed on it
     cudaGraphExec_t chunk; // 16 CG iterations, instantiated on first use
     bool have_chunk;
+    // Anderson mixing of the SP loop (allocated on first use)
+    double *a_dv, *a_df;   // [kMaxDepth][np] rings of iterate / residual differences
+    double *a_vprev, *a_fprev, *a_f;   // [np]
+    double* a_partial;     // [nblk][kMaxK]
+    double* a_out;         // [kMaxK] device sums
+    double* a_host;        // [kMaxK] pinned
+    int a_depth, a_count;
 };
 
 namespace khp {
@@ -259,6 +266,106 @@ __global__ void __launch_bounds__(kT) max_finish_kernel(const double* partial, i
     if (threadIdx.x == 0) *out = sm[0];
 }
 
+// ------------------------------------------------------------------------
+// Anderson mixing (type II) for the fixed point V = G(V) = V_ext + phi[V]:
+// F_k = G(V_k) - V_k; history columns dV_i = V_{i+1} - V_i and
+// dF_i = F_{i+1} - F_i of the last m steps; gamma = argmin |F_k - dF gamma|
+// from the normal equations (m <= 8, solved on the host);
+// V_{k+1} = V_k + beta F_k - sum_i gamma_i (dV_i + beta dF_i).
+constexpr int kMaxDepth = 8;
+constexpr int kMaxK = kMaxDepth * (kMaxDepth + 1) / 2 + kMaxDepth;
+
+__global__ void anderson_residual_kernel(long long np, const double* Vext, const double* phi, const double* V,
+                                         double* f, double* vprev, double* fprev, double* dv, double* df) {
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
+        const double v = V[p];
+        const double F = (Vext ? Vext[p] : 0.0) + phi[p] - v;
+        f[p] = F;
+        if (dv) {
+            dv[p] = v - vprev[p];
+            df[p] = F - fprev[p];
+        }
+        vprev[p] = v;
+        fprev[p] = F;
+    }
+}
+
+// block partials of dF_i . dF_j (i <= j, packed by rows) and dF_i . F
+template <int M>
+__global__ void __launch_bounds__(kT) anderson_gram_kernel(long long np, const double* __restrict__ df,
+                                                           const double* __restrict__ f, double* partial) {
+    constexpr int K = M * (M + 1) / 2 + M;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
+        double d[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) d[i] = df[(long long)i * np + p];
+        const double F = f[p];
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int j = i; j < M; ++j) {
+                acc[k] = fma(d[i], d[j], acc[k]);
+                ++k;
+            }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            acc[k] = fma(d[i], F, acc[k]);
+            ++k;
+        }
+    }
+    __shared__ double sm[kT / 32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sm[warp][k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += kT) {
+        double v = 0.0;
+        for (int w = 0; w < kT / 32; ++w) v += sm[w][k];
+        partial[(size_t)blockIdx.x * K + k] = v;
+    }
+}
+
+__global__ void anderson_sum_kernel(const double* partial, int nblk, int K, double* out) {
+    const int k = threadIdx.x;
+    if (k >= K) return;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += partial[(size_t)b * K + k];
+    out[k] = v;
+}
+
+struct AndersonCoef {
+    double gamma[kMaxDepth];
+};
+
+__global__ void anderson_update_kernel(long long np, int m, double beta, const AndersonCoef c, double* V,
+                                       const double* f, const double* dv, const double* df, double* partial) {
+    __shared__ double sm[kT];
+    double mx = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
+        const double v = V[p];
+        double vn = v + beta * f[p];
+        for (int i = 0; i < m; ++i)
+            vn -= c.gamma[i] * (dv[(long long)i * np + p] + beta * df[(long long)i * np + p]);
+        V[p] = vn;
+        mx = fmax(mx, fabs(vn - v));
+    }
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int st = kT / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[2 * blockIdx.x] = sm[0];
+}
+
 __global__ void copy_gate_values_kernel(long long np, const uint8_t* gate, const double* src, double* gphi) {
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT)
         gphi[p] = gate[p] ? src[p] : 0.0;
@@ -289,11 +396,55 @@ khp::poisson::Geo geo(const khp_poisson_s* P) {
 void free_all(khp_poisson_s* P) {
     if (P->have_chunk) cudaGraphExecDestroy(P->chunk);
     if (P->work) cudaStreamDestroy(P->work);
-    double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s};
+    double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s,
+                      P->a_dv, P->a_df, P->a_vprev, P->a_fprev, P->a_f, P->a_partial, P->a_out};
     for (double* b : bufs)
         if (b) cudaFree(b);
     if (P->gate) cudaFree(P->gate);
     if (P->host_pinned) cudaFreeHost(P->host_pinned);
+    if (P->a_host) cudaFreeHost(P->a_host);
+}
+
+// gamma from the packed normal equations (G packed by rows, then b):
+// Jacobi-equilibrated Cholesky with a relative diagonal floor of 1e-14
+bool anderson_solve(const double* packed, int m, double* gamma) {
+    double G[khp::poisson::kMaxDepth][khp::poisson::kMaxDepth], b[khp::poisson::kMaxDepth], d[khp::poisson::kMaxDepth];
+    int k = 0;
+    for (int i = 0; i < m; ++i)
+        for (int j = i; j < m; ++j) G[i][j] = G[j][i] = packed[k++];
+    for (int i = 0; i < m; ++i) b[i] = packed[k++];
+    for (int i = 0; i < m; ++i) {
+        if (!(G[i][i] > 0.0) || !std::isfinite(G[i][i])) return false;
+        d[i] = 1.0 / std::sqrt(G[i][i]);
+    }
+    for (int i = 0; i < m; ++i) {
+        b[i] *= d[i];
+        for (int j = 0; j < m; ++j) G[i][j] *= d[i] * d[j];
+        G[i][i] += 1e-14;
+    }
+    for (int j = 0; j < m; ++j) {          // G = L L^T in place (lower)
+        double s = G[j][j];
+        for (int q = 0; q < j; ++q) s -= G[j][q] * G[j][q];
+        if (!(s > 0.0)) return false;
+        G[j][j] = std::sqrt(s);
+        for (int i = j + 1; i < m; ++i) {
+            double t = G[i][j];
+            for (int q = 0; q < j; ++q) t -= G[i][q] * G[j][q];
+            G[i][j] = t / G[j][j];
+        }
+    }
+    for (int i = 0; i < m; ++i) {          // L y = b
+        double t = b[i];
+        for (int q = 0; q < i; ++q) t -= G[i][q] * b[q];
+        b[i] = t / G[i][i];
+    }
+    for (int i = m - 1; i >= 0; --i) {     // L^T x = y
+        double t = b[i];
+        for (int q = i + 1; q < m; ++q) t -= G[q][i] * b[q];
+        b[i] = t / G[i][i];
+    }
+    for (int i = 0; i < m; ++i) gamma[i] = b[i] * d[i];
+    return true;
 }
 
 }  // namespace
@@ -432,6 +583,82 @@ khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* p
     PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->work));
     PCK(cudaStreamSynchronize(P->work));
     if (max_change) *max_change = P->host_pinned[6];
+    return KHP_OK;
+}
+
+khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double* phi_dev, double beta, int depth,
+                           double* V_dev, double* max_change) {
+    khp_set_error(KHP_OK, "");
+    using namespace khp::poisson;
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!phi_dev || !V_dev) return pfail(KHP_ERR_INVALID_ARG, "phi or V is NULL");
+    if (!(beta > 0.0 && beta <= 1.0)) return pfail(KHP_ERR_INVALID_ARG, "beta must be in (0, 1]");
+    if (depth < 1 || depth > kMaxDepth) return pfail(KHP_ERR_INVALID_ARG, "depth out of range 1..8");
+    const long long np = P->np;
+    if (!P->a_dv) {
+        cudaError_t e;
+        if ((e = cudaMalloc(&P->a_dv, sizeof(double) * kMaxDepth * np)) != cudaSuccess ||
+            (e = cudaMalloc(&P->a_df, sizeof(double) * kMaxDepth * np)) != cudaSuccess ||
+            (e = cudaMalloc(&P->a_vprev, sizeof(double) * np)) != cudaSuccess ||
+            (e = cudaMalloc(&P->a_fprev, sizeof(double) * np)) != cudaSuccess ||
+            (e = cudaMalloc(&P->a_f, sizeof(double) * np)) != cudaSuccess ||
+            (e = cudaMalloc(&P->a_partial, sizeof(double) * kMaxK * P->nblk)) != cudaSuccess ||
+            (e = cudaMalloc(&P->a_out, sizeof(double) * kMaxK)) != cudaSuccess ||
+            (e = cudaMallocHost(&P->a_host, sizeof(double) * kMaxK)) != cudaSuccess)
+            return pfail(KHP_ERR_OOM, std::string("Anderson history: ") + cudaGetErrorString(e));
+        P->a_count = 0;
+        P->a_depth = depth;
+    }
+    if (depth != P->a_depth) {            // a new depth starts a new history
+        P->a_count = 0;
+        P->a_depth = depth;
+    }
+    PCK(cudaStreamSynchronize(P->stream));
+    cudaStream_t st = P->work;
+    const int nb = P->nblk;
+    // the newest differences go to ring slot (count - 1) % depth
+    double* dv = nullptr;
+    double* df = nullptr;
+    if (P->a_count > 0) {
+        const int slot = (P->a_count - 1) % depth;
+        dv = P->a_dv + (size_t)slot * np;
+        df = P->a_df + (size_t)slot * np;
+    }
+    anderson_residual_kernel<<<nb, kT, 0, st>>>(np, V_ext_dev, phi_dev, V_dev, P->a_f, P->a_vprev, P->a_fprev, dv,
+                                                df);
+    PCK(cudaGetLastError());
+    const int m = std::min(P->a_count, depth);
+    AndersonCoef c{};
+    if (m > 0) {
+        const int K = m * (m + 1) / 2 + m;
+        switch (m) {
+#define KHP_AG(M) case M: anderson_gram_kernel<M><<<nb, kT, 0, st>>>(np, P->a_df, P->a_f, P->a_partial); break;
+            KHP_AG(1) KHP_AG(2) KHP_AG(3) KHP_AG(4) KHP_AG(5) KHP_AG(6) KHP_AG(7) KHP_AG(8)
+#undef KHP_AG
+        }
+        anderson_sum_kernel<<<1, 64, 0, st>>>(P->a_partial, nb, K, P->a_out);
+        PCK(cudaGetLastError());
+        PCK(cudaMemcpyAsync(P->a_host, P->a_out, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+        PCK(cudaStreamSynchronize(st));
+        // a singular history (e.g. a repeated iterate) falls back to the
+        // plain damped step
+        if (!anderson_solve(P->a_host, m, c.gamma))
+            for (int i = 0; i < m; ++i) c.gamma[i] = 0.0;
+    }
+    anderson_update_kernel<<<nb, kT, 0, st>>>(np, m, beta, c, V_dev, P->a_f, P->a_dv, P->a_df, P->partial);
+    max_finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, P->s + 6);
+    PCK(cudaGetLastError());
+    PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    P->a_count += 1;
+    if (max_change) *max_change = P->host_pinned[6];
+    return KHP_OK;
+}
+
+khp_status khp_sp_anderson_reset(khp_poisson P) {
+    khp_set_error(KHP_OK, "");
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    P->a_count = 0;
     return KHP_OK;
 }
 

@@ -63,6 +63,18 @@ class Poisson:
                                           ctypes.byref(ch)))
         return ch.value
 
+    def anderson(self, V, phi, beta, depth, V_ext=None):
+        """Anderson-mixed update of V in place (khp_sp_anderson: residual
+        V_ext + phi - V, history of the last `depth` calls on the handle);
+        returns max |dV|."""
+        ch = ctypes.c_double(0.0)
+        _lib.check(self.lib.khp_sp_anderson(self.handle, _ptr(V_ext), _ptr(phi), float(beta), int(depth), _ptr(V),
+                                            ctypes.byref(ch)))
+        return ch.value
+
+    def reset_mixing(self):
+        _lib.check(self.lib.khp_sp_anderson_reset(self.handle))
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.khp_poisson_destroy(self.handle)
@@ -103,9 +115,11 @@ class SPResult:
 
 
 def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, tol_v=1e-8, strain=None,
-             B=None, gauge=0, solve_kw=None):
+             B=None, gauge=0, solve_kw=None, anderson_depth=0):
     """Self-consistent loop from V = V_ext: `iters` iterations at most, or
-    until max |dV| <= tol_v.  Returns SPResult (V on the device)."""
+    until max |dV| <= tol_v.  Linear mixing with weight `mix`, or Anderson
+    mixing (damping `mix`) over `anderson_depth` > 0 previous iterates.
+    Returns SPResult (V on the device)."""
     kw = dict(block_m=max(n_states + 8, 16), degree=40, tol=1e-11, seed=1)
     kw.update(solve_kw or {})
     V_ext = _dev(V_ext, torch.float64, grid.device).reshape(-1)
@@ -114,6 +128,8 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
     kT = KB_EV * T
     hist, piters = [], []
     warm = None
+    if anderson_depth > 0:
+        poisson.reset_mixing()
     for _ in range(iters):
         grid.set_fields(V, strain, None, None, B, gauge)
         r = grid.eigensolve(n_states, warm_start=warm, **kw)
@@ -123,7 +139,10 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
         rho = grid.density(r.evecs, f / grid.h ** 3)
         poisson.solve(rho, phi)
         piters.append(poisson.last_iterations)
-        dv = poisson.update(V, phi, mix, V_ext)
+        if anderson_depth > 0:
+            dv = poisson.anderson(V, phi, mix, anderson_depth, V_ext)
+        else:
+            dv = poisson.update(V, phi, mix, V_ext)
         hist.append(dv)
         if dv <= tol_v:
             break

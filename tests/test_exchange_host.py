@@ -63,3 +63,17 @@ def test_anisotropic_exchange_matches_oracle(seed):
         Jto, ao, bo, _ = ex_or.anisotropic_exchange(J, gL, gR, th, n, B)
         assert abs(a - ao) <= 1e-13 * J and abs(b - bo) <= 1e-13 * J
         assert abs(Jt[2, 2] - Jto[2, 2]) <= 1e-13 * J
+
+
+def test_charging_energy_filter_matches_oracle():
+    """The CI truncation filter (Fermi-Dirac at E_C): package and oracle
+    keep the same orbitals; at low T exactly those with E_i - E_0 <= E_C."""
+    from oracle import ci as ci_or
+    from paper_2607_08447_b300.ci import kept_orbitals
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        E = np.sort(rng.uniform(0.0, 5e-3, 8)) - 0.01
+        e_c = rng.uniform(0.0, 5e-3)
+        for T in (0.1, 1.5):
+            assert kept_orbitals(E, e_c, T) == ci_or.truncate_orbitals(E, e_c, T)
+        assert kept_orbitals(E, e_c, 0.01) == int(np.count_nonzero(E - E[0] <= e_c))

@@ -51,3 +51,25 @@ def test_ci_rejects_six_band_handle(khp):
         ci_exchange(g, P, 2, 0.044)
     P.close()
     g.close()
+
+
+def test_ci_charging_energy_truncation_matches_oracle(khp):
+    """CI space cut by the charging-energy filter (Fermi-Dirac at E_C):
+    E_C between the second and third H0 orbital energies keeps two of the
+    four solved orbitals on both sides."""
+    from paper_2607_08447_b300.ci import ci_exchange
+    from paper_2607_08447_b300.poisson import Poisson
+    p = inputs.small_problem(14, 6, 6, h=0.5, seed=5, strain=True)
+    gate = _end_gates(p)
+    E4, _ = ci_oracle.h0_orbitals(p, 4)
+    e_c = 0.5 * ((E4[1] - E4[0]) + (E4[2] - E4[0]))
+    w_or, s2_or, j_or, E_or = ci_oracle.ci_pipeline(p, 4, gate, e_c=e_c, T_c=0.5)
+    assert len(E_or) == 2
+    g = khp.KPGrid.from_problem(p, bands=3)
+    P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V))
+    r = ci_exchange(g, P, 4, p.material["delta_so"], solve_kw=dict(tol=1e-12), e_c=e_c, T_c=0.5)
+    assert len(r.orbital_energies) == 2 and len(r.energies) == 6
+    assert np.abs(r.energies - w_or).max() <= 1e-9
+    assert abs(r.exchange - j_or) <= 1e-9
+    P.close()
+    g.close()

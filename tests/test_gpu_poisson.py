@@ -87,3 +87,67 @@ def test_sp_loop_matches_oracle(khp, bands):
     assert abs(r.mu - mu_or) <= 1e-9
     P.close()
     g.close()
+
+
+def test_anderson_matches_oracle_on_linear_map(khp):
+    """khp_sp_anderson against the oracle's Anderson mixing, step by step,
+    on G(V) = A V + c (A a symmetric contraction coupling all points through
+    a low-rank term plus a diagonal); with depth >= the rank + 1 both reach
+    the fixed point; the first step equals linear mixing."""
+    from paper_2607_08447_b300.poisson import Poisson
+    from oracle.poisson import Anderson
+    nx, ny, nz = 11, 6, 5
+    n = nx * ny * nz
+    rng = np.random.default_rng(8)
+    U, _ = np.linalg.qr(rng.standard_normal((n, 4)))
+    A = U @ np.diag([0.9, -0.8, 0.7, 0.5]) @ U.T + 0.05 * np.eye(n)
+    c = rng.standard_normal(n)
+    Vext = rng.standard_normal(n) * 0.1
+    gate = _end_gates(nx, ny, nz)
+    P = Poisson(nx, ny, nz, 0.5, gate, np.zeros((nz, ny, nx)))
+    for depth, beta in ((6, 0.7), (2, 0.4)):
+        P.reset_mixing()
+        acc = Anderson(beta, depth)
+        V = torch.zeros(n, dtype=torch.float64, device="cuda")
+        Vo = np.zeros(n)
+        ext = torch.from_numpy(Vext).cuda()
+        for k in range(8):
+            GV = A @ V.cpu().numpy() + c
+            phi = torch.from_numpy(GV - Vext).cuda()
+            dv = P.anderson(V, phi, beta, depth, ext)
+            Vo = acc.step(Vo, A @ Vo + c)
+            # the library solves the normal equations, the oracle a least
+            # squares: they agree to cond(dF)^2 eps, which grows as the
+            # history turns dependent near termination (k >= 4 here)
+            scale = np.abs(Vo).max()
+            tol = 1e-9 if k < 4 else 1e-6
+            assert np.abs(V.cpu().numpy() - Vo).max() <= tol * scale, (depth, k)
+            assert dv > 0
+        if depth == 6:
+            Vstar = np.linalg.solve(np.eye(n) - A, c)
+            assert np.abs(V.cpu().numpy() - Vstar).max() <= 1e-8 * np.abs(Vstar).max()
+    with pytest.raises(khp.KHPError):
+        P.anderson(V, phi, 0.5, 9, ext)
+    P.close()
+
+
+@pytest.mark.parametrize("bands", [6, 3])
+def test_sp_loop_anderson_matches_oracle(khp, bands):
+    """Four self-consistent iterations with Anderson mixing (depth 3,
+    damping 0.5) on both sides from the same start."""
+    from paper_2607_08447_b300.poisson import Poisson, sp_solve
+    p = inputs.small_problem(10, 6, 6, h=0.5, seed=5, strain=True)
+    gate = _end_gates(p.nx, p.ny, p.nz)
+    gphi = np.zeros_like(p.V)
+    iters, n, nh = 4, 8, 2.0
+    V_or, E_or, mu_or, hist_or = po.sp_loop(p, p.V, gate, gphi, n, nh, 1.5, 0.5, iters, bands=bands,
+                                            anderson_depth=3)
+    g = khp.KPGrid.from_problem(p, bands=bands)
+    P = Poisson(p.nx, p.ny, p.nz, p.h, gate, gphi)
+    r = sp_solve(g, P, p.V, n, nh, T=1.5, mix=0.5, iters=iters, tol_v=0.0, strain=p.strain,
+                 solve_kw=dict(block_m=16, degree=16, tol=1e-12), anderson_depth=3)
+    assert np.abs(np.array(r.history) - np.array(hist_or)).max() <= 1e-9
+    assert np.abs(r.V.cpu().numpy() - V_or).max() <= 1e-10
+    assert np.abs(r.evals - E_or).max() <= 1e-10
+    P.close()
+    g.close()
