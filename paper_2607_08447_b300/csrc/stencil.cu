@@ -16,6 +16,68 @@ namespace khp {
 
 __device__ __forceinline__ bool inr(int i, int n) { return (unsigned)i < (unsigned)n; }
 
+// Complex updates with a real coefficient.  For FP32 each is one packed
+// FP32x2 instruction (fma/add/sub .rn.f32x2, sm_100 and later) acting on
+// (re, im); every lane rounds exactly like the scalar .rn instruction.
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+// acc += m x
+template <typename R>
+__device__ __forceinline__ void axpy_c(cx_t<R>& acc, R m, cx_t<R> x) {
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long d;
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(x.x, x.y)), "l"(pk(m, m)), "l"(pk(acc.x, acc.y)));
+        acc = upk(d);
+    } else {
+        acc.x = fma(m, x.x, acc.x);
+        acc.y = fma(m, x.y, acc.y);
+    }
+}
+
+// acc += -i a x  (re += a x.im, im -= a x.re)
+template <typename R>
+__device__ __forceinline__ void axpy_mi(cx_t<R>& acc, R a, cx_t<R> x) {
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long d;
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(x.y, x.x)), "l"(pk(a, -a)), "l"(pk(acc.x, acc.y)));
+        acc = upk(d);
+    } else {
+        acc.x = fma(a, x.y, acc.x);
+        acc.y = fma(-a, x.x, acc.y);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ cx_t<R> cadd(cx_t<R> a, cx_t<R> b) {
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long d;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a.x, a.y)), "l"(pk(b.x, b.y)));
+        return upk(d);
+    } else {
+        return mk<R>(a.x + b.x, a.y + b.y);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ cx_t<R> csub(cx_t<R> a, cx_t<R> b) {
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long d;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a.x, a.y)), "l"(pk(b.x, b.y)));
+        return upk(d);
+    } else {
+        return mk<R>(a.x - b.x, a.y - b.y);
+    }
+}
+
 template <typename R, int VG>
 __device__ __forceinline__ void load_vg(cx_t<R> (&v)[VG], const cx_t<R>* p) {
     if constexpr (VG == 2 && sizeof(R) == 4) {
@@ -57,10 +119,7 @@ __device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], uns
 #pragma unroll
             for (int s = 0; s < NS; ++s)
 #pragma unroll
-                for (int v = 0; v < VG; ++v) {
-                    acc[3 * s + k][v].x = fma(m, x[3 * s + k][v].x, acc[3 * s + k][v].x);
-                    acc[3 * s + k][v].y = fma(m, x[3 * s + k][v].y, acc[3 * s + k][v].y);
-                }
+                for (int v = 0; v < VG; ++v) axpy_c<R>(acc[3 * s + k][v], m, x[3 * s + k][v]);
         }
     }
     // off-diagonal (i, j): 3 -> (1,2), 4 -> (0,2), 5 -> (0,1)
@@ -74,10 +133,8 @@ __device__ __forceinline__ void sym3(cx_t<R> (&acc)[6][VG], const R (&M)[6], uns
             for (int s = 0; s < NS; ++s)
 #pragma unroll
                 for (int v = 0; v < VG; ++v) {
-                    acc[3 * s + i][v].x = fma(m, x[3 * s + j][v].x, acc[3 * s + i][v].x);
-                    acc[3 * s + i][v].y = fma(m, x[3 * s + j][v].y, acc[3 * s + i][v].y);
-                    acc[3 * s + j][v].x = fma(m, x[3 * s + i][v].x, acc[3 * s + j][v].x);
-                    acc[3 * s + j][v].y = fma(m, x[3 * s + i][v].y, acc[3 * s + j][v].y);
+                    axpy_c<R>(acc[3 * s + i][v], m, x[3 * s + j][v]);
+                    axpy_c<R>(acc[3 * s + j][v], m, x[3 * s + i][v]);
                 }
         }
     }
@@ -101,14 +158,8 @@ __device__ __forceinline__ void pair_entry(cx_t<R> (&acc)[6][VG], int i, int j, 
 #pragma unroll
         for (int w = 0; w < VG; ++w) {
             cx_t<R>& A = acc[3 * sp + i][w];
-            const cx_t<R> U = u[3 * sp + j][w];
-            A.x = fma(mc, U.x, A.x);
-            A.y = fma(mc, U.y, A.y);
-            if (SYMPH) {
-                const cx_t<R> Vv = v[3 * sp + j][w];
-                A.x = fma(ms, Vv.y, A.x);
-                A.y = fma(-ms, Vv.x, A.y);
-            }
+            axpy_c<R>(A, mc, u[3 * sp + j][w]);
+            if (SYMPH) axpy_mi<R>(A, ms, v[3 * sp + j][w]);
         }
 }
 
@@ -177,14 +228,8 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
 #pragma unroll
             for (int v = 0; v < VG; ++v) {
                 C o = mk<R>(R(0), R(0));
-                if (pp) {
-                    o.x = a.gamma * pv[b][v].x;
-                    o.y = a.gamma * pv[b][v].y;
-                }
-                if (SRC) {
-                    o.x = fma(sc[v], sv[b][v].x, o.x);
-                    o.y = fma(sc[v], sv[b][v].y, o.y);
-                }
+                if (pp) axpy_c<R>(o, a.gamma, pv[b][v]);
+                if (SRC) axpy_c<R>(o, sc[v], sv[b][v]);
                 acc[b][v] = o;
             }
     }
@@ -207,18 +252,12 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
                 if (rowm & (1u << (2 * b2))) {
                     const R sr = a.c.soz_re[b][b2];
 #pragma unroll
-                    for (int v = 0; v < VG; ++v) {
-                        acc[b][v].x = fma(sr, xs[b2][v].x, acc[b][v].x);
-                        acc[b][v].y = fma(sr, xs[b2][v].y, acc[b][v].y);
-                    }
+                    for (int v = 0; v < VG; ++v) axpy_c<R>(acc[b][v], sr, xs[b2][v]);
                 }
                 if (rowm & (2u << (2 * b2))) {
                     const R si = a.c.soz_im[b][b2];
 #pragma unroll
-                    for (int v = 0; v < VG; ++v) {
-                        acc[b][v].x = fma(-si, xs[b2][v].y, acc[b][v].x);
-                        acc[b][v].y = fma(si, xs[b2][v].x, acc[b][v].y);
-                    }
+                    for (int v = 0; v < VG; ++v) axpy_mi<R>(acc[b][v], -si, xs[b2][v]);
                 }
             }
         }
@@ -294,12 +333,8 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
                     }
 #pragma unroll
                     for (int v = 0; v < VG; ++v) {
-                        u[b][v].x = xpv[v].x + xmv[v].x;
-                        u[b][v].y = xpv[v].y + xmv[v].y;
-                        if (PH == PH_SYM && ph) {
-                            w[b][v].x = xpv[v].x - xmv[v].x;
-                            w[b][v].y = xpv[v].y - xmv[v].y;
-                        }
+                        u[b][v] = cadd<R>(xpv[v], xmv[v]);
+                        if (PH == PH_SYM && ph) w[b][v] = csub<R>(xpv[v], xmv[v]);
                     }
                 }
             }
