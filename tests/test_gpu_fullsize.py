@@ -139,3 +139,27 @@ def test_c5_gradients_full_size(khp):
         worst = max(worst, abs(fd - dA[k]) / max(1.0, abs(dA[k])))
     assert worst <= 1e-6, worst
     g.close()
+
+
+def test_c2_g_tensors_predict_zeeman_splitting(khp):
+    """g-tensors at full size (the bench's g-tensor configuration): the
+    g-matrix of the lowest doublet, from the response projections at
+    B = +-0.01 T, predicts the splitting mu_B b |g n| of the two lowest
+    states that the eigensolver finds at B = b n (b = 0.02 T, two
+    directions), to the order-b^3 and solver-tolerance terms; the projected
+    position pairs up (Kramers) on the two doublets."""
+    from paper_2607_08447_b300.gtensor import MU_B, g_tensors
+    p = inputs.config2()
+    g = khp.KPGrid.from_problem(p)
+    kw = dict(block_m=12, degree=200, precision=2, tol=1e-11, seed=1)
+    r = g_tensors(g, solve_kw=kw)
+    w = np.linalg.eigvalsh(r.position)
+    assert abs(w[1] - w[0]) <= 1e-5 and abs(w[3] - w[2]) <= 1e-5
+    b = 0.02
+    for n in (np.array([1.0, 0.0, 0.0]), np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])):
+        g.set_B(b * n)
+        s = g.eigensolve(4, **kw)
+        split = (s.evals[1] - s.evals[0]) / (MU_B * b)
+        pred = np.linalg.norm(r.g_bonding @ n)
+        assert abs(split - pred) <= 1e-4 * max(1.0, pred), (n, split, pred)
+    g.close()
