@@ -42,7 +42,7 @@ CROP = (32, 12, 12)
 # (dram__bytes_read.sum + dram__bytes_write.sum = 2.519 GB + 0.829 GB over
 # 24 x 368640 point-vectors, one ncu capture of the FP64 stencil at C2).  Valid for the
 # kernel version profiled there; set to None when the kernel changes.
-NCU_TRAFFIC_FP64_PER_PV = (2.519110e9 + 0.8291136e9) / (24 * 368640)
+NCU_TRAFFIC_FP64_PER_PV = (2.462602e9 + 0.828694e9) / (24 * 368640)
 
 
 def _args():
@@ -59,6 +59,8 @@ def _args():
                          "sweep (uneven 96..160 x 40..48 x 40..48 grids, 12 states each) with "
                          "khp_eigensolve_batched in chunks, against sequential single solves")
     ap.add_argument("--sweep-chunk", type=int, default=8)
+    ap.add_argument("--sweep-plain", type=int, default=4,
+                    help="sweep points also solved in plain FP64 for the mixed-vs-plain speed-up")
     ap.add_argument("--profile", choices=["plain", "mixed", "dc"], default=None,
                     help="one short C2 solve (6 outer iterations) for profiler captures; prints its stats")
     return ap.parse_args()
@@ -675,6 +677,23 @@ def run_sweep(args):
     evals_b, tb = timed(batched)
     evals_s, ts = timed(sequential)
     dmax = max(float(np.abs(a - b).max()) for a, b in zip(evals_b, evals_s)) if probs else 0.0
+
+    # plain FP64 (the same tolerance) on a sample of this rank's points,
+    # batched the same way, against the defect-corrected batched solve
+    sample = probs[: args.sweep_plain]
+
+    def batched_sample(kws):
+        grids = [khp.KPGrid.from_problem(p) for p in sample]
+        rs = khp.solve_batched(grids, n, block_m=bm, graph=True, **kws)
+        ev = [r.evals for r in rs]
+        for g in grids:
+            g.close()
+        return ev
+
+    plain_kw = dict(degree=SOLVE_KW["degree"], precision=0, tol=1e-10, seed=1)
+    ev_dc, t_dc = timed(lambda: batched_sample(kw))
+    ev_fp64, t_fp64 = timed(lambda: batched_sample(plain_kw))
+    d_plain = max(float(np.abs(a - b).max()) for a, b in zip(ev_dc, ev_fp64)) if sample else 0.0
     line = {"metric": "sweep eigenpairs/s (batched detuning sweep)", "value": n * len(allp) / tb,
             "unit": "eigenpairs/s", "n_gpus": world, "higher_is_better": True, "scaling": "strong",
             "dtype": "fp32 filter + fp64 RR", "data": "synthetic",
@@ -683,7 +702,13 @@ def run_sweep(args):
                                    f"block_m autotuned = {bm}", "autotune_ms": tune_ms,
                        "parallelism": f"sweep sharded over {world} rank(s), no collective"},
             "sequential": {"value": n * len(allp) / ts, "unit": "eigenpairs/s", "s": ts},
-            "batched_s": tb, "speedup_vs_sequential": ts / tb, "max_abs_dE_batched_vs_single_ev": dmax}
+            "batched_s": tb, "speedup_vs_sequential": ts / tb, "max_abs_dE_batched_vs_single_ev": dmax,
+            "vs_plain_fp64": {"points": len(sample), "mixed_batched_s": t_dc, "fp64_batched_s": t_fp64,
+                              "speedup": t_fp64 / t_dc if t_dc > 0 else None,
+                              "max_abs_dE_ev": d_plain,
+                              "note": "same points, block width and tolerance (1e-10 eV); plain FP64 at degree "
+                                      f"{SOLVE_KW['degree']}, mixed = defect-corrected FP32 filter at degree "
+                                      f"{MIXED_DEGREE}"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
