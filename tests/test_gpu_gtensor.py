@@ -77,3 +77,22 @@ def test_g_tensors_mirror_symmetric_double_dot(khp):
     assert np.abs(GR - S @ GL @ S).max() <= 1e-7 * np.abs(GL).max()
     assert np.abs(r.gsym_right - S @ r.gsym_left @ S).max() <= 1e-7 * np.abs(GL).max()
     g.close()
+
+
+@pytest.mark.parametrize("bands,mask", [(3, False), (6, True)])
+def test_position_moments_h0_and_masked_grids(khp, bands, mask):
+    """The moments kernel on a 3-band H0 handle and on a masked 6-band
+    handle (the points a mask excludes still count with whatever X holds
+    there) against the plain sum."""
+    p = inputs.small_problem(9, 7, 5, h=0.5, seed=4, strain=False, mask=mask)
+    nb = bands
+    m = 3
+    X = inputs.random_block(nb * p.n_points, m, seed=77)
+    g = khp.KPGrid.from_problem(p, bands=bands)
+    D = g.position_moments(torch.from_numpy(X).cuda())
+    z, y, x = np.meshgrid(np.arange(p.nz), np.arange(p.ny), np.arange(p.nx), indexing="ij")
+    for a, (c, n_a) in enumerate(((x, p.nx), (y, p.ny), (z, p.nz))):
+        r = np.repeat(((c - 0.5 * (n_a - 1)) * p.h).reshape(-1), nb)
+        ref = X.conj().T @ (r[:, None] * X)
+        assert np.abs(D[a] - ref).max() <= 1e-13 * np.abs(ref).max()
+    g.close()

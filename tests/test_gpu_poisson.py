@@ -151,3 +151,20 @@ def test_sp_loop_anderson_matches_oracle(khp, bands):
     assert np.abs(r.evals - E_or).max() <= 1e-10
     P.close()
     g.close()
+
+
+def test_anderson_without_external_potential(khp):
+    """V_ext = NULL means zero: the first Anderson step is V + beta (phi - V)."""
+    from paper_2607_08447_b300.poisson import Poisson
+    nx, ny, nz = 6, 5, 4
+    n = nx * ny * nz
+    rng = np.random.default_rng(2)
+    P = Poisson(nx, ny, nz, 0.5, _end_gates(nx, ny, nz), np.zeros((nz, ny, nx)))
+    V0 = rng.standard_normal(n)
+    phi = rng.standard_normal(n)
+    V = torch.from_numpy(V0.copy()).cuda()
+    dv = P.anderson(V, torch.from_numpy(phi).cuda(), 0.4, 3, None)
+    ref = V0 + 0.4 * (phi - V0)
+    assert np.abs(V.cpu().numpy() - ref).max() <= 1e-15 * np.abs(ref).max()
+    assert abs(dv - np.abs(ref - V0).max()) <= 1e-15
+    P.close()
