@@ -100,6 +100,29 @@ __device__ __forceinline__ void store_vg(cx_t<R>* p, const cx_t<R> (&v)[VG]) {
     }
 }
 
+// Streams read or written once per step (prev, the defect source, y): FP32
+// blocks go through the evict-first path so the L1 and L2 keep the
+// neighbour planes of x.
+template <typename R, int VG>
+__device__ __forceinline__ void load_vg_once(cx_t<R> (&v)[VG], const cx_t<R>* p) {
+    if constexpr (VG == 2 && sizeof(R) == 4) {
+        const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = mk<R>(q.x, q.y);
+        v[1] = mk<R>(q.z, q.w);
+    } else {
+        load_vg<R, VG>(v, p);
+    }
+}
+
+template <typename R, int VG>
+__device__ __forceinline__ void store_vg_once(cx_t<R>* p, const cx_t<R> (&v)[VG]) {
+    if constexpr (VG == 2 && sizeof(R) == 4) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0].x, v[0].y, v[1].x, v[1].y));
+    } else {
+        store_vg<R, VG>(p, v);
+    }
+}
+
 // acc[s*3 + i][v] (+)= sum_j M_ij x[s*3 + j][v] for the NS spins, M real
 // symmetric (00,11,22,12,02,01); entries whose bit is clear in nz are
 // structurally zero and skipped (warp-uniform branches)
@@ -215,8 +238,8 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
         C pv[6][VG], sv[6][VG];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            if (pp) load_vg<R, VG>(pv[b], pp + b * ld);
-            if (SRC) load_vg<R, VG>(sv[b], a.src + p * ps + col + b * ld);
+            if (pp) load_vg_once<R, VG>(pv[b], pp + b * ld);
+            if (SRC) load_vg_once<R, VG>(sv[b], a.src + p * ps + col + b * ld);
         }
         R sc[VG];
         if (SRC) {
@@ -364,7 +387,7 @@ __global__ void __launch_bounds__(256, MINB) stencil_kernel(const StencilArgs<R>
     }
 
 #pragma unroll
-    for (int b = 0; b < NB; ++b) store_vg<R, VG>(yp + b * ld, acc[b]);
+    for (int b = 0; b < NB; ++b) store_vg_once<R, VG>(yp + b * ld, acc[b]);
 }
 
 template <typename R, int VG, int PH>
