@@ -99,6 +99,7 @@ class CIResult:
     exchange: float             # E_triplet - E_singlet (eV)
     orbital_energies: np.ndarray
     coulomb: np.ndarray         # spatial Coulomb integrals J[i, j, k, l] (eV)
+    orbitals: object = None     # the H0 orbitals used (device tensor [3 Np][n])
 
 
 def kept_orbitals(E, e_c, T):
@@ -159,4 +160,23 @@ def ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=None, method=0, e_c=Non
     s2 = np.real(np.einsum("ik,ij,jk->k", v.conj(), _total_spin_squared(n, dets), v))
     singlet = w[np.flatnonzero(s2 < 1.0)[0]]
     triplet = w[np.flatnonzero(s2 > 1.0)[0]]
-    return CIResult(w, s2, float(triplet - singlet), E, Jsp)
+    return CIResult(w, s2, float(triplet - singlet), E, Jsp, psi)
+
+
+def ci_detuning_sweep(grid, poisson, potentials, n_orb, delta_so, strain=None, solve_kw=None, method=0,
+                      e_c=None, T_c=1.0):
+    """The CI at every potential of a detuning sweep (Sec. III A: the CI
+    matrix is rebuilt for each gate configuration).  `potentials` is a
+    sequence of V fields for the H0 handle `grid`; each H0 solve starts
+    from the previous point's orbitals.  Returns the list of CIResult."""
+    out = []
+    warm = None
+    for V in potentials:
+        grid.set_fields(V, strain)
+        kw = dict(solve_kw or {})
+        if warm is not None and warm.shape[1] == int(n_orb):
+            kw["warm_start"] = warm
+        r = ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=kw, method=method, e_c=e_c, T_c=T_c)
+        warm = r.orbitals if r.orbitals.shape[1] == int(n_orb) else None
+        out.append(r)
+    return out

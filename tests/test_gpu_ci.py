@@ -73,3 +73,26 @@ def test_ci_charging_energy_truncation_matches_oracle(khp):
     assert abs(r.exchange - j_or) <= 1e-9
     P.close()
     g.close()
+
+
+def test_ci_detuning_sweep_matches_oracle(khp):
+    """CI along a detuning sweep (three potentials: the double well tilted by
+    a linear field of -1, 0, +1 meV across the box), warm-started H0 solves,
+    against the oracle pipeline run at each point."""
+    from paper_2607_08447_b300.ci import ci_detuning_sweep
+    from paper_2607_08447_b300.poisson import Poisson
+    p = inputs.small_problem(14, 6, 6, h=0.5, seed=5, strain=True)
+    gate = _end_gates(p)
+    x = (np.arange(p.nx) - 0.5 * (p.nx - 1)) / (p.nx - 1)
+    pots = [p.V + eps * x[None, None, :] for eps in (-1e-3, 0.0, 1e-3)]
+    g = khp.KPGrid.from_problem(p, bands=3)
+    P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V))
+    rs = ci_detuning_sweep(g, P, pots, 2, p.material["delta_so"], strain=p.strain, solve_kw=dict(tol=1e-12))
+    assert len(rs) == 3
+    for V, r in zip(pots, rs):
+        w_or, s2_or, j_or, E_or = ci_oracle.ci_pipeline(p.with_(V=V), 2, gate)
+        assert np.abs(r.orbital_energies - E_or).max() <= 1e-10
+        assert np.abs(r.energies - w_or).max() <= 1e-9
+        assert abs(r.exchange - j_or) <= 1e-9
+    P.close()
+    g.close()
