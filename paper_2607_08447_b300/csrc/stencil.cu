@@ -435,6 +435,7 @@ static cudaError_t launch_ph(const StencilArgs<R>& a, unsigned blocks, cudaStrea
                 return cudaGetLastError();                                                           \
             }
             KHP_LD_CASE(16)
+            KHP_LD_CASE(20)
             KHP_LD_CASE(24)
             KHP_LD_CASE(32)
 #undef KHP_LD_CASE

@@ -34,7 +34,7 @@ def _grid(khp, p):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("m", [1, 5, 8, 24])
+@pytest.mark.parametrize("m", [1, 5, 8, 16, 20, 24, 32])
 def test_stencil_fp64_matches_csr(khp, case, m):
     p = _problem(CASES[case])
     H = kp.assemble(p)
@@ -49,7 +49,7 @@ def test_stencil_fp64_matches_csr(khp, case, m):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("m", [2, 7, 24])
+@pytest.mark.parametrize("m", [2, 7, 16, 20, 24, 32])
 def test_stencil_fp32_matches_csr(khp, case, m):
     p = _problem(CASES[case])
     H = kp.assemble(p)
