@@ -77,3 +77,4 @@ def test_charging_energy_filter_matches_oracle():
         for T in (0.1, 1.5):
             assert kept_orbitals(E, e_c, T) == ci_or.truncate_orbitals(E, e_c, T)
         assert kept_orbitals(E, e_c, 0.01) == int(np.count_nonzero(E - E[0] <= e_c))
+        assert ci_or.truncate_orbitals(E, e_c, 0.01) == int(np.count_nonzero(E - E[0] <= e_c))
