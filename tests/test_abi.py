@@ -57,3 +57,26 @@ def test_host_side_validation_without_device(lib):
     assert lib.khp_apply(None, None, None, 4, 0) == 1
     assert lib.khp_eigensolve(None, None, None, None, None, None) == 1
     assert lib.khp_destroy(None) == 0
+
+
+def test_host_side_validation_of_the_next_rows(lib):
+    """The entry points of the H0, Poisson/SP, CI and g-tensor rows reject
+    NULL handles and out-of-range sizes with INVALID_ARG before any CUDA
+    call."""
+    from paper_2607_08447_b300 import _lib
+    h = ctypes.c_void_p()
+    mat = _lib.Material(4.285, 0.339, 1.446, 0.044, -0.42, 2.38, -2.1, -4.85)
+    assert lib.khp_create_grid_h0(ctypes.byref(h), 4, 0, 4, 1.0, ctypes.byref(mat), None, None, None) == 1
+    buf = (ctypes.c_double * 64)()
+    assert lib.khp_position_moments(None, buf, 4, buf) == 1
+    assert lib.khp_pair_densities(None, buf, 2, buf) == 1
+    assert lib.khp_project_rows(None, buf, None, 8, 2, 0, buf, None) == 1
+    P = ctypes.c_void_p()
+    assert lib.khp_poisson_create(ctypes.byref(P), 0, 4, 4, 0.5, 11.7, None, None, None) == 1
+    assert lib.khp_poisson_create(ctypes.byref(P), 4, 4, 4, 0.5, -1.0, buf, buf, None) == 1
+    ch = ctypes.c_double()
+    assert lib.khp_sp_update(None, None, buf, 0.5, buf, ctypes.byref(ch)) == 1
+    assert lib.khp_sp_anderson(None, None, buf, 0.5, 4, buf, ctypes.byref(ch)) == 1
+    assert b"NULL" in lib.khp_last_error()
+    assert lib.khp_sp_anderson_reset(None) == 1
+    assert lib.khp_poisson_destroy(None) == 0
