@@ -163,3 +163,27 @@ def test_c2_g_tensors_predict_zeeman_splitting(khp):
         pred = np.linalg.norm(r.g_bonding @ n)
         assert abs(split - pred) <= 1e-4 * max(1.0, pred), (n, split, pred)
     g.close()
+
+
+@pytest.fixture(scope="module")
+def c2_h0_csr():
+    p = inputs.config2()
+    return p, kp.assemble_h0(p.with_(B=np.zeros(3)))
+
+
+@pytest.mark.parametrize("kw", [dict(degree=120, precision=0), dict(degree=200, precision=2)])
+def test_c2_h0_residuals_through_oracle_csr(khp, c2_h0_csr, kw):
+    """The spin-independent H0 (1.1M unknowns at the C2 grid and fields, the
+    CI orbital basis) in the bench's plain and defect-corrected settings:
+    residuals and Rayleigh quotients through the oracle's CSR H0,
+    orthonormality."""
+    p, H = c2_h0_csr
+    g = khp.KPGrid.from_problem(p, bands=3)
+    r = g.eigensolve(16, block_m=24, tol=1e-10, seed=1, **kw)
+    V = r.evecs.cpu().numpy()
+    res = np.linalg.norm(H @ V - V * r.evals[None, :], axis=0)
+    assert res.max() <= 2e-10, res
+    assert np.abs(V.conj().T @ V - np.eye(16)).max() < 1e-12
+    rq = np.real(np.einsum("ij,ij->j", V.conj(), H @ V))
+    assert np.abs(rq - r.evals).max() <= 1e-12
+    g.close()
