@@ -40,10 +40,10 @@ def test_position_moments_reject_bad_sizes(khp):
     g.close()
 
 
-@pytest.mark.parametrize("rot", ["identity", "device"])
-def test_g_tensors_match_oracle(khp, rot):
+@pytest.mark.parametrize("rot,gauge", [("identity", 0), ("device", 0), ("device", 1)])
+def test_g_tensors_match_oracle(khp, rot, gauge):
     from paper_2607_08447_b300.gtensor import g_tensors
-    p = inputs.small_problem(12, 6, 6, h=1.0, seed=3, strain=True, rot=rot, B=(0.2, -0.1, 0.3))
+    p = inputs.small_problem(12, 6, 6, h=1.0, seed=3, strain=True, rot=rot, B=(0.2, -0.1, 0.3), gauge=gauge)
     ref = gt_or.dqd_g_tensors(p)
     g = khp.KPGrid.from_problem(p)
     r = g_tensors(g, solve_kw=dict(tol=1e-12))

@@ -772,3 +772,21 @@ def test_anderson_first_step_is_linear_mixing():
     V, GV = rng.standard_normal(10), rng.standard_normal(10)
     acc = po_oracle.Anderson(0.3, depth=4)
     assert np.abs(acc.step(V, GV) - (0.7 * V + 0.3 * GV)).max() < 1e-15
+
+
+@pytest.mark.parametrize("rot", ["identity", "device"])
+def test_g_tensor_of_a_doublet_is_gauge_invariant(rot):
+    """A gauge change multiplies H(B) by a unitary phase e^{i chi(B)} with
+    chi linear in B, which adds i [dchi/dB, H] to dH/dB; its matrix elements
+    between the two states of a degenerate doublet vanish.  So g^T g of the
+    lowest doublet is the same in the symmetric and the Landau gauge (to the
+    finite-difference terms, ~1e-9 here)."""
+    p = _box(12, 6, 6, seed=3, rot=rot)
+    Gs = []
+    for gauge in (0, 1):
+        q = p.with_(gauge=gauge)
+        _, U = gt_oracle.lowest_states(q, 2)
+        g = gt_oracle.g_matrix(gt_oracle.magnetic_response(q, U))
+        Gs.append(g.T @ g)
+    assert np.abs(Gs[0] - Gs[1]).max() < 2e-8
+    assert np.abs(Gs[0]).max() > 1e-2
