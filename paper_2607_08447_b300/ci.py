@@ -165,7 +165,7 @@ def ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=None, method=0, e_c=Non
 
 def ci_detuning_sweep(grid, poisson, potentials, n_orb, delta_so, strain=None, solve_kw=None, method=0,
                       e_c=None, T_c=1.0):
-    """The CI at every potential of a detuning sweep (Sec. III A: the CI
+    """The CI at every potential of a detuning sweep (Fig. 2(f): the CI
     matrix is rebuilt for each gate configuration).  `potentials` is a
     sequence of V fields for the H0 handle `grid`; each H0 solve starts
     from the previous point's orbitals.  Returns the list of CIResult."""
