@@ -39,7 +39,7 @@ SOLVE_KW = dict(n_states=16, block_m=24, degree=120, precision=0, tol=1e-10, see
 MIXED_DEGREE = 200   # defect-corrected FP32 filter (precision 2)
 CROP = (32, 12, 12)
 # DRAM bytes per point-vector of the FP64 fused stencil launch, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum = 2.519 GB + 0.829 GB over
+# (dram__bytes_read.sum + dram__bytes_write.sum = 2.463 GB + 0.829 GB over
 # 24 x 368640 point-vectors, one ncu capture of the FP64 stencil at C2).  Valid for the
 # kernel version profiled there; set to None when the kernel changes.
 NCU_TRAFFIC_FP64_PER_PV = (2.462602e9 + 0.828694e9) / (24 * 368640)
@@ -163,9 +163,10 @@ def _fp32_peak_tflops(torch):
     return 2 * 8192 ** 3 / (best * 1e-3) / 1e12
 
 
-def _crop(p):
-    """The workload's physics on a bounded CROP-sized box (cpu baseline sample)."""
-    nx, ny, nz = CROP
+def _crop(p, size=CROP):
+    """The workload's physics on a bounded box of `size` points (cpu
+    baseline sample), centred in the full grid."""
+    nx, ny, nz = size
     x0, y0, z0 = (p.nx - nx) // 2, (p.ny - ny) // 2, (p.nz - nz) // 2
     sl = (slice(z0, z0 + nz), slice(y0, y0 + ny), slice(x0, x0 + nx))
     V = np.ascontiguousarray(p.V[sl])
@@ -194,6 +195,46 @@ def _arpack_baseline(q, n, full_unknowns):
     return {"value": n / t * scale, "unit": UNIT, "cores": os.cpu_count(), "kind": "scipy eigsh (ARPACK)",
             "sample": (f"eigsh(k={n}, which='SA', tol=1e-10) on the oracle CSR of the {CROP[0]}x{CROP[1]}x"
                        f"{CROP[2]} crop: {t:.2f} s, scaled by the unknowns ratio {scale:.4g}")}
+
+
+def _oracle_next_rows(p):
+    """The oracle timed beside the NEXT rows, each on a stated crop of the
+    C2 physics (centred), unscaled: the H0 (block Lanczos, 16 states), three
+    SP iterations (dense eigensolver, direct Poisson), the two-hole CI
+    (2 orbitals) and the double-dot g-tensors (dense, 7 assembled
+    operators)."""
+    from oracle import ci as ci_o
+    from oracle import eig, kp
+    from oracle import gtensor as gt_o
+    from oracle import poisson as po_o
+    out = {}
+
+    def gates(q):
+        g = np.zeros((q.nz, q.ny, q.nx), dtype=np.uint8)
+        g[:, :, 0] = 1
+        g[:, :, -1] = 1
+        return g
+
+    q = _crop(p).with_(B=np.zeros(3))
+    H = kp.assemble_h0(q)
+    t0 = time.perf_counter()
+    eig.lowest_block_lanczos(H, 16, tol=1e-10)
+    out["h0"] = {"s": time.perf_counter() - t0, "sample": f"{CROP[0]}x{CROP[1]}x{CROP[2]} crop, "
+                 f"{H.shape[0]} unknowns, 16 states, block Lanczos"}
+    q = _crop(p, (10, 6, 6))
+    t0 = time.perf_counter()
+    po_o.sp_loop(q, q.V, gates(q), np.zeros_like(q.V), 8, 2.0, 1.5, 0.3, 3, bands=6)
+    out["sp"] = {"s_per_iteration": (time.perf_counter() - t0) / 3,
+                 "sample": f"10x6x6 crop, {q.n_unknowns} unknowns, 8 states, 2 holes, 3 iterations"}
+    q = _crop(p, (14, 6, 6)).with_(B=np.zeros(3))
+    t0 = time.perf_counter()
+    ci_o.ci_pipeline(q, 2, gates(q))
+    out["ci"] = {"s": time.perf_counter() - t0, "sample": "14x6x6 crop, 2 H0 orbitals, K = 6"}
+    q = _crop(p, (12, 6, 6))
+    t0 = time.perf_counter()
+    gt_o.dqd_g_tensors(q)
+    out["gtensor"] = {"s": time.perf_counter() - t0, "sample": f"12x6x6 crop, {q.n_unknowns} unknowns"}
+    return out
 
 
 def _cpu_baseline(p, n, full_unknowns):
@@ -403,6 +444,9 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(p, n, p.n_unknowns)
+        for key, v in _oracle_next_rows(p).items():
+            if key in line:
+                line[key]["oracle_cpu"] = dict(v, cores=os.cpu_count(), kind="oracle")
         line["cpu_baseline_arpack"] = _arpack_baseline(_crop(p), n, p.n_unknowns)
     if rank == 0:
         print(json.dumps(line), flush=True)
