@@ -261,11 +261,14 @@ khp_status khp_sp_update(khp_poisson p, const double* V_ext_dev, const double* p
  * F_k = V_ext + phi - V_k of the fixed point and the differences
  * dV_i = V_{i+1} - V_i, dF_i = F_{i+1} - F_i of the last m = min(k, depth)
  * calls (kept on the handle):
- *     gamma   = argmin |F_k - dF gamma|_2   (normal equations, host, m <= 8)
+ *     gamma   = argmin |F_k - dF gamma|_2   (m <= 8; tall-skinny QR of
+ *               [dF | F] by Givens rotations on the device, the small
+ *               factor's SVD on the host; minimum-norm solution with
+ *               singular values <= eps max(Np, m) sigma_max dropped)
  *     V_{k+1} = V_k + beta F_k - sum_i gamma_i (dV_i + beta dF_i)
  * The first call after khp_poisson_create, khp_sp_anderson_reset or a
- * change of depth is the linear step V + beta F.  A singular history
- * falls back to that step.
+ * change of depth is the linear step V + beta F.  A zero history gives
+ * gamma = 0, that step.
  *  V_ext_dev  float64 [Np] or NULL (zero);  phi_dev float64 [Np]
  *  V_dev      float64 [Np], updated in place
  *  max_change max |V_{k+1} - V_k| (host)
@@ -273,6 +276,22 @@ khp_status khp_sp_update(khp_poisson p, const double* V_ext_dev, const double* p
  * outside 1..8), OOM (history buffers: (2 depth_max + 3) Np doubles). */
 khp_status khp_sp_anderson(khp_poisson p, const double* V_ext_dev, const double* phi_dev, double beta, int depth,
                            double* V_dev, double* max_change);
+
+/* Fermi level of the Schroedinger-Poisson loop (Sec. II B: the hole
+ * density of the loop sums the states with Fermi-Dirac weights at the
+ * device temperature; the number of holes is fixed).  Host-only, no device
+ * work.
+ *  E_host    float64 [n] level energies [eV] (any order)
+ *  n_holes   number of holes, 0 < n_holes < n
+ *  kT        thermal energy [eV], > 0
+ *  mu_out    mu with sum_i 1 / (1 + exp((E_i - mu) / kT)) = n_holes
+ *  occ_host  optional float64 [n] output, the occupations at mu
+ * Safeguarded Newton iteration (bisection inside a bracket whenever the
+ * Newton step leaves it or stalls); converges to rounding for any spread
+ * of the levels.  Errors: INVALID_ARG (NULL, n < 1, kT <= 0, n_holes
+ * outside (0, n), non-finite level). */
+khp_status khp_fermi_level(const double* E_host, int n, double n_holes, double kT, double* mu_out,
+                           double* occ_host);
 
 /* Forget the Anderson history (start of a new self-consistent loop). */
 khp_status khp_sp_anderson_reset(khp_poisson p);
@@ -357,8 +376,8 @@ khp_status khp_eigs_backward(khp_handle h, const void* evecs_dev, const double* 
  * exits).  Limits: n_gates <= 16 (larger counts fail with
  * KHP_ERR_INVALID_ARG), n <= 64.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before
- *    capturing the stream into a CUDA graph.
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
  *  - All calls share the array: calls whose kernels overlap on the GPU
  *    (other streams or unordered host threads) race and must be serialised
  *    by the caller.

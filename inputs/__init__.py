@@ -14,6 +14,7 @@ from .gen import (  # noqa: F401
     config3,
     config4,
     config5,
+    crop,
     small_problem,
     random_block,
     smooth_noise,

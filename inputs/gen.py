@@ -237,6 +237,20 @@ def small_problem(nx, ny, nz, h=1.0, seed=7, rot="identity", B=(0.0, 0.0, 0.0),
                    n_states=n_states, block_m=block_m, seed=seed)
 
 
+def crop(p: Problem, size) -> Problem:
+    """The same fields on a box of `size` = (nx, ny, nz) points cut from the
+    centre of p's grid (a smaller instance of the same workload)."""
+    nx, ny, nz = size
+    x0, y0, z0 = (p.nx - nx) // 2, (p.ny - ny) // 2, (p.nz - nz) // 2
+    sl = (slice(z0, z0 + nz), slice(y0, y0 + ny), slice(x0, x0 + nx))
+    V = np.ascontiguousarray(p.V[sl])
+    eps = None if p.strain is None else np.ascontiguousarray(p.strain[(slice(None),) + sl])
+    msk = None if p.mask is None else np.ascontiguousarray(p.mask[sl])
+    lev = None if p.levers is None else np.ascontiguousarray(p.levers[(slice(None),) + sl])
+    return p.with_(nx=nx, ny=ny, nz=nz, V=V, strain=eps, mask=msk, levers=lev,
+                   name=f"{p.name}_crop{nx}x{ny}x{nz}")
+
+
 def random_block(n_rows: int, m: int, seed: int) -> np.ndarray:
     """Complex128 [n_rows][m] block with i.i.d. N(0,1) real and imaginary parts."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -15,7 +15,13 @@ of the Hermitian matrix H.  The oracle is that definition:
   are exact for that subspace, and stops when every wanted residual
   ||H y - theta y|| is below `tol`.  A block (not single-vector) Krylov space
   is used so that exactly degenerate pairs (Kramers doublets at B = 0) are
-  both found.
+  both found;
+* `lowest_arpack`: ARPACK's implicitly restarted Lanczos (SciPy `eigsh`,
+  which='SA', a library routine) for the largest grids at B != 0, where no
+  level is exactly degenerate (a single-vector Krylov space holds one vector
+  of each exactly degenerate eigenspace, so this path is not used at B = 0).
+  Its products H x run through a multithreaded CSR product of PyTorch's CPU
+  backend; the returned residuals are recomputed from the assembled H.
 
 Masked points are removed from the matrix before solving and the returned
 vectors carry zeros there.
@@ -118,3 +124,36 @@ def lowest_block_lanczos(H, n, block=4, keep=None, basis_max=None, tol=1e-11,
     if return_residuals:
         return out + (res[:n], cycle + 1)
     return out
+
+
+def lowest_arpack(H, n, tol=1e-13, ncv=None, seed=12345, mask=None, return_residuals=False):
+    """Lowest n eigenpairs (ascending) by ARPACK (see module doc).  `tol` is
+    ARPACK's relative Ritz-estimate tolerance; the residuals returned with
+    `return_residuals` are ||H v - w v|| recomputed from H."""
+    import scipy.sparse.linalg as spla
+    import torch
+    N = H.shape[0]
+    Ha, idx = _active(H, mask)
+    Ha = Ha.tocsr()
+    Na = Ha.shape[0]
+    Ht = torch.sparse_csr_tensor(torch.from_numpy(Ha.indptr.astype(np.int64)),
+                                 torch.from_numpy(Ha.indices.astype(np.int64)),
+                                 torch.from_numpy(np.ascontiguousarray(Ha.data, dtype=np.complex128)),
+                                 size=(Na, Na))
+    count = [0]
+
+    def mv(x):
+        count[0] += 1
+        return (Ht @ torch.from_numpy(np.ascontiguousarray(np.asarray(x).reshape(-1), dtype=np.complex128))).numpy()
+
+    op = spla.LinearOperator((Na, Na), matvec=mv, dtype=np.complex128)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v0 = rng.standard_normal(Na) + 1j * rng.standard_normal(Na)
+    ncv = ncv or min(Na - 1, max(4 * n, 2 * n + 20))
+    w, v = spla.eigsh(op, k=n, which="SA", tol=tol, ncv=ncv, v0=v0, maxiter=100000)
+    o = np.argsort(w)
+    w, v = w[o], v[:, o]
+    if not return_residuals:
+        return w, _embed(v, idx, N)
+    res = np.linalg.norm(Ha @ v - v * w[None, :], axis=0)
+    return w, _embed(v, idx, N), res, count[0]

@@ -46,6 +46,7 @@ static khp_status fail(khp_status s, const std::string& msg) {
 }
 
 khp_status khp_set_error(khp_status s, const std::string& msg) { return fail(s, msg); }
+void khp_clear_error() { g_err.clear(); }
 
 #define CK(call)                                                                        \
     do {                                                                                \

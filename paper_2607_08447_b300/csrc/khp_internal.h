@@ -99,3 +99,5 @@ cudaError_t launch_backward(const double2* psi, long long np, int n, const doubl
 // Records the message returned by khp_last_error() on this thread and
 // passes the status through (khp_api.cu).
 khp_status khp_set_error(khp_status s, const std::string& msg);
+// Clears the calling thread's last-error message (start of every entry point).
+void khp_clear_error();

@@ -16,6 +16,7 @@
 // whose kernels overlap on the GPU (different streams, or different host
 // threads without ordering) race on it.  Each call overwrites every entry
 // it reads, so nothing has to be cleared between calls.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -54,6 +55,7 @@ extern "C" khp_status khp_eigs_backward_noalloc(khp_handle g, const void* evecs_
                                                 double* dLdstrain_dev, const double* levers_dev, int n_gates,
                                                 double* dLdalpha_host) {
     using namespace khp;
+    khp_clear_error();
     if (!g) return khp_set_error(KHP_ERR_INVALID_ARG, "handle is NULL");
     if (!evecs_dev || !evals_host || !dLdE_host || !dLdV_dev)
         return khp_set_error(KHP_ERR_INVALID_ARG, "NULL argument");
@@ -64,7 +66,7 @@ extern "C" khp_status khp_eigs_backward_noalloc(khp_handle g, const void* evecs_
     if (n_gates > 0 && (!levers_dev || !dLdalpha_host))
         return khp_set_error(KHP_ERR_INVALID_ARG, "levers/alpha output NULL");
     for (int i = 0; i < n; ++i)
-        if (!(dLdE_host[i] == dLdE_host[i]) || !(evals_host[i] == evals_host[i]))
+        if (!std::isfinite(dLdE_host[i]) || !std::isfinite(evals_host[i]))
             return khp_set_error(KHP_ERR_INVALID_ARG, "non-finite input");
     for (int i = 0; i < n;) {
         int j = i + 1;

@@ -11,6 +11,7 @@
 // 16 iterations, replayed as one captured CUDA graph of 16 iterations.
 // Reductions run in two fixed-order stages (deterministic).
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -36,9 +37,8 @@ struct khp_poisson_s {
     // Anderson mixing of the SP loop (allocated on first use)
     double *a_dv, *a_df;   // [kMaxDepth][np] rings of iterate / residual differences
     double *a_vprev, *a_fprev, *a_f;   // [np]
-    double* a_partial;     // [nblk][kMaxK]
-    double* a_out;         // [kMaxK] device sums
-    double* a_host;        // [kMaxK] pinned
+    double* a_partial;     // [nblk][kMaxR] per-block triangular factors
+    double* a_host;        // [nblk][kMaxR] pinned copy of a_partial
     int a_depth, a_count;
 };
 
@@ -269,11 +269,16 @@ __global__ void __launch_bounds__(kT) max_finish_kernel(const double* partial, i
 // ------------------------------------------------------------------------
 // Anderson mixing (type II) for the fixed point V = G(V) = V_ext + phi[V]:
 // F_k = G(V_k) - V_k; history columns dV_i = V_{i+1} - V_i and
-// dF_i = F_{i+1} - F_i of the last m steps; gamma = argmin |F_k - dF gamma|
-// from the normal equations (m <= 8, solved on the host);
+// dF_i = F_{i+1} - F_i of the last m steps; gamma = argmin |F_k - dF gamma|;
 // V_{k+1} = V_k + beta F_k - sum_i gamma_i (dV_i + beta dF_i).
+// The least squares is solved through a QR factorisation of the tall
+// matrix A = [dF | F] (Np x (m+1)) without forming A^T A: every thread
+// folds its rows into a triangular factor by Givens rotations, the factors
+// of a block are merged the same way (a tall-skinny QR), and the host
+// merges the blocks' factors and solves R11 gamma = r12 through the SVD of
+// R11 (least-squares semantics for a rank-deficient history).
 constexpr int kMaxDepth = 8;
-constexpr int kMaxK = kMaxDepth * (kMaxDepth + 1) / 2 + kMaxDepth;
+constexpr int kMaxR = (kMaxDepth + 1) * (kMaxDepth + 2) / 2;   // packed (m+1)x(m+1) upper triangle
 
 __global__ void anderson_residual_kernel(long long np, const double* Vext, const double* phi, const double* V,
                                          double* f, double* vprev, double* fprev, double* dv, double* df) {
@@ -290,55 +295,87 @@ __global__ void anderson_residual_kernel(long long np, const double* Vext, const
     }
 }
 
-// block partials of dF_i . dF_j (i <= j, packed by rows) and dF_i . F
-template <int M>
-__global__ void __launch_bounds__(kT) anderson_gram_kernel(long long np, const double* __restrict__ df,
-                                                           const double* __restrict__ f, double* partial) {
-    constexpr int K = M * (M + 1) / 2 + M;
-    double acc[K];
+// Packed row-major upper triangle of a C x C matrix: row k holds columns
+// k..C-1 starting at offset k C - k (k - 1) / 2.
+__host__ __device__ constexpr int tri_at(int C, int k) { return k * C - k * (k - 1) / 2; }
+
+// Fold the row a (C entries) into the triangular factor R by Givens
+// rotations, so that R^T R gains a a^T.
+template <int C>
+__device__ __forceinline__ void givens_fold(double (&R)[C * (C + 1) / 2], double (&a)[C]) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
-        double d[M];
+    for (int k = 0; k < C; ++k) {
+        const int rk = tri_at(C, k);
+        const double y = a[k];
+        if (y != 0.0) {
+            const double x = R[rk];
+            const double r = hypot(x, y);
+            const double c = x / r, sn = y / r;
+            R[rk] = r;
 #pragma unroll
-        for (int i = 0; i < M; ++i) d[i] = df[(long long)i * np + p];
-        const double F = f[p];
-        int k = 0;
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-#pragma unroll
-            for (int j = i; j < M; ++j) {
-                acc[k] = fma(d[i], d[j], acc[k]);
-                ++k;
+            for (int j = k + 1; j < C; ++j) {
+                const double rj = R[rk + j - k];
+                R[rk + j - k] = c * rj + sn * a[j];
+                a[j] = c * a[j] - sn * rj;
             }
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-            acc[k] = fma(d[i], F, acc[k]);
-            ++k;
         }
-    }
-    __shared__ double sm[kT / 32][K];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double v = acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sm[warp][k] = v;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += kT) {
-        double v = 0.0;
-        for (int w = 0; w < kT / 32; ++w) v += sm[w][k];
-        partial[(size_t)blockIdx.x * K + k] = v;
     }
 }
 
-__global__ void anderson_sum_kernel(const double* partial, int nblk, int K, double* out) {
-    const int k = threadIdx.x;
-    if (k >= K) return;
-    double v = 0.0;
-    for (int b = 0; b < nblk; ++b) v += partial[(size_t)b * K + k];
-    out[k] = v;
+// Fold every row of another factor Q into R.
+template <int C>
+__device__ __forceinline__ void givens_merge(double (&R)[C * (C + 1) / 2], const double (&Q)[C * (C + 1) / 2]) {
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        double a[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) a[j] = j < k ? 0.0 : Q[tri_at(C, k) + j - k];
+        givens_fold<C>(R, a);
+    }
+}
+
+// One triangular factor of [dF_0 .. dF_{M-1} | F] per block into
+// partial[block][C (C + 1) / 2], C = M + 1.
+template <int M>
+__global__ void __launch_bounds__(kT) anderson_qr_kernel(long long np, const double* __restrict__ df,
+                                                         const double* __restrict__ f, double* partial) {
+    constexpr int C = M + 1;
+    constexpr int K = C * (C + 1) / 2;
+    double R[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) R[k] = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
+        double a[C];
+#pragma unroll
+        for (int i = 0; i < M; ++i) a[i] = df[(long long)i * np + p];
+        a[M] = f[p];
+        givens_fold<C>(R, a);
+    }
+    // merge within the warp, halving the active lanes each level
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int off = 16; off > 0; off >>= 1) {
+        double Q[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) Q[k] = __shfl_down_sync(0xffffffffu, R[k], off);
+        if (lane < off) givens_merge<C>(R, Q);
+    }
+    __shared__ double sm[kT / 32][K];
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sm[warp][k] = R[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll 1
+        for (int w = 1; w < kT / 32; ++w) {
+            double Q[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) Q[k] = sm[w][k];
+            givens_merge<C>(R, Q);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) partial[(size_t)blockIdx.x * K + k] = R[k];
+    }
 }
 
 struct AndersonCoef {
@@ -397,7 +434,7 @@ void free_all(khp_poisson_s* P) {
     if (P->have_chunk) cudaGraphExecDestroy(P->chunk);
     if (P->work) cudaStreamDestroy(P->work);
     double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s,
-                      P->a_dv, P->a_df, P->a_vprev, P->a_fprev, P->a_f, P->a_partial, P->a_out};
+                      P->a_dv, P->a_df, P->a_vprev, P->a_fprev, P->a_f, P->a_partial};
     for (double* b : bufs)
         if (b) cudaFree(b);
     if (P->gate) cudaFree(P->gate);
@@ -405,46 +442,92 @@ void free_all(khp_poisson_s* P) {
     if (P->a_host) cudaFreeHost(P->a_host);
 }
 
-// gamma from the packed normal equations (G packed by rows, then b):
-// Jacobi-equilibrated Cholesky with a relative diagonal floor of 1e-14
-bool anderson_solve(const double* packed, int m, double* gamma) {
-    double G[khp::poisson::kMaxDepth][khp::poisson::kMaxDepth], b[khp::poisson::kMaxDepth], d[khp::poisson::kMaxDepth];
-    int k = 0;
-    for (int i = 0; i < m; ++i)
-        for (int j = i; j < m; ++j) G[i][j] = G[j][i] = packed[k++];
-    for (int i = 0; i < m; ++i) b[i] = packed[k++];
-    for (int i = 0; i < m; ++i) {
-        if (!(G[i][i] > 0.0) || !std::isfinite(G[i][i])) return false;
-        d[i] = 1.0 / std::sqrt(G[i][i]);
-    }
-    for (int i = 0; i < m; ++i) {
-        b[i] *= d[i];
-        for (int j = 0; j < m; ++j) G[i][j] *= d[i] * d[j];
-        G[i][i] += 1e-14;
-    }
-    for (int j = 0; j < m; ++j) {          // G = L L^T in place (lower)
-        double s = G[j][j];
-        for (int q = 0; q < j; ++q) s -= G[j][q] * G[j][q];
-        if (!(s > 0.0)) return false;
-        G[j][j] = std::sqrt(s);
-        for (int i = j + 1; i < m; ++i) {
-            double t = G[i][j];
-            for (int q = 0; q < j; ++q) t -= G[i][q] * G[j][q];
-            G[i][j] = t / G[j][j];
+// Host side of the tall-skinny QR: fold the blocks' factors into one
+// R = [[R11, r12], [0, r22]] of [dF | F] by Givens rotations, then
+// gamma = pinv(R11) r12 through a one-sided Jacobi SVD of R11 (the
+// singular values of R11 are those of dF); singular values at or below
+// eps max(Np, m) sigma_max count as zero, the cutoff of LAPACK's
+// minimum-norm least squares.  A zero history gives gamma = 0, the plain
+// damped step.
+void anderson_solve(const double* factors, int nblk, int m, long long np, double* gamma) {
+    constexpr int D = khp::poisson::kMaxDepth + 1;
+    const int C = m + 1;
+    const int K = C * (C + 1) / 2;
+    double R[D][D] = {};
+    for (int b = 0; b < nblk; ++b) {
+        const double* Q = factors + (size_t)b * K;
+        for (int k = 0; k < C; ++k) {
+            double a[D] = {};
+            for (int j = k; j < C; ++j) a[j] = Q[khp::poisson::tri_at(C, k) + j - k];
+            for (int i = 0; i < C; ++i) {
+                const double y = a[i];
+                if (y == 0.0) continue;
+                const double x = R[i][i];
+                const double r = std::hypot(x, y);
+                const double c = x / r, sn = y / r;
+                R[i][i] = r;
+                for (int j = i + 1; j < C; ++j) {
+                    const double rj = R[i][j];
+                    R[i][j] = c * rj + sn * a[j];
+                    a[j] = c * a[j] - sn * rj;
+                }
+            }
         }
     }
-    for (int i = 0; i < m; ++i) {          // L y = b
-        double t = b[i];
-        for (int q = 0; q < i; ++q) t -= G[i][q] * b[q];
-        b[i] = t / G[i][i];
+    // one-sided Jacobi on the columns of A = R11: A V = U diag(sigma)
+    double A[D][D], V[D][D];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            A[i][j] = R[i][j];
+            V[i][j] = i == j ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    al += A[i][p] * A[i][p];
+                    be += A[i][q] * A[i][q];
+                    ga += A[i][p] * A[i][q];
+                }
+                if (ga == 0.0 || std::fabs(ga) <= DBL_EPSILON * std::sqrt(al * be)) continue;
+                rotated = true;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (int i = 0; i < m; ++i) {
+                    const double ap = A[i][p], aq = A[i][q];
+                    A[i][p] = c * ap - sn * aq;
+                    A[i][q] = sn * ap + c * aq;
+                    const double vp = V[i][p], vq = V[i][q];
+                    V[i][p] = c * vp - sn * vq;
+                    V[i][q] = sn * vp + c * vq;
+                }
+            }
+        if (!rotated) break;
     }
-    for (int i = m - 1; i >= 0; --i) {     // L^T x = y
-        double t = b[i];
-        for (int q = i + 1; q < m; ++q) t -= G[q][i] * b[q];
-        b[i] = t / G[i][i];
+    double sig[D], smax = 0.0;
+    for (int j = 0; j < m; ++j) {
+        double t = 0.0;
+        for (int i = 0; i < m; ++i) t += A[i][j] * A[i][j];
+        sig[j] = std::sqrt(t);
+        smax = std::max(smax, sig[j]);
     }
-    for (int i = 0; i < m; ++i) gamma[i] = b[i] * d[i];
-    return true;
+    const double cut = DBL_EPSILON * (double)std::max<long long>(np, m) * smax;
+    for (int i = 0; i < m; ++i) gamma[i] = 0.0;
+    for (int j = 0; j < m; ++j) {
+        if (!(sig[j] > cut) || !std::isfinite(sig[j])) continue;
+        double ur = 0.0;                   // u_j . r12 with u_j = A[:, j] / sigma_j
+        for (int i = 0; i < m; ++i) ur += A[i][j] * R[i][m];
+        const double w = ur / (sig[j] * sig[j]);
+        for (int i = 0; i < m; ++i) gamma[i] += V[i][j] * w;
+    }
+    for (int i = 0; i < m; ++i)
+        if (!std::isfinite(gamma[i])) {
+            for (int k = 0; k < m; ++k) gamma[k] = 0.0;
+            break;
+        }
 }
 
 }  // namespace
@@ -602,9 +685,8 @@ khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double*
             (e = cudaMalloc(&P->a_vprev, sizeof(double) * np)) != cudaSuccess ||
             (e = cudaMalloc(&P->a_fprev, sizeof(double) * np)) != cudaSuccess ||
             (e = cudaMalloc(&P->a_f, sizeof(double) * np)) != cudaSuccess ||
-            (e = cudaMalloc(&P->a_partial, sizeof(double) * kMaxK * P->nblk)) != cudaSuccess ||
-            (e = cudaMalloc(&P->a_out, sizeof(double) * kMaxK)) != cudaSuccess ||
-            (e = cudaMallocHost(&P->a_host, sizeof(double) * kMaxK)) != cudaSuccess)
+            (e = cudaMalloc(&P->a_partial, sizeof(double) * kMaxR * P->nblk)) != cudaSuccess ||
+            (e = cudaMallocHost(&P->a_host, sizeof(double) * kMaxR * P->nblk)) != cudaSuccess)
             return pfail(KHP_ERR_OOM, std::string("Anderson history: ") + cudaGetErrorString(e));
         P->a_count = 0;
         P->a_depth = depth;
@@ -630,20 +712,16 @@ khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double*
     const int m = std::min(P->a_count, depth);
     AndersonCoef c{};
     if (m > 0) {
-        const int K = m * (m + 1) / 2 + m;
+        const int K = (m + 1) * (m + 2) / 2;
         switch (m) {
-#define KHP_AG(M) case M: anderson_gram_kernel<M><<<nb, kT, 0, st>>>(np, P->a_df, P->a_f, P->a_partial); break;
-            KHP_AG(1) KHP_AG(2) KHP_AG(3) KHP_AG(4) KHP_AG(5) KHP_AG(6) KHP_AG(7) KHP_AG(8)
-#undef KHP_AG
+#define KHP_AQ(M) case M: anderson_qr_kernel<M><<<nb, kT, 0, st>>>(np, P->a_df, P->a_f, P->a_partial); break;
+            KHP_AQ(1) KHP_AQ(2) KHP_AQ(3) KHP_AQ(4) KHP_AQ(5) KHP_AQ(6) KHP_AQ(7) KHP_AQ(8)
+#undef KHP_AQ
         }
-        anderson_sum_kernel<<<1, 64, 0, st>>>(P->a_partial, nb, K, P->a_out);
         PCK(cudaGetLastError());
-        PCK(cudaMemcpyAsync(P->a_host, P->a_out, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+        PCK(cudaMemcpyAsync(P->a_host, P->a_partial, sizeof(double) * K * nb, cudaMemcpyDeviceToHost, st));
         PCK(cudaStreamSynchronize(st));
-        // a singular history (e.g. a repeated iterate) falls back to the
-        // plain damped step
-        if (!anderson_solve(P->a_host, m, c.gamma))
-            for (int i = 0; i < m; ++i) c.gamma[i] = 0.0;
+        anderson_solve(P->a_host, nb, m, np, c.gamma);
     }
     anderson_update_kernel<<<nb, kT, 0, st>>>(np, m, beta, c, V_dev, P->a_f, P->a_dv, P->a_df, P->partial);
     max_finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, P->s + 6);
@@ -652,6 +730,65 @@ khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double*
     PCK(cudaStreamSynchronize(st));
     P->a_count += 1;
     if (max_change) *max_change = P->host_pinned[6];
+    return KHP_OK;
+}
+
+// Fermi level of the SP loop's occupations (Sec. II B; host only).  The
+// hole count N(mu) = sum_i f((E_i - mu) / kT), f(x) = 1 / (1 + e^x), rises
+// monotonically in mu with slope N'(mu) = sum_i f (1 - f) / kT.  Newton's
+// method on N(mu) = n_holes, kept inside a bracket [lo, hi] that every
+// evaluation narrows (N < n_holes moves lo up, N > n_holes moves hi down);
+// a Newton step that leaves the bracket, or stalls on a flat stretch of N
+// between well separated levels, is replaced by the bracket's midpoint.
+khp_status khp_fermi_level(const double* E_host, int n, double n_holes, double kT, double* mu_out,
+                           double* occ_host) {
+    khp_set_error(KHP_OK, "");
+    if (!E_host || !mu_out) return pfail(KHP_ERR_INVALID_ARG, "E or mu is NULL");
+    if (n < 1) return pfail(KHP_ERR_INVALID_ARG, "n must be >= 1");
+    if (!(kT > 0.0) || !std::isfinite(kT)) return pfail(KHP_ERR_INVALID_ARG, "kT must be > 0");
+    if (!(n_holes > 0.0 && n_holes < n)) return pfail(KHP_ERR_INVALID_ARG, "n_holes must lie in (0, n)");
+    double emin = E_host[0], emax = E_host[0];
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(E_host[i])) return pfail(KHP_ERR_INVALID_ARG, "non-finite level");
+        emin = std::min(emin, E_host[i]);
+        emax = std::max(emax, E_host[i]);
+    }
+    auto occ = [&](double e, double mu) {
+        const double x = (e - mu) / kT;
+        if (x >= 0.0) {
+            const double t = std::exp(-x);
+            return t / (1.0 + t);
+        }
+        return 1.0 / (1.0 + std::exp(x));
+    };
+    // N(lo) <= n e^-(L) < n_holes and N(hi) >= n - n e^-(L) > n_holes
+    const double L = std::log((double)n) + 60.0 + std::fabs(std::log(std::min(n_holes, n - n_holes)));
+    double lo = emin - L * kT, hi = emax + L * kT;
+    double mu = 0.5 * (lo + hi), dx = hi - lo, dxold = dx;
+    for (int it = 0; it < 400; ++it) {
+        double N = 0.0, dN = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double f = occ(E_host[i], mu);
+            N += f;
+            dN += f * (1.0 - f);
+        }
+        dN /= kT;
+        const double r = N - n_holes;
+        if (r == 0.0) break;
+        if (r < 0.0) lo = mu; else hi = mu;
+        const double newton = dN > 0.0 ? mu - r / dN : lo;
+        // bisect when Newton leaves the bracket or would not halve the
+        // step of the iteration before last
+        const bool bisect = !(newton > lo && newton < hi) || std::fabs(2.0 * r) > std::fabs(dxold * dN);
+        dxold = dx;
+        const double prev = mu;
+        mu = bisect ? 0.5 * (lo + hi) : newton;
+        dx = mu - prev;
+        if (std::fabs(dx) <= 2.0 * DBL_EPSILON * std::max(std::fabs(mu), kT)) break;
+    }
+    *mu_out = mu;
+    if (occ_host)
+        for (int i = 0; i < n; ++i) occ_host[i] = occ(E_host[i], mu);
     return KHP_OK;
 }
 

@@ -3,8 +3,8 @@
 `Poisson` wraps khp_poisson_create / khp_poisson_solve / khp_sp_update
 (include/khp.h).  `sp_solve` runs the self-consistent loop: the library's
 eigensolver (warm-started from the previous iteration), occupations from a
-fixed hole number at temperature T (Fermi level by bisection over the n
-eigenvalues on the host), the library's density, the library's Poisson
+fixed hole number at temperature T (the library's Fermi level over the n
+eigenvalues, khp_fermi_level), the library's density, the library's Poisson
 solve and potential update.  All grid-sized work runs in the library.
 """
 from __future__ import annotations
@@ -88,20 +88,16 @@ class Poisson:
 
 
 def fermi_level(E, n_holes, kT):
-    """mu with sum_i f((E_i - mu) / kT) = n_holes (bisection, host)."""
-    E = np.asarray(E, dtype=np.float64)
-
-    def count(mu):
-        return np.sum(0.5 * (1.0 - np.tanh(0.5 * (E - mu) / kT)))
-
-    lo, hi = E.min() - 50 * kT - 1.0, E.max() + 50 * kT + 1.0
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if count(mid) < n_holes:
-            lo = mid
-        else:
-            hi = mid
-    return 0.5 * (lo + hi)
+    """(mu, occupations): the Fermi level holding `n_holes` holes in the
+    levels E at thermal energy kT, and the Fermi-Dirac occupations there
+    (khp_fermi_level, host side of the library)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    occ = np.empty_like(E)
+    mu = ctypes.c_double(0.0)
+    lib = _lib.load()
+    _lib.check(lib.khp_fermi_level(_lib.dptr(E), int(E.size), float(n_holes), float(kT), ctypes.byref(mu),
+                                   _lib.dptr(occ)))
+    return mu.value, occ
 
 
 @dataclass
@@ -134,8 +130,7 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
         grid.set_fields(V, strain, None, None, B, gauge)
         r = grid.eigensolve(n_states, warm_start=warm, **kw)
         warm = r.evecs
-        mu = fermi_level(r.evals, n_holes, kT)
-        f = 0.5 * (1.0 - np.tanh(0.5 * (r.evals - mu) / kT))
+        mu, f = fermi_level(r.evals, n_holes, kT)
         rho = grid.density(r.evecs, f / grid.h ** 3)
         poisson.solve(rho, phi)
         piters.append(poisson.last_iterations)

@@ -1,7 +1,9 @@
 """Host-side arithmetic of the package (the steps that run on small
 matrices on the host) against the oracle's separately written versions,
-on random inputs: the Fermi level of the SP loop, the spin-orbit block and
-the Slater-Condon two-hole matrix of the CI, and the total-spin operator.
+on random inputs: the Fermi level of the SP loop (the library's
+khp_fermi_level, a Newton iteration, against the oracle's bisection), the
+spin-orbit block and the Slater-Condon two-hole matrix of the CI, and the
+total-spin operator.
 No GPU needed."""
 import numpy as np
 import pytest
@@ -13,16 +15,47 @@ from paper_2607_08447_b300 import ci as ci_pkg
 from paper_2607_08447_b300 import poisson as po_pkg
 
 
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_08447_b300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_fermi_level_matches_oracle(seed):
+def test_fermi_level_matches_oracle(lib, seed):
+    """The library's Fermi level (safeguarded Newton, khp_fermi_level)
+    against the oracle's bisection, which shares no code with it: random
+    levels, well separated levels with kT far below the spacing (flat count
+    between levels), an exactly degenerate cluster, fractional fillings."""
     rng = np.random.default_rng(seed)
-    E = np.sort(rng.uniform(-5e-3, 5e-3, 16))
-    for T, nh in ((1.5, 2.0), (20.0, 3.0), (0.3, 1.0)):
-        kT = 8.617333262e-5 * T
-        mu_p = po_pkg.fermi_level(E, nh, kT)
-        mu_o = po_or.fermi_level(E, nh, kT)
-        assert abs(mu_p - mu_o) <= 1e-12
-        assert abs(np.sum(po_or.occupations(E, mu_p, kT)) - nh) <= 1e-9
+    cases = [np.sort(rng.uniform(-5e-3, 5e-3, 16)),
+             np.array([0.0, 1e-3, 2e-3, 5e-3, 9e-3, 2e-2]) + rng.uniform(-1e-2, 1e-2),
+             np.array([1e-3, 1e-3, 1e-3 + 1e-9, 4e-3, 4e-3, 8e-3, 8e-3, 1.2e-2])]
+    for E in cases:
+        for T, nh in ((1.5, 2.0), (20.0, 3.0), (0.3, 1.0), (4.0, 2.5), (1.5, 0.01)):
+            kT = 8.617333262e-5 * T
+            mu_p, occ = po_pkg.fermi_level(E, nh, kT)
+            mu_o = po_or.fermi_level(E, nh, kT)
+            f_o = po_or.occupations(E, mu_o, kT)
+            # both sides' occupations hold n_holes; mu agrees to the flatness
+            # of the count (dN/dmu) times rounding
+            assert abs(np.sum(occ) - nh) <= 1e-12 * len(E), (T, nh)
+            assert np.abs(occ - f_o).max() <= 1e-10, (T, nh)
+            slope = np.sum(f_o * (1 - f_o)) / kT
+            assert abs(mu_p - mu_o) <= 1e-12 + 1e-14 * len(E) / slope, (T, nh, mu_p, mu_o)
+
+
+def test_fermi_level_rejects_bad_input(lib):
+    import ctypes
+    from paper_2607_08447_b300 import _lib
+    E = np.array([0.0, 1e-3, 2e-3])
+    mu = ctypes.c_double()
+    assert lib.khp_fermi_level(_lib.dptr(E), 3, 3.0, 1e-4, ctypes.byref(mu), None) == 1
+    assert lib.khp_fermi_level(_lib.dptr(E), 3, 1.0, 0.0, ctypes.byref(mu), None) == 1
+    E[1] = np.inf
+    assert lib.khp_fermi_level(_lib.dptr(E), 3, 1.0, 1e-4, ctypes.byref(mu), None) == 1
+    assert b"non-finite" in lib.khp_last_error()
 
 
 def test_spin_orbit_block_matches_oracle():

@@ -305,6 +305,24 @@ def test_block_lanczos_matches_dense():
         assert subspace_sin_angle(vd[:, :8], vl) < 1e-9
 
 
+def test_arpack_matches_dense_and_block_lanczos():
+    """The ARPACK path (used for the largest grids at B != 0) against dense
+    LAPACK on config 1 with a field and against block Lanczos on a 6x6x6
+    device-frame grid with strain and a tilted field."""
+    c1 = inputs.config1().with_(B=np.array([0.0, 0.3, 0.6]))
+    for p, ref in ((c1, "dense"), (_box(6, 6, 6, rot="device", B=(0.4, 0.2, -0.9)), "lanczos")):
+        H = kp.assemble(p)
+        if ref == "dense":
+            wr, vr = eig.lowest_dense(H, 12)
+        else:
+            wr, vr = eig.lowest_block_lanczos(H, 12, tol=1e-12)
+        wa, va, res, nmv = eig.lowest_arpack(H, 10, return_residuals=True)
+        assert np.abs(wa - wr[:10]).max() < 1e-12
+        assert res.max() < 1e-11
+        assert np.all(np.diff(wr[:11]) > 1e-9)      # no exact degeneracy at B != 0
+        assert subspace_sin_angle(vr[:, :10], va) < 1e-9
+
+
 def test_dense_matches_numpy_full_diagonalisation():
     p = _box(4, 3, 3, rot="device", B=(0.0, 0.5, 0.5))
     H = kp.assemble(p)
@@ -620,6 +638,48 @@ def test_ci_coulomb_tensor_symmetries_and_exchange_sign():
     w, s2, jex = ci_oracle.exchange(ci_oracle.ci_matrix(ci_oracle.one_body(E, ci_oracle.orbital_overlaps(phi), 0.0),
                                                         J, 2)[0], 2)
     assert s2[0] < 1e-9 and jex > 0
+
+
+def _spin_orbitals(phi):
+    """Columns 2 i + s: orbital i (three components per point) times spin s,
+    embedded in the 6-band row order 6 p + 3 s + o."""
+    N3, n = phi.shape
+    Np = N3 // 3
+    P = phi.reshape(Np, 3, n)
+    out = np.zeros((Np, 2, 3, n, 2), dtype=complex)
+    for s in range(2):
+        out[:, s, :, :, s] = P
+    return out.reshape(6 * Np, 2 * n)
+
+
+@pytest.mark.parametrize("n_orb", [None, 5])
+def test_ci_one_body_is_the_projected_full_operator(n_orb):
+    """The CI one-body block (H0 energies plus the spin-orbit term between
+    H0 orbitals, Eqs. 11-12) equals the full 6x6 operator at B = 0 (pinned
+    separately above) projected on the spin-orbitals, entry by entry, since
+    H = H0 x 1_spin + H_SOI.  In the complete basis of all 3 Np H0 orbitals
+    its spectrum is the full operator's.  The orbitals carry random phases,
+    so a dropped conjugate, a transposed overlap O[i,o,j,q] or swapped spin
+    indices of the spin-orbit matrix change the entries."""
+    p = inputs.small_problem(3, 2, 2, h=0.5, seed=9, rot="device", strain=True)
+    nb = 3 * p.n_points
+    n = nb if n_orb is None else n_orb
+    E, phi = eig.lowest_dense(kp.assemble_h0(p), n)
+    rng = np.random.default_rng(17)
+    phi = phi * np.exp(2j * np.pi * rng.uniform(size=n))[None, :]
+    h1 = ci_oracle.one_body(E, ci_oracle.orbital_overlaps(phi), p.material["delta_so"])
+    H = kp.assemble(p).toarray()
+    S = _spin_orbitals(phi)
+    proj = S.conj().T @ H @ S
+    scale = np.abs(H).max()
+    assert np.abs(h1 - proj).max() <= 1e-12 * scale
+    if n_orb is None:
+        assert np.abs(S.conj().T @ S - np.eye(2 * nb)).max() <= 1e-12
+        assert np.abs(np.linalg.eigvalsh(h1) - np.linalg.eigvalsh(H)).max() <= 1e-12 * scale
+    # the pin separates the plausible slips
+    O = ci_oracle.orbital_overlaps(phi)
+    for bad in (O.transpose(0, 3, 2, 1), O.conj(), O.transpose(2, 1, 0, 3)):
+        assert np.abs(ci_oracle.one_body(E, bad, p.material["delta_so"]) - proj).max() > 1e-6 * scale
 
 
 # --------------------------------------------------------------------------

@@ -50,6 +50,27 @@ def test_noalloc_backward_matches_allocating_entry_point(khp):
         assert np.abs(dV1 - dV0).max() <= 1e-12 * np.abs(dV0).max()
         assert np.abs(dS1 - dS0).max() <= 1e-12 * np.abs(dS0).max()
         assert np.abs(da1 - da0).max() <= 1e-12 * np.abs(da0).max()
+    # the shared scratch after a larger call: 16 gates, then 3, then none
+    # (and no strain output), each against the allocating entry point
+    lev16 = torch.from_numpy(inputs.random_block(16, grid.np_, seed=41).real.copy()).cuda().contiguous()
+    g = [0.7, -0.2, 1.1, 0.4, -2.0, 0.9]
+    for ng, want in ((16, True), (3, True), (0, False)):
+        lv = lev16[:ng].contiguous() if ng else None
+        s0, dV0, dS0, da0 = _call(lib, "khp_eigs_backward", grid, V, ev, g, lv, ng, want)
+        s1, dV1, dS1, da1 = _call(lib, "khp_eigs_backward_noalloc", grid, V, ev, g, lv, ng, want)
+        assert s0 == 0 and s1 == 0, (ng, s0, s1)
+        assert np.abs(dV1 - dV0).max() <= 1e-12 * np.abs(dV0).max()
+        if want:
+            assert np.abs(dS1 - dS0).max() <= 1e-12 * np.abs(dS0).max()
+        if ng:
+            assert np.abs(da1 - da0).max() <= 1e-12 * np.abs(da0).max()
+    assert lib.khp_last_error() == b""
+    # non-finite dL/dE (Inf as well as NaN) is rejected like the allocating call
+    for bad in (np.inf, -np.inf, np.nan):
+        gb = [1.0, bad, 0.0, 0.0, 0.0, 0.0]
+        st0, *_ = _call(lib, "khp_eigs_backward", grid, V, ev, gb, None, 0, False)
+        st1, *_ = _call(lib, "khp_eigs_backward_noalloc", grid, V, ev, gb, None, 0, False)
+        assert st0 == 1 and st1 == 1, (bad, st0, st1)
     # gates beyond the fixed scratch are rejected with a clear error
     many = torch.zeros((17, grid.np_), dtype=torch.float64, device="cuda")
     st, *_ = _call(lib, "khp_eigs_backward_noalloc", grid, V, ev, [1.0] * 6, many, 17)
