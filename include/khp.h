@@ -38,6 +38,8 @@
 extern "C" {
 #endif
 
+#define KHP_STATS_HISTORY 64
+
 typedef struct khp_grid* khp_handle;
 
 typedef enum {
@@ -132,6 +134,14 @@ typedef struct {
     int batch_rounds;          /* batched call: lock-step rounds executed      */
     int batch_graphs;          /* batched call: CUDA graphs instantiated       */
     double autotune_ms;        /* batched call: time spent in autotune trials  */
+    /* per-phase device time (CUDA events on the handle's stream; single
+     * solves only): Gram matrices G = Y^H Y, S = Y^H W; the m x m problem;
+     * the rotation X = Y Q, HX = W Q with the residual norms; and the work
+     * between the filter and the Gram (block combine and the H Y apply) */
+    double ms_gram, ms_small, ms_rotate, ms_between;
+    double bytes_rr;           /* algorithmic HBM bytes of the Gram and rotation passes */
+    int n_history;             /* outer iterations recorded (incl. the start)  */
+    double res_history[KHP_STATS_HISTORY]; /* max residual [eV] after each (first 64) */
 } khp_stats;
 
 /* Create a grid handle.
@@ -184,6 +194,24 @@ khp_status khp_set_potential_strain_field(khp_handle h, const double* V_dev,
  *  X and Y must not overlap.  m in 1..64 (m even for precision 1 fast path;
  *  odd m handled too). */
 khp_status khp_apply(khp_handle h, const void* X_dev, void* Y_dev, int m, int precision);
+
+/* One fused step of the Chebyshev filter (the three-term recurrence of the
+ * Rayleigh-Chebyshev iteration, Sec. II B) on the columns
+ * [col0, col0 + ncol) of row-major [N][ld] blocks:
+ *     y = alpha (H x) + beta x + gamma prev + src_coef[col] src
+ *  precision 0: x, prev, y complex128;  1: x, prev, src, y complex64
+ *  prev_dev  NULL drops the gamma term;  src_dev NULL drops the source term
+ *            (src needs precision 1 and src_coef_host, float64 [ld])
+ *  y must not alias x, prev or src; columns outside the range are left
+ *  unchanged.  Asynchronous on the handle's stream.  FP32 steps without a
+ *  point mask, in the crystal or [110] frame and at B = 0 or in the
+ *  symmetric gauge, with even ld and col0, run in the plane-marching kernel
+ *  (TMA-staged z-planes); other steps in the per-point kernel.
+ * Errors: INVALID_ARG (NULL or aliased blocks, ld outside 1..64, columns
+ * outside the row, non-finite coefficients), STATE (fields not set). */
+khp_status khp_filter_step(khp_handle h, const void* x_dev, const void* prev_dev, const void* src_dev,
+                           const double* src_coef_host, void* y_dev, int ld, int col0, int ncol,
+                           double alpha, double beta, double gamma, int precision);
 
 /* The two dense contractions of the Rayleigh-Ritz step (Sec. II B), on the
  * handle's grid length N, for a block that is not the solver's own.

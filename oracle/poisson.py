@@ -148,3 +148,131 @@ def sp_loop(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, mix, iters, 
         hist.append(float(np.abs(Vn - V).max()))
         V = Vn
     return V, E, mu, hist
+
+
+# --------------------------------------------------------------------------
+# Predictor-corrector Schroedinger-Poisson loop (Trellakis et al., J. Appl.
+# Phys. 81, 7880 (1997)).  The paper says only that the loop is repeated
+# until convergence (Sec. II B); at its temperature (1.5 K, Sec. III A)
+# mixing V alone oscillates between near-degenerate wells.  The scheme
+# replaces the Poisson step by a nonlinear one in which every state keeps
+# its wave function while its energy follows the local change of the
+# potential:
+#     rho[phi](p) = sum_i P_i(p) f((E_i + phi(p) - phi_k(p) - mu) / kT),
+#     P_i(p) = sum_b |psi_i(p, b)|^2 / h^3,
+#     h^3 sum_p rho[phi](p) = n_holes          (fixes mu for every phi),
+#     A phi = (e / eps) rho[phi]               (free points; gates fixed),
+# solved by Newton's method.  At a fixed point (phi = phi_k) rho is the
+# Fermi-Dirac density of the states of H(V_ext + phi), so the loop ends at
+# a solution of the plain Schroedinger-Poisson equations.
+
+def state_densities(evecs, h, bands=6):
+    """P[i][p] = sum_b |psi_i(p, b)|^2 / h^3 (nm^-3)."""
+    N, n = evecs.shape
+    P = (np.abs(evecs) ** 2).reshape(N // bands, bands, n).sum(axis=1)
+    return np.ascontiguousarray(P.T) / h ** 3
+
+
+def local_density(P, E, mu, kT, dphi):
+    """rho_p, D_p = -d rho_p / d phi_p at fixed mu, with the local energies
+    E_i + dphi_p."""
+    x = (np.asarray(E)[:, None] + dphi[None, :] - mu) / kT
+    f = 0.5 * (1.0 - np.tanh(0.5 * x))
+    rho = np.sum(P * f, axis=0)
+    D = np.sum(P * f * (1.0 - f), axis=0) / kT
+    return rho, D
+
+
+def local_fermi_level(P, E, n_holes, kT, dphi, h):
+    """mu with h^3 sum_p rho_p(mu) = n_holes (bisection; the count rises
+    monotonically with mu)."""
+    lo = np.min(E) + dphi.min() - 50 * kT - 1.0
+    hi = np.max(E) + dphi.max() + 50 * kT + 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        rho, _ = local_density(P, E, mid, kT, dphi)
+        if h ** 3 * rho.sum() < n_holes:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def nonlinear_residual(A, gate, gate_phi, coef, phi, P, E, n_holes, kT, phi_k, h):
+    """(F, mu, D): F = A phi - coef rho[phi] on free points, phi - phi_gate
+    at gates; mu from the hole count; D = -d rho / d phi (local)."""
+    dphi = phi - phi_k
+    mu = local_fermi_level(P, E, n_holes, kT, dphi, h)
+    rho, D = local_density(P, E, mu, kT, dphi)
+    F = A @ phi - np.where(gate, gate_phi, coef * rho)
+    return F, mu, D
+
+
+def nonlinear_jacobian_solve(A, gate, coef, D, h, F):
+    """delta with J delta = -F, J the derivative of F including the response
+    of mu:  J = A + coef diag(D) - coef h^3 D D^T / (h^3 sum D) on the free
+    points (identity rows at gates), by Sherman-Morrison over a sparse LU
+    of the first two terms."""
+    free = ~gate
+    Dm = h ** 3 * D.sum()
+    Df = np.where(free, D, 0.0)
+    M = (A + sp.diags(np.where(free, coef * D, 0.0))).tocsc()
+    lu = spla.splu(M)
+    y1 = lu.solve(-F)
+    if Dm <= 0.0:
+        return y1
+    u = coef * Df
+    v = h ** 3 * Df / Dm
+    y2 = lu.solve(u)
+    return y1 + y2 * (v @ y1) / (1.0 - v @ y2)
+
+
+def nonlinear_poisson(nx, ny, nz, h, gate_mask, gate_phi, P, E, n_holes, kT, phi_k, eps_r=EPS_SI,
+                      tol=1e-12, max_newton=60):
+    """phi solving the predictor's nonlinear Poisson problem from phi = phi_k:
+    Newton steps with backtracking (the step is halved until |F| falls).
+    Returns (phi, mu, Newton steps)."""
+    A, gate = assemble(nx, ny, nz, h, gate_mask)
+    coef = e_over_eps(eps_r)
+    gphi = np.asarray(gate_phi, dtype=np.float64).reshape(-1)
+    phi = np.where(gate, gphi, np.asarray(phi_k, dtype=np.float64).reshape(-1))
+    phi_k = np.asarray(phi_k, dtype=np.float64).reshape(-1)
+    F, mu, D = nonlinear_residual(A, gate, gphi, coef, phi, P, E, n_holes, kT, phi_k, h)
+    for it in range(max_newton):
+        delta = nonlinear_jacobian_solve(A, gate, coef, D, h, F)
+        if np.abs(delta).max() <= tol:
+            return phi + delta, mu, it + 1
+        step, nF = 1.0, np.linalg.norm(F)
+        for _ in range(30):
+            trial = phi + step * delta
+            F2, mu2, D2 = nonlinear_residual(A, gate, gphi, coef, trial, P, E, n_holes, kT, phi_k, h)
+            if np.linalg.norm(F2) < nF:
+                break
+            step *= 0.5
+        phi, F, mu, D = trial, F2, mu2, D2
+    return phi, mu, max_newton
+
+
+def sp_loop_pc(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, iters, bands=6, eps_r=EPS_SI,
+               newton_tol=1e-12):
+    """Predictor-corrector Schroedinger-Poisson iterations from V = V_ext
+    (phi_0 = 0 at free points, the gate values at gates; dense eigensolver,
+    sparse direct solves).  Returns (V, E, mu, history of max |dV|)."""
+    nx, ny, nz, h = prob.nx, prob.ny, prob.nz, prob.h
+    kT = KB_EV * T
+    V_ext = np.asarray(V_ext, dtype=np.float64).reshape(-1)
+    gate = np.asarray(gate_mask, dtype=bool).reshape(-1)
+    phi = np.where(gate, np.asarray(gate_phi, dtype=np.float64).reshape(-1), 0.0)
+    V = V_ext + phi
+    hist = []
+    for _ in range(iters):
+        q = prob.with_(V=V.reshape(nz, ny, nx))
+        H = kp.assemble(q) if bands == 6 else kp.assemble_h0(q)
+        E, psi = eig.lowest_dense(H, n_states, mask=prob.mask)
+        P = state_densities(psi, h, bands)
+        phi, mu, _ = nonlinear_poisson(nx, ny, nz, h, gate_mask, gate_phi, P, E, n_holes, kT, phi, eps_r,
+                                       tol=newton_tol)
+        Vn = V_ext + phi
+        hist.append(float(np.abs(Vn - V).max()))
+        V = Vn
+    return V, E, mu, hist

@@ -26,7 +26,7 @@ EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_po
             "khp_eigensolve_batched",
             "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",
             "khp_last_error", "khp_version", "khp_sp_anderson", "khp_sp_anderson_reset",
-            "khp_fermi_level"]
+            "khp_fermi_level", "khp_filter_step"]
 
 
 class Material(ctypes.Structure):
@@ -54,10 +54,15 @@ class Stats(ctypes.Structure):
                 ("flops_per_pv", ctypes.c_double), ("bytes_per_pv_fp64", ctypes.c_double),
                 ("bytes_per_pv_fp32", ctypes.c_double), ("block_m", ctypes.c_int),
                 ("batch_rounds", ctypes.c_int), ("batch_graphs", ctypes.c_int),
-                ("autotune_ms", ctypes.c_double)]
+                ("autotune_ms", ctypes.c_double),
+                ("ms_gram", ctypes.c_double), ("ms_small", ctypes.c_double), ("ms_rotate", ctypes.c_double),
+                ("ms_between", ctypes.c_double), ("bytes_rr", ctypes.c_double), ("n_history", ctypes.c_int),
+                ("res_history", ctypes.c_double * 64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "res_history"}
+        d["res_history"] = [self.res_history[i] for i in range(min(self.n_history, 64))]
+        return d
 
 
 class KHPError(RuntimeError):
@@ -92,6 +97,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.khp_rotate.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
     lib.khp_set_potential_strain_field.argtypes = [vp, vp, vp, vp, dp, i, dp, i]
     lib.khp_apply.argtypes = [vp, vp, vp, i, i]
+    lib.khp_filter_step.argtypes = [vp, vp, vp, vp, dp, vp, i, i, i, d, d, d, i]
     lib.khp_eigensolve.argtypes = [vp, ctypes.POINTER(SolverOpts), dp, vp, dp, ctypes.POINTER(Stats)]
     lib.khp_eigensolve_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(SolverOpts), dp,
                                            ctypes.POINTER(vp), dp, ctypes.POINTER(Stats), i]

@@ -279,6 +279,7 @@ khp_status apply_op(khp_grid* g, const cx_t<R>* x, const cx_t<R>* prev, cx_t<R>*
     a.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
     a.src = nullptr;
     a.nb = g->nb;
+    a.err = g->dflag;
     fill_coeffs<R>(g, a.c, alpha);
     CK(launch_stencil<R>(a, g->stream));
     g->launches += 1;
@@ -466,10 +467,13 @@ static khp_status create_grid(khp_handle* out, int nx, int ny, int nz, double h_
         (e = cudaMallocHost(&g->host_pinned, sizeof(double) * 8 * KHP_MAX_M)) != cudaSuccess)
         return bail(fail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
                          std::string("allocation: ") + cudaGetErrorString(e)));
-    if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess || (e = cudaEventCreate(&g->ev1)) != cudaSuccess)
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&g->evp[k]);
+    if (e != cudaSuccess || (e = cudaEventCreate(&g->ev0)) != cudaSuccess || (e = cudaEventCreate(&g->ev1)) != cudaSuccess)
         return bail(fail(KHP_ERR_CUDA, std::string("event: ") + cudaGetErrorString(e)));
     if ((e = prepare_oz()) != cudaSuccess)
         return bail(fail(KHP_ERR_CUDA, std::string("projection set-up: ") + cudaGetErrorString(e)));
+    if ((e = prepare_plane()) != cudaSuccess)
+        return bail(fail(KHP_ERR_CUDA, std::string("stencil set-up: ") + cudaGetErrorString(e)));
     if (mask_dev) {
         if ((e = cudaMalloc(&g->mask, np)) != cudaSuccess ||
             (e = cudaMemcpyAsync(g->mask, mask_dev, np, cudaMemcpyDeviceToDevice, g->stream)) != cudaSuccess)
@@ -507,6 +511,8 @@ khp_status khp_destroy(khp_handle g) {
     if (g->host_pinned) cudaFreeHost(g->host_pinned);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
+    for (int k = 0; k < 5; ++k)
+        if (g->evp[k]) cudaEventDestroy(g->evp[k]);
     delete g;
     return KHP_OK;
 }
@@ -581,6 +587,53 @@ khp_status khp_apply(khp_handle g, const void* X_dev, void* Y_dev, int m, int pr
     return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
 }
 
+khp_status khp_filter_step(khp_handle g, const void* x_dev, const void* prev_dev, const void* src_dev,
+                           const double* src_coef_host, void* y_dev, int ld, int col0, int ncol, double alpha,
+                           double beta, double gamma, int precision) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!g->fields_set) return fail(KHP_ERR_STATE, "fields not set");
+    if (!x_dev || !y_dev) return fail(KHP_ERR_INVALID_ARG, "x or y is NULL");
+    if (x_dev == y_dev || (prev_dev && prev_dev == y_dev) || (src_dev && src_dev == y_dev))
+        return fail(KHP_ERR_INVALID_ARG, "y must not alias x, prev or src");
+    if (ld < 1 || ld > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "ld out of range 1..64");
+    if (col0 < 0 || ncol < 1 || col0 + ncol > ld) return fail(KHP_ERR_INVALID_ARG, "columns outside the row");
+    if (precision != 0 && precision != 1) return fail(KHP_ERR_INVALID_ARG, "precision must be 0 or 1");
+    if (src_dev && (precision != 1 || !src_coef_host))
+        return fail(KHP_ERR_INVALID_ARG, "src needs precision 1 and src_coef");
+    const double sc[3] = {alpha, beta, gamma};
+    if (!finite_all(sc, 3) || (src_dev && !finite_all(src_coef_host, ld)))
+        return fail(KHP_ERR_INVALID_ARG, "non-finite coefficient");
+    if (precision == 0) {
+        StencilArgs<double> a;
+        a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+        a.ld = ld; a.col0 = col0; a.ncol = ncol;
+        a.alpha = alpha; a.beta = beta; a.gamma = gamma;
+        a.x = (const double2*)x_dev; a.prev = (const double2*)prev_dev; a.y = (double2*)y_dev;
+        a.onsite = g->onsite64;
+        a.phase = g->has_phase ? g->phase64 : nullptr;
+        a.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
+        a.mask = g->mask; a.src = nullptr; a.nb = g->nb; a.err = g->dflag;
+        fill_coeffs<double>(g, a.c, alpha);
+        CK(launch_stencil<double>(a, g->stream));
+    } else {
+        StencilArgs<float> a;
+        a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+        a.ld = ld; a.col0 = col0; a.ncol = ncol;
+        a.alpha = (float)alpha; a.beta = (float)beta; a.gamma = (float)gamma;
+        a.x = (const float2*)x_dev; a.prev = (const float2*)prev_dev; a.y = (float2*)y_dev;
+        a.onsite = g->onsite32;
+        a.phase = (const float2*)(g->has_phase ? g->phase32 : nullptr);
+        a.phase_mode = g->has_phase ? g->phase_mode : PH_NONE;
+        a.mask = g->mask; a.src = (const float2*)src_dev; a.nb = g->nb; a.err = g->dflag;
+        for (int c = 0; c < 64; ++c) a.src_coef[c] = (src_dev && c < ld) ? (float)src_coef_host[c] : 0.f;
+        fill_coeffs<float>(g, a.c, alpha);
+        CK(launch_stencil<float>(a, g->stream));
+    }
+    g->launches += 1;
+    return KHP_OK;
+}
+
 khp_status khp_project_rows(khp_handle g, const void* Y_dev, const void* W_dev, long long rows, int m, int method,
                             double* G_host, double* S_host) {
     g_err.clear();
@@ -648,14 +701,21 @@ struct Solver {
     double* theta;   // [m]
     double* res;     // [m]
 
+    bool timing = false;   // record the phase events (not under stream capture)
+    bool rr_timed = false;
     khp_status rr(double2* Y, double2* W) {
+        if (timing) CK(cudaEventRecord(g->evp[0], g->stream));
         if (tc) CK(launch_gram_oz(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
         else CK(launch_gram(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        if (timing) CK(cudaEventRecord(g->evp[1], g->stream));
         CK(launch_small(G, G + m * m, m, 1, Q, theta, g->dflag, g->stream));
+        if (timing) CK(cudaEventRecord(g->evp[2], g->stream));
         if (tc)
             CK(launch_rotate_oz(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
         else
             CK(launch_rotate(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
+        if (timing) CK(cudaEventRecord(g->evp[3], g->stream));
+        rr_timed = timing;
         g->launches += 5;
         return KHP_OK;
     }
@@ -806,6 +866,7 @@ struct Solve {
                                  sizeof(double2) * o.warm_cols, g->n, cudaMemcpyDeviceToDevice, g->stream));
         CKS(S.orth(B[ib[0]]));
         CKS(apply_op<double>(g, B[ib[0]], nullptr, B[ib[3]], m, 0, m, 1.0, 0.0, 0.0));
+        S.timing = timing;
         CKS(S.rr(B[ib[0]], B[ib[3]]));
         CKS(S.copy_out());
         return KHP_OK;
@@ -820,9 +881,31 @@ struct Solve {
             if (timed32) st.ms_filter_fp32 += ms;
             else st.ms_filter_fp64 += ms;
         }
+        if (S.rr_timed) {
+            float t01 = 0.f, t12 = 0.f, t23 = 0.f, tf = 0.f;
+            CK(cudaEventElapsedTime(&t01, g->evp[0], g->evp[1]));
+            CK(cudaEventElapsedTime(&t12, g->evp[1], g->evp[2]));
+            CK(cudaEventElapsedTime(&t23, g->evp[2], g->evp[3]));
+            st.ms_gram += t01;
+            st.ms_small += t12;
+            st.ms_rotate += t23;
+            // Gram: Y and W read; rotation: Y and W read, X and HX written
+            st.bytes_rr += 6.0 * (double)g->n * m * sizeof(double2);
+            if (timed32 || timed64) {
+                CK(cudaEventElapsedTime(&tf, g->ev1, g->evp[0]));
+                st.ms_between += tf;
+            }
+            S.rr_timed = false;
+        }
         if (timed32) st.pv_fp32 += (double)g->np * na * (phase == P_DC ? deg - 1 : deg);
         if (timed64) st.pv_fp64 += (double)g->np * na * deg;
         timed32 = timed64 = false;
+        {
+            double rm = 0;
+            for (int i = 0; i < n; ++i) rm = std::max(rm, rs[i]);
+            if (st.n_history < KHP_STATS_HISTORY) st.res_history[st.n_history] = rm;
+            st.n_history++;
+        }
         if (trace && it > 0) {
             double rm = 0;
             for (int i = 0; i < n; ++i) rm = std::max(rm, rs[i]);
@@ -836,6 +919,7 @@ struct Solve {
     // host decisions; sets finished when the solve is over
     khp_status decide() {
         recover = false;
+        if (flags & 8) return fail(KHP_ERR_CUDA, "stencil copy pipeline wait ran out");
         if (flags & 4) return fail(KHP_ERR_BREAKDOWN, "non-finite Ritz values");
         double rmax = 0;
         for (int i = 0; i < n; ++i) rmax = std::max(rmax, std::isnan(rs[i]) ? HUGE_VAL : rs[i]);
@@ -954,6 +1038,7 @@ struct Solve {
             if (phase == P_CLEAN) clean_done++;
         }
         st.filter_applies += (long long)(deg + 1) * na / m;
+        S.timing = timing;
         CKS(S.rr(Y, B[ib[3]]));
         CKS(S.copy_out());
         if (!timing) timed32 = timed64 = false;
@@ -995,6 +1080,7 @@ struct Solve {
             sa.mask = g->mask;
             sa.src = R32;
             sa.nb = g->nb;
+            sa.err = g->dflag;
             for (int c = 0; c < 64; ++c) sa.src_coef[c] = (c >= nlock && c < m) ? (float)(al * Dcur[c]) : 0.f;
             fill_coeffs<float>(g, sa.c, al);
             CK(launch_stencil<float>(sa, g->stream));

@@ -104,6 +104,7 @@ struct StencilArgs {
     R src_coef[64];
     Coeffs<R> c;
     int nb;                 // bands per point: 6, or 3 for the spin-independent H0
+    int* err;               // device status word (bit 8: a pipeline wait ran out), or null
 };
 
 }  // namespace khp
@@ -160,4 +161,5 @@ struct khp_grid {
 
     long long launches;    // kernel launches issued (per call accounting)
     cudaEvent_t ev0, ev1;  // filter timing
+    cudaEvent_t evp[5];    // phase timing: Gram | small problem | rotation, and the H Y apply
 };

@@ -17,6 +17,12 @@ namespace khp {
 // stencil.cu
 template <typename R>
 cudaError_t launch_stencil(const StencilArgs<R>& a, cudaStream_t st);
+// plane-marching FP32 stencil (TMA-staged planes); cudaErrorNotSupported
+// when the step is outside what it covers (the caller then uses the
+// per-point kernel).  prepare_plane() opts its kernels into their shared
+// memory (per device, outside stream capture).
+cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStream_t st);
+cudaError_t prepare_plane();
 cudaError_t launch_field_setup(khp_grid* g, const double* V, const double* strain,
                                const double* levers, const double* alpha, int ng, int* bad);
 cudaError_t launch_onsite_rowmax(khp_grid* g, double* partial, int nblocks, double* out);

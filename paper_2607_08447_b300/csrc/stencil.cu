@@ -9,6 +9,13 @@
 // 6 x VG values, the 18 neighbours' values (pairs +delta/-delta share one
 // real symmetric 3x3 orbital matrix, so the two neighbour values are summed
 // first), and writes y = alpha*(H x) + beta*x + gamma*prev.
+#include <cuda.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <type_traits>
+
 #include "khp_common.cuh"
 #include "khp_internal.h"
 
@@ -482,12 +489,509 @@ static cudaError_t launch_vg(const StencilArgs<R>& a, cudaStream_t st) {
 
 template <typename R>
 cudaError_t launch_stencil(const StencilArgs<R>& a, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        const cudaError_t e = launch_stencil_plane(a, a.err, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     if ((a.ncol % 2) == 0 && (a.col0 % 2) == 0 && (a.ld % 2) == 0) return launch_vg<R, 2>(a, st);
     return launch_vg<R, 1>(a, st);
 }
 
 template cudaError_t launch_stencil<double>(const StencilArgs<double>&, cudaStream_t);
 template cudaError_t launch_stencil<float>(const StencilArgs<float>&, cudaStream_t);
+
+// ------------------------------------------- plane-marching FP32 stencil
+// The same fused step y = alpha (H x) + beta x + gamma prev + c_col src for
+// FP32 blocks, organised for data reuse: a CTA owns an x-y tile of TX x TY
+// points and V = 4 vector columns (one per thread) and marches through a
+// range of z-planes.  The planes of x, each with a one-point halo in x and
+// y, arrive in a four-deep shared-memory ring by TMA (cp.async.bulk.tensor,
+// one box per band, so a band of a plane is a dense [y][x][col] array read
+// without bank conflicts); the box reads zeros outside the grid, which is
+// the Dirichlet wall.  prev and the defect source arrive by TMA as well, one
+// plane per step.  All 19 neighbour values then come from shared memory and
+// every byte of x, prev and src crosses HBM once (the halo is re-read from
+// L2).  Each copy completes on an mbarrier; every wait is bounded (about a
+// second), and a wait that runs out sets bit 8 of the error flag, drains
+// the copies in flight and leaves the kernel.
+namespace plane {
+
+constexpr int TX = 16;
+constexpr int V = 4;
+constexpr int NSLOT = 4;
+constexpr int HX = TX + 2;
+
+// NSX: depth of the ring of x planes (4: plane z + 3 is loaded while plane z
+// is computed; 3: plane z + 2 is loaded into the slot of plane z - 1 as soon
+// as the pairs that reach across planes are summed).  NPS: buffers of the
+// prev/src planes (2: the plane after next is loaded while a plane is
+// computed).
+template <int NB, int TY, int NSX, int NPS>
+struct Geo {
+    static constexpr int HY = TY + 2;
+    static constexpr int THREADS = TX * TY * V;
+    static constexpr int XBAND = HY * HX * V;           // float2 per band of a halo plane
+    static constexpr int XSLOT = NB * XBAND;
+    static constexpr int PBAND = TY * TX * V;           // float2 per band of a prev/src plane
+    static constexpr int PPLANE = NB * PBAND;
+    static constexpr int NBAR = NSX + NPS;
+    static constexpr int SMEM = (NSX * XSLOT + 2 * NPS * PPLANE) * 8 + 8 * NBAR;
+};
+
+struct Work {
+    int ntx, nty, ngroups, zch, nzc;
+    int cbase;                 // first column of group 0 (even)
+    int* err;                  // bit 8 set when a pipeline wait runs out
+};
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the phase with the given parity: false after ~2^31 cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+template <int NB, int PH, bool SRC, int TY, int NSX, int NPS>
+__global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, TY, NSX, NPS>::THREADS)
+    stencil_plane_kernel(const StencilArgs<float> a, const Work w, const __grid_constant__ CUtensorMap mx,
+                         const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap ms) {
+    using G = Geo<NB, TY, NSX, NPS>;
+    using C = float2;
+    constexpr int NS = NB / 3;
+    static_assert(G::THREADS >= 96, "three issuing warps");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    C* xring = reinterpret_cast<C*>(smem);
+    C* pbuf = xring + NSX * G::XSLOT;             // [NPS][PPLANE]
+    C* sbuf = pbuf + NPS * G::PPLANE;             // [NPS][PPLANE]
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbuf + NPS * G::PPLANE);
+
+    // work item: column group fastest, so the groups of one tile run together
+    int item = blockIdx.x;
+    const int g = item % w.ngroups;
+    item /= w.ngroups;
+    const int txi = item % w.ntx;
+    item /= w.ntx;
+    const int tyi = item % w.nty;
+    const int zc = item / w.nty;
+    const int tx0 = txi * TX, ty0 = tyi * TY;
+    const int z0 = zc * w.zch;
+    const int zlast = min(z0 + w.zch, a.nz) - 1;
+    const int zs = z0 - 1;                      // first plane of the ring
+    const int cg = w.cbase + g * V;             // first column of this group
+
+    const int tid = threadIdx.x;
+    const int col = tid % V;
+    const int lx = (tid / V) % TX;
+    const int ly = tid / (V * TX);
+    const int gx = tx0 + lx, gy = ty0 + ly;
+    const int c = cg + col;
+    const bool live = gx < a.nx && gy < a.ny;
+    const bool store = live && c >= a.col0 && c < a.col0 + a.ncol;
+    const bool has_prev = a.prev != nullptr;
+    const bool has_ps = has_prev || SRC;
+    const long long plane_pts = (long long)a.nx * a.ny;
+    const long long ps = (long long)NB * a.ld;  // complex per point
+    // copies are issued by lane 0 of warp 0 (x), warp 1 (prev) and warp 2 (src)
+    const bool ix_thread = tid == 0;
+    const bool ip_thread = tid == 32 && has_prev;
+    const bool is_thread = tid == 64 && SRC;
+
+    auto xslot = [&](int q) { return (q - zs) % NSX; };
+    auto xpar = [&](int q) { return (uint32_t)(((q - zs) / NSX) & 1); };
+    auto pslot = [&](int q) { return (q - z0) % NPS; };
+    auto ppar = [&](int q) { return (uint32_t)(((q - z0) / NPS) & 1); };
+    auto xbar = [&](int q) { return sa(bars + xslot(q)); };
+    auto pbar = [&](int q) { return sa(bars + NSX + pslot(q)); };
+
+    auto issue_x = [&](int q) {          // plane q into its ring slot
+        const uint32_t bar = xbar(q);
+        mbar_expect(bar, G::XSLOT * 8);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            tma_load5(sa(xring + xslot(q) * G::XSLOT + b * G::XBAND), &mx, 2 * cg, b, tx0 - 1, ty0 - 1, q, bar);
+    };
+    auto issue_p = [&](int q, const CUtensorMap* map, C* buf) {   // one prev/src plane
+        const uint32_t bar = pbar(q);
+        mbar_expect(bar, G::PPLANE * 8);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            tma_load5(sa(buf + pslot(q) * G::PPLANE + b * G::PBAND), map, 2 * cg, b, tx0, ty0, q, bar);
+    };
+
+    if (tid == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&mx)) : "memory");
+        for (int s = 0; s < NSX; ++s) mbar_init(sa(bars + s), 1);
+        for (int s = 0; s < NPS; ++s) mbar_init(sa(bars + NSX + s), (has_prev ? 1 : 0) + (SRC ? 1 : 0));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // prologue: the first NSX planes of x and NPS planes of prev/src
+    const int x_first_last = min(zs + NSX - 1, zlast + 1);
+    const int p_first_last = min(z0 + NPS - 1, zlast);
+    if (ix_thread)
+        for (int q = zs; q <= x_first_last; ++q) issue_x(q);
+    if (ip_thread)
+        for (int q = z0; q <= p_first_last; ++q) issue_p(q, &mp, pbuf);
+    if (is_thread)
+        for (int q = z0; q <= p_first_last; ++q) issue_p(q, &ms, sbuf);
+    int issued_x = x_first_last, issued_p = has_ps ? p_first_last : z0 - 1;
+    int waited_x = zs - 1, waited_p = z0 - 1;
+
+    // per-point fields of the current plane (prefetched one plane ahead)
+    auto load_fields = [&](int z, float (&o)[6], float2 (&cs)[9]) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 9; ++d) cs[d] = make_float2(1.f, 0.f);
+        if (!live || z > zlast) return;
+        const long long p = gx + (long long)a.nx * gy + plane_pts * z;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k] = __ldg(a.onsite + p * 6 + k);
+        if (PH == PH_SYM) {
+#pragma unroll
+            for (int d = 0; d < 9; ++d)
+                if (a.c.pair_phase & (1u << d)) cs[d] = __ldg(a.phase + p * 9 + d);
+        }
+    };
+    float o_cur[6], o_nxt[6];
+    float2 cs_cur[9], cs_nxt[9];
+    load_fields(z0, o_cur, cs_cur);
+
+    // shared-memory address of band b at offset (dx, dy) in the slot of plane q
+    auto xat = [&](int q, int b, int dx, int dy) -> const C* {
+        return xring + xslot(q) * G::XSLOT + b * G::XBAND + ((ly + 1 + dy) * HX + (lx + 1 + dx)) * V + col;
+    };
+    // pair d: (x+ + x-) and (x+ - x-) of the needed bands, then the pair's
+    // alpha-scaled orbital matrix (times the Peierls phase) into acc
+    auto pair = [&](C (&acc)[6][1], int z, auto dc) {
+        constexpr int d = decltype(dc)::value;
+        constexpr unsigned nzd = cubic_nz(d);
+        constexpr unsigned need = need_of(nzd);
+        constexpr int dx = pair_dx(d), dy = pair_dy(d), dz = pair_dz(d);
+        const bool ph = PH == PH_SYM && (a.c.pair_phase & (1u << d));
+        C u[6][1], v[6][1];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            if (!(need & (1u << o))) continue;
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) {
+                const int b = 3 * sp + o;
+                const C xp = *xat(z + dz, b, dx, dy);
+                const C xm = *xat(z - dz, b, -dx, -dy);
+                u[b][0] = cadd<float>(xp, xm);
+                if (PH == PH_SYM) v[b][0] = csub<float>(xp, xm);
+            }
+        }
+        float cth = 1.f, sth = 0.f;
+        if (PH == PH_SYM && ph) {
+            cth = cs_cur[d].x;
+            sth = cs_cur[d].y;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (!(nzd & (1u << k))) continue;
+            const float m = a.c.hop[d][k];
+            const int i = k < 3 ? k : (k == 3 ? 1 : 0);
+            const int j = k < 3 ? k : (k == 5 ? 1 : 2);
+            if (PH == PH_SYM && ph) {
+                const float mc = m * cth, msn = m * sth;
+                pair_entry<float, 1, true, NS>(acc, i, j, mc, msn, u, v);
+                if (k >= 3) pair_entry<float, 1, true, NS>(acc, j, i, mc, msn, u, v);
+            } else {
+                pair_entry<float, 1, false, NS>(acc, i, j, m, 0.f, u, v);
+                if (k >= 3) pair_entry<float, 1, false, NS>(acc, j, i, m, 0.f, u, v);
+            }
+        }
+    };
+
+    bool failed = false;
+    for (int z = z0; z <= zlast; ++z) {
+        // planes z - 1 .. z + 1 of x (one new plane per step after the first)
+        for (int q = waited_x + 1; q <= z + 1; ++q) failed |= !mbar_wait(xbar(q), xpar(q));
+        waited_x = z + 1;
+        load_fields(z + 1, o_nxt, cs_nxt);
+
+        C acc[6][1];
+#pragma unroll
+        for (int b = 0; b < 6; ++b) acc[b][0] = make_float2(0.f, 0.f);
+        // the pairs that reach planes z - 1 and z + 1 first
+        pair(acc, z, std::integral_constant<int, 2>{});
+        pair(acc, z, std::integral_constant<int, 5>{});
+        pair(acc, z, std::integral_constant<int, 6>{});
+        pair(acc, z, std::integral_constant<int, 7>{});
+        pair(acc, z, std::integral_constant<int, 8>{});
+        if (NSX == 3) {
+            // plane z - 1 is done with: plane z + 2 goes into its slot
+            __syncthreads();
+            if (ix_thread && z + 2 <= zlast + 1) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_x(z + 2);
+            }
+            if (z + 2 <= zlast + 1) issued_x = z + 2;
+        }
+        // centre: on-site orbital matrix (+ beta), spin-orbit and Zeeman
+        {
+            C xs[6][1];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) xs[b][0] = *xat(z, b, 0, 0);
+            float oo[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) oo[k] = a.alpha * o_cur[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) oo[k] += a.beta;
+            sym3<float, 1, false, NS>(acc, oo, a.c.onsite_nz | 7u, xs);
+#pragma unroll
+            for (int b = 0; b < (NB == 6 ? 6 : 0); ++b) {
+                const unsigned rowm = a.c.soz_nz[b];
+#pragma unroll
+                for (int b2 = 0; b2 < 6; ++b2) {
+                    if (rowm & (1u << (2 * b2))) axpy_c<float>(acc[b][0], a.c.soz_re[b][b2], xs[b2][0]);
+                    if (rowm & (2u << (2 * b2))) axpy_mi<float>(acc[b][0], -a.c.soz_im[b][b2], xs[b2][0]);
+                }
+            }
+        }
+        // the pairs inside plane z
+        pair(acc, z, std::integral_constant<int, 0>{});
+        pair(acc, z, std::integral_constant<int, 1>{});
+        pair(acc, z, std::integral_constant<int, 3>{});
+        pair(acc, z, std::integral_constant<int, 4>{});
+
+        // gamma prev + c_col src
+        if (has_ps) {
+            failed |= !mbar_wait(pbar(z), ppar(z));
+            waited_p = z;
+            const int pi = pslot(z) * G::PPLANE + (ly * TX + lx) * V + col;
+            const float sc = SRC ? a.src_coef[min(max(c, 0), 63)] : 0.f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (has_prev) axpy_c<float>(acc[b][0], a.gamma, pbuf[pi + b * G::PBAND]);
+                if (SRC) axpy_c<float>(acc[b][0], sc, sbuf[pi + b * G::PBAND]);
+            }
+        }
+        if (store) {
+            C* yp = a.y + (gx + (long long)a.nx * gy + plane_pts * z) * ps + c;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) __stcs(yp + b * a.ld, acc[b][0]);
+        }
+        // every thread is done with this step's buffers; a wait that ran out
+        // anywhere ends the CTA (after its copies in flight have landed)
+        if (__syncthreads_or(failed)) {
+            if (tid == 0) {
+                atomicOr(w.err, 8);
+                for (int q = waited_x + 1; q <= issued_x; ++q) mbar_wait(xbar(q), xpar(q));
+                for (int q = waited_p + 1; q <= issued_p; ++q) mbar_wait(pbar(q), ppar(q));
+            }
+            return;
+        }
+        const bool more_p = has_ps && z + NPS <= zlast;
+        if (NSX == 4 && ix_thread && z + 3 <= zlast + 1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_x(z + 3);
+        }
+        if (more_p && (ip_thread || is_thread)) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (ip_thread) issue_p(z + NPS, &mp, pbuf);
+            if (is_thread) issue_p(z + NPS, &ms, sbuf);
+        }
+        if (NSX == 4 && z + 3 <= zlast + 1) issued_x = z + 3;
+        if (more_p) issued_p = z + NPS;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o_cur[k] = o_nxt[k];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) cs_cur[d] = cs_nxt[d];
+    }
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 5-d map of a [nz][ny][nx][nb][ld] complex64 block as floats: dims
+// (2 ld, nb, nx, ny, nz), box (2 V, 1, bx, by, 1)
+bool make_map(CUtensorMap* m, const void* base, int ld, int nb, int nx, int ny, int nz, int bx, int by) {
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[5] = {(cuuint64_t)2 * ld, (cuuint64_t)nb, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t row = (cuuint64_t)ld * 8;
+    const cuuint64_t strides[4] = {row, row * nb, row * nb * nx, row * nb * nx * ny};
+    const cuuint32_t box[5] = {2 * V, 1, (cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// KHP_STENCIL_PLANE=0 in the environment selects the per-point kernel for
+// every FP32 step (for comparisons); read once.
+bool enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = std::getenv("KHP_STENCIL_PLANE");
+        on = (e && e[0] == '0') ? 0 : 1;
+    }
+    return on == 1;
+}
+
+template <int NB, int PH, bool SRC, int TY, int NSX, int NPS>
+cudaError_t launch_t(const StencilArgs<float>& a, const Work& w, unsigned items, const CUtensorMap& mx,
+                     const CUtensorMap& mp, const CUtensorMap& ms, cudaStream_t st) {
+    using G = Geo<NB, TY, NSX, NPS>;
+    stencil_plane_kernel<NB, PH, SRC, TY, NSX, NPS><<<items, G::THREADS, G::SMEM, st>>>(a, w, mx, mp, ms);
+    return cudaGetLastError();
+}
+
+template <int TY, int NSX, int NPS>
+cudaError_t dispatch(const StencilArgs<float>& a, const Work& w, unsigned n, int mode, const CUtensorMap& mx,
+                     const CUtensorMap& mp, const CUtensorMap& ms, cudaStream_t st) {
+    if (a.nb == 6) {
+        if (mode == PH_SYM)
+            return a.src ? launch_t<6, PH_SYM, true, TY, NSX, NPS>(a, w, n, mx, mp, ms, st)
+                         : launch_t<6, PH_SYM, false, TY, NSX, NPS>(a, w, n, mx, mp, ms, st);
+        return a.src ? launch_t<6, PH_NONE, true, TY, NSX, NPS>(a, w, n, mx, mp, ms, st)
+                     : launch_t<6, PH_NONE, false, TY, NSX, NPS>(a, w, n, mx, mp, ms, st);
+    }
+    return a.src ? launch_t<3, PH_NONE, true, TY, NSX, NPS>(a, w, n, mx, mp, ms, st)
+                 : launch_t<3, PH_NONE, false, TY, NSX, NPS>(a, w, n, mx, mp, ms, st);
+}
+
+template <int NB, int PH, bool SRC, int TY, int NSX, int NPS>
+cudaError_t prep_t() {
+    return cudaFuncSetAttribute(stencil_plane_kernel<NB, PH, SRC, TY, NSX, NPS>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<NB, TY, NSX, NPS>::SMEM);
+}
+
+template <int TY, int NSX, int NPS>
+cudaError_t prep_cfg() {
+    cudaError_t e = prep_t<6, PH_NONE, false, TY, NSX, NPS>();
+    if (e == cudaSuccess) e = prep_t<6, PH_NONE, true, TY, NSX, NPS>();
+    if (e == cudaSuccess) e = prep_t<6, PH_SYM, false, TY, NSX, NPS>();
+    if (e == cudaSuccess) e = prep_t<6, PH_SYM, true, TY, NSX, NPS>();
+    if (e == cudaSuccess) e = prep_t<3, PH_NONE, false, TY, NSX, NPS>();
+    if (e == cudaSuccess) e = prep_t<3, PH_NONE, true, TY, NSX, NPS>();
+    return e;
+}
+
+// Pipeline shape: 0 = tile 16 x 4, x ring of 4 planes, one prev/src plane
+// (two 256-thread CTAs per SM); 1 = tile 16 x 4, x ring of 3 planes, two
+// prev/src planes (two CTAs per SM); 2 = tile 16 x 8, ring of 4, one
+// prev/src plane (one 512-thread CTA per SM).  KHP_PLANE_CFG=0/1/2 in the
+// environment overrides the default (read once).
+int config() {
+    static int cfg = -1;
+    if (cfg < 0) {
+        const char* e = std::getenv("KHP_PLANE_CFG");
+        cfg = (e && e[0] >= '0' && e[0] <= '2') ? e[0] - '0' : 0;
+    }
+    return cfg;
+}
+
+}  // namespace plane
+
+cudaError_t prepare_plane() {
+    using namespace plane;
+    cudaError_t e = prep_cfg<4, 4, 1>();
+    if (e == cudaSuccess) e = prep_cfg<4, 3, 2>();
+    if (e == cudaSuccess) e = prep_cfg<8, 4, 1>();
+    return e;
+}
+
+// Takes the step when the plane kernel covers it (FP32, no mask, the
+// crystal or [110] frame, B = 0 or the symmetric gauge, even row length and
+// first column); returns cudaErrorNotSupported otherwise.
+cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStream_t st) {
+    using namespace plane;
+    if (!enabled() || a.mask || (a.ld & 1) || (a.col0 & 1) || a.ncol < 1 || !err) return cudaErrorNotSupported;
+    if (a.nb != 6 && a.nb != 3) return cudaErrorNotSupported;
+    bool cubic = true;
+    for (int d = 0; d < 9; ++d) cubic = cubic && (a.c.hop_nz[d] & ~cubic_nz(d)) == 0;
+    if (!cubic) return cudaErrorNotSupported;
+    const int mode = a.phase ? a.phase_mode : PH_NONE;
+    if (mode == PH_GEN || (a.nb == 3 && mode != PH_NONE)) return cudaErrorNotSupported;
+    const long long np = (long long)a.nx * a.ny * a.nz;
+    if (np == 0) return cudaSuccess;
+    const int cfg = config();
+    const int kTY = cfg == 2 ? 8 : 4;
+    const int per_sm = cfg == 2 ? 1 : 2;
+    Work w;
+    w.ntx = (a.nx + TX - 1) / TX;
+    w.nty = (a.ny + kTY - 1) / kTY;
+    w.cbase = a.col0 & ~1;
+    w.ngroups = (a.col0 + a.ncol - w.cbase + V - 1) / V;
+    w.err = err;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // z-chunk: the fewest passes over the grid in waves of one CTA per SM
+    // (each chunk also reads its two boundary planes of x)
+    const long long tiles = (long long)w.ntx * w.nty * w.ngroups;
+    int best = a.nz;
+    double best_cost = 1e300;
+    for (int zch = 4; zch <= a.nz + 3; ++zch) {
+        const int zc = std::min(zch, a.nz);
+        const long long items = tiles * ((a.nz + zc - 1) / zc);
+        const double waves = std::ceil((double)items / (sms * per_sm));
+        const double cost = waves * (zc + 0.7);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = zc; }
+        if (zch >= a.nz) break;
+    }
+    w.zch = best;
+    w.nzc = (a.nz + w.zch - 1) / w.zch;
+    const long long items = tiles * w.nzc;
+    if (items > 0x7fffffffLL) return cudaErrorNotSupported;
+    CUtensorMap mx, mp, ms;
+    std::memset(&mp, 0, sizeof(mp));
+    std::memset(&ms, 0, sizeof(ms));
+    if (!make_map(&mx, a.x, a.ld, a.nb, a.nx, a.ny, a.nz, HX, kTY + 2)) return cudaErrorNotSupported;
+    if (a.prev && !make_map(&mp, a.prev, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
+    if (a.src && !make_map(&ms, a.src, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
+    const unsigned n = (unsigned)items;
+    if (cfg == 1) return dispatch<4, 3, 2>(a, w, n, mode, mx, mp, ms, st);
+    if (cfg == 2) return dispatch<8, 4, 1>(a, w, n, mode, mx, mp, ms, st);
+    return dispatch<4, 4, 1>(a, w, n, mode, mx, mp, ms, st);
+}
 
 // ------------------------------------------------------------ field set-up
 struct FieldArgs {

@@ -8,6 +8,9 @@ whose backward is the library's Hellmann-Feynman adjoint.
 from __future__ import annotations
 
 import ctypes
+import json
+import os
+import time
 from dataclasses import dataclass
 
 import numpy as np
@@ -28,6 +31,21 @@ def _dev(t, dtype, device):
     if not torch.is_tensor(t):
         t = torch.as_tensor(np.ascontiguousarray(t))
     return t.to(device=device, dtype=dtype).contiguous()
+
+
+def _log_solve(grid, opts, stats, evals, status):
+    """With KHP_LOG_JSONL=<path> in the environment, append one JSON object
+    per eigensolve: grid, options, status, eigenvalues, the per-phase device
+    times and the residual history of the outer iterations."""
+    path = os.environ.get("KHP_LOG_JSONL")
+    if not path:
+        return
+    rec = {"time": time.time(), "grid": [grid.nx, grid.ny, grid.nz], "bands": grid.bands,
+           "n_states": opts.n_states, "block_m": opts.block_m, "degree": opts.degree,
+           "precision": opts.precision, "tol_ev": opts.tol_ev, "status": int(status),
+           "evals": [float(e) for e in evals], "stats": stats}
+    with open(path, "a") as fh:
+        fh.write(json.dumps(rec) + "\n")
 
 
 @dataclass
@@ -119,6 +137,23 @@ class KPGrid:
         _lib.check(self.lib.khp_apply(self.handle, _ptr(X), _ptr(Y), m, int(precision)))
         return Y
 
+    def filter_step(self, x, y, alpha, beta, gamma=0.0, prev=None, src=None, src_coef=None, col0=0, ncol=None,
+                    precision=1):
+        """One fused Chebyshev step into y (khp_filter_step) on the columns
+        [col0, col0 + ncol):  y = alpha H x + beta x + gamma prev + src_coef[col] src.
+        x, prev, src, y: [N, ld] complex64 (precision 1) or complex128 (0)."""
+        dt = torch.complex128 if precision == 0 else torch.complex64
+        x = _dev(x, dt, self.device)
+        prev = _dev(prev, dt, self.device)
+        src = _dev(src, dt, self.device)
+        ld = x.shape[1]
+        ncol = ld - col0 if ncol is None else ncol
+        sc = None if src_coef is None else np.ascontiguousarray(np.asarray(src_coef, dtype=np.float64).reshape(ld))
+        _lib.check(self.lib.khp_filter_step(self.handle, _ptr(x), _ptr(prev), _ptr(src), _lib.dptr(sc), _ptr(y),
+                                            ld, int(col0), int(ncol), float(alpha), float(beta), float(gamma),
+                                            int(precision)))
+        return y
+
     def project_rows(self, Y, W=None, method=0):
         """Y^H Y and Y^H W for any complex128 [rows][m] blocks (see project)."""
         Y = _dev(Y, torch.complex128, self.device)
@@ -176,8 +211,10 @@ class KPGrid:
         st = _lib.Stats()
         status = self.lib.khp_eigensolve(self.handle, ctypes.byref(opts), _lib.dptr(evals), _ptr(evecs),
                                          _lib.dptr(res), ctypes.byref(st))
+        stats = st.as_dict()
+        _log_solve(self, opts, stats, evals, status)
         _lib.check(status, allow=(4,) if allow_not_converged else ())
-        return SolveResult(evals, evecs, res, st.as_dict(), status)
+        return SolveResult(evals, evecs, res, stats, status)
 
     def density(self, evecs, w):
         evecs = _dev(evecs, torch.complex128, self.device)

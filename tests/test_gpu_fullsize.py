@@ -1,8 +1,10 @@
 """Full-size checks on the 160x48x48 workload (2.21M unknowns) in the launch
 configuration bench.py times (16 states, block 24, degree 120, tol 1e-10 eV).
 
-* eigenvalues against the stored FP64 oracle values (block Lanczos, written
-  by tests/golden/make_golden.py, which calls only the oracle);
+* eigenvalues against the stored FP64 oracle values (ARPACK, written by
+  tests/golden/make_golden.py, which calls only the oracle);
+* on the central 64x24x24 cut of the same fields: eigenvalues against the
+  stored oracle values and the subspace angle against oracle eigenvectors;
 * residuals recomputed through the oracle's CSR matrix, orthonormality;
 * the n-state subspace angle bound from the oracle's gap;
 * the mixed-precision solver against the plain one (same tolerance).
@@ -15,16 +17,48 @@ import torch
 
 import inputs
 from oracle import kp
+from tests.metrics import subspace_sin_angle
 
 pytestmark = pytest.mark.gpu
 
 SOLVE = dict(n_states=16, block_m=24, degree=120, tol=1e-10, seed=1)
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c2_evals.txt")
+GOLDEN_MID = os.path.join(os.path.dirname(__file__), "golden", "c2mid_evals.txt")
 
 
-def _golden():
-    rows = [l.split() for l in open(GOLDEN) if not l.startswith("#")]
+def _golden(path=GOLDEN):
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
     return np.array([float(r[1]) for r in rows]), np.array([float(r[2]) for r in rows])
+
+
+@pytest.fixture(scope="module")
+def c2mid(khp):
+    """The 160x48x48 workload's fields cut to the central 64x24x24 points
+    (221184 unknowns), solved in the bench's launch configuration, with the
+    oracle's eigenvectors (ARPACK, a few minutes on the host)."""
+    from oracle import eig
+    p = inputs.crop(inputs.config2(), (64, 24, 24))
+    g = khp.KPGrid.from_problem(p)
+    w, v = eig.lowest_arpack(kp.assemble(p), 17)
+    yield p, g, w, v
+    g.close()
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(degree=200, precision=2)])
+def test_c2mid_eigenpairs_vs_oracle(c2mid, kw):
+    """Eigenvalues against the stored oracle values (|dE| <= 1e-10 eV) and
+    the largest principal angle of the 16-state subspace against the
+    oracle's eigenvectors (<= 1e-7), plain FP64 and defect-corrected FP32
+    filter."""
+    p, g, w, v = c2mid
+    r = g.eigensolve(**dict(SOLVE, **kw))
+    assert r.stats["converged"] == 16
+    ws, _ = _golden(GOLDEN_MID)
+    assert np.abs(ws[:17] - w).max() <= 1e-12          # the stored values are this oracle's
+    assert np.abs(r.evals - ws[:16]).max() <= 1e-10, np.abs(r.evals - ws[:16])
+    assert ws[16] - ws[15] > 1e-6                       # n = 16 cuts no cluster
+    sin = subspace_sin_angle(v[:, :16], r.evecs.cpu().numpy())
+    assert sin <= 1e-7, sin
 
 
 @pytest.fixture(scope="module")

@@ -64,6 +64,65 @@ def test_stencil_fp32_matches_csr(khp, case, m):
     assert np.abs(Y - ref).max() <= 2e-6 * scale * 10
 
 
+STEP_CASES = [
+    # several 16 x 8 tiles with ragged edges in x and y, B along [110]
+    dict(shape=(37, 19, 11), rot="device", B=(0.5, 0.0, 0.0), gauge=0, strain=True, mask=False),
+    # exactly one tile, B = 0
+    dict(shape=(16, 8, 3), rot="identity", B=(0, 0, 0), gauge=0, strain=True, mask=False),
+    # tall in z (several z-chunks per tile), tilted field
+    dict(shape=(5, 3, 30), rot="device", B=(0.2, 0.1, 0.4), gauge=0, strain=True, mask=False),
+    # Landau gauge and a point mask: the per-point kernel
+    dict(shape=(9, 11, 6), rot="device", B=(0.3, -0.8, 1.1), gauge=1, strain=True, mask=False),
+    dict(shape=(10, 5, 7), rot="identity", B=(0.0, 0.7, 0.2), gauge=0, strain=False, mask=True),
+]
+
+
+@pytest.mark.parametrize("case", range(len(STEP_CASES)))
+@pytest.mark.parametrize("ld,col0,ncol", [(24, 0, 24), (24, 6, 18), (20, 2, 13), (8, 0, 8), (6, 1, 4), (2, 0, 2)])
+def test_filter_step_fp32_matches_oracle(khp, case, ld, col0, ncol):
+    """The fused FP32 Chebyshev step of the defect-corrected filter,
+    y = alpha H x + beta x + gamma prev + c_col src on columns
+    [col0, col0 + ncol), against the oracle's CSR product in FP64 on the
+    same (FP32) inputs; the other columns of y stay untouched."""
+    p = _problem(STEP_CASES[case], seed=11)
+    H = kp.assemble(p)
+    N = p.n_unknowns
+    x, prev, src, y0 = (inputs.random_block(N, ld, seed=300 + k).astype(np.complex64) for k in range(4))
+    if p.mask is not None:
+        x[np.repeat(p.mask.reshape(-1) == 0, 6)] = 0.0
+    coef = np.random.default_rng(ld + col0).uniform(-1.0, 1.0, ld)
+    alpha, beta, gamma = 0.37, -0.81, -0.55
+    g = _grid(khp, p)
+    y = torch.from_numpy(y0.copy()).cuda()
+    g.filter_step(x, y, alpha, beta, gamma, prev=prev, src=src, src_coef=coef, col0=col0, ncol=ncol)
+    Y = y.cpu().numpy()
+    xd = x.astype(np.complex128)
+    ref = alpha * (H @ xd) + beta * xd + gamma * prev.astype(np.complex128) + src.astype(np.complex128) * coef
+    if p.mask is not None:
+        ref[np.repeat(p.mask.reshape(-1) == 0, 6)] = 0.0
+    cs = slice(col0, col0 + ncol)
+    scale = np.abs(alpha * (H @ xd)).max() + np.abs(xd).max() + np.abs(prev).max() + np.abs(src).max()
+    assert np.abs(Y[:, cs] - ref[:, cs]).max() <= 2e-6 * scale
+    out = np.ones(ld, dtype=bool)
+    out[cs] = False
+    assert np.array_equal(Y[:, out], y0[:, out])
+
+
+@pytest.mark.parametrize("case", [0, 3])
+def test_filter_step_fp64_matches_oracle(khp, case):
+    p = _problem(STEP_CASES[case], seed=12)
+    H = kp.assemble(p)
+    N, ld = p.n_unknowns, 12
+    x, prev = inputs.random_block(N, ld, seed=401), inputs.random_block(N, ld, seed=402)
+    g = _grid(khp, p)
+    y = torch.zeros((N, ld), dtype=torch.complex128, device="cuda")
+    g.filter_step(x, y, 0.4, 0.3, -0.9, prev=prev, col0=2, ncol=8, precision=0)
+    ref = 0.4 * (H @ x) + 0.3 * x - 0.9 * prev
+    Y = y.cpu().numpy()
+    assert np.abs(Y[:, 2:10] - ref[:, 2:10]).max() <= 1e-13 * np.abs(ref).max()
+    assert np.all(Y[:, :2] == 0) and np.all(Y[:, 10:] == 0)
+
+
 def test_hermitian_matrix_free(khp):
     p = _problem(CASES[2])
     g = _grid(khp, p)

@@ -84,7 +84,15 @@ def test_sp_loop_matches_oracle(khp, bands):
     assert np.abs(np.array(r.history) - np.array(hist_or)).max() <= 1e-9
     assert np.abs(r.V.cpu().numpy() - V_or).max() <= 1e-10
     assert np.abs(r.evals - E_or).max() <= 1e-10
-    assert abs(r.mu - mu_or) <= 1e-9
+    # the Fermi levels come from different methods (the library's Newton
+    # iteration, the oracle's bisection); with a filled Kramers doublet the
+    # hole count is flat to rounding across the gap, so mu itself is fixed
+    # only to that width: compare the occupations it yields
+    kT = po.KB_EV * 1.5
+    f_lib = po.occupations(r.evals, r.mu, kT)
+    f_or = po.occupations(E_or, mu_or, kT)
+    assert np.abs(f_lib - f_or).max() <= 1e-9
+    assert abs(f_lib.sum() - nh) <= 1e-9
     P.close()
     g.close()
 
