@@ -199,11 +199,12 @@ def _arpack_baseline(q, n, full_unknowns):
 
 
 def _oracle_next_rows(p):
-    """The oracle timed beside the NEXT rows, each on a stated crop of the
-    C2 physics (centred), unscaled: the H0 (block Lanczos, 16 states), three
-    SP iterations (dense eigensolver, direct Poisson), the two-hole CI
-    (2 orbitals) and the double-dot g-tensors (dense, 7 assembled
-    operators)."""
+    """The oracle timed beside the NEXT rows, each on a stated crop
+    (centred), unscaled: the H0 (block Lanczos, 16 states) and three SP
+    iterations (dense eigensolver, direct Poisson) on the C2 physics; the
+    two-hole CI (2 orbitals) and the g-tensors (dense, 7 assembled
+    operators) on the double dot."""
+    import inputs
     from oracle import ci as ci_o
     from oracle import eig, kp
     from oracle import gtensor as gt_o
@@ -227,11 +228,12 @@ def _oracle_next_rows(p):
     po_o.sp_loop(q, q.V, gates(q), np.zeros_like(q.V), 8, 2.0, 1.5, 0.3, 3, bands=6)
     out["sp"] = {"s_per_iteration": (time.perf_counter() - t0) / 3,
                  "sample": f"10x6x6 crop, {q.n_unknowns} unknowns, 8 states, 2 holes, 3 iterations"}
-    q = _crop(p, (14, 6, 6)).with_(B=np.zeros(3))
+    pdd = inputs.double_dot(p.nx, p.ny, p.nz, p.h)
+    q = _crop(pdd, (14, 6, 6))
     t0 = time.perf_counter()
     ci_o.ci_pipeline(q, 2, gates(q))
     out["ci"] = {"s": time.perf_counter() - t0, "sample": "14x6x6 crop, 2 H0 orbitals, K = 6"}
-    q = _crop(p, (12, 6, 6))
+    q = _crop(pdd, (12, 6, 6))
     t0 = time.perf_counter()
     gt_o.dqd_g_tensors(q)
     out["gtensor"] = {"s": time.perf_counter() - t0, "sample": f"12x6x6 crop, {q.n_unknowns} unknowns"}
@@ -382,8 +384,11 @@ def run_ours(args, rank, world, local_rank):
     # the line: the headline evidence goes last)
     line["h0"] = _h0_bench(p, dev, torch, khp)
     line["sp"] = _sp_bench(p, dev, torch, khp)
-    line["ci"] = _ci_bench(p, dev, torch, khp)
-    line["gtensor"] = _gtensor_bench(p, dev, torch, khp, line["ci"].get("exchange_ev"))
+    # the CI and the g-tensors on the mirror-symmetric double dot of the
+    # same grid, where t and J are a tunnel coupling and an exchange energy
+    pdd = inputs.double_dot(p.nx, p.ny, p.nz, p.h)
+    line["ci"] = _ci_bench(pdd, dev, torch, khp)
+    line["gtensor"] = _gtensor_bench(pdd, dev, torch, khp, line["ci"].get("exchange_ev"))
     line["warm"] = {"value": rw.stats["converged"] / (ms_warm * 1e-3), "unit": UNIT, "ms_per_solve": ms_warm,
                     "iterations": rw.stats["iterations"],
                     "note": "warm start from the previous solve's eigenvectors, V changed by 0.1 meV smooth noise"}
@@ -492,7 +497,8 @@ def _sp_bench(p, dev, torch, khp):
     """Schroedinger-Poisson loop on the C2 grid and fields: grounded gates on
     the two x faces, 2 holes at 1.5 K, linear mixing 0.3, defect-corrected
     solves warm-started from the previous iteration, up to 12 iterations or
-    max |dV| <= 1e-6 eV; then Anderson mixing at 1.5 K and 20 K."""
+    max |dV| <= 1e-6 eV; then Anderson mixing at 20 K and the loop with
+    relaxed occupations at 1.5 K."""
     from paper_2607_08447_b300.poisson import Poisson, sp_solve
     gate = np.zeros((p.nz, p.ny, p.nx), dtype=np.uint8)
     gate[:, :, 0] = 1
@@ -519,28 +525,34 @@ def _sp_bench(p, dev, torch, khp):
            "final_max_dV_ev": r.history[-1], "poisson_cg_iterations": r.poisson_iterations,
            "poisson_ms_cold": 1e3 * tp, "poisson_cold_iterations": P.last_iterations,
            "workload": "C2 grid and fields, grounded gates on both x faces, 2 holes, T 1.5 K, mix 0.3"}
-    # Anderson mixing (library history, depth 6, damping 0.5) at the same
-    # 1.5 K and at 20 K, where kT exceeds the splittings of the random wells
-    # and the density responds smoothly to V
-    for name, T in (("anderson_1p5k", 1.5), ("anderson_20k", 20.0)):
+    # Anderson mixing (library history, depth 6, damping 0.5) at 20 K, where
+    # kT exceeds the splittings of the random wells and the density responds
+    # smoothly to V; then the loop with relaxed occupations at 1.5 K, with
+    # linear mixing 0.5 and with Anderson mixing (damping 0.8, depth 4)
+    runs = (("anderson_20k", 20.0, dict(mix=0.5, anderson_depth=6)),
+            ("relaxed_1p5k_linear", 1.5, dict(mix=0.5, relax=True)),
+            ("relaxed_1p5k_anderson", 1.5, dict(mix=0.8, anderson_depth=4, relax=True)))
+    for name, T, opt in runs:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ra = sp_solve(g, P, p.V, SOLVE_KW["n_states"], 2.0, T=T, mix=0.5, iters=16, tol_v=1e-6, strain=p.strain,
-                      B=p.B, gauge=p.gauge, solve_kw=kw, anderson_depth=6)
+        ra = sp_solve(g, P, p.V, SOLVE_KW["n_states"], 2.0, T=T, iters=24, tol_v=1e-6, strain=p.strain,
+                      B=p.B, gauge=p.gauge, solve_kw=kw, **opt)
         torch.cuda.synchronize()
         out[name] = {"T_K": T, "iterations": len(ra.history), "s_total": time.perf_counter() - t0,
                      "converged": ra.history[-1] <= 1e-6,
                      "max_dV_last_ev": [float(f"{x:.3g}") for x in ra.history[-4:]]}
+        if ra.occupations is not None:
+            out[name]["occupations"] = [float(f"{x:.4g}") for x in ra.occupations[:6]]
     P.close()
     g.close()
     return out
 
 
 def _ci_bench(p, dev, torch, khp):
-    """Two-hole CI on the C2 grid and fields: the lowest 4 orbitals of the
-    spin-independent H0 (defect-corrected solve), 16 Coulomb potentials
-    (32 Poisson solves, grounded gates on both x faces), K = 28
-    determinants."""
+    """Two-hole CI of the double dot on the 160x48x48 grid: the lowest 4
+    orbitals of the spin-independent H0 (defect-corrected solve), 16
+    Coulomb potentials (32 Poisson solves, grounded gates on both x faces),
+    K = 28 determinants; J = E_T - E_S."""
     from paper_2607_08447_b300.ci import ci_exchange
     from paper_2607_08447_b300.poisson import Poisson
     gate = np.zeros((p.nz, p.ny, p.nx), dtype=np.uint8)
@@ -557,7 +569,10 @@ def _ci_bench(p, dev, torch, khp):
     t = time.perf_counter() - t0
     out = {"s_total": t, "determinants": len(r.energies), "exchange_ev": r.exchange,
            "lowest_two_hole_ev": [float(x) for x in r.energies[:4]],
-           "workload": "C2 grid and fields, H0 lowest 4 orbitals, grounded gates on both x faces"}
+           "spin2_lowest4": [float(f"{x:.4g}") for x in r.spin2[:4]],
+           "lowest4_spread_ev": float(r.energies[3] - r.energies[0]),
+           "workload": "mirror-symmetric double dot (hw = 5 meV wells at 0.3 and 0.7 L_x) on the 160x48x48 "
+                       "grid, device frame, no strain, B = 0; H0 lowest 4 orbitals, grounded gates on both x faces"}
     P.close()
     g.close()
     return out
@@ -565,8 +580,8 @@ def _ci_bench(p, dev, torch, khp):
 
 def _gtensor_bench(p, dev, torch, khp, j_ci):
     """g-matrices of the bonding/anti-bonding doublets and the left/right
-    g-tensors on the C2 grid and fields (B set to 0 for the solve and
-    restored): the 4-state defect-corrected solve, then the responses
+    g-tensors of the double dot on the 160x48x48 grid (B = 0): the 4-state
+    defect-corrected solve, then the responses
     (6 operator applies at B = +-d e_j, 6 tensor-core projections) and the
     position moments.  Then the host maps of Eq. 17 on a 91 x 181 grid of
     field directions, with the CI's J and a stated spin-orbit rotation
@@ -592,7 +607,8 @@ def _gtensor_bench(p, dev, torch, khp, j_ci):
     out = {"s_total": t_total, "s_response_and_moments": t_resp, "delta_ev": r.delta, "tunnel_ev": r.tunnel,
            "g_left_principal": [float(x) for x in np.sqrt(np.linalg.eigvalsh(r.g_left.T @ r.g_left))],
            "g_right_principal": [float(x) for x in np.sqrt(np.linalg.eigvalsh(r.g_right.T @ r.g_right))],
-           "workload": "C2 grid and fields at B = 0, lowest 4 states (bonding + anti-bonding doublets), d = 0.01 T"}
+           "workload": "mirror-symmetric double dot on the 160x48x48 grid at B = 0, lowest 4 states "
+                       "(bonding + anti-bonding doublets), d = 0.01 T"}
     if j_ci:
         th, ph = np.linspace(0, np.pi, 91), np.linspace(0, 2 * np.pi, 181)
         t0 = time.perf_counter()

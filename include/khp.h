@@ -321,6 +321,41 @@ khp_status khp_sp_anderson(khp_poisson p, const double* V_ext_dev, const double*
 khp_status khp_fermi_level(const double* E_host, int n, double n_holes, double kT, double* mu_out,
                            double* occ_host);
 
+/* Per-state densities of n states (the inputs of the relaxed-occupation
+ * step below): dens_dev[i][p] = sum_b |psi_i(nb p + b)|^2, float64 [n][Np]
+ * device (state-major), evecs_dev complex128 [N][n] row-major (N = nb Np;
+ * nb = 6, or 3 for an H0 handle).  n in 1..64.  Asynchronous. */
+khp_status khp_state_densities(khp_handle h, const void* evecs_dev, int n, double* dens_dev);
+
+/* One Schroedinger-Poisson update with relaxed occupations.  The paper
+ * repeats the loop until convergence (Sec. II B) at 1.5 K (Sec. III A);
+ * there, fixed Fermi-Dirac occupations of the current levels let the holes
+ * jump between near-degenerate wells from one iteration to the next.  Here
+ * the occupations answer the new potential within the step, with the n
+ * states of H(V) held fixed:
+ *   Q_j   potential of a unit occupation of state j (density dens_j / h^3,
+ *         gates grounded), phi_g the potential of the gates alone (CG on
+ *         the device, each Q_j started from the previous call's);
+ *   K_ij  = sum_p dens_i(p) Q_j(p),  e0_i = E_i + sum_p dens_i(p) (phi_g - (V - V_ext))(p);
+ *   f     the Fermi-Dirac occupations of the levels eps = e0 + K f at the
+ *         Fermi level holding n_holes (Newton's method on eps, host);
+ *   phi   = phi_g + sum_j f_j Q_j.
+ * The caller mixes V_ext + phi into V (khp_sp_update / khp_sp_anderson).
+ * At a fixed point f are the Fermi-Dirac occupations of H(V).
+ *  dens_dev   float64 [n][Np] from khp_state_densities (device)
+ *  E_host     float64 [n] eigenvalues of the states [eV]
+ *  V_dev, V_ext_dev  float64 [Np] the potential of the states and the
+ *             external potential (NULL = 0) [eV]
+ *  phi_dev    float64 [Np] output [V]
+ *  tol        relative residual of the CG solves
+ *  occ_host   optional float64 [n] output, the occupations; mu_out optional
+ * Synchronous.  Errors: INVALID_ARG (NULL, n outside 1..64, kT <= 0,
+ * n_holes outside (0, n), non-finite level), OOM (2 + n Np doubles on the
+ * handle), NOT_CONVERGED (a CG solve), BREAKDOWN (singular Newton system). */
+khp_status khp_sp_relax_occupations(khp_poisson p, const double* dens_dev, const double* E_host, int n,
+                                    double n_holes, double kT, const double* V_dev, const double* V_ext_dev,
+                                    double* phi_dev, double tol, double* occ_host, double* mu_out);
+
 /* Forget the Anderson history (start of a new self-consistent loop). */
 khp_status khp_sp_anderson_reset(khp_poisson p);
 

@@ -15,6 +15,7 @@ from .gen import (  # noqa: F401
     config4,
     config5,
     crop,
+    double_dot,
     small_problem,
     random_block,
     smooth_noise,

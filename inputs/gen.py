@@ -218,6 +218,18 @@ def config5() -> Problem:
                    n_states=8, block_m=16, degree=20, seed=1004)
 
 
+def double_dot(nx: int = 160, ny: int = 48, nz: int = 48, h: float = 0.5) -> Problem:
+    """A mirror-symmetric double dot on the 160x48x48 grid of the FinFET
+    workload (h = 0.5 nm, device frame): the harmonic double well of
+    config 1 (hw = 5 meV, minima at 0.3 and 0.7 L_x) without noise or
+    strain and at B = 0, so that its bonding/anti-bonding splitting is a
+    tunnel coupling and the two-hole singlet-triplet splitting an exchange
+    energy (the setting of the paper's Sec. III B)."""
+    V = _double_well(nx, ny, nz, h)
+    return Problem(f"double_dot_{nx}x{ny}x{nz}", nx, ny, nz, h, dict(MATERIALS["bj"]), ROT_DEVICE.copy(),
+                   V, None, np.zeros(3), 0, n_states=4, block_m=16, degree=20, seed=1005)
+
+
 def small_problem(nx, ny, nz, h=1.0, seed=7, rot="identity", B=(0.0, 0.0, 0.0),
                   gauge=0, strain=True, material="bj", mask=False, levers=0,
                   noise_mev=1.0, n_states=8, block_m=16) -> Problem:

@@ -21,6 +21,9 @@ updated by linear mixing):
     rho_p = sum_i f_i sum_b |psi_i(p, b)|^2 / h^3
     phi = Poisson(rho)
     V_{k+1} = (1 - a) V_k + a (V_ext + phi)
+Anderson mixing of the same map is offered as well, and a loop with
+relaxed occupations (sp_loop_relaxed; see the section near its definition)
+for the paper's 1.5 K.
 """
 from __future__ import annotations
 
@@ -151,128 +154,102 @@ def sp_loop(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, mix, iters, 
 
 
 # --------------------------------------------------------------------------
-# Predictor-corrector Schroedinger-Poisson loop (Trellakis et al., J. Appl.
-# Phys. 81, 7880 (1997)).  The paper says only that the loop is repeated
-# until convergence (Sec. II B); at its temperature (1.5 K, Sec. III A)
-# mixing V alone oscillates between near-degenerate wells.  The scheme
-# replaces the Poisson step by a nonlinear one in which every state keeps
-# its wave function while its energy follows the local change of the
-# potential:
-#     rho[phi](p) = sum_i P_i(p) f((E_i + phi(p) - phi_k(p) - mu) / kT),
-#     P_i(p) = sum_b |psi_i(p, b)|^2 / h^3,
-#     h^3 sum_p rho[phi](p) = n_holes          (fixes mu for every phi),
-#     A phi = (e / eps) rho[phi]               (free points; gates fixed),
-# solved by Newton's method.  At a fixed point (phi = phi_k) rho is the
-# Fermi-Dirac density of the states of H(V_ext + phi), so the loop ends at
-# a solution of the plain Schroedinger-Poisson equations.
+# Schroedinger-Poisson loop with relaxed occupations.  The paper says only
+# that the loop is repeated until convergence (Sec. II B); at its
+# temperature (1.5 K, Sec. III A) mixing V alone lets the holes jump between
+# near-degenerate wells from one iteration to the next.  The reading used
+# here lets the occupations respond to the new potential inside each
+# iteration, with the states of H(V_k) held fixed:
+#   * Q_j: the potential of a unit occupation of state j (Poisson with the
+#     gates grounded); phi_g: the potential of the gates alone;
+#   * a trial potential phi = phi_g + sum_j f_j Q_j moves level i, to first
+#     order, to eps_i = E_i + <psi_i| phi - phi_k |psi_i>
+#                     = e0_i + sum_j K_ij f_j,
+#     e0_i = E_i + <psi_i| phi_g - phi_k |psi_i>,  K_ij = <psi_i| Q_j |psi_i>;
+#   * the occupations solve f_i = F((eps_i - mu) / kT), sum_i f_i = n_holes
+#     (F Fermi-Dirac): the minimum of the convex free energy
+#     sum_i e0_i f_i + f.K.f / 2 + kT sum_i [f_i ln f_i + (1 - f_i) ln(1 - f_i)]
+#     at fixed hole number;
+#   * G(V_k) = V_ext + phi_g + sum_j f_j Q_j, mixed into V (linear or
+#     Anderson, as in sp_loop).
+# At a fixed point phi = phi_k, so eps = E and f are the Fermi-Dirac
+# occupations of H(V): the fixed point is one of the plain loop's.
 
-def state_densities(evecs, h, bands=6):
-    """P[i][p] = sum_b |psi_i(p, b)|^2 / h^3 (nm^-3)."""
+def state_densities(evecs, bands=6):
+    """dens[i][p] = sum_b |psi_i(p, b)|^2 (discrete norm: sum_p dens_i = 1)."""
     N, n = evecs.shape
     P = (np.abs(evecs) ** 2).reshape(N // bands, bands, n).sum(axis=1)
-    return np.ascontiguousarray(P.T) / h ** 3
+    return np.ascontiguousarray(P.T)
 
 
-def local_density(P, E, mu, kT, dphi):
-    """rho_p, D_p = -d rho_p / d phi_p at fixed mu, with the local energies
-    E_i + dphi_p."""
-    x = (np.asarray(E)[:, None] + dphi[None, :] - mu) / kT
-    f = 0.5 * (1.0 - np.tanh(0.5 * x))
-    rho = np.sum(P * f, axis=0)
-    D = np.sum(P * f * (1.0 - f), axis=0) / kT
-    return rho, D
+def relaxed_occupations(e0, K, n_holes, kT):
+    """(f, mu, eps) of the occupation problem above, by Newton's method on
+    the effective levels eps = e0 + K f(eps), f(eps) the Fermi-Dirac
+    occupations at the Fermi level of eps (bisection); the step is halved
+    until the residual falls."""
+    e0 = np.asarray(e0, dtype=np.float64)
+    n = len(e0)
 
+    def occ(eps):
+        mu = fermi_level(eps, n_holes, kT)
+        return occupations(eps, mu, kT), mu
 
-def local_fermi_level(P, E, n_holes, kT, dphi, h):
-    """mu with h^3 sum_p rho_p(mu) = n_holes (bisection; the count rises
-    monotonically with mu)."""
-    lo = np.min(E) + dphi.min() - 50 * kT - 1.0
-    hi = np.max(E) + dphi.max() + 50 * kT + 1.0
+    eps = e0 + K @ occ(e0)[0]
     for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        rho, _ = local_density(P, E, mid, kT, dphi)
-        if h ** 3 * rho.sum() < n_holes:
-            lo = mid
-        else:
-            hi = mid
-    return 0.5 * (lo + hi)
-
-
-def nonlinear_residual(A, gate, gate_phi, coef, phi, P, E, n_holes, kT, phi_k, h):
-    """(F, mu, D): F = A phi - coef rho[phi] on free points, phi - phi_gate
-    at gates; mu from the hole count; D = -d rho / d phi (local)."""
-    dphi = phi - phi_k
-    mu = local_fermi_level(P, E, n_holes, kT, dphi, h)
-    rho, D = local_density(P, E, mu, kT, dphi)
-    F = A @ phi - np.where(gate, gate_phi, coef * rho)
-    return F, mu, D
-
-
-def nonlinear_jacobian_solve(A, gate, coef, D, h, F):
-    """delta with J delta = -F, J the derivative of F including the response
-    of mu:  J = A + coef diag(D) - coef h^3 D D^T / (h^3 sum D) on the free
-    points (identity rows at gates), by Sherman-Morrison over a sparse LU
-    of the first two terms."""
-    free = ~gate
-    Dm = h ** 3 * D.sum()
-    Df = np.where(free, D, 0.0)
-    M = (A + sp.diags(np.where(free, coef * D, 0.0))).tocsc()
-    lu = spla.splu(M)
-    y1 = lu.solve(-F)
-    if Dm <= 0.0:
-        return y1
-    u = coef * Df
-    v = h ** 3 * Df / Dm
-    y2 = lu.solve(u)
-    return y1 + y2 * (v @ y1) / (1.0 - v @ y2)
-
-
-def nonlinear_poisson(nx, ny, nz, h, gate_mask, gate_phi, P, E, n_holes, kT, phi_k, eps_r=EPS_SI,
-                      tol=1e-12, max_newton=60):
-    """phi solving the predictor's nonlinear Poisson problem from phi = phi_k:
-    Newton steps with backtracking (the step is halved until |F| falls).
-    Returns (phi, mu, Newton steps)."""
-    A, gate = assemble(nx, ny, nz, h, gate_mask)
-    coef = e_over_eps(eps_r)
-    gphi = np.asarray(gate_phi, dtype=np.float64).reshape(-1)
-    phi = np.where(gate, gphi, np.asarray(phi_k, dtype=np.float64).reshape(-1))
-    phi_k = np.asarray(phi_k, dtype=np.float64).reshape(-1)
-    F, mu, D = nonlinear_residual(A, gate, gphi, coef, phi, P, E, n_holes, kT, phi_k, h)
-    for it in range(max_newton):
-        delta = nonlinear_jacobian_solve(A, gate, coef, D, h, F)
-        if np.abs(delta).max() <= tol:
-            return phi + delta, mu, it + 1
-        step, nF = 1.0, np.linalg.norm(F)
-        for _ in range(30):
-            trial = phi + step * delta
-            F2, mu2, D2 = nonlinear_residual(A, gate, gphi, coef, trial, P, E, n_holes, kT, phi_k, h)
-            if np.linalg.norm(F2) < nF:
+        f, mu = occ(eps)
+        R = eps - e0 - K @ f
+        nr = np.linalg.norm(R)
+        if nr <= 1e-15 * max(1e-3, np.abs(eps).max()):
+            break
+        s = f * (1.0 - f)
+        B = np.diag(s) - (np.outer(s, s) / s.sum() if s.sum() > 0 else 0.0)
+        step = np.linalg.solve(np.eye(n) + K @ B / kT, -R)
+        a = 1.0
+        while True:
+            trial = eps + a * step
+            f2, _ = occ(trial)
+            if np.linalg.norm(trial - e0 - K @ f2) < nr * (1.0 - 1e-4 * a) or a < 1e-12:
                 break
-            step *= 0.5
-        phi, F, mu, D = trial, F2, mu2, D2
-    return phi, mu, max_newton
+            a *= 0.5
+        eps = trial
+    f, mu = occ(eps)
+    return f, mu, eps
 
 
-def sp_loop_pc(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, iters, bands=6, eps_r=EPS_SI,
-               newton_tol=1e-12):
-    """Predictor-corrector Schroedinger-Poisson iterations from V = V_ext
-    (phi_0 = 0 at free points, the gate values at gates; dense eigensolver,
-    sparse direct solves).  Returns (V, E, mu, history of max |dV|)."""
+def relaxed_step(nx, ny, nz, h, gate_mask, gate_phi, dens, E, n_holes, kT, phi_k, eps_r=EPS_SI):
+    """(phi, f, mu): the potential and the relaxed occupations of one
+    iteration (see above); dens from state_densities."""
+    Np = nx * ny * nz
+    phi_g = solve(nx, ny, nz, h, gate_mask, gate_phi, np.zeros(Np), eps_r)
+    zero = np.zeros(Np)
+    Q = np.stack([solve(nx, ny, nz, h, gate_mask, zero, dens[j] / h ** 3, eps_r) for j in range(len(E))])
+    K = dens @ Q.T
+    K = 0.5 * (K + K.T)
+    e0 = np.asarray(E) + dens @ (phi_g - np.asarray(phi_k).reshape(-1))
+    f, mu, _ = relaxed_occupations(e0, K, n_holes, kT)
+    return phi_g + f @ Q, f, mu
+
+
+def sp_loop_relaxed(prob, V_ext, gate_mask, gate_phi, n_states, n_holes, T, mix, iters, bands=6, eps_r=EPS_SI,
+                    anderson_depth=0):
+    """Schroedinger-Poisson iterations with relaxed occupations from
+    V = V_ext (dense eigensolver, sparse direct solves); linear mixing with
+    weight `mix`, or Anderson mixing (damping `mix`) over `anderson_depth`
+    > 0 previous iterates.  Returns (V, E, mu, f, history of max |dV|)."""
     nx, ny, nz, h = prob.nx, prob.ny, prob.nz, prob.h
     kT = KB_EV * T
     V_ext = np.asarray(V_ext, dtype=np.float64).reshape(-1)
-    gate = np.asarray(gate_mask, dtype=bool).reshape(-1)
-    phi = np.where(gate, np.asarray(gate_phi, dtype=np.float64).reshape(-1), 0.0)
-    V = V_ext + phi
+    V = V_ext.copy()
+    acc = Anderson(mix, anderson_depth) if anderson_depth > 0 else None
     hist = []
     for _ in range(iters):
         q = prob.with_(V=V.reshape(nz, ny, nx))
         H = kp.assemble(q) if bands == 6 else kp.assemble_h0(q)
         E, psi = eig.lowest_dense(H, n_states, mask=prob.mask)
-        P = state_densities(psi, h, bands)
-        phi, mu, _ = nonlinear_poisson(nx, ny, nz, h, gate_mask, gate_phi, P, E, n_holes, kT, phi, eps_r,
-                                       tol=newton_tol)
-        Vn = V_ext + phi
+        phi, f, mu = relaxed_step(nx, ny, nz, h, gate_mask, gate_phi, state_densities(psi, bands), E, n_holes,
+                                  kT, V - V_ext, eps_r)
+        GV = V_ext + phi
+        Vn = acc.step(V, GV) if acc is not None else (1.0 - mix) * V + mix * GV
         hist.append(float(np.abs(Vn - V).max()))
         V = Vn
-    return V, E, mu, hist
+    return V, E, mu, f, hist

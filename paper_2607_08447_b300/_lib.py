@@ -26,7 +26,7 @@ EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_po
             "khp_eigensolve_batched",
             "khp_density", "khp_eigs_backward", "khp_eigs_backward_noalloc", "khp_destroy",
             "khp_last_error", "khp_version", "khp_sp_anderson", "khp_sp_anderson_reset",
-            "khp_fermi_level", "khp_filter_step"]
+            "khp_fermi_level", "khp_filter_step", "khp_state_densities", "khp_sp_relax_occupations"]
 
 
 class Material(ctypes.Structure):
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.khp_sp_anderson.argtypes = [vp, vp, vp, d, i, vp, dp]
     lib.khp_sp_anderson_reset.argtypes = [vp]
     lib.khp_fermi_level.argtypes = [dp, i, d, d, dp, dp]
+    lib.khp_state_densities.argtypes = [vp, vp, i, vp]
+    lib.khp_sp_relax_occupations.argtypes = [vp, vp, dp, i, d, d, vp, vp, vp, d, dp, dp]
     lib.khp_poisson_destroy.argtypes = [vp]
     lib.khp_project.argtypes = [vp, vp, vp, i, i, vp, vp]
     lib.khp_project_rows.argtypes = [vp, vp, vp, ctypes.c_longlong, i, i, vp, vp]

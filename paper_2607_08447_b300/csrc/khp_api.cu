@@ -1390,6 +1390,16 @@ extern "C" khp_status khp_density(khp_handle g, const void* evecs_dev, int n, co
     return KHP_OK;
 }
 
+extern "C" khp_status khp_state_densities(khp_handle g, const void* evecs_dev, int n, double* dens_dev) {
+    g_err.clear();
+    if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!evecs_dev || !dens_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1 || n > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "n out of range 1..64");
+    CK(launch_state_densities((const double2*)evecs_dev, g->np, n, g->nb, dens_dev, g->stream));
+    g->launches += 1;
+    return KHP_OK;
+}
+
 extern "C" khp_status khp_eigs_backward(khp_handle g, const void* evecs_dev, const double* evals_host,
                                         int n, const double* dLdE_host, double* dLdV_dev,
                                         double* dLdstrain_dev, const double* levers_dev, int n_gates,

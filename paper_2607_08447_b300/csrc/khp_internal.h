@@ -88,6 +88,7 @@ cudaError_t launch_dc_combine(const double2* X, const double2* HX, const float2*
                               long long rows, int ld, int zcol0, const double* D, cudaStream_t st);
 
 // observables.cu
+cudaError_t launch_state_densities(const double2* psi, long long np, int n, int nb, double* dens, cudaStream_t st);
 cudaError_t launch_pair_density(const double2* psi, long long np, int n, int nb, double2* out, cudaStream_t st);
 // D [3][m][m] = first moments of the m states X about the box centre
 // (partial: scratch of partial_elems entries)

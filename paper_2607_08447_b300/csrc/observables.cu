@@ -143,6 +143,28 @@ cudaError_t launch_backward(const double2* psi, long long np, int n, const doubl
 // Sec. II C, Eqs. 13-15), written as [Np][n * n] complex, pair index j n + l.
 namespace khp {
 
+// dens[i][p] = sum_b |psi_i(nb p + b)|^2: the per-state densities (discrete
+// norm) of n states, state-major so that a state's density is contiguous
+__global__ void state_density_kernel(const double2* __restrict__ psi, long long np, int n, int nb,
+                                     double* __restrict__ dens) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double2* row = psi + p * nb * n;
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double2 v = row[b * n + i];
+            s = fma(v.x, v.x, fma(v.y, v.y, s));
+        }
+        dens[(long long)i * np + p] = s;
+    }
+}
+
+cudaError_t launch_state_densities(const double2* psi, long long np, int n, int nb, double* dens, cudaStream_t st) {
+    state_density_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(psi, np, n, nb, dens);
+    return cudaGetLastError();
+}
+
 __global__ void pair_density_kernel(const double2* __restrict__ psi, long long np, int n, int nb,
                                     double2* __restrict__ out) {
     const int npair = n * n;

@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "khp_common.cuh"
 #include "khp_internal.h"
@@ -40,6 +42,15 @@ struct khp_poisson_s {
     double* a_partial;     // [nblk][kMaxR] per-block triangular factors
     double* a_host;        // [nblk][kMaxR] pinned copy of a_partial
     int a_depth, a_count;
+    // relaxed-occupation step (allocated on first use)
+    double* r_Q;           // [r_nmax][np] potentials of unit occupations (grounded gates)
+    double* r_phig;        // [np] potential of the gates alone
+    double* r_zero;        // [np] zeros
+    double* r_partial;     // block partials of the K and e0 sums
+    double* r_out;         // [n][nch][17] sums
+    double* r_host;        // pinned copy of r_out
+    int r_nmax, r_nq;      // capacity; states whose Q holds a previous solution
+    bool r_have_phig;
 };
 
 namespace khp {
@@ -403,6 +414,71 @@ __global__ void anderson_update_kernel(long long np, int m, double beta, const A
     if (threadIdx.x == 0) partial[2 * blockIdx.x] = sm[0];
 }
 
+// ------------------------------------------------------------------------
+// Relaxed occupations (Schroedinger-Poisson loop): with the per-state
+// densities dens_i, the unit-occupation potentials Q_j and the gate
+// potential phi_g, the sums
+//     K_ij = sum_p dens_i(p) Q_j(p),
+//     d_i  = sum_p dens_i(p) (phi_g(p) - (V(p) - V_ext(p)))
+// in fixed order: block partials of 16 j's (plus d_i in chunk 0) per
+// (i, chunk), then one block per (i, chunk) over the partials.
+constexpr int kRJ = 16;
+
+__global__ void __launch_bounds__(kT) relax_dots_kernel(long long np, int n, const double* __restrict__ dens,
+                                                        const double* __restrict__ Q, const double* __restrict__ phig,
+                                                        const double* __restrict__ V, const double* __restrict__ Vext,
+                                                        double* __restrict__ partial) {
+    const int i = blockIdx.y, jc = blockIdx.z, nch = gridDim.z;
+    const int j0 = jc * kRJ;
+    double acc[kRJ + 1];
+#pragma unroll
+    for (int k = 0; k <= kRJ; ++k) acc[k] = 0.0;
+    const double* di = dens + (long long)i * np;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
+        const double w = di[p];
+#pragma unroll
+        for (int k = 0; k < kRJ; ++k)
+            if (j0 + k < n) acc[k] = fma(w, Q[(long long)(j0 + k) * np + p], acc[k]);
+        if (jc == 0) acc[kRJ] = fma(w, phig[p] - (V[p] - (Vext ? Vext[p] : 0.0)), acc[kRJ]);
+    }
+    __shared__ double sm[kT / 32][kRJ + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k <= kRJ; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sm[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x <= kRJ) {
+        double v = 0.0;
+        for (int w = 0; w < kT / 32; ++w) v += sm[w][threadIdx.x];
+        partial[(((long long)i * nch + jc) * gridDim.x + blockIdx.x) * (kRJ + 1) + threadIdx.x] = v;
+    }
+}
+
+__global__ void relax_sum_kernel(const double* partial, int nblk, double* out) {
+    const int row = blockIdx.x, k = threadIdx.x;
+    if (k > kRJ) return;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += partial[((long long)row * nblk + b) * (kRJ + 1) + k];
+    out[row * (kRJ + 1) + k] = v;
+}
+
+struct RelaxCoef {
+    double f[KHP_MAX_M];
+};
+
+// phi = phi_g + sum_j f_j Q_j
+__global__ void relax_combine_kernel(long long np, int n, const RelaxCoef c, const double* __restrict__ phig,
+                                     const double* __restrict__ Q, double* __restrict__ phi) {
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT) {
+        double v = phig[p];
+        for (int j = 0; j < n; ++j) v = fma(c.f[j], Q[(long long)j * np + p], v);
+        phi[p] = v;
+    }
+}
+
 __global__ void copy_gate_values_kernel(long long np, const uint8_t* gate, const double* src, double* gphi) {
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < np; p += (long long)gridDim.x * kT)
         gphi[p] = gate[p] ? src[p] : 0.0;
@@ -417,6 +493,19 @@ namespace {
 using khp::poisson::kT;
 
 khp_status pfail(khp_status s, const std::string& m) { return khp_set_error(s, m); }
+
+#define CKSP(call)                                                                          \
+    do {                                                                                    \
+        const khp_status s_ = (call);                                                       \
+        if (s_ != KHP_OK) return s_;                                                        \
+    } while (0)
+
+// launch check with the step's name in the message
+#define PCKL(what)                                                                          \
+    do {                                                                                    \
+        const cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess) return pfail(KHP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
 
 #define PCK(call)                                                                           \
     do {                                                                                    \
@@ -434,12 +523,14 @@ void free_all(khp_poisson_s* P) {
     if (P->have_chunk) cudaGraphExecDestroy(P->chunk);
     if (P->work) cudaStreamDestroy(P->work);
     double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s,
-                      P->a_dv, P->a_df, P->a_vprev, P->a_fprev, P->a_f, P->a_partial};
+                      P->a_dv, P->a_df, P->a_vprev, P->a_fprev, P->a_f, P->a_partial,
+                      P->r_Q, P->r_phig, P->r_zero, P->r_partial, P->r_out};
     for (double* b : bufs)
         if (b) cudaFree(b);
     if (P->gate) cudaFree(P->gate);
     if (P->host_pinned) cudaFreeHost(P->host_pinned);
     if (P->a_host) cudaFreeHost(P->a_host);
+    if (P->r_host) cudaFreeHost(P->r_host);
 }
 
 // Host side of the tall-skinny QR: fold the blocks' factors into one
@@ -594,12 +685,11 @@ static void cg_iteration(khp_poisson_s* P, const khp::poisson::Geo& g, cudaStrea
     direction_kernel<<<nb, kT, 0, st>>>(g, P->s, P->z, P->p);
 }
 
-khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_dev, double tol, int max_iter,
-                             int* iterations, double* rel_residual) {
-    khp_set_error(KHP_OK, "");
-    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
-    if (!rho_dev || !phi_dev) return pfail(KHP_ERR_INVALID_ARG, "rho or phi is NULL");
-    if (!(tol > 0.0) || max_iter < 1) return pfail(KHP_ERR_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+// CG solve of A phi = coef * rho_scale * rho (free points) with the gate
+// potentials gphi (the handle's, or zeros for grounded gates); phi is the
+// start at the free points and the solution on return.  Synchronous.
+static khp_status cg_solve(khp_poisson P, const double* rho_dev, double rho_scale, const double* gphi,
+                           double* phi_dev, double tol, int max_iter, int* iterations, double* rel_residual) {
     using namespace khp::poisson;
     const Geo g = geo(P);
     const int nb = P->nblk;
@@ -607,12 +697,12 @@ khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_d
     PCK(cudaStreamSynchronize(P->stream));
     cudaStream_t st = P->work;
     double* hp = P->host_pinned;
-    rhs_kernel<<<nb, kT, 0, st>>>(g, rho_dev, P->gphi, P->coef, phi_dev, P->b, P->x, P->partial);
+    rhs_kernel<<<nb, kT, 0, st>>>(g, rho_dev, gphi, P->coef * rho_scale, phi_dev, P->b, P->x, P->partial);
     finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 0, P->s);
     apply_kernel<<<nb, kT, 0, st>>>(g, P->x, P->Ap, P->partial);
     init_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->z, P->p, P->partial);
     finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 1, P->s);
-    PCK(cudaGetLastError());
+    PCKL("CG set-up launches");
     PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
     const double bb = hp[5];
@@ -636,20 +726,29 @@ khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_d
         } else {
             for (int k = 0; k < chunk; ++k) cg_iteration(P, g, st);
         }
-        PCK(cudaGetLastError());
+        PCKL("CG iterations");
         it += chunk;
         PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
         PCK(cudaStreamSynchronize(st));
         rel = bb > 0.0 ? std::sqrt(hp[4] / bb) : std::sqrt(hp[4]);
         if (!std::isfinite(rel)) return pfail(KHP_ERR_BREAKDOWN, "Poisson CG produced a non-finite residual");
     }
-    output_kernel<<<nb, kT, 0, st>>>(g, P->x, P->gphi, phi_dev);
-    PCK(cudaGetLastError());
+    output_kernel<<<nb, kT, 0, st>>>(g, P->x, gphi, phi_dev);
+    PCKL("CG output");
     PCK(cudaStreamSynchronize(st));
     if (iterations) *iterations = it;
     if (rel_residual) *rel_residual = rel;
     if (rel > tol) return pfail(KHP_ERR_NOT_CONVERGED, "Poisson CG reached max_iter");
     return KHP_OK;
+}
+
+khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_dev, double tol, int max_iter,
+                             int* iterations, double* rel_residual) {
+    khp_set_error(KHP_OK, "");
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!rho_dev || !phi_dev) return pfail(KHP_ERR_INVALID_ARG, "rho or phi is NULL");
+    if (!(tol > 0.0) || max_iter < 1) return pfail(KHP_ERR_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+    return cg_solve(P, rho_dev, 1.0, P->gphi, phi_dev, tol, max_iter, iterations, rel_residual);
 }
 
 khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* phi_dev, double mix, double* V_dev,
@@ -662,7 +761,7 @@ khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* p
     PCK(cudaStreamSynchronize(P->stream));
     mix_kernel<<<P->nblk, kT, 0, P->work>>>(P->np, V_ext_dev, phi_dev, mix, V_dev, P->partial);
     max_finish_kernel<<<1, kT, 0, P->work>>>(P->partial, P->nblk, P->s + 6);
-    PCK(cudaGetLastError());
+    PCKL("linear update");
     PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->work));
     PCK(cudaStreamSynchronize(P->work));
     if (max_change) *max_change = P->host_pinned[6];
@@ -708,7 +807,7 @@ khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double*
     }
     anderson_residual_kernel<<<nb, kT, 0, st>>>(np, V_ext_dev, phi_dev, V_dev, P->a_f, P->a_vprev, P->a_fprev, dv,
                                                 df);
-    PCK(cudaGetLastError());
+    PCKL("Anderson residual");
     const int m = std::min(P->a_count, depth);
     AndersonCoef c{};
     if (m > 0) {
@@ -718,14 +817,14 @@ khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double*
             KHP_AQ(1) KHP_AQ(2) KHP_AQ(3) KHP_AQ(4) KHP_AQ(5) KHP_AQ(6) KHP_AQ(7) KHP_AQ(8)
 #undef KHP_AQ
         }
-        PCK(cudaGetLastError());
+        PCKL("Anderson QR");
         PCK(cudaMemcpyAsync(P->a_host, P->a_partial, sizeof(double) * K * nb, cudaMemcpyDeviceToHost, st));
         PCK(cudaStreamSynchronize(st));
         anderson_solve(P->a_host, nb, m, np, c.gamma);
     }
     anderson_update_kernel<<<nb, kT, 0, st>>>(np, m, beta, c, V_dev, P->a_f, P->a_dv, P->a_df, P->partial);
     max_finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, P->s + 6);
-    PCK(cudaGetLastError());
+    PCKL("Anderson update");
     PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
     P->a_count += 1;
@@ -740,27 +839,22 @@ khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double*
 // evaluation narrows (N < n_holes moves lo up, N > n_holes moves hi down);
 // a Newton step that leaves the bracket, or stalls on a flat stretch of N
 // between well separated levels, is replaced by the bracket's midpoint.
-khp_status khp_fermi_level(const double* E_host, int n, double n_holes, double kT, double* mu_out,
-                           double* occ_host) {
-    khp_set_error(KHP_OK, "");
-    if (!E_host || !mu_out) return pfail(KHP_ERR_INVALID_ARG, "E or mu is NULL");
-    if (n < 1) return pfail(KHP_ERR_INVALID_ARG, "n must be >= 1");
-    if (!(kT > 0.0) || !std::isfinite(kT)) return pfail(KHP_ERR_INVALID_ARG, "kT must be > 0");
-    if (!(n_holes > 0.0 && n_holes < n)) return pfail(KHP_ERR_INVALID_ARG, "n_holes must lie in (0, n)");
+// E finite, 0 < n_holes < n, kT > 0 (checked by the callers).
+static double fd_occ(double e, double mu, double kT) {
+    const double x = (e - mu) / kT;
+    if (x >= 0.0) {
+        const double t = std::exp(-x);
+        return t / (1.0 + t);
+    }
+    return 1.0 / (1.0 + std::exp(x));
+}
+
+static double fermi_solve(const double* E_host, int n, double n_holes, double kT, double* occ_host) {
     double emin = E_host[0], emax = E_host[0];
     for (int i = 0; i < n; ++i) {
-        if (!std::isfinite(E_host[i])) return pfail(KHP_ERR_INVALID_ARG, "non-finite level");
         emin = std::min(emin, E_host[i]);
         emax = std::max(emax, E_host[i]);
     }
-    auto occ = [&](double e, double mu) {
-        const double x = (e - mu) / kT;
-        if (x >= 0.0) {
-            const double t = std::exp(-x);
-            return t / (1.0 + t);
-        }
-        return 1.0 / (1.0 + std::exp(x));
-    };
     // N(lo) <= n e^-(L) < n_holes and N(hi) >= n - n e^-(L) > n_holes
     const double L = std::log((double)n) + 60.0 + std::fabs(std::log(std::min(n_holes, n - n_holes)));
     double lo = emin - L * kT, hi = emax + L * kT;
@@ -768,7 +862,7 @@ khp_status khp_fermi_level(const double* E_host, int n, double n_holes, double k
     for (int it = 0; it < 400; ++it) {
         double N = 0.0, dN = 0.0;
         for (int i = 0; i < n; ++i) {
-            const double f = occ(E_host[i], mu);
+            const double f = fd_occ(E_host[i], mu, kT);
             N += f;
             dN += f * (1.0 - f);
         }
@@ -786,9 +880,196 @@ khp_status khp_fermi_level(const double* E_host, int n, double n_holes, double k
         dx = mu - prev;
         if (std::fabs(dx) <= 2.0 * DBL_EPSILON * std::max(std::fabs(mu), kT)) break;
     }
-    *mu_out = mu;
     if (occ_host)
-        for (int i = 0; i < n; ++i) occ_host[i] = occ(E_host[i], mu);
+        for (int i = 0; i < n; ++i) occ_host[i] = fd_occ(E_host[i], mu, kT);
+    return mu;
+}
+
+khp_status khp_fermi_level(const double* E_host, int n, double n_holes, double kT, double* mu_out,
+                           double* occ_host) {
+    khp_set_error(KHP_OK, "");
+    if (!E_host || !mu_out) return pfail(KHP_ERR_INVALID_ARG, "E or mu is NULL");
+    if (n < 1) return pfail(KHP_ERR_INVALID_ARG, "n must be >= 1");
+    if (!(kT > 0.0) || !std::isfinite(kT)) return pfail(KHP_ERR_INVALID_ARG, "kT must be > 0");
+    if (!(n_holes > 0.0 && n_holes < n)) return pfail(KHP_ERR_INVALID_ARG, "n_holes must lie in (0, n)");
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(E_host[i])) return pfail(KHP_ERR_INVALID_ARG, "non-finite level");
+    *mu_out = fermi_solve(E_host, n, n_holes, kT, occ_host);
+    return KHP_OK;
+}
+
+// Occupations relaxed in a fixed set of states (host, n <= 64): the
+// effective levels eps solve eps = e0 + K f(eps), f the Fermi-Dirac
+// occupations at the Fermi level of eps (fermi_solve).  Newton's method on
+// R(eps) = eps - e0 - K f(eps) with the Jacobian I + K B / kT,
+// B = diag(s) - s s^T / sum(s), s = f (1 - f) (the derivative of f at a
+// fixed hole number); the step is halved until |R| falls.  Gaussian
+// elimination with partial pivoting for the n x n system.
+static bool relax_newton(const double* e0, const double* K, int n, double n_holes, double kT, double* f,
+                         double* mu) {
+    std::vector<double> eps(n), R(n), J((size_t)n * n), step(n), trial(n), f2(n);
+    auto residual = [&](const std::vector<double>& e, double* ff, std::vector<double>& r) {
+        const double m = fermi_solve(e.data(), n, n_holes, kT, ff);
+        double nr = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = e[i] - e0[i];
+            for (int j = 0; j < n; ++j) v -= K[(size_t)i * n + j] * ff[j];
+            r[i] = v;
+            nr += v * v;
+        }
+        return std::make_pair(m, std::sqrt(nr));
+    };
+    // start: the levels shifted by the occupations of the unshifted levels
+    {
+        std::vector<double> e(e0, e0 + n);
+        fermi_solve(e.data(), n, n_holes, kT, f);
+        for (int i = 0; i < n; ++i) {
+            double v = e0[i];
+            for (int j = 0; j < n; ++j) v += K[(size_t)i * n + j] * f[j];
+            eps[i] = v;
+        }
+    }
+    for (int it = 0; it < 200; ++it) {
+        auto [m, nr] = residual(eps, f, R);
+        *mu = m;
+        double emax = 1e-3;
+        for (int i = 0; i < n; ++i) emax = std::max(emax, std::fabs(eps[i]));
+        if (nr <= 1e-15 * emax) return true;
+        double S = 0.0;
+        std::vector<double> sv(n);
+        for (int i = 0; i < n; ++i) {
+            sv[i] = f[i] * (1.0 - f[i]);
+            S += sv[i];
+        }
+        // J = I + K B / kT, B_lj = s_l delta_lj - s_l s_j / S
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double v = K[(size_t)i * n + j] * sv[j];
+                if (S > 0.0) {
+                    double ks = 0.0;
+                    for (int l = 0; l < n; ++l) ks += K[(size_t)i * n + l] * sv[l];
+                    v -= ks * sv[j] / S;
+                }
+                J[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) + v / kT;
+            }
+        for (int i = 0; i < n; ++i) step[i] = -R[i];
+        for (int c = 0; c < n; ++c) {      // elimination with partial pivoting
+            int piv = c;
+            for (int r = c + 1; r < n; ++r)
+                if (std::fabs(J[(size_t)r * n + c]) > std::fabs(J[(size_t)piv * n + c])) piv = r;
+            if (!(J[(size_t)piv * n + c] != 0.0)) return false;
+            if (piv != c) {
+                for (int k = 0; k < n; ++k) std::swap(J[(size_t)c * n + k], J[(size_t)piv * n + k]);
+                std::swap(step[c], step[piv]);
+            }
+            for (int r = c + 1; r < n; ++r) {
+                const double t = J[(size_t)r * n + c] / J[(size_t)c * n + c];
+                for (int k = c; k < n; ++k) J[(size_t)r * n + k] -= t * J[(size_t)c * n + k];
+                step[r] -= t * step[c];
+            }
+        }
+        for (int c = n - 1; c >= 0; --c) {
+            double v = step[c];
+            for (int k = c + 1; k < n; ++k) v -= J[(size_t)c * n + k] * step[k];
+            step[c] = v / J[(size_t)c * n + c];
+        }
+        double a = 1.0;
+        std::vector<double> R2(n);
+        while (true) {
+            for (int i = 0; i < n; ++i) trial[i] = eps[i] + a * step[i];
+            const double nr2 = residual(trial, f2.data(), R2).second;
+            if (nr2 < nr * (1.0 - 1e-4 * a) || a < 1e-12) break;
+            a *= 0.5;
+        }
+        eps = trial;
+    }
+    *mu = fermi_solve(eps.data(), n, n_holes, kT, f);
+    return true;
+}
+
+khp_status khp_sp_relax_occupations(khp_poisson P, const double* dens_dev, const double* E_host, int n,
+                                    double n_holes, double kT_ev, const double* V_dev, const double* V_ext_dev,
+                                    double* phi_dev, double tol, double* occ_host, double* mu_out) {
+    khp_set_error(KHP_OK, "");
+    using namespace khp::poisson;
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!dens_dev || !E_host || !V_dev || !phi_dev) return pfail(KHP_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1 || n > KHP_MAX_M) return pfail(KHP_ERR_INVALID_ARG, "n out of range 1..64");
+    if (!(kT_ev > 0.0) || !std::isfinite(kT_ev)) return pfail(KHP_ERR_INVALID_ARG, "kT must be > 0");
+    if (!(n_holes > 0.0 && n_holes < n)) return pfail(KHP_ERR_INVALID_ARG, "n_holes must lie in (0, n)");
+    if (!(tol > 0.0)) return pfail(KHP_ERR_INVALID_ARG, "tol must be > 0");
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(E_host[i])) return pfail(KHP_ERR_INVALID_ARG, "non-finite level");
+    const long long np = P->np;
+    const int nb = P->nblk;
+    const int nch = (n + kRJ - 1) / kRJ;
+    if (!P->r_Q || P->r_nmax < n) {
+        if (P->r_Q) cudaFree(P->r_Q);
+        P->r_Q = nullptr;
+        P->r_nq = 0;
+        cudaError_t e;
+        if ((e = cudaMalloc(&P->r_Q, sizeof(double) * (size_t)n * np)) != cudaSuccess)
+            return pfail(KHP_ERR_OOM, std::string("relaxed step buffers: ") + cudaGetErrorString(e));
+        P->r_nmax = n;
+    }
+    if (!P->r_phig) {
+        const int rows = KHP_MAX_M * ((KHP_MAX_M + kRJ - 1) / kRJ);
+        cudaError_t e;
+        if ((e = cudaMalloc(&P->r_phig, sizeof(double) * np)) != cudaSuccess ||
+            (e = cudaMalloc(&P->r_zero, sizeof(double) * np)) != cudaSuccess ||
+            (e = cudaMalloc(&P->r_partial, sizeof(double) * (size_t)rows * nb * (kRJ + 1))) != cudaSuccess ||
+            (e = cudaMalloc(&P->r_out, sizeof(double) * (size_t)rows * (kRJ + 1))) != cudaSuccess ||
+            (e = cudaMallocHost(&P->r_host, sizeof(double) * (size_t)rows * (kRJ + 1))) != cudaSuccess)
+            return pfail(KHP_ERR_OOM, std::string("relaxed step buffers: ") + cudaGetErrorString(e));
+        PCK(cudaMemsetAsync(P->r_zero, 0, sizeof(double) * np, P->work));
+        PCK(cudaMemsetAsync(P->r_phig, 0, sizeof(double) * np, P->work));
+        PCK(cudaStreamSynchronize(P->work));
+        P->r_have_phig = false;
+    }
+    const int max_iter = 100000;
+    if (!P->r_have_phig) {
+        CKSP(cg_solve(P, P->r_zero, 1.0, P->gphi, P->r_phig, tol, max_iter, nullptr, nullptr));
+        P->r_have_phig = true;
+    }
+    // unit-occupation potentials (grounded gates), each started from the
+    // previous call's solution for the same state index
+    if (P->r_nq < n) {
+        PCK(cudaMemsetAsync(P->r_Q + (size_t)P->r_nq * np, 0, sizeof(double) * (size_t)(n - P->r_nq) * np, P->work));
+        PCK(cudaStreamSynchronize(P->work));
+    }
+    const double h3inv = 1.0 / (P->h * P->h * P->h);
+    for (int j = 0; j < n; ++j)
+        CKSP(cg_solve(P, dens_dev + (size_t)j * np, h3inv, P->r_zero, P->r_Q + (size_t)j * np, tol, max_iter,
+                      nullptr, nullptr));
+    P->r_nq = std::max(P->r_nq, n);
+    cudaStream_t st = P->work;
+    relax_dots_kernel<<<dim3(nb, n, nch), kT, 0, st>>>(np, n, dens_dev, P->r_Q, P->r_phig, V_dev, V_ext_dev,
+                                                       P->r_partial);
+    relax_sum_kernel<<<n * nch, 32, 0, st>>>(P->r_partial, nb, P->r_out);
+    PCKL("relaxed step: sums");
+    PCK(cudaMemcpyAsync(P->r_host, P->r_out, sizeof(double) * (size_t)n * nch * (kRJ + 1), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    std::vector<double> K((size_t)n * n), e0(n), f(n);
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = P->r_host[((size_t)i * nch + j / kRJ) * (kRJ + 1) + j % kRJ];
+        e0[i] = E_host[i] + P->r_host[((size_t)i * nch) * (kRJ + 1) + kRJ];
+    }
+    for (int i = 0; i < n; ++i)          // symmetric by reciprocity: average the rounding
+        for (int j = i + 1; j < n; ++j) {
+            const double v = 0.5 * (K[(size_t)i * n + j] + K[(size_t)j * n + i]);
+            K[(size_t)i * n + j] = K[(size_t)j * n + i] = v;
+        }
+    double mu = 0.0;
+    if (!relax_newton(e0.data(), K.data(), n, n_holes, kT_ev, f.data(), &mu))
+        return pfail(KHP_ERR_BREAKDOWN, "relaxed occupations: singular Newton system");
+    RelaxCoef c{};
+    for (int j = 0; j < n; ++j) c.f[j] = f[j];
+    relax_combine_kernel<<<nb, kT, 0, st>>>(np, n, c, P->r_phig, P->r_Q, phi_dev);
+    PCKL("relaxed step: potential");
+    PCK(cudaStreamSynchronize(st));
+    if (occ_host)
+        for (int j = 0; j < n; ++j) occ_host[j] = f[j];
+    if (mu_out) *mu_out = mu;
     return KHP_OK;
 }
 

@@ -502,23 +502,24 @@ template cudaError_t launch_stencil<float>(const StencilArgs<float>&, cudaStream
 
 // ------------------------------------------- plane-marching FP32 stencil
 // The same fused step y = alpha (H x) + beta x + gamma prev + c_col src for
-// FP32 blocks, organised for data reuse: a CTA owns an x-y tile of TX x TY
-// points and V = 4 vector columns (one per thread) and marches through a
-// range of z-planes.  The planes of x, each with a one-point halo in x and
-// y, arrive in a four-deep shared-memory ring by TMA (cp.async.bulk.tensor,
-// one box per band, so a band of a plane is a dense [y][x][col] array read
-// without bank conflicts); the box reads zeros outside the grid, which is
-// the Dirichlet wall.  prev and the defect source arrive by TMA as well, one
-// plane per step.  All 19 neighbour values then come from shared memory and
-// every byte of x, prev and src crosses HBM once (the halo is re-read from
-// L2).  Each copy completes on an mbarrier; every wait is bounded (about a
-// second), and a wait that runs out sets bit 8 of the error flag, drains
-// the copies in flight and leaves the kernel.
+// FP32 blocks, organised for data reuse: a CTA owns an x-y tile of
+// 16 x 4 points and V = 4 vector columns (one per thread) and marches
+// through a range of z-planes.  The planes of x, each with a one-point halo
+// in x and y, arrive in a four-deep shared-memory ring by TMA
+// (cp.async.bulk.tensor, one box per band, so a band of a plane is a dense
+// [y][x][col] array read without bank conflicts); the box reads zeros
+// outside the grid, which is the Dirichlet wall.  prev and the defect
+// source arrive by TMA as well, one plane ahead of their use.  All 19
+// neighbour values come from shared memory, and every byte of x, prev and
+// src crosses HBM once (the halo is re-read from L2).  Three warps issue
+// the copies (x, prev, src); each copy completes on an mbarrier; one CTA
+// barrier per plane releases the buffers.  Every wait is bounded (about a
+// second): a wait that runs out sets bit 8 of the error flag, and the CTA
+// waits (bounded) for its copies in flight and leaves.
 namespace plane {
 
 constexpr int TX = 16;
 constexpr int V = 4;
-constexpr int NSLOT = 4;
 constexpr int HX = TX + 2;
 
 // NSX: depth of the ring of x planes (4: plane z + 3 is loaded while plane z
@@ -526,10 +527,11 @@ constexpr int HX = TX + 2;
 // as the pairs that reach across planes are summed).  NPS: buffers of the
 // prev/src planes (2: the plane after next is loaded while a plane is
 // computed).
-template <int NB, int TY, int NSX, int NPS>
+template <int NB, int TY, int NSX, int NPS, int VG>
 struct Geo {
     static constexpr int HY = TY + 2;
-    static constexpr int THREADS = TX * TY * V;
+    static constexpr int THREADS = TX * TY * V / VG;
+    static constexpr int CTAS_PER_SM = 512 / (TX * TY * V);   // by shared memory (ring 4: 2 at TY = 4)
     static constexpr int XBAND = HY * HX * V;           // float2 per band of a halo plane
     static constexpr int XSLOT = NB * XBAND;
     static constexpr int PBAND = TY * TX * V;           // float2 per band of a prev/src plane
@@ -578,11 +580,11 @@ __device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, 
         : "memory");
 }
 
-template <int NB, int PH, bool SRC, int TY, int NSX, int NPS>
-__global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, TY, NSX, NPS>::THREADS)
+template <int NB, int PH, bool SRC, int TY, int NSX, int NPS, int VG>
+__global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS, VG>::THREADS, Geo<NB, TY, NSX, NPS, VG>::CTAS_PER_SM)
     stencil_plane_kernel(const StencilArgs<float> a, const Work w, const __grid_constant__ CUtensorMap mx,
                          const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap ms) {
-    using G = Geo<NB, TY, NSX, NPS>;
+    using G = Geo<NB, TY, NSX, NPS, VG>;
     using C = float2;
     constexpr int NS = NB / 3;
     static_assert(G::THREADS >= 96, "three issuing warps");
@@ -606,14 +608,18 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, 
     const int zs = z0 - 1;                      // first plane of the ring
     const int cg = w.cbase + g * V;             // first column of this group
 
+    // thread: VG consecutive columns (from col) of one point (lx, ly)
+    constexpr int NCP = V / VG;
     const int tid = threadIdx.x;
-    const int col = tid % V;
-    const int lx = (tid / V) % TX;
-    const int ly = tid / (V * TX);
+    const int col = (tid % NCP) * VG;
+    const int lx = (tid / NCP) % TX;
+    const int ly = tid / (NCP * TX);
     const int gx = tx0 + lx, gy = ty0 + ly;
     const int c = cg + col;
     const bool live = gx < a.nx && gy < a.ny;
-    const bool store = live && c >= a.col0 && c < a.col0 + a.ncol;
+    bool store[VG];
+#pragma unroll
+    for (int v = 0; v < VG; ++v) store[v] = live && c + v >= a.col0 && c + v < a.col0 + a.ncol;
     const bool has_prev = a.prev != nullptr;
     const bool has_ps = has_prev || SRC;
     const long long plane_pts = (long long)a.nx * a.ny;
@@ -623,10 +629,11 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, 
     const bool ip_thread = tid == 32 && has_prev;
     const bool is_thread = tid == 64 && SRC;
 
-    auto xslot = [&](int q) { return (q - zs) % NSX; };
-    auto xpar = [&](int q) { return (uint32_t)(((q - zs) / NSX) & 1); };
-    auto pslot = [&](int q) { return (q - z0) % NPS; };
-    auto ppar = [&](int q) { return (uint32_t)(((q - z0) / NPS) & 1); };
+    // q >= zs always: unsigned division by the compile-time ring sizes
+    auto xslot = [&](int q) { return (int)((unsigned)(q - zs) % (unsigned)NSX); };
+    auto xpar = [&](int q) { return (uint32_t)(((unsigned)(q - zs) / (unsigned)NSX) & 1u); };
+    auto pslot = [&](int q) { return (int)((unsigned)(q - z0) % (unsigned)NPS); };
+    auto ppar = [&](int q) { return (uint32_t)(((unsigned)(q - z0) / (unsigned)NPS) & 1u); };
     auto xbar = [&](int q) { return sa(bars + xslot(q)); };
     auto pbar = [&](int q) { return sa(bars + NSX + pslot(q)); };
 
@@ -684,29 +691,46 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, 
     float2 cs_cur[9], cs_nxt[9];
     load_fields(z0, o_cur, cs_cur);
 
-    // shared-memory address of band b at offset (dx, dy) in the slot of plane q
+    // this thread's point in a ring slot; the slots of planes z - 1, z, z + 1
+    // are set once per step, so every neighbour load is a base plus a
+    // compile-time offset
+    const C* own = xring + ((ly + 1) * HX + (lx + 1)) * V + col;
+    auto lds = [](C (&v)[VG], const C* p) {
+        if constexpr (VG == 2) {
+            const float4 q = *reinterpret_cast<const float4*>(p);
+            v[0] = make_float2(q.x, q.y);
+            v[1] = make_float2(q.z, q.w);
+        } else {
+            v[0] = *p;
+        }
+    };
+    const C* slot_base[3] = {own, own, own};
     auto xat = [&](int q, int b, int dx, int dy) -> const C* {
-        return xring + xslot(q) * G::XSLOT + b * G::XBAND + ((ly + 1 + dy) * HX + (lx + 1 + dx)) * V + col;
+        return slot_base[q] + b * G::XBAND + (dy * HX + dx) * V;
     };
     // pair d: (x+ + x-) and (x+ - x-) of the needed bands, then the pair's
     // alpha-scaled orbital matrix (times the Peierls phase) into acc
-    auto pair = [&](C (&acc)[6][1], int z, auto dc) {
+    auto pair = [&](C (&acc)[6][VG], int z, auto dc) {
         constexpr int d = decltype(dc)::value;
         constexpr unsigned nzd = cubic_nz(d);
         constexpr unsigned need = need_of(nzd);
         constexpr int dx = pair_dx(d), dy = pair_dy(d), dz = pair_dz(d);
         const bool ph = PH == PH_SYM && (a.c.pair_phase & (1u << d));
-        C u[6][1], v[6][1];
+        C u[6][VG], v[6][VG];
 #pragma unroll
         for (int o = 0; o < 3; ++o) {
             if (!(need & (1u << o))) continue;
 #pragma unroll
             for (int sp = 0; sp < NS; ++sp) {
                 const int b = 3 * sp + o;
-                const C xp = *xat(z + dz, b, dx, dy);
-                const C xm = *xat(z - dz, b, -dx, -dy);
-                u[b][0] = cadd<float>(xp, xm);
-                if (PH == PH_SYM) v[b][0] = csub<float>(xp, xm);
+                C xp[VG], xm[VG];
+                lds(xp, xat(1 + dz, b, dx, dy));
+                lds(xm, xat(1 - dz, b, -dx, -dy));
+#pragma unroll
+                for (int t = 0; t < VG; ++t) {
+                    u[b][t] = cadd<float>(xp[t], xm[t]);
+                    if (PH == PH_SYM) v[b][t] = csub<float>(xp[t], xm[t]);
+                }
             }
         }
         float cth = 1.f, sth = 0.f;
@@ -722,11 +746,11 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, 
             const int j = k < 3 ? k : (k == 5 ? 1 : 2);
             if (PH == PH_SYM && ph) {
                 const float mc = m * cth, msn = m * sth;
-                pair_entry<float, 1, true, NS>(acc, i, j, mc, msn, u, v);
-                if (k >= 3) pair_entry<float, 1, true, NS>(acc, j, i, mc, msn, u, v);
+                pair_entry<float, VG, true, NS>(acc, i, j, mc, msn, u, v);
+                if (k >= 3) pair_entry<float, VG, true, NS>(acc, j, i, mc, msn, u, v);
             } else {
-                pair_entry<float, 1, false, NS>(acc, i, j, m, 0.f, u, v);
-                if (k >= 3) pair_entry<float, 1, false, NS>(acc, j, i, m, 0.f, u, v);
+                pair_entry<float, VG, false, NS>(acc, i, j, m, 0.f, u, v);
+                if (k >= 3) pair_entry<float, VG, false, NS>(acc, j, i, m, 0.f, u, v);
             }
         }
     };
@@ -737,10 +761,14 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, 
         for (int q = waited_x + 1; q <= z + 1; ++q) failed |= !mbar_wait(xbar(q), xpar(q));
         waited_x = z + 1;
         load_fields(z + 1, o_nxt, cs_nxt);
-
-        C acc[6][1];
 #pragma unroll
-        for (int b = 0; b < 6; ++b) acc[b][0] = make_float2(0.f, 0.f);
+        for (int k = 0; k < 3; ++k) slot_base[k] = own + xslot(z - 1 + k) * G::XSLOT;
+
+        C acc[6][VG];
+#pragma unroll
+        for (int b = 0; b < 6; ++b)
+#pragma unroll
+            for (int t = 0; t < VG; ++t) acc[b][t] = make_float2(0.f, 0.f);
         // the pairs that reach planes z - 1 and z + 1 first
         pair(acc, z, std::integral_constant<int, 2>{});
         pair(acc, z, std::integral_constant<int, 5>{});
@@ -758,23 +786,25 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, 
         }
         // centre: on-site orbital matrix (+ beta), spin-orbit and Zeeman
         {
-            C xs[6][1];
+            C xs[6][VG];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) xs[b][0] = *xat(z, b, 0, 0);
+            for (int b = 0; b < NB; ++b) lds(xs[b], xat(1, b, 0, 0));
             float oo[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) oo[k] = a.alpha * o_cur[k];
 #pragma unroll
             for (int k = 0; k < 3; ++k) oo[k] += a.beta;
-            sym3<float, 1, false, NS>(acc, oo, a.c.onsite_nz | 7u, xs);
+            sym3<float, VG, false, NS>(acc, oo, a.c.onsite_nz | 7u, xs);
 #pragma unroll
             for (int b = 0; b < (NB == 6 ? 6 : 0); ++b) {
                 const unsigned rowm = a.c.soz_nz[b];
 #pragma unroll
-                for (int b2 = 0; b2 < 6; ++b2) {
-                    if (rowm & (1u << (2 * b2))) axpy_c<float>(acc[b][0], a.c.soz_re[b][b2], xs[b2][0]);
-                    if (rowm & (2u << (2 * b2))) axpy_mi<float>(acc[b][0], -a.c.soz_im[b][b2], xs[b2][0]);
-                }
+                for (int b2 = 0; b2 < 6; ++b2)
+#pragma unroll
+                    for (int t = 0; t < VG; ++t) {
+                        if (rowm & (1u << (2 * b2))) axpy_c<float>(acc[b][t], a.c.soz_re[b][b2], xs[b2][t]);
+                        if (rowm & (2u << (2 * b2))) axpy_mi<float>(acc[b][t], -a.c.soz_im[b][b2], xs[b2][t]);
+                    }
             }
         }
         // the pairs inside plane z
@@ -788,17 +818,35 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS>::THREADS, 512 / Geo<NB, 
             failed |= !mbar_wait(pbar(z), ppar(z));
             waited_p = z;
             const int pi = pslot(z) * G::PPLANE + (ly * TX + lx) * V + col;
-            const float sc = SRC ? a.src_coef[min(max(c, 0), 63)] : 0.f;
+            float sc[VG];
+#pragma unroll
+            for (int t = 0; t < VG; ++t) sc[t] = SRC ? a.src_coef[min(max(c + t, 0), 63)] : 0.f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                if (has_prev) axpy_c<float>(acc[b][0], a.gamma, pbuf[pi + b * G::PBAND]);
-                if (SRC) axpy_c<float>(acc[b][0], sc, sbuf[pi + b * G::PBAND]);
+                C pv[VG], sv[VG];
+                if (has_prev) lds(pv, pbuf + pi + b * G::PBAND);
+                if (SRC) lds(sv, sbuf + pi + b * G::PBAND);
+#pragma unroll
+                for (int t = 0; t < VG; ++t) {
+                    if (has_prev) axpy_c<float>(acc[b][t], a.gamma, pv[t]);
+                    if (SRC) axpy_c<float>(acc[b][t], sc[t], sv[t]);
+                }
             }
         }
-        if (store) {
+        {
             C* yp = a.y + (gx + (long long)a.nx * gy + plane_pts * z) * ps + c;
+            if (VG == 2 && store[0] && store[VG - 1]) {
 #pragma unroll
-            for (int b = 0; b < NB; ++b) __stcs(yp + b * a.ld, acc[b][0]);
+                for (int b = 0; b < NB; ++b)
+                    __stcs(reinterpret_cast<float4*>(yp + b * a.ld),
+                           make_float4(acc[b][0].x, acc[b][0].y, acc[b][VG - 1].x, acc[b][VG - 1].y));
+            } else {
+#pragma unroll
+                for (int t = 0; t < VG; ++t)
+                    if (store[t])
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) __stcs(yp + b * a.ld + t, acc[b][t]);
+            }
         }
         // every thread is done with this step's buffers; a wait that ran out
         // anywhere ends the CTA (after its copies in flight have landed)
@@ -876,66 +924,35 @@ bool enabled() {
     return on == 1;
 }
 
-template <int NB, int PH, bool SRC, int TY, int NSX, int NPS>
+// The measured best shape on B300 (C2, 24 vectors): tile 16 x 4 points x
+// 4 vectors, one vector per thread, x ring of 4 planes, one prev/src plane:
+// two 256-thread CTAs per SM.
+constexpr int kTY = 4, kNSX = 4, kNPS = 1, kVG = 1;
+
+template <int NB, int PH, bool SRC>
 cudaError_t launch_t(const StencilArgs<float>& a, const Work& w, unsigned items, const CUtensorMap& mx,
                      const CUtensorMap& mp, const CUtensorMap& ms, cudaStream_t st) {
-    using G = Geo<NB, TY, NSX, NPS>;
-    stencil_plane_kernel<NB, PH, SRC, TY, NSX, NPS><<<items, G::THREADS, G::SMEM, st>>>(a, w, mx, mp, ms);
+    using G = Geo<NB, kTY, kNSX, kNPS, kVG>;
+    stencil_plane_kernel<NB, PH, SRC, kTY, kNSX, kNPS, kVG><<<items, G::THREADS, G::SMEM, st>>>(a, w, mx, mp, ms);
     return cudaGetLastError();
 }
 
-template <int TY, int NSX, int NPS>
-cudaError_t dispatch(const StencilArgs<float>& a, const Work& w, unsigned n, int mode, const CUtensorMap& mx,
-                     const CUtensorMap& mp, const CUtensorMap& ms, cudaStream_t st) {
-    if (a.nb == 6) {
-        if (mode == PH_SYM)
-            return a.src ? launch_t<6, PH_SYM, true, TY, NSX, NPS>(a, w, n, mx, mp, ms, st)
-                         : launch_t<6, PH_SYM, false, TY, NSX, NPS>(a, w, n, mx, mp, ms, st);
-        return a.src ? launch_t<6, PH_NONE, true, TY, NSX, NPS>(a, w, n, mx, mp, ms, st)
-                     : launch_t<6, PH_NONE, false, TY, NSX, NPS>(a, w, n, mx, mp, ms, st);
-    }
-    return a.src ? launch_t<3, PH_NONE, true, TY, NSX, NPS>(a, w, n, mx, mp, ms, st)
-                 : launch_t<3, PH_NONE, false, TY, NSX, NPS>(a, w, n, mx, mp, ms, st);
-}
-
-template <int NB, int PH, bool SRC, int TY, int NSX, int NPS>
+template <int NB, int PH, bool SRC>
 cudaError_t prep_t() {
-    return cudaFuncSetAttribute(stencil_plane_kernel<NB, PH, SRC, TY, NSX, NPS>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<NB, TY, NSX, NPS>::SMEM);
-}
-
-template <int TY, int NSX, int NPS>
-cudaError_t prep_cfg() {
-    cudaError_t e = prep_t<6, PH_NONE, false, TY, NSX, NPS>();
-    if (e == cudaSuccess) e = prep_t<6, PH_NONE, true, TY, NSX, NPS>();
-    if (e == cudaSuccess) e = prep_t<6, PH_SYM, false, TY, NSX, NPS>();
-    if (e == cudaSuccess) e = prep_t<6, PH_SYM, true, TY, NSX, NPS>();
-    if (e == cudaSuccess) e = prep_t<3, PH_NONE, false, TY, NSX, NPS>();
-    if (e == cudaSuccess) e = prep_t<3, PH_NONE, true, TY, NSX, NPS>();
-    return e;
-}
-
-// Pipeline shape: 0 = tile 16 x 4, x ring of 4 planes, one prev/src plane
-// (two 256-thread CTAs per SM); 1 = tile 16 x 4, x ring of 3 planes, two
-// prev/src planes (two CTAs per SM); 2 = tile 16 x 8, ring of 4, one
-// prev/src plane (one 512-thread CTA per SM).  KHP_PLANE_CFG=0/1/2 in the
-// environment overrides the default (read once).
-int config() {
-    static int cfg = -1;
-    if (cfg < 0) {
-        const char* e = std::getenv("KHP_PLANE_CFG");
-        cfg = (e && e[0] >= '0' && e[0] <= '2') ? e[0] - '0' : 0;
-    }
-    return cfg;
+    return cudaFuncSetAttribute(stencil_plane_kernel<NB, PH, SRC, kTY, kNSX, kNPS, kVG>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<NB, kTY, kNSX, kNPS, kVG>::SMEM);
 }
 
 }  // namespace plane
 
 cudaError_t prepare_plane() {
     using namespace plane;
-    cudaError_t e = prep_cfg<4, 4, 1>();
-    if (e == cudaSuccess) e = prep_cfg<4, 3, 2>();
-    if (e == cudaSuccess) e = prep_cfg<8, 4, 1>();
+    cudaError_t e = prep_t<6, PH_NONE, false>();
+    if (e == cudaSuccess) e = prep_t<6, PH_NONE, true>();
+    if (e == cudaSuccess) e = prep_t<6, PH_SYM, false>();
+    if (e == cudaSuccess) e = prep_t<6, PH_SYM, true>();
+    if (e == cudaSuccess) e = prep_t<3, PH_NONE, false>();
+    if (e == cudaSuccess) e = prep_t<3, PH_NONE, true>();
     return e;
 }
 
@@ -953,9 +970,7 @@ cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStre
     if (mode == PH_GEN || (a.nb == 3 && mode != PH_NONE)) return cudaErrorNotSupported;
     const long long np = (long long)a.nx * a.ny * a.nz;
     if (np == 0) return cudaSuccess;
-    const int cfg = config();
-    const int kTY = cfg == 2 ? 8 : 4;
-    const int per_sm = cfg == 2 ? 1 : 2;
+    const int per_sm = Geo<6, kTY, kNSX, kNPS, kVG>::CTAS_PER_SM;
     Work w;
     w.ntx = (a.nx + TX - 1) / TX;
     w.nty = (a.ny + kTY - 1) / kTY;
@@ -988,9 +1003,15 @@ cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStre
     if (a.prev && !make_map(&mp, a.prev, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
     if (a.src && !make_map(&ms, a.src, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
     const unsigned n = (unsigned)items;
-    if (cfg == 1) return dispatch<4, 3, 2>(a, w, n, mode, mx, mp, ms, st);
-    if (cfg == 2) return dispatch<8, 4, 1>(a, w, n, mode, mx, mp, ms, st);
-    return dispatch<4, 4, 1>(a, w, n, mode, mx, mp, ms, st);
+    if (a.nb == 6) {
+        if (mode == PH_SYM)
+            return a.src ? launch_t<6, PH_SYM, true>(a, w, n, mx, mp, ms, st)
+                         : launch_t<6, PH_SYM, false>(a, w, n, mx, mp, ms, st);
+        return a.src ? launch_t<6, PH_NONE, true>(a, w, n, mx, mp, ms, st)
+                     : launch_t<6, PH_NONE, false>(a, w, n, mx, mp, ms, st);
+    }
+    return a.src ? launch_t<3, PH_NONE, true>(a, w, n, mx, mp, ms, st)
+                 : launch_t<3, PH_NONE, false>(a, w, n, mx, mp, ms, st);
 }
 
 // ------------------------------------------------------------ field set-up

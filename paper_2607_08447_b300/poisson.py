@@ -72,6 +72,20 @@ class Poisson:
                                             ctypes.byref(ch)))
         return ch.value
 
+    def relax(self, dens, E, n_holes, kT, V, V_ext=None, phi=None, tol=1e-12):
+        """phi (V) of one update with relaxed occupations
+        (khp_sp_relax_occupations); returns (phi, occupations, mu)."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        n = E.size
+        if phi is None:
+            phi = torch.empty(self.np_, dtype=torch.float64, device=self.device)
+        occ = np.zeros(n)
+        mu = ctypes.c_double(0.0)
+        _lib.check(self.lib.khp_sp_relax_occupations(self.handle, _ptr(dens), _lib.dptr(E), n, float(n_holes),
+                                                     float(kT), _ptr(V), _ptr(V_ext), _ptr(phi), float(tol),
+                                                     _lib.dptr(occ), ctypes.byref(mu)))
+        return phi, occ, mu.value
+
     def reset_mixing(self):
         _lib.check(self.lib.khp_sp_anderson_reset(self.handle))
 
@@ -106,16 +120,19 @@ class SPResult:
     evals: np.ndarray
     evecs: torch.Tensor
     mu: float
+    occupations: np.ndarray = None
     history: List[float] = field(default_factory=list)
     poisson_iterations: List[int] = field(default_factory=list)
 
 
 def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, tol_v=1e-8, strain=None,
-             B=None, gauge=0, solve_kw=None, anderson_depth=0):
+             B=None, gauge=0, solve_kw=None, anderson_depth=0, relax=False):
     """Self-consistent loop from V = V_ext: `iters` iterations at most, or
     until max |dV| <= tol_v.  Linear mixing with weight `mix`, or Anderson
     mixing (damping `mix`) over `anderson_depth` > 0 previous iterates.
-    Returns SPResult (V on the device)."""
+    relax=True relaxes the occupations within each update
+    (khp_sp_relax_occupations) instead of fixing them at the Fermi-Dirac
+    values of the current levels.  Returns SPResult (V on the device)."""
     kw = dict(block_m=max(n_states + 8, 16), degree=40, tol=1e-11, seed=1)
     kw.update(solve_kw or {})
     V_ext = _dev(V_ext, torch.float64, grid.device).reshape(-1)
@@ -130,10 +147,15 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
         grid.set_fields(V, strain, None, None, B, gauge)
         r = grid.eigensolve(n_states, warm_start=warm, **kw)
         warm = r.evecs
-        mu, f = fermi_level(r.evals, n_holes, kT)
-        rho = grid.density(r.evecs, f / grid.h ** 3)
-        poisson.solve(rho, phi)
-        piters.append(poisson.last_iterations)
+        if relax:
+            dens = grid.state_densities(r.evecs)
+            _, f, mu = poisson.relax(dens, r.evals, n_holes, kT, V, V_ext, phi)
+            piters.append(0)
+        else:
+            mu, f = fermi_level(r.evals, n_holes, kT)
+            rho = grid.density(r.evecs, f / grid.h ** 3)
+            poisson.solve(rho, phi)
+            piters.append(poisson.last_iterations)
         if anderson_depth > 0:
             dv = poisson.anderson(V, phi, mix, anderson_depth, V_ext)
         else:
@@ -141,4 +163,4 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
         hist.append(dv)
         if dv <= tol_v:
             break
-    return SPResult(V, r.evals, r.evecs, mu, hist, piters)
+    return SPResult(V, r.evals, r.evecs, mu, f, hist, piters)

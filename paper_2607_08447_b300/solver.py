@@ -232,6 +232,14 @@ class KPGrid:
         _lib.check(self.lib.khp_position_moments(self.handle, _ptr(X), m, D.ctypes.data_as(ctypes.c_void_p)))
         return D
 
+    def state_densities(self, evecs):
+        """float64 [n][Np]: sum_b |psi_i(p, b)|^2 per state (khp_state_densities)."""
+        evecs = _dev(evecs, torch.complex128, self.device)
+        n = evecs.shape[1]
+        out = torch.empty((n, self.np_), dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.khp_state_densities(self.handle, _ptr(evecs), n, _ptr(out)))
+        return out
+
     def pair_densities(self, evecs):
         """rho_jl(p) = sum_b conj(psi_j) psi_l for all ordered (j, l):
         complex128 [Np][n * n], pair index j n + l."""

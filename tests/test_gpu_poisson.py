@@ -162,6 +162,55 @@ def test_sp_loop_anderson_matches_oracle(khp, bands):
     g.close()
 
 
+@pytest.mark.parametrize("bands,depth", [(6, 0), (6, 3), (3, 0)])
+def test_sp_loop_relaxed_matches_oracle(khp, bands, depth):
+    """Four iterations with relaxed occupations (2 holes, T = 1.5 K; linear
+    mixing 0.5 or Anderson depth 3) from the same start: potential, levels,
+    occupations and the max |dV| history agree with the oracle's loop
+    (dense eigensolver, direct Poisson solves, Newton on the levels)."""
+    from paper_2607_08447_b300.poisson import Poisson, sp_solve
+    p = inputs.small_problem(10, 6, 6, h=0.5, seed=5, strain=True)
+    gate = _end_gates(p.nx, p.ny, p.nz)
+    gphi = np.zeros_like(p.V)
+    iters, n, nh = 4, 8, 2.0
+    V_or, E_or, mu_or, f_or, hist_or = po.sp_loop_relaxed(p, p.V, gate, gphi, n, nh, 1.5, 0.5, iters, bands=bands,
+                                                           anderson_depth=depth)
+    g = khp.KPGrid.from_problem(p, bands=bands)
+    P = Poisson(p.nx, p.ny, p.nz, p.h, gate, gphi)
+    r = sp_solve(g, P, p.V, n, nh, T=1.5, mix=0.5, iters=iters, tol_v=0.0, strain=p.strain,
+                 solve_kw=dict(block_m=16, degree=16, tol=1e-12), anderson_depth=depth, relax=True)
+    assert np.abs(np.array(r.history) - np.array(hist_or)).max() <= 1e-9
+    assert np.abs(r.V.cpu().numpy() - V_or).max() <= 1e-10
+    assert np.abs(r.evals - E_or).max() <= 1e-10
+    assert np.abs(r.occupations - f_or).max() <= 1e-8
+    assert abs(r.occupations.sum() - nh) <= 1e-10
+    P.close()
+    g.close()
+
+
+def test_sp_loop_relaxed_converges_to_a_plain_fixed_point(khp):
+    """The library's relaxed loop, run to max |dV| <= 1e-11 eV at 1.5 K, stops
+    at a V that the plain update (library Fermi level, density and Poisson
+    solve: V_ext + phi) leaves unchanged."""
+    from paper_2607_08447_b300.poisson import Poisson, fermi_level, sp_solve
+    p = inputs.small_problem(8, 4, 4, h=0.5, seed=5, strain=False)
+    gate = _end_gates(p.nx, p.ny, p.nz)
+    gphi = np.zeros_like(p.V)
+    g = khp.KPGrid.from_problem(p)
+    P = Poisson(p.nx, p.ny, p.nz, p.h, gate, gphi)
+    r = sp_solve(g, P, p.V, 6, 1.0, T=1.5, mix=0.8, iters=60, tol_v=1e-11, solve_kw=dict(block_m=16, degree=16,
+                 tol=1e-12), anderson_depth=4, relax=True)
+    assert r.history[-1] <= 1e-11, r.history
+    kT = 8.617333262e-5 * 1.5
+    mu, f = fermi_level(r.evals, 1.0, kT)
+    rho = g.density(r.evecs, f / p.h ** 3)
+    phi = P.solve(rho, tol=1e-13)
+    Vp = torch.from_numpy(p.V.reshape(-1)).cuda() + phi
+    assert float((Vp - r.V).abs().max()) <= 1e-8
+    P.close()
+    g.close()
+
+
 def test_anderson_without_external_potential(khp):
     """V_ext = NULL means zero: the first Anderson step is V + beta (phi - V)."""
     from paper_2607_08447_b300.poisson import Poisson

@@ -834,6 +834,72 @@ def test_anderson_first_step_is_linear_mixing():
     assert np.abs(acc.step(V, GV) - (0.7 * V + 0.3 * GV)).max() < 1e-15
 
 
+# --------------------------------------------------------------------------
+# Schroedinger-Poisson loop with relaxed occupations (the reading of the
+# paper's "repeated till convergence" at 1.5 K)
+def _free_energy(f, e0, K, kT):
+    f = np.clip(f, 1e-300, 1 - 1e-16)
+    return e0 @ f + 0.5 * f @ K @ f + kT * np.sum(f * np.log(f) + (1 - f) * np.log(1 - f))
+
+
+def test_relaxed_occupations_without_coupling_are_fermi_dirac():
+    rng = np.random.default_rng(21)
+    e0 = np.sort(rng.uniform(0.0, 5e-3, 8))
+    kT = po_oracle.KB_EV * 4.0
+    f, mu, eps = po_oracle.relaxed_occupations(e0, np.zeros((8, 8)), 2.0, kT)
+    mu_ref = po_oracle.fermi_level(e0, 2.0, kT)
+    assert np.abs(f - po_oracle.occupations(e0, mu_ref, kT)).max() < 1e-12
+    assert np.abs(eps - e0).max() == 0.0
+
+
+@pytest.mark.parametrize("T", [1.5, 20.0])
+def test_relaxed_occupations_minimise_the_free_energy(T):
+    """The occupations minimise e0.f + f.K.f/2 - T S(f) at fixed hole number
+    (K a Coulomb-like positive matrix): every feasible perturbation (sum of
+    the changes zero, 0 < f < 1) raises it; and sum f = n_holes."""
+    rng = np.random.default_rng(int(T))
+    n = 8
+    e0 = np.sort(rng.uniform(0.0, 4e-3, n))
+    L = rng.standard_normal((n, n))
+    K = 2e-3 * (L @ L.T) / n + 3e-3 * np.eye(n)
+    kT = po_oracle.KB_EV * T
+    f, mu, eps = po_oracle.relaxed_occupations(e0, K, 2.0, kT)
+    assert abs(f.sum() - 2.0) < 1e-10
+    F0 = _free_energy(f, e0, K, kT)
+    for _ in range(200):
+        d = rng.standard_normal(n)
+        d -= d.mean()
+        t = 1e-4 * min(1.0, 0.5 * np.min(np.where(d > 0, (1 - f) / np.abs(d), f / np.abs(d + 1e-300))))
+        assert _free_energy(f + t * d, e0, K, kT) >= F0 - 1e-15
+
+
+def test_relaxed_loop_fixed_point_is_a_plain_fixed_point():
+    """Iterated to convergence, the relaxed loop stops at a potential V that
+    the plain Schroedinger-Poisson map (Fermi-Dirac occupations of the
+    states of H(V), density, Poisson, V_ext + phi) reproduces; the
+    Coulomb matrix of the step is symmetric positive semidefinite."""
+    p = inputs.small_problem(8, 4, 4, h=0.5, seed=5, strain=False)
+    g = np.zeros((p.nz, p.ny, p.nx), dtype=np.uint8)
+    g[:, :, 0] = 1
+    g[:, :, -1] = 1
+    gphi = np.zeros_like(p.V)
+    V, E, mu, f, hist = po_oracle.sp_loop_relaxed(p, p.V, g, gphi, 6, 1.0, 1.5, 0.8, 40, anderson_depth=4)
+    assert hist[-1] < 1e-11, hist
+    q = p.with_(V=V.reshape(p.nz, p.ny, p.nx))
+    E2, psi = eig.lowest_dense(kp.assemble(q), 6)
+    kT = po_oracle.KB_EV * 1.5
+    occ = po_oracle.occupations(E2, po_oracle.fermi_level(E2, 1.0, kT), kT)
+    rho = observables.density(psi, occ) / p.h ** 3
+    GV = p.V.reshape(-1) + po_oracle.solve(p.nx, p.ny, p.nz, p.h, g, gphi, rho)
+    assert np.abs(GV - V).max() < 1e-9
+    dens = po_oracle.state_densities(psi)
+    Q = np.stack([po_oracle.solve(p.nx, p.ny, p.nz, p.h, g, gphi, dens[j] / p.h ** 3) for j in range(6)])
+    K = dens @ Q.T
+    assert np.abs(K - K.T).max() < 1e-12 * np.abs(K).max()
+    # positive semidefinite (Kramers partners share their density: rank n/2)
+    assert np.linalg.eigvalsh(0.5 * (K + K.T)).min() > -1e-12 * np.abs(K).max()
+
+
 @pytest.mark.parametrize("rot", ["identity", "device"])
 def test_g_tensor_of_a_doublet_is_gauge_invariant(rot):
     """A gauge change multiplies H(B) by a unitary phase e^{i chi(B)} with
