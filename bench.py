@@ -416,8 +416,11 @@ def run_ours(args, rank, world, local_rank):
                          "max_abs_dE_vs_fp64_ev": float(np.abs(rm.evals - evals_plain).max()),
                          "iterations_fp32": sm["iterations_fp32"], "iterations": sm["iterations"],
                          "max_residual": sm["max_residual"], "precision": "fp32 filter (defect-corrected) + FP64-accurate Rayleigh-Ritz on the tensor cores",
-                         "degree": MIXED_DEGREE}
-        line["stencil_fp32"] = {"bound": "hbm", "kernel": "stencil_kernel<float> defect-corrected step (reads Z_k, Z_k-1, R; writes Z_k+1)",
+                         "degree": MIXED_DEGREE,
+                         "phase_ms": {"fp32_filter": sm["ms_filter_fp32"], "combine_and_fp64_HY": sm["ms_between"],
+                                      "gram": sm["ms_gram"], "small_eig": sm["ms_small"], "rotation": sm["ms_rotate"]},
+                         "residual_history_ev": [float(f"{x:.3g}") for x in sm["res_history"]]}
+        line["stencil_fp32"] = {"bound": "hbm", "kernel": "stencil_plane_kernel (FP32, TMA-staged planes) defect-corrected step (reads Z_k, Z_k-1, R; writes Z_k+1)",
                                 "achieved": b32 / (t32 * 1e-3) / 1e9, "peak": hbm,
                                 "unit": "GB/s", "frac": b32 / (t32 * 1e-3) / 1e9 / hbm,
                                 "frac_of_nominal_8tbs": b32 / (t32 * 1e-3) / 1e9 / 8000.0,

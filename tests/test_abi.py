@@ -80,3 +80,18 @@ def test_host_side_validation_of_the_next_rows(lib):
     assert b"NULL" in lib.khp_last_error()
     assert lib.khp_sp_anderson_reset(None) == 1
     assert lib.khp_poisson_destroy(None) == 0
+
+
+def test_host_side_validation_of_the_added_calls(lib):
+    """khp_filter_step, khp_state_densities, khp_sp_relax_occupations and
+    khp_fermi_level reject NULL handles, bad sizes and bad physics
+    parameters before any CUDA call."""
+    buf = (ctypes.c_double * 64)()
+    assert lib.khp_filter_step(None, buf, None, None, None, buf, 8, 0, 8, 1.0, 0.0, 0.0, 1) == 1
+    assert lib.khp_state_densities(None, buf, 4, buf) == 1
+    mu = ctypes.c_double()
+    assert lib.khp_sp_relax_occupations(None, buf, buf, 4, 1.0, 1e-4, buf, None, buf, 1e-12, None, None) == 1
+    E = (ctypes.c_double * 4)(0.0, 1e-3, 2e-3, 3e-3)
+    assert lib.khp_fermi_level(E, 4, 0.0, 1e-4, ctypes.byref(mu), None) == 1
+    assert lib.khp_fermi_level(E, 4, 1.0, 1e-4, ctypes.byref(mu), None) == 0
+    assert E[0] < mu.value < E[1] + 0.5e-3
