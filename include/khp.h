@@ -249,6 +249,7 @@ khp_status khp_eigensolve(khp_handle h, const khp_solver_opts* opts, double* eva
 /* Flags of khp_eigensolve_batched. */
 #define KHP_BATCH_GRAPH 1      /* capture every round of the batch into one CUDA graph */
 #define KHP_BATCH_AUTOTUNE 2   /* choose block_m by timed trial solves (opts->block_m ignored) */
+#define KHP_BATCH_GROUPED 4    /* one launch per filter step across the problems (precision 2) */
 
 /* Poisson step of the Schroedinger-Poisson loop (Sec. II B).  On the
  * Schroedinger grid (nx, ny, nz, spacing h_nm), the potential phi [V] of the
@@ -378,6 +379,13 @@ khp_status khp_poisson_destroy(khp_poisson p);
  *             the round's topology is unchanged.
  *             KHP_BATCH_AUTOTUNE: block_m is chosen among n+4, n+8, n+12 by
  *             timed trial solves of the smallest problem.
+ *             KHP_BATCH_GROUPED: in rounds where every active problem runs
+ *             the defect-corrected FP32 filter (precision 2), the round runs
+ *             on one stream and step k of all problems' filters is one
+ *             launch of the plane-marching stencil whose work items are
+ *             (problem, z-chunk, vector group, x-y tile), up to 8 problems
+ *             per launch; the results equal the ungrouped ones bit for bit.
+ *             Rounds it does not cover run as without the flag.
  * Warm starts are not accepted here.  Returns NOT_CONVERGED if any problem
  * hit max_iter (all results are still written). */
 khp_status khp_eigensolve_batched(const khp_handle* hs, int count, const khp_solver_opts* opts,

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libkhp.so")
 KHP_OK = 0
 KHP_BATCH_GRAPH = 1
 KHP_BATCH_AUTOTUNE = 2
+KHP_BATCH_GROUPED = 4
 STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KHP_ERR_OOM",
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}

@@ -998,6 +998,7 @@ struct Solve {
         double2* Y = nullptr;
         if (phase == P_DC) {
             CKS(issue_dc());
+            if (deferred) return KHP_OK;   // the caller launches the steps, then finish_issue()
             Y = B[ib[0]];
         } else if (phase == P_FP32) {
             float2* fb[3] = {g->blk32[0], g->blk32[1], g->blk32[2]};
@@ -1037,6 +1038,12 @@ struct Solve {
             CKS(apply_op<double>(g, Y, nullptr, B[ib[3]], m, nlock, na, 1.0, 0.0, 0.0));
             if (phase == P_CLEAN) clean_done++;
         }
+        return issue_tail(Y);
+    }
+
+    // after the filter: Rayleigh-Ritz of Y (W = H Y in B[ib[3]]), copies out
+    khp_status issue_tail(double2* Y) {
+        double2** B = g->blk64;
         st.filter_applies += (long long)(deg + 1) * na / m;
         S.timing = timing;
         CKS(S.rr(Y, B[ib[3]]));
@@ -1044,6 +1051,21 @@ struct Solve {
         if (!timing) timed32 = timed64 = false;
         ++it;
         return KHP_OK;
+    }
+
+    // batched rounds: with `defer` set, issue() of a defect-corrected
+    // iteration enqueues the work before the FP32 filter and hands the
+    // filter's steps to the caller (one grouped launch per step across the
+    // problems of the round); finish_issue() then enqueues the rest
+    std::vector<StencilArgs<float>>* defer = nullptr;
+    bool deferred = false;
+    std::vector<double> dc_D;
+    int dc_iz = 0;
+
+    khp_status finish_issue() {
+        deferred = false;
+        CKS(issue_dc_tail());
+        return issue_tail(g->blk64[ib[0]]);
     }
 
     // Defect-corrected FP32 filter: Y = X diag(D_d) + Z_d with the scalar
@@ -1063,7 +1085,7 @@ struct Solve {
         CK(launch_dc_residual(B[ib[0]], B[ib[3]], R32, zb[0], g->n, m, nlock, na, th.data(), sigma1 / e,
                               g->stream));
         g->launches += 1;
-        if (timing) CK(cudaEventRecord(g->ev0, g->stream));
+        if (timing && !defer) CK(cudaEventRecord(g->ev0, g->stream));
         int iz = 0, ip = -1, in = 1;
         double sigma = sigma1;
         for (int k = 1; k < deg; ++k) {
@@ -1083,7 +1105,8 @@ struct Solve {
             sa.err = g->dflag;
             for (int c = 0; c < 64; ++c) sa.src_coef[c] = (c >= nlock && c < m) ? (float)(al * Dcur[c]) : 0.f;
             fill_coeffs<float>(g, sa.c, al);
-            CK(launch_stencil<float>(sa, g->stream));
+            if (defer) defer->push_back(sa);
+            else CK(launch_stencil<float>(sa, g->stream));
             g->launches += 1;
             for (int c = nlock; c < m; ++c) Dnext[c] = al * (th[c] - cm) * Dcur[c] + ga * Dprev[c];
             std::swap(Dprev, Dcur);
@@ -1092,11 +1115,25 @@ struct Solve {
             ip = iz; iz = in; in = free_;
             sigma = sn;
         }
+        st.launches_fp32 += deg - 1;
+        dc_D = Dcur;
+        dc_iz = iz;
+        if (defer) {
+            // the steps run in the caller's grouped launches: no filter timing
+            deferred = true;
+            timed32 = false;
+            return KHP_OK;
+        }
         if (timing) CK(cudaEventRecord(g->ev1, g->stream));
         timed32 = true;
-        st.launches_fp32 += deg - 1;
-        // Y = X D + Z in FP64, then W = H Y (FP64) on the active columns
-        CK(launch_dc_combine(B[ib[0]], B[ib[3]], zb[iz], B[ib[1]], B[ib[2]], g->n, m, nlock, Dcur.data(),
+        return issue_dc_tail();
+    }
+
+    // Y = X D + Z in FP64, then W = H Y (FP64) on the active columns
+    khp_status issue_dc_tail() {
+        double2** B = g->blk64;
+        float2* zb[3] = {g->blk32[0], g->blk32[1], g->blk32[2]};
+        CK(launch_dc_combine(B[ib[0]], B[ib[3]], zb[dc_iz], B[ib[1]], B[ib[2]], g->n, m, nlock, dc_D.data(),
                              g->stream));
         g->launches += 1;
         CKS(apply_op<double>(g, B[ib[1]], nullptr, B[ib[2]], m, nlock, na, 1.0, 0.0, 0.0));
@@ -1294,7 +1331,75 @@ extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, co
             if (!S[i].finished) act.push_back(i);
         }
         if (act.empty()) break;
-        if (graph) {
+        bool grouped = (flags & KHP_BATCH_GROUPED) != 0;
+        for (int i : act) grouped = grouped && S[i].phase == Solve::P_DC && !S[i].recover;
+        if (grouped) {
+            // the round on the master stream: every problem's work before
+            // its filter, then step k of all filters as grouped launches,
+            // then every problem's combine, H Y and Rayleigh-Ritz
+            for (int i : act) hs[i]->stream = bs.master;
+            struct Restore {
+                std::vector<int>* act; BatchStreams* bs; const khp_handle* hs;
+                ~Restore() { for (int i : *act) hs[i]->stream = bs->own[i]; }
+            } restore{&act, &bs, hs};
+            if (graph) CK(cudaStreamBeginCapture(bs.master, cudaStreamCaptureModeThreadLocal));
+            auto body = [&]() -> khp_status {
+                std::vector<std::vector<StencilArgs<float>>> steps(count);
+                size_t kmax = 0;
+                for (int i : act) {
+                    S[i].defer = &steps[i];
+                    const khp_status r = S[i].issue();
+                    S[i].defer = nullptr;
+                    if (r != KHP_OK) return r;
+                    kmax = std::max(kmax, steps[i].size());
+                }
+                std::vector<const StencilArgs<float>*> ptr;
+                for (size_t k = 0; k < kmax; ++k) {
+                    ptr.clear();
+                    for (int i : act)
+                        if (k < steps[i].size()) ptr.push_back(&steps[i][k]);
+                    const cudaError_t e = launch_stencil_plane_group(ptr.data(), (int)ptr.size(), bs.master);
+                    if (e == cudaErrorNotSupported) {
+                        for (const StencilArgs<float>* a : ptr) CK(launch_stencil<float>(*a, bs.master));
+                    } else {
+                        CK(e);
+                    }
+                }
+                for (int i : act)
+                    if (S[i].deferred) CKS(S[i].finish_issue());
+                return KHP_OK;
+            };
+            const khp_status bsr = body();
+            if (graph) {
+                cudaGraph_t gr = nullptr;
+                const cudaError_t ee = cudaStreamEndCapture(bs.master, &gr);
+                if (bsr != KHP_OK) { if (gr) cudaGraphDestroy(gr); return bsr; }
+                if (ee != cudaSuccess) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return fail(KHP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+                }
+                bool updated = false;
+                if (exec) {
+                    cudaGraphExecUpdateResultInfo info;
+                    updated = cudaGraphExecUpdate(exec, gr, &info) == cudaSuccess;
+                    if (!updated) {
+                        cudaGetLastError();
+                        cudaGraphExecDestroy(exec);
+                        exec = nullptr;
+                    }
+                }
+                if (!updated) {
+                    const cudaError_t ie = cudaGraphInstantiate(&exec, gr, 0);
+                    if (ie != cudaSuccess) { cudaGraphDestroy(gr); exec = nullptr; CK(ie); }
+                    graphs_built++;
+                }
+                cudaGraphDestroy(gr);
+                CK(cudaGraphLaunch(exec, bs.master));
+            } else if (bsr != KHP_OK) {
+                return bsr;
+            }
+            CK(cudaStreamSynchronize(bs.master));
+        } else if (graph) {
             // one CUDA graph per round: fork every active problem's iteration
             // from the master stream onto its own stream and join back
             CK(cudaStreamBeginCapture(bs.master, cudaStreamCaptureModeThreadLocal));

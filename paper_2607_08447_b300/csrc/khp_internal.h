@@ -22,6 +22,10 @@ cudaError_t launch_stencil(const StencilArgs<R>& a, cudaStream_t st);
 // per-point kernel).  prepare_plane() opts its kernels into their shared
 // memory (per device, outside stream capture).
 cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStream_t st);
+// the same step of `count` problems in grouped launches (batched rounds);
+// cudaErrorNotSupported, with nothing launched, when the plane kernel does
+// not cover all of them alike
+cudaError_t launch_stencil_plane_group(const StencilArgs<float>* const* a, int count, cudaStream_t st);
 cudaError_t prepare_plane();
 cudaError_t launch_field_setup(khp_grid* g, const double* V, const double* strain,
                                const double* levers, const double* alpha, int ng, int* bad);

@@ -15,6 +15,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "khp_common.cuh"
 #include "khp_internal.h"
@@ -580,10 +581,11 @@ __device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, 
         : "memory");
 }
 
+// One work item (column group, tile, z-chunk) of one step; a, w and the
+// maps live in the kernel's parameter space (grid constants).
 template <int NB, int PH, bool SRC, int TY, int NSX, int NPS, int VG>
-__global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS, VG>::THREADS, Geo<NB, TY, NSX, NPS, VG>::CTAS_PER_SM)
-    stencil_plane_kernel(const StencilArgs<float> a, const Work w, const __grid_constant__ CUtensorMap mx,
-                         const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap ms) {
+__device__ __forceinline__ void plane_item(const StencilArgs<float>& a, const Work& w, const CUtensorMap& mx,
+                                           const CUtensorMap& mp, const CUtensorMap& ms, int item0) {
     using G = Geo<NB, TY, NSX, NPS, VG>;
     using C = float2;
     constexpr int NS = NB / 3;
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS, VG>::THREADS, Geo<NB, TY
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbuf + NPS * G::PPLANE);
 
     // work item: column group fastest, so the groups of one tile run together
-    int item = blockIdx.x;
+    int item = item0;
     const int g = item % w.ngroups;
     item /= w.ngroups;
     const int txi = item % w.ntx;
@@ -877,6 +879,34 @@ __global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS, VG>::THREADS, Geo<NB, TY
     }
 }
 
+template <int NB, int PH, bool SRC, int TY, int NSX, int NPS, int VG>
+__global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS, VG>::THREADS, Geo<NB, TY, NSX, NPS, VG>::CTAS_PER_SM)
+    stencil_plane_kernel(const __grid_constant__ StencilArgs<float> a, const __grid_constant__ Work w,
+                         const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mp,
+                         const __grid_constant__ CUtensorMap ms) {
+    plane_item<NB, PH, SRC, TY, NSX, NPS, VG>(a, w, mx, mp, ms, blockIdx.x);
+}
+
+// The same step of up to KG problems of a batch in one launch: the work
+// items of problem q are blocks item0[q] .. item0[q + 1] - 1.
+constexpr int KG = 8;
+struct GroupParams {
+    CUtensorMap mx[KG], mp[KG], ms[KG];
+    StencilArgs<float> a[KG];
+    Work w[KG];
+    int item0[KG + 1];
+    int count;
+};
+
+template <int NB, int PH, bool SRC, int TY, int NSX, int NPS, int VG>
+__global__ void __launch_bounds__(Geo<NB, TY, NSX, NPS, VG>::THREADS, Geo<NB, TY, NSX, NPS, VG>::CTAS_PER_SM)
+    stencil_plane_group_kernel(const __grid_constant__ GroupParams gp) {
+    int q = 0;
+    while (q + 1 < gp.count && (int)blockIdx.x >= gp.item0[q + 1]) ++q;
+    plane_item<NB, PH, SRC, TY, NSX, NPS, VG>(gp.a[q], gp.w[q], gp.mx[q], gp.mp[q], gp.ms[q],
+                                              (int)blockIdx.x - gp.item0[q]);
+}
+
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -945,63 +975,78 @@ cudaError_t prep_t() {
 
 }  // namespace plane
 
-cudaError_t prepare_plane() {
-    using namespace plane;
-    cudaError_t e = prep_t<6, PH_NONE, false>();
-    if (e == cudaSuccess) e = prep_t<6, PH_NONE, true>();
-    if (e == cudaSuccess) e = prep_t<6, PH_SYM, false>();
-    if (e == cudaSuccess) e = prep_t<6, PH_SYM, true>();
-    if (e == cudaSuccess) e = prep_t<3, PH_NONE, false>();
-    if (e == cudaSuccess) e = prep_t<3, PH_NONE, true>();
-    return e;
-}
 
-// Takes the step when the plane kernel covers it (FP32, no mask, the
-// crystal or [110] frame, B = 0 or the symmetric gauge, even row length and
-// first column); returns cudaErrorNotSupported otherwise.
-cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStream_t st) {
-    using namespace plane;
+namespace plane {
+
+// Work split and tensor maps of one step; cudaErrorNotSupported when the
+// plane kernel does not cover it (FP32 only: no mask, the crystal or [110]
+// frame, B = 0 or the symmetric gauge, even row length and first column).
+cudaError_t prepare(const StencilArgs<float>& a, int* err, Work* w, CUtensorMap* mx, CUtensorMap* mp,
+                    CUtensorMap* ms, int* mode, long long* items) {
     if (!enabled() || a.mask || (a.ld & 1) || (a.col0 & 1) || a.ncol < 1 || !err) return cudaErrorNotSupported;
     if (a.nb != 6 && a.nb != 3) return cudaErrorNotSupported;
     bool cubic = true;
     for (int d = 0; d < 9; ++d) cubic = cubic && (a.c.hop_nz[d] & ~cubic_nz(d)) == 0;
     if (!cubic) return cudaErrorNotSupported;
-    const int mode = a.phase ? a.phase_mode : PH_NONE;
-    if (mode == PH_GEN || (a.nb == 3 && mode != PH_NONE)) return cudaErrorNotSupported;
-    const long long np = (long long)a.nx * a.ny * a.nz;
-    if (np == 0) return cudaSuccess;
+    *mode = a.phase ? a.phase_mode : PH_NONE;
+    if (*mode == PH_GEN || (a.nb == 3 && *mode != PH_NONE)) return cudaErrorNotSupported;
     const int per_sm = Geo<6, kTY, kNSX, kNPS, kVG>::CTAS_PER_SM;
-    Work w;
-    w.ntx = (a.nx + TX - 1) / TX;
-    w.nty = (a.ny + kTY - 1) / kTY;
-    w.cbase = a.col0 & ~1;
-    w.ngroups = (a.col0 + a.ncol - w.cbase + V - 1) / V;
-    w.err = err;
+    w->ntx = (a.nx + TX - 1) / TX;
+    w->nty = (a.ny + kTY - 1) / kTY;
+    w->cbase = a.col0 & ~1;
+    w->ngroups = (a.col0 + a.ncol - w->cbase + V - 1) / V;
+    w->err = err;
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // z-chunk: the fewest passes over the grid in waves of one CTA per SM
-    // (each chunk also reads its two boundary planes of x)
-    const long long tiles = (long long)w.ntx * w.nty * w.ngroups;
+    // z-chunk: the fewest passes over the grid in waves of the resident
+    // CTAs (each chunk also reads its two boundary planes of x)
+    const long long tiles = (long long)w->ntx * w->nty * w->ngroups;
     int best = a.nz;
     double best_cost = 1e300;
     for (int zch = 4; zch <= a.nz + 3; ++zch) {
         const int zc = std::min(zch, a.nz);
-        const long long items = tiles * ((a.nz + zc - 1) / zc);
-        const double waves = std::ceil((double)items / (sms * per_sm));
+        const long long it = tiles * ((a.nz + zc - 1) / zc);
+        const double waves = std::ceil((double)it / (sms * per_sm));
         const double cost = waves * (zc + 0.7);
         if (cost < best_cost - 1e-9) { best_cost = cost; best = zc; }
         if (zch >= a.nz) break;
     }
-    w.zch = best;
-    w.nzc = (a.nz + w.zch - 1) / w.zch;
-    const long long items = tiles * w.nzc;
-    if (items > 0x7fffffffLL) return cudaErrorNotSupported;
+    w->zch = std::max(1, best);
+    w->nzc = (a.nz + w->zch - 1) / w->zch;
+    *items = tiles * w->nzc;
+    if (*items > 0x7fffffffLL) return cudaErrorNotSupported;
+    std::memset(mp, 0, sizeof(*mp));
+    std::memset(ms, 0, sizeof(*ms));
+    if (!make_map(mx, a.x, a.ld, a.nb, a.nx, a.ny, a.nz, HX, kTY + 2)) return cudaErrorNotSupported;
+    if (a.prev && !make_map(mp, a.prev, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
+    if (a.src && !make_map(ms, a.src, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
+    return cudaSuccess;
+}
+
+template <int NB, int PH, bool SRC>
+cudaError_t launch_group_t(const GroupParams& gp, unsigned items, cudaStream_t st) {
+    using G = Geo<NB, kTY, kNSX, kNPS, kVG>;
+    stencil_plane_group_kernel<NB, PH, SRC, kTY, kNSX, kNPS, kVG><<<items, G::THREADS, G::SMEM, st>>>(gp);
+    return cudaGetLastError();
+}
+
+template <int NB, int PH, bool SRC>
+cudaError_t prep_group_t() {
+    return cudaFuncSetAttribute(stencil_plane_group_kernel<NB, PH, SRC, kTY, kNSX, kNPS, kVG>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<NB, kTY, kNSX, kNPS, kVG>::SMEM);
+}
+
+}  // namespace plane
+
+cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStream_t st) {
+    using namespace plane;
+    if ((long long)a.nx * a.ny * a.nz == 0) return cudaSuccess;
+    Work w;
     CUtensorMap mx, mp, ms;
-    std::memset(&mp, 0, sizeof(mp));
-    std::memset(&ms, 0, sizeof(ms));
-    if (!make_map(&mx, a.x, a.ld, a.nb, a.nx, a.ny, a.nz, HX, kTY + 2)) return cudaErrorNotSupported;
-    if (a.prev && !make_map(&mp, a.prev, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
-    if (a.src && !make_map(&ms, a.src, a.ld, a.nb, a.nx, a.ny, a.nz, TX, kTY)) return cudaErrorNotSupported;
+    int mode = PH_NONE;
+    long long items = 0;
+    const cudaError_t e = prepare(a, err, &w, &mx, &mp, &ms, &mode, &items);
+    if (e != cudaSuccess) return e;
     const unsigned n = (unsigned)items;
     if (a.nb == 6) {
         if (mode == PH_SYM)
@@ -1012,6 +1057,90 @@ cudaError_t launch_stencil_plane(const StencilArgs<float>& a, int* err, cudaStre
     }
     return a.src ? launch_t<3, PH_NONE, true>(a, w, n, mx, mp, ms, st)
                  : launch_t<3, PH_NONE, false>(a, w, n, mx, mp, ms, st);
+}
+
+// The same filter step of several problems as grouped launches: the
+// problems are partitioned by gauge mode, and each part goes out in
+// launches of up to KG problems.  cudaErrorNotSupported, with nothing
+// launched, unless the plane kernel covers every step with the same bands
+// and source term.
+cudaError_t launch_stencil_plane_group(const StencilArgs<float>* const* a, int count, cudaStream_t st) {
+    using namespace plane;
+    if (count < 1) return cudaSuccess;
+    struct Prep {
+        Work w;
+        CUtensorMap mx, mp, ms;
+        int mode;
+        long long items;
+    };
+    std::vector<Prep> pr(count);
+    for (int i = 0; i < count; ++i) {
+        const StencilArgs<float>& ai = *a[i];
+        if ((long long)ai.nx * ai.ny * ai.nz == 0) return cudaErrorNotSupported;
+        const cudaError_t e = prepare(ai, ai.err, &pr[i].w, &pr[i].mx, &pr[i].mp, &pr[i].ms, &pr[i].mode,
+                                      &pr[i].items);
+        if (e != cudaSuccess) return e;
+        if (ai.nb != a[0]->nb || (ai.src != nullptr) != (a[0]->src != nullptr)) return cudaErrorNotSupported;
+    }
+    const bool src = a[0]->src != nullptr;
+    GroupParams gp;
+    for (int mode : {PH_NONE, PH_SYM}) {
+        int q = 0;
+        long long total = 0;
+        auto flush = [&]() -> cudaError_t {
+            if (q == 0) return cudaSuccess;
+            gp.count = q;
+            gp.item0[q] = (int)total;
+            const unsigned n = (unsigned)total;
+            cudaError_t e;
+            if (a[0]->nb == 6) {
+                if (mode == PH_SYM)
+                    e = src ? launch_group_t<6, PH_SYM, true>(gp, n, st) : launch_group_t<6, PH_SYM, false>(gp, n, st);
+                else
+                    e = src ? launch_group_t<6, PH_NONE, true>(gp, n, st) : launch_group_t<6, PH_NONE, false>(gp, n, st);
+            } else {
+                e = src ? launch_group_t<3, PH_NONE, true>(gp, n, st) : launch_group_t<3, PH_NONE, false>(gp, n, st);
+            }
+            q = 0;
+            total = 0;
+            return e;
+        };
+        for (int i = 0; i < count; ++i) {
+            if (pr[i].mode != mode) continue;
+            if (q == KG || total + pr[i].items > 0x7fffffffLL) {
+                const cudaError_t e = flush();
+                if (e != cudaSuccess) return e;
+            }
+            gp.a[q] = *a[i];
+            gp.w[q] = pr[i].w;
+            gp.mx[q] = pr[i].mx;
+            gp.mp[q] = pr[i].mp;
+            gp.ms[q] = pr[i].ms;
+            gp.item0[q] = (int)total;
+            total += pr[i].items;
+            ++q;
+        }
+        const cudaError_t e = flush();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t prepare_plane() {
+    using namespace plane;
+    cudaError_t e = prep_t<6, PH_NONE, false>();
+    if (e == cudaSuccess) e = prep_t<6, PH_NONE, true>();
+    if (e == cudaSuccess) e = prep_t<6, PH_SYM, false>();
+    if (e == cudaSuccess) e = prep_t<6, PH_SYM, true>();
+    if (e == cudaSuccess) e = prep_t<3, PH_NONE, false>();
+    if (e == cudaSuccess) e = prep_t<3, PH_NONE, true>();
+    if (e == cudaSuccess) e = prep_group_t<6, PH_NONE, false>();
+    if (e == cudaSuccess) e = prep_group_t<6, PH_NONE, true>();
+    if (e == cudaSuccess) e = prep_group_t<6, PH_SYM, false>();
+    if (e == cudaSuccess) e = prep_group_t<6, PH_SYM, true>();
+    if (e == cudaSuccess) e = prep_group_t<3, PH_NONE, false>();
+    if (e == cudaSuccess) e = prep_group_t<3, PH_NONE, true>();
+    return e;
 }
 
 // ------------------------------------------------------------ field set-up

@@ -285,10 +285,12 @@ def _projections(p):
 
 
 def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precision=0, refine_sweeps=-1,
-                  tol=1e-9, seed=1, graph=True, autotune=False, allow_not_converged=False, projections="tensor"):
+                  tol=1e-9, seed=1, graph=True, autotune=False, allow_not_converged=False, projections="tensor",
+                  grouped=False):
     """Solve every grid's lowest states in one khp_eigensolve_batched call
-    (lock-step rounds, optionally one CUDA graph per round and an autotuned
-    block width).  Returns a list of SolveResult."""
+    (lock-step rounds, optionally one CUDA graph per round, an autotuned
+    block width, and grouped filter launches across the problems).
+    Returns a list of SolveResult."""
     lib = _lib.load()
     count = len(grids)
     opts = _lib.SolverOpts()
@@ -302,7 +304,8 @@ def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precisio
     evals = np.zeros((count, n_states))
     res = np.zeros((count, n_states))
     st = (_lib.Stats * count)()
-    flags = (_lib.KHP_BATCH_GRAPH if graph else 0) | (_lib.KHP_BATCH_AUTOTUNE if autotune else 0)
+    flags = ((_lib.KHP_BATCH_GRAPH if graph else 0) | (_lib.KHP_BATCH_AUTOTUNE if autotune else 0)
+             | (_lib.KHP_BATCH_GROUPED if grouped else 0))
     status = lib.khp_eigensolve_batched(hs, count, ctypes.byref(opts), _lib.dptr(evals), ptrs,
                                         _lib.dptr(res), st, flags)
     _lib.check(status, allow=(4,) if allow_not_converged else ())

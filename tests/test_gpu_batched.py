@@ -56,6 +56,25 @@ def test_batched_mixed_and_autotune(khp):
         assert np.abs(r.evals - w).max() <= 1e-10
 
 
+@pytest.mark.parametrize("graph", [True, False])
+def test_batched_grouped_filter_launches(khp, graph):
+    """Defect-corrected FP32 filter (precision 2) with one grouped launch per
+    filter step across the problems (KHP_BATCH_GROUPED; the B = 0 point and
+    the B != 0 points go out in separate groups): eigenvalues equal to the
+    ungrouped batch and to the dense oracle."""
+    probs = _sweep(5)
+    grids = [khp.KPGrid.from_problem(p) for p in probs]
+    kw = dict(block_m=16, degree=40, precision=2, tol=1e-10)
+    rg = khp.solve_batched(grids, 8, graph=graph, grouped=True, **kw)
+    ru = khp.solve_batched(grids, 8, graph=graph, grouped=False, **kw)
+    for p, a, b in zip(probs, rg, ru):
+        assert np.abs(a.evals - b.evals).max() <= 1e-14
+        w, _ = eig.lowest_dense(kp.assemble(p), 8)
+        assert np.abs(a.evals - w).max() <= 1e-10
+        V = a.evecs.cpu().numpy()
+        assert np.abs(V.conj().T @ V - np.eye(8)).max() < 1e-12
+
+
 def test_batched_rejects_bad_input(khp):
     probs = _sweep(2)
     grids = [khp.KPGrid.from_problem(p) for p in probs]
