@@ -393,6 +393,7 @@ def run_ours(args, rank, world, local_rank):
                     "iterations": rw.stats["iterations"],
                     "note": "warm start from the previous solve's eigenvectors, V changed by 0.1 meV smooth noise"}
     line["projections"] = _projections_bench(grid, p.n_unknowns, SOLVE_KW["block_m"], hbm, torch)
+    step32 = _fp32_step_bench(grid, p, SOLVE_KW["block_m"], hbm, torch)
 
     # mixed precision to the same tolerance: every filter apply in FP32,
     # defect-corrected by the FP64 residual; FP64 H Y and Rayleigh-Ritz
@@ -463,6 +464,7 @@ def run_ours(args, rank, world, local_rank):
     for key in ("mixed", "stencil_fp32"):
         if key in line:
             line[key] = line.pop(key)
+    line["stencil_fp32_step"] = step32
     line["roofline"] = roofline
     line["clocks"] = clocks
     line["gpu_launches"] = int(sum(s["kernel_launches"] for s in stats))
@@ -622,6 +624,38 @@ def _gtensor_bench(p, dev, torch, khp, j_ci):
         out["jpar_range_ev"] = [float(jl.min()), float(jl.max())]
     g.close()
     return out
+
+
+def _fp32_step_bench(grid, p, m, hbm, torch):
+    """The FP32 filter step alone at full width (khp_filter_step: the
+    defect-corrected form y = alpha H x + beta x + gamma prev + c_col src
+    on all m columns of the C2 blocks), 20 launches timed with CUDA events
+    on the handle's stream after 3 warm-up launches.  Algorithmic bytes per
+    point-vector: x, prev and src read and y written (4 x 48 B) plus the
+    per-point field tables (onsite 24 B, phases 72 B) over the m columns."""
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    blocks = [torch.randn((p.n_unknowns, m), dtype=torch.complex64, device="cuda", generator=gen) for _ in range(4)]
+    x, prev, src, y = blocks
+    coef = np.linspace(-1.0, 1.0, m)
+    for _ in range(3):
+        grid.filter_step(x, y, 0.3, -0.2, -0.5, prev=prev, src=src, src_coef=coef)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(grid.stream)
+    K = 20
+    for _ in range(K):
+        grid.filter_step(x, y, 0.3, -0.2, -0.5, prev=prev, src=src, src_coef=coef)
+    e1.record(grid.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    bpv = 4 * 48.0 + 96.0 / m
+    byts = p.n_points * m * bpv
+    del blocks, x, prev, src, y
+    return {"bound": "hbm", "kernel": "stencil_plane_kernel, defect-corrected FP32 step, full width",
+            "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": byts / (ms * 1e-3) / 1e9 / hbm, "frac_of_nominal_8tbs": byts / (ms * 1e-3) / 1e9 / 8000.0,
+            "ms_per_launch": ms, "algorithmic_bytes_per_launch": byts, "bytes_per_pv": bpv,
+            "point_vectors_per_launch": p.n_points * m}
 
 
 def _projections_bench(grid, N, m, hbm, torch):

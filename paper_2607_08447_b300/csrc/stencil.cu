@@ -685,8 +685,7 @@ __device__ __forceinline__ void plane_item(const StencilArgs<float>& a, const Wo
         for (int k = 0; k < 6; ++k) o[k] = __ldg(a.onsite + p * 6 + k);
         if (PH == PH_SYM) {
 #pragma unroll
-            for (int d = 0; d < 9; ++d)
-                if (a.c.pair_phase & (1u << d)) cs[d] = __ldg(a.phase + p * 9 + d);
+            for (int d = 0; d < 9; ++d) cs[d] = __ldg(a.phase + p * 9 + d);
         }
     };
     float o_cur[6], o_nxt[6];
@@ -717,7 +716,10 @@ __device__ __forceinline__ void plane_item(const StencilArgs<float>& a, const Wo
         constexpr unsigned nzd = cubic_nz(d);
         constexpr unsigned need = need_of(nzd);
         constexpr int dx = pair_dx(d), dy = pair_dy(d), dz = pair_dz(d);
-        const bool ph = PH == PH_SYM && (a.c.pair_phase & (1u << d));
+        // in the symmetric gauge every pair takes the phase path (pairs
+        // without a phase carry (1, 0)): no runtime branch in the body, so
+        // the shared-memory loads of later pairs can be scheduled early
+        constexpr bool ph = PH == PH_SYM;
         C u[6][VG], v[6][VG];
 #pragma unroll
         for (int o = 0; o < 3; ++o) {
@@ -786,7 +788,8 @@ __device__ __forceinline__ void plane_item(const StencilArgs<float>& a, const Wo
             }
             if (z + 2 <= zlast + 1) issued_x = z + 2;
         }
-        // centre: on-site orbital matrix (+ beta), spin-orbit and Zeeman
+        // centre: on-site orbital matrix (+ beta), spin-orbit and Zeeman;
+        // all entries are applied (zeros add nothing), with no runtime branch
         {
             C xs[6][VG];
 #pragma unroll
@@ -796,18 +799,16 @@ __device__ __forceinline__ void plane_item(const StencilArgs<float>& a, const Wo
             for (int k = 0; k < 6; ++k) oo[k] = a.alpha * o_cur[k];
 #pragma unroll
             for (int k = 0; k < 3; ++k) oo[k] += a.beta;
-            sym3<float, VG, false, NS>(acc, oo, a.c.onsite_nz | 7u, xs);
+            sym3<float, VG, false, NS>(acc, oo, 63u, xs);
 #pragma unroll
-            for (int b = 0; b < (NB == 6 ? 6 : 0); ++b) {
-                const unsigned rowm = a.c.soz_nz[b];
+            for (int b = 0; b < (NB == 6 ? 6 : 0); ++b)
 #pragma unroll
                 for (int b2 = 0; b2 < 6; ++b2)
 #pragma unroll
                     for (int t = 0; t < VG; ++t) {
-                        if (rowm & (1u << (2 * b2))) axpy_c<float>(acc[b][t], a.c.soz_re[b][b2], xs[b2][t]);
-                        if (rowm & (2u << (2 * b2))) axpy_mi<float>(acc[b][t], -a.c.soz_im[b][b2], xs[b2][t]);
+                        axpy_c<float>(acc[b][t], a.c.soz_re[b][b2], xs[b2][t]);
+                        axpy_mi<float>(acc[b][t], -a.c.soz_im[b][b2], xs[b2][t]);
                     }
-            }
         }
         // the pairs inside plane z
         pair(acc, z, std::integral_constant<int, 0>{});
@@ -999,7 +1000,8 @@ cudaError_t prepare(const StencilArgs<float>& a, int* err, Work* w, CUtensorMap*
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // z-chunk: the fewest passes over the grid in waves of the resident
-    // CTAs (each chunk also reads its two boundary planes of x)
+    // CTAs; a chunk costs its planes plus about three planes of start-up
+    // (its two boundary planes of x and the first copies in flight)
     const long long tiles = (long long)w->ntx * w->nty * w->ngroups;
     int best = a.nz;
     double best_cost = 1e300;
@@ -1007,7 +1009,7 @@ cudaError_t prepare(const StencilArgs<float>& a, int* err, Work* w, CUtensorMap*
         const int zc = std::min(zch, a.nz);
         const long long it = tiles * ((a.nz + zc - 1) / zc);
         const double waves = std::ceil((double)it / (sms * per_sm));
-        const double cost = waves * (zc + 0.7);
+        const double cost = waves * (zc + 3.0);
         if (cost < best_cost - 1e-9) { best_cost = cost; best = zc; }
         if (zch >= a.nz) break;
     }
