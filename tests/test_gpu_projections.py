@@ -65,6 +65,40 @@ def _check_gram(G, Y, W):
     return err.max()
 
 
+def test_gram_worst_case_digit_patterns(khp):
+    """The exact FP32 accumulation of the digit products holds at its bound:
+    every entry of Y equal to the largest value whose 49-bit balanced
+    base-128 digits are all extreme and of one sign (leading digit 127, the
+    others +63), so that every digit product of a level has the same sign
+    and every row sits at its exponent block's maximum.  G = Y^H Y is then
+    N v^2 (up to the sign pattern of the columns), computed exactly in
+    integers here."""
+    p, g = _grid(khp)
+    N, m = p.n_unknowns, 24
+    # F = 2^49 - 1 - (64 + 64*128 + ... + 64*128^5): digits u_s = 127 of
+    # F + the balancing offset; v = 16 F / 2^52 lies in [1, 2)
+    bal = sum(64 * 128 ** k for k in range(6))
+    F = 2 ** 49 - 1 - bal
+    mant = 16 * F
+    v = mant / 2.0 ** 52
+    assert 1.0 <= v < 2.0 and float(mant) == mant
+    signs = np.where(np.arange(m) % 3 == 1, -1.0, 1.0)
+    Y = np.empty((N, m), dtype=np.complex128)
+    Y.real = v * signs[None, :]
+    Y.imag = v * signs[None, ::-1]
+    G, _ = g.project(Y, None, method=0)
+    # exact: G_ij = N v^2 (s_i s_j + t_i t_j) + i N v^2 (s_i t_j - t_i s_j)
+    t = signs[::-1]
+    v2 = mant * mant                                  # v^2 = v2 / 2^104, exact integer
+    for i in range(m):
+        for j in range(m):
+            re = N * v2 * int(signs[i] * signs[j] + t[i] * t[j])
+            im = N * v2 * int(signs[i] * t[j] - t[i] * signs[j])
+            ref = complex(re / 2.0 ** 104, im / 2.0 ** 104)
+            scale = 2 * N * v * v
+            assert abs(G[i, j] - ref) <= 4 * EPS49 * scale, (i, j, G[i, j], ref)
+
+
 @pytest.mark.parametrize("m", [1, 5, 8, 24, 32])
 def test_gram_matches_extended_precision(khp, m):
     p, g = _grid(khp)
