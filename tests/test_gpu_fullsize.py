@@ -243,3 +243,58 @@ def test_c2_h0_residuals_through_oracle_csr(khp, c2_h0_csr, kw):
     rq = np.real(np.einsum("ij,ij->j", V.conj(), H @ V))
     assert np.abs(rq - r.evals).max() <= 1e-12
     g.close()
+
+
+def test_c2_filter_steps_sampled_against_oracle_rows(khp):
+    """The two stencil kernels in the bench's launch configuration at full
+    size (2.21M unknowns, 24 columns): the defect-corrected FP32 step of the
+    plane-marching kernel (y = alpha H x + beta x + gamma prev + c_col src)
+    and the FP64 apply of the per-point kernel, checked on 3000 sampled rows
+    against the oracle's CSR rows applied to the same inputs in FP64."""
+    p = inputs.config2()
+    g = khp.KPGrid.from_problem(p)
+    H = kp.assemble(p).tocsr()
+    N, ld = p.n_unknowns, 24
+    rng = np.random.default_rng(77)
+    rows = np.sort(rng.choice(N, 3000, replace=False))
+    Hs = H[rows]
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    x, prev, src = (torch.randn((N, ld), dtype=torch.complex64, device="cuda", generator=gen) for _ in range(3))
+    y = torch.zeros((N, ld), dtype=torch.complex64, device="cuda")
+    coef = np.linspace(-0.7, 0.9, ld)
+    al, be, ga = 0.41, -0.63, -0.37
+    g.filter_step(x, y, al, be, ga, prev=prev, src=src, src_coef=coef)
+    xd = x.cpu().numpy().astype(np.complex128)
+    ref = (al * (Hs @ xd) + be * xd[rows] + ga * prev.cpu().numpy()[rows].astype(np.complex128)
+           + src.cpu().numpy()[rows].astype(np.complex128) * coef)
+    got = y.cpu().numpy()[rows].astype(np.complex128)
+    scale = np.abs(al * (Hs @ xd)).max() + np.abs(xd).max() + 2 * np.abs(prev.cpu().numpy()).max()
+    assert np.abs(got - ref).max() <= 2e-6 * scale
+    del x, prev, src, y
+    X = torch.randn((N, ld), dtype=torch.complex128, device="cuda", generator=gen)
+    Y = g.apply(X, precision=0)
+    refd = Hs @ X.cpu().numpy()
+    assert np.abs(Y.cpu().numpy()[rows] - refd).max() <= 1e-13 * np.abs(refd).max()
+    g.close()
+
+
+def test_c4_batched_residuals_through_oracle_csr(khp):
+    """Two points of the 64-point sweep at full size (the bench's
+    batched configuration: grouped filter launches, defect-corrected FP32
+    filter, degree 200, block width 16, tol 1e-10 eV): residuals and
+    Rayleigh quotients of the 12 returned states through the oracle's CSR
+    matrices, orthonormality."""
+    probs = inputs.config4()[:2]
+    grids = [khp.KPGrid.from_problem(q) for q in probs]
+    rs = khp.solve_batched(grids, 12, block_m=16, degree=200, precision=2, tol=1e-10, seed=1, graph=True,
+                           grouped=True)
+    for q, r in zip(probs, rs):
+        H = kp.assemble(q)
+        V = r.evecs.cpu().numpy()
+        res = np.linalg.norm(H @ V - V * r.evals[None, :], axis=0)
+        assert res.max() <= 2e-10, res
+        assert np.abs(V.conj().T @ V - np.eye(12)).max() < 1e-12
+        rq = np.real(np.einsum("ij,ij->j", V.conj(), H @ V))
+        assert np.abs(rq - r.evals).max() <= 1e-12
+    for gr in grids:
+        gr.close()
