@@ -661,8 +661,9 @@ def _fp32_step_bench(grid, p, m, hbm, torch):
 def _projections_bench(grid, N, m, hbm, torch):
     """The Rayleigh-Ritz contractions at the bench's block size: Gram
     (G = Y^H Y, S = Y^H HY; reads 2 blocks) and rotation (X = Y Q, HX = W Q;
-    reads 2, writes 2 blocks), on the tensor cores (split-digit BF16
-    products, 28 digit pairs) and on the FP64 ALUs.  CUDA events on the
+    reads 2, writes 2 blocks), as split-digit BF16 products (28 digit
+    pairs) on the tcgen05 tensor cores ("tensor", the solver's default) and
+    through mma.sync ("mma"), and on the FP64 ALUs.  CUDA events on the
     handle's stream around 5 calls after 2 warm-up calls."""
     gen = torch.Generator(device="cuda").manual_seed(7)
     Y = torch.randn((N, m), dtype=torch.complex128, device="cuda", generator=gen)
@@ -686,19 +687,23 @@ def _projections_bench(grid, N, m, hbm, torch):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 5
 
-    for name, method in (("tensor", 0), ("fp64", 1)):
+    for name, method in (("tensor", 0), ("mma", 2), ("fp64", 1)):
         tg = t(lambda: grid.project(Y, W, method=method))
         tr = t(lambda: grid.rotate(Y, Q, W, method=method, out=X, out_w=HX))
         out[name] = {"gram_ms": tg, "rotate_ms": tr,
                      "gram_gbs": 2 * blk / (tg * 1e-3) / 1e9, "rotate_gbs": 4 * blk / (tr * 1e-3) / 1e9}
     mma_flop = 28 * 2.0 * (2 * m) ** 2 * N * 2          # per contraction pair (G and S, or X and HX)
+    for name in ("tensor", "mma"):
+        tc = out[name]
+        tc["gram_hbm_frac"] = tc["gram_gbs"] / hbm
+        tc["rotate_hbm_frac"] = tc["rotate_gbs"] / hbm
+        tc["gram_bf16_tflops"] = mma_flop / (tc["gram_ms"] * 1e-3) / 1e12
+        tc["rotate_bf16_tflops"] = mma_flop / (tc["rotate_ms"] * 1e-3) / 1e12
     tc = out["tensor"]
-    tc["gram_hbm_frac"] = tc["gram_gbs"] / hbm
-    tc["rotate_hbm_frac"] = tc["rotate_gbs"] / hbm
-    tc["gram_bf16_tflops"] = mma_flop / (tc["gram_ms"] * 1e-3) / 1e12
-    tc["rotate_bf16_tflops"] = mma_flop / (tc["rotate_ms"] * 1e-3) / 1e12
     out["speedup_gram"] = out["fp64"]["gram_ms"] / tc["gram_ms"]
     out["speedup_rotate"] = out["fp64"]["rotate_ms"] / tc["rotate_ms"]
+    out["tcgen05_vs_mma_gram"] = out["mma"]["gram_ms"] / tc["gram_ms"]
+    out["tcgen05_vs_mma_rotate"] = out["mma"]["rotate_ms"] / tc["rotate_ms"]
     out["note"] = ("times include the library's stream synchronisation and the m x m host copy; "
                    "algorithmic bytes: Gram 2 blocks read, rotation 2 read + 2 written (N x m complex128)")
     return out

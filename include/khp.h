@@ -85,10 +85,13 @@ typedef struct {
  *  warm_start_dev optional complex128 [N][warm_cols] start vectors (row-major);
  *                 remaining columns are random.  NULL for a cold start.
  *  projections    how the Rayleigh-Ritz contractions (Gram matrices and
- *                 subspace rotation) run: 0 = on the tensor cores as exact
+ *                 subspace rotation) run: 0 = on the 5th-generation tensor
+ *                 cores (tcgen05.mma, accumulators in TMEM) as exact
  *                 split-digit BF16 products recombined in FP64 (FP64
  *                 accurate; block_m <= 32, wider blocks use 1); 1 = FP64
- *                 ALU.  Zero-initialised options select 0. */
+ *                 ALU; 2 = the same split-digit products through the
+ *                 warp-level mma.sync path.  Zero-initialised options
+ *                 select 0. */
 typedef struct {
     int n_states;
     int block_m;
@@ -221,11 +224,14 @@ khp_status khp_filter_step(khp_handle h, const void* x_dev, const void* prev_dev
  *  khp_rotate: X = Y Q and (W_dev given) HX = W Q, Q m x m complex128
  *    row-major in host memory; X may be Y and HX may be W (in place).
  *  Y_dev, W_dev, X_dev, HX_dev: complex128 [N][m] row-major on the device.
- *  method 0: tensor cores, exact split-digit BF16 products recombined in FP64
- *    (m <= 32); 1: FP64 ALU.  Both synchronise the handle's stream; the
- *    first call allocates the handle's reduction scratch.
+ *  method 0: tcgen05 tensor cores (accumulators in TMEM), exact split-digit
+ *    BF16 products recombined in FP64 (m <= 32); 1: FP64 ALU; 2: the same
+ *    split-digit products through mma.sync (m <= 32).  All synchronise the
+ *    handle's stream; the first call allocates the handle's reduction
+ *    scratch.
  * Errors: INVALID_ARG for NULL pointers, m outside 1..64, a bad method or
- * method 0 with m > 32. */
+ * method 0 or 2 with m > 32; CUDA when a tensor-core pipeline wait of
+ * method 0 ran out (bounded waits). */
 khp_status khp_project(khp_handle h, const void* Y_dev, const void* W_dev, int m, int method,
                        double* G_host, double* S_host);
 /* khp_project over `rows` rows instead of the handle's N (any block of

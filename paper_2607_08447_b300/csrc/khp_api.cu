@@ -470,7 +470,7 @@ static khp_status create_grid(khp_handle* out, int nx, int ny, int nz, double h_
     for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreate(&g->evp[k]);
     if (e != cudaSuccess || (e = cudaEventCreate(&g->ev0)) != cudaSuccess || (e = cudaEventCreate(&g->ev1)) != cudaSuccess)
         return bail(fail(KHP_ERR_CUDA, std::string("event: ") + cudaGetErrorString(e)));
-    if ((e = prepare_oz()) != cudaSuccess)
+    if ((e = prepare_oz()) != cudaSuccess || (e = prepare_tc()) != cudaSuccess)
         return bail(fail(KHP_ERR_CUDA, std::string("projection set-up: ") + cudaGetErrorString(e)));
     if ((e = prepare_plane()) != cudaSuccess)
         return bail(fail(KHP_ERR_CUDA, std::string("stencil set-up: ") + cudaGetErrorString(e)));
@@ -641,18 +641,23 @@ khp_status khp_project_rows(khp_handle g, const void* Y_dev, const void* W_dev, 
     if (rows < 1) return fail(KHP_ERR_INVALID_ARG, "rows must be >= 1");
     if (!Y_dev || !G_host || (W_dev && !S_host)) return fail(KHP_ERR_INVALID_ARG, "Y, G or S is NULL");
     if (m < 1 || m > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "m out of range 1..64");
-    if (method != 0 && method != 1) return fail(KHP_ERR_INVALID_ARG, "method must be 0 or 1");
-    if (method == 0 && !oz_supported(m, m)) return fail(KHP_ERR_INVALID_ARG, "method 0 takes m <= 32");
+    if (method < 0 || method > 2) return fail(KHP_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+    if (method != 1 && !oz_supported(m, m)) return fail(KHP_ERR_INVALID_ARG, "methods 0 and 2 take m <= 32");
     CKS(ensure_partial(g));
     const int nblk = std::min(dense_blocks(rows), dense_blocks(g->n));
     const double2* Y = (const double2*)Y_dev;
     const double2* W = (const double2*)W_dev;
-    if (method == 0) CK(launch_gram_oz(Y, W, rows, m, 0, m, g->partial, nblk, g->small, g->stream));
+    CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+    if (method == 0) CK(launch_gram_tc(Y, W, rows, m, 0, m, g->partial, nblk, g->small, g->dflag, g->stream));
+    else if (method == 2) CK(launch_gram_oz(Y, W, rows, m, 0, m, g->partial, nblk, g->small, g->stream));
     else CK(launch_gram(Y, W, rows, m, 0, m, g->partial, nblk, g->small, g->stream));
     CK(cudaMemcpyAsync(G_host, g->small, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, g->stream));
     if (W)
         CK(cudaMemcpyAsync(S_host, g->small + m * m, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, g->stream));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    if (flag & 8) return fail(KHP_ERR_CUDA, "tensor-core pipeline wait ran out");
     return KHP_OK;
 }
 
@@ -668,21 +673,28 @@ khp_status khp_rotate(khp_handle g, const void* Y_dev, const void* W_dev, const 
     if (!g) return fail(KHP_ERR_INVALID_ARG, "handle is NULL");
     if (!Y_dev || !Q_host || !X_dev || (W_dev && !HX_dev)) return fail(KHP_ERR_INVALID_ARG, "Y, Q, X or HX is NULL");
     if (m < 1 || m > KHP_MAX_M) return fail(KHP_ERR_INVALID_ARG, "m out of range 1..64");
-    if (method != 0 && method != 1) return fail(KHP_ERR_INVALID_ARG, "method must be 0 or 1");
-    if (method == 0 && !oz_supported(m, m)) return fail(KHP_ERR_INVALID_ARG, "method 0 takes m <= 32");
+    if (method < 0 || method > 2) return fail(KHP_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+    if (method != 1 && !oz_supported(m, m)) return fail(KHP_ERR_INVALID_ARG, "methods 0 and 2 take m <= 32");
     CKS(ensure_partial(g));
     const int nblk = dense_blocks(g->n);
     double2* Qd = g->small + 2 * m * m;
     CK(cudaMemcpyAsync(Qd, Q_host, sizeof(double2) * m * m, cudaMemcpyHostToDevice, g->stream));
     const double2* Y = (const double2*)Y_dev;
     const double2* W = (const double2*)W_dev;
+    CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
     if (method == 0)
+        CK(launch_rotate_tc(Y, W, m, 0, m, Qd, m, nullptr, (double2*)X_dev, (double2*)HX_dev, g->n, nullptr, nblk,
+                            nullptr, g->dflag, g->stream));
+    else if (method == 2)
         CK(launch_rotate_oz(Y, W, m, 0, m, Qd, m, nullptr, (double2*)X_dev, (double2*)HX_dev, g->n, nullptr, nblk,
                             nullptr, g->stream));
     else
         CK(launch_rotate(Y, W, m, 0, m, Qd, m, nullptr, (double2*)X_dev, (double2*)HX_dev, g->n, nullptr, nblk,
                          nullptr, g->stream));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    if (flag & 8) return fail(KHP_ERR_CUDA, "tensor-core pipeline wait ran out");
     return KHP_OK;
 }
 
@@ -695,7 +707,7 @@ struct Solver {
     khp_grid* g;
     int m;
     int nblk;
-    bool tc = false; // Gram and rotation on the tensor cores (split-digit, FP64 accurate)
+    int proj = 1;    // Gram and rotation: 0 tcgen05, 1 FP64 ALU, 2 mma.sync (split-digit, FP64 accurate)
     double2* G;      // [2 m m]: G then S
     double2* Q;      // [m m]
     double* theta;   // [m]
@@ -705,12 +717,16 @@ struct Solver {
     bool rr_timed = false;
     khp_status rr(double2* Y, double2* W) {
         if (timing) CK(cudaEventRecord(g->evp[0], g->stream));
-        if (tc) CK(launch_gram_oz(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        if (proj == 0) CK(launch_gram_tc(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->dflag, g->stream));
+        else if (proj == 2) CK(launch_gram_oz(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
         else CK(launch_gram(Y, W, g->n, m, 0, m, g->partial, nblk, G, g->stream));
         if (timing) CK(cudaEventRecord(g->evp[1], g->stream));
         CK(launch_small(G, G + m * m, m, 1, Q, theta, g->dflag, g->stream));
         if (timing) CK(cudaEventRecord(g->evp[2], g->stream));
-        if (tc)
+        if (proj == 0)
+            CK(launch_rotate_tc(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->dflag,
+                                g->stream));
+        else if (proj == 2)
             CK(launch_rotate_oz(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
         else
             CK(launch_rotate(Y, W, m, 0, m, Q, m, theta, Y, W, g->n, (double*)g->partial, nblk, res, g->stream));
@@ -720,10 +736,14 @@ struct Solver {
         return KHP_OK;
     }
     khp_status orth(double2* Y) {
-        if (tc) CK(launch_gram_oz(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->stream));
+        if (proj == 0) CK(launch_gram_tc(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->dflag, g->stream));
+        else if (proj == 2) CK(launch_gram_oz(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->stream));
         else CK(launch_gram(Y, nullptr, g->n, m, 0, m, g->partial, nblk, G, g->stream));
         CK(launch_small(G, nullptr, m, 0, Q, nullptr, g->dflag, g->stream));
-        if (tc)
+        if (proj == 0)
+            CK(launch_rotate_tc(Y, nullptr, m, 0, m, Q, m, nullptr, Y, nullptr, g->n, nullptr, nblk, nullptr, g->dflag,
+                                g->stream));
+        else if (proj == 2)
             CK(launch_rotate_oz(Y, nullptr, m, 0, m, Q, m, nullptr, Y, nullptr, g->n, nullptr, nblk, nullptr, g->stream));
         else
             CK(launch_rotate(Y, nullptr, m, 0, m, Q, m, nullptr, Y, nullptr, g->n, nullptr, nblk, nullptr, g->stream));
@@ -791,7 +811,7 @@ struct Solve {
     enum { P_FP32, P_CLEAN, P_FP64, P_DC };
     int phase = P_FP64, clean_sweeps = 0, clean_done = 0, stall = 0;
     double best = 1e300, floor32 = 0;
-    bool converged = false, finished = false, timing = true, trace = false, dc = false;
+    bool converged = false, finished = false, timing = true, trace = false, trace_cols = false, dc = false;
     bool timed32 = false, timed64 = false, recover = false, need_bound = false;
     int it = 0;
     // decisions for the next issue()
@@ -812,8 +832,9 @@ struct Solve {
         if (!(opts->tol_ev > 0.0)) return fail(KHP_ERR_INVALID_ARG, "tol_ev must be > 0");
         if (opts->warm_start_dev && (opts->warm_cols < 1 || opts->warm_cols > m))
             return fail(KHP_ERR_INVALID_ARG, "warm_cols must be in 1..block_m");
-        if (opts->projections < 0 || opts->projections > 1)
-            return fail(KHP_ERR_INVALID_ARG, "projections must be 0 (tensor cores) or 1 (FP64 ALU)");
+        if (opts->projections < 0 || opts->projections > 2)
+            return fail(KHP_ERR_INVALID_ARG,
+                        "projections must be 0 (tcgen05 tensor cores), 1 (FP64 ALU) or 2 (mma.sync tensor cores)");
         return KHP_OK;
     }
 
@@ -842,7 +863,7 @@ struct Solve {
             g->bound_valid = true;
         }
         S.g = g; S.m = m; S.nblk = dense_blocks(g->n);
-        S.tc = o.projections == 0 && oz_supported(m, m);
+        S.proj = (o.projections != 1 && tc_supported(m, m)) ? o.projections : 1;
         S.G = g->small; S.Q = g->small + 2 * m * m;
         S.theta = g->dvec; S.res = g->dvec + m;
         max_iter = o.max_iter > 0 ? o.max_iter : 1000;
@@ -854,9 +875,11 @@ struct Solve {
         clean_sweeps = mixed ? (o.refine_sweeps < 0 ? 1 : o.refine_sweeps) : 0;
         // residual floor of FP32 blocks (measured on B300: ~2.5e-7 x lambda_max)
         floor32 = 3e-7 * lam_up;
-        // KHP_TRACE=1 in the environment prints one line per outer iteration
+        // KHP_TRACE=1 in the environment prints one line per outer iteration,
+        // KHP_TRACE=2 adds the Ritz values and residuals of every column
         const char* tr = std::getenv("KHP_TRACE");
-        trace = tr && tr[0] == '1';
+        trace = tr && (tr[0] == '1' || tr[0] == '2');
+        trace_cols = tr && tr[0] == '2';
         double2** B = g->blk64;
         CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
         CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, o.seed, g->mask, g->stream, g->nb));
@@ -913,13 +936,17 @@ struct Solve {
             std::fprintf(stderr, "khp it %d phase %d nlock %d deg %d a %.6e low %.6e rmax %.3e t %.1f ms\n", it - 1,
                          phase, nlock, deg, a, low, rm, ms);
         }
+        if (trace_cols) {
+            for (int i = 0; i < m; ++i)
+                std::fprintf(stderr, "khp col it %d %d theta %.17e res %.3e\n", it, i, th[i], rs[i]);
+        }
         return KHP_OK;
     }
 
     // host decisions; sets finished when the solve is over
     khp_status decide() {
         recover = false;
-        if (flags & 8) return fail(KHP_ERR_CUDA, "stencil copy pipeline wait ran out");
+        if (flags & 8) return fail(KHP_ERR_CUDA, "stencil copy or tensor-core pipeline wait ran out");
         if (flags & 4) return fail(KHP_ERR_BREAKDOWN, "non-finite Ritz values");
         double rmax = 0;
         for (int i = 0; i < n; ++i) rmax = std::max(rmax, std::isnan(rs[i]) ? HUGE_VAL : rs[i]);

@@ -60,6 +60,18 @@ cudaError_t launch_rotate_oz(const double2* Y, const double2* W, int ld, int col
                              int mq, const double* theta, double2* X, double2* HX, long long rows,
                              double* res_partial, int nblk, double* res_out, cudaStream_t st);
 
+// ozaki_tc.cu: the same contractions and outputs with the digit products on
+// the 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM); m, mq
+// <= 32 (tc_supported).  A bounded wait that runs out sets bit 8 of *err.
+// prepare_tc() opts the kernels into their shared memory.
+bool tc_supported(int m, int mq);
+cudaError_t prepare_tc();
+cudaError_t launch_gram_tc(const double2* Y, const double2* W, long long rows, int ld, int col0, int m,
+                           double2* partial, int nblk, double2* out, int* err, cudaStream_t st);
+cudaError_t launch_rotate_tc(const double2* Y, const double2* W, int ld, int col0, int m, const double2* Q,
+                             int mq, const double* theta, double2* X, double2* HX, long long rows,
+                             double* res_partial, int nblk, double* res_out, int* err, cudaStream_t st);
+
 // mode 0: Q = R^-1 of the (equilibrated) Cholesky factor of G (G = R^H R)
 // mode 1: generalized Rayleigh-Ritz  S q = theta G q  ->  theta ascending,
 //         Q = R^-1 Qhat (columns G-orthonormal)

@@ -168,8 +168,9 @@ class KPGrid:
 
     def project(self, Y, W=None, method=0):
         """G = Y^H Y and S = Y^H W (Hermitian, from their upper triangles):
-        method 0 on the tensor cores (split-digit products, FP64 accurate,
-        m <= 32), 1 on the FP64 ALUs.  Returns numpy (G, S or None)."""
+        method 0 on the tcgen05 tensor cores (split-digit products, FP64
+        accurate, m <= 32), 1 on the FP64 ALUs, 2 the same products through
+        mma.sync.  Returns numpy (G, S or None)."""
         Y = _dev(Y, torch.complex128, self.device)
         W = _dev(W, torch.complex128, self.device)
         m = Y.shape[1]
@@ -276,12 +277,16 @@ class KPGrid:
 
 
 def _projections(p):
-    """'tensor' (tensor-core split-digit products, the default) or 'fp64'."""
-    if p in ("tensor", 0):
+    """'tensor' (split-digit products on the tcgen05 tensor cores, the
+    default), 'fp64' (FP64 ALU) or 'mma' (the same products through the
+    warp-level mma.sync tensor-core path)."""
+    if p in ("tensor", "tcgen05", 0):
         return 0
     if p in ("fp64", 1):
         return 1
-    raise ValueError("projections must be 'tensor' or 'fp64'")
+    if p in ("mma", 2):
+        return 2
+    raise ValueError("projections must be 'tensor', 'fp64' or 'mma'")
 
 
 def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precision=0, refine_sweeps=-1,

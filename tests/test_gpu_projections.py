@@ -1,7 +1,8 @@
 """Rayleigh-Ritz contractions on the tensor cores (split-digit BF16 products
 recombined in FP64) against FP64 references: the Gram matrices G = Y^H Y,
 S = Y^H (H Y) and the rotation X = Y Q, through the C-ABI (khp_project,
-khp_rotate), and the eigensolver with either projection path.
+khp_rotate), and the eigensolver with each projection path.  Method 0 is
+the tcgen05 path (accumulators in TMEM), 2 the mma.sync path, 1 FP64 ALU.
 
 Accuracy bar: the split keeps 49 bits below each block's exponent bound and
 accumulates exactly, so each entry must agree with an extended-precision
@@ -65,7 +66,8 @@ def _check_gram(G, Y, W):
     return err.max()
 
 
-def test_gram_worst_case_digit_patterns(khp):
+@pytest.mark.parametrize("method", [0, 2])
+def test_gram_worst_case_digit_patterns(khp, method):
     """The exact FP32 accumulation of the digit products holds at its bound:
     every entry of Y equal to the largest value whose 49-bit balanced
     base-128 digits are all extreme and of one sign (leading digit 127, the
@@ -86,7 +88,7 @@ def test_gram_worst_case_digit_patterns(khp):
     Y = np.empty((N, m), dtype=np.complex128)
     Y.real = v * signs[None, :]
     Y.imag = v * signs[None, ::-1]
-    G, _ = g.project(Y, None, method=0)
+    G, _ = g.project(Y, None, method=method)
     # exact: G_ij = N v^2 (s_i s_j + t_i t_j) + i N v^2 (s_i t_j - t_i s_j)
     t = signs[::-1]
     v2 = mant * mant                                  # v^2 = v2 / 2^104, exact integer
@@ -99,12 +101,12 @@ def test_gram_worst_case_digit_patterns(khp):
             assert abs(G[i, j] - ref) <= 4 * EPS49 * scale, (i, j, G[i, j], ref)
 
 
-@pytest.mark.parametrize("m", [1, 5, 8, 24, 32])
+@pytest.mark.parametrize("m", [1, 5, 8, 12, 24, 32])
 def test_gram_matches_extended_precision(khp, m):
     p, g = _grid(khp)
     Y = _block(p.n_unknowns, m, seed=40 + m)
     W = g.apply(torch.from_numpy(Y)).cpu().numpy()
-    for method in (0, 1):
+    for method in (0, 1, 2):
         G, S = g.project(Y, W, method=method)
         assert _check_gram(G, Y, Y) <= 16 * EPS49, method
         assert _check_gram(S, Y, W) <= 16 * EPS49, method
@@ -114,7 +116,8 @@ def test_gram_matches_extended_precision(khp, m):
         assert _check_gram(Gonly, Y, Y) <= 16 * EPS49, method
 
 
-def test_gram_column_scales_and_zero_columns(khp):
+@pytest.mark.parametrize("method", [0, 2])
+def test_gram_column_scales_and_zero_columns(khp, method):
     """Columns spread over 60 decades, one all-zero column: the per-chunk
     column exponents keep every entry accurate relative to its own norms."""
     p, g = _grid(khp)
@@ -123,22 +126,23 @@ def test_gram_column_scales_and_zero_columns(khp):
     cs[7] = 0.0
     Y = _block(p.n_unknowns, m, seed=77, col_scale=cs)
     W = g.apply(torch.from_numpy(Y)).cpu().numpy()
-    G, S = g.project(Y, W, method=0)
+    G, S = g.project(Y, W, method=method)
     assert _check_gram(G, Y, Y) <= 16 * EPS49
     assert _check_gram(S, Y, W) <= 16 * EPS49
     assert np.all(G[7] == 0) and np.all(G[:, 7] == 0)
 
 
-def test_gram_propagates_nan(khp):
+@pytest.mark.parametrize("method", [0, 2])
+def test_gram_propagates_nan(khp, method):
     p, g = _grid(khp)
     Y = _block(p.n_unknowns, 8, seed=5)
     Y[1234, 3] = np.nan
-    G, _ = g.project(Y, None, method=0)
+    G, _ = g.project(Y, None, method=method)
     assert np.isnan(G[3, 3].real)
     assert np.isfinite(G[0, 1]) and np.isfinite(G[5, 6])
 
 
-@pytest.mark.parametrize("m", [1, 5, 24, 32])
+@pytest.mark.parametrize("m", [1, 5, 12, 24, 32])
 def test_rotation_matches_extended_precision(khp, m):
     p, g = _grid(khp)
     rs = 10.0 ** np.random.default_rng(3).uniform(-20, 20, p.n_unknowns)
@@ -148,7 +152,7 @@ def test_rotation_matches_extended_precision(khp, m):
     Q = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
     Q[:, 0] *= 1e-12
     Ql = Q.real.astype(np.longdouble), Q.imag.astype(np.longdouble)
-    for method in (0, 1):
+    for method in (0, 1, 2):
         X, HX = g.rotate(Y, Q, W, method=method)
         for A, B in ((Y, X), (W, HX)):
             Al = A.real.astype(np.longdouble), A.imag.astype(np.longdouble)
@@ -161,16 +165,37 @@ def test_rotation_matches_extended_precision(khp, m):
             assert (err / scale).max() <= 16 * EPS49, method
 
 
-def test_rotation_in_place(khp):
+@pytest.mark.parametrize("method", [0, 2])
+def test_rotation_in_place(khp, method):
     p, g = _grid(khp)
     m = 24
     Y = torch.from_numpy(_block(p.n_unknowns, m, seed=9)).cuda()
     W = torch.from_numpy(_block(p.n_unknowns, m, seed=10)).cuda()
     rng = np.random.default_rng(1)
     Q = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
-    X_ref, HX_ref = g.rotate(Y, Q, W, method=0)
-    g.rotate(Y, Q, W, method=0, out=Y, out_w=W)
+    X_ref, HX_ref = g.rotate(Y, Q, W, method=method)
+    g.rotate(Y, Q, W, method=method, out=Y, out_w=W)
     assert torch.equal(Y, X_ref) and torch.equal(W, HX_ref)
+
+
+def test_rotation_without_w_and_nan(khp):
+    """X = Y Q alone (the re-orthonormalisation), and a NaN in one row of Y
+    reaching only that row of X."""
+    p, g = _grid(khp)
+    m = 16
+    Y = _block(p.n_unknowns, m, seed=12)
+    Y[777, 2] = np.nan
+    rng = np.random.default_rng(4)
+    Q = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    X, HX = g.rotate(Y, Q, None, method=0)
+    assert HX is None
+    X = X.cpu().numpy()
+    assert np.isnan(X[777]).all()
+    ok = np.ones(p.n_unknowns, dtype=bool)
+    ok[777] = False
+    ref = Y[ok] @ Q
+    scale = np.outer(np.linalg.norm(Y[ok], axis=1), np.linalg.norm(Q, axis=0))
+    assert (np.abs(X[ok] - ref) / scale).max() <= 16 * EPS49
 
 
 @pytest.mark.parametrize("case", ["config1", "field"])
@@ -184,8 +209,10 @@ def test_eigensolve_tensor_vs_fp64_projections(khp, case):
     g = khp.KPGrid.from_problem(p)
     rt = g.eigensolve(**kw, tol=1e-10, seed=2, projections="tensor")
     rf = g.eigensolve(**kw, tol=1e-10, seed=2, projections="fp64")
+    rm = g.eigensolve(**kw, tol=1e-10, seed=2, projections="mma")
     assert rt.stats["converged"] == kw["n_states"]
     assert np.abs(rt.evals - rf.evals).max() <= 1e-12
+    assert np.abs(rm.evals - rf.evals).max() <= 1e-12
     H = kp.assemble(p)
     V = rt.evecs.cpu().numpy()
     res = np.linalg.norm(H @ V - V * rt.evals[None, :], axis=0)
