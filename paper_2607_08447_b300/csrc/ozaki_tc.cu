@@ -55,8 +55,8 @@ __device__ __forceinline__ void split7(double v, int emax, uint32_t (&d)[kS]) {
     long long F = 0;
     if (ex != 0 && emax < 2047) {
         const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = emax - ex + 4;   // >= 4
-        if (sh < 64) F = (long long)((mant >> sh) + ((mant >> (sh - 1)) & 1ull));
+        const int sh = emax - ex + 4;   // >= 4; round half up with one variable shift
+        if (sh <= 64) F = (long long)(((mant >> (sh - 1)) + 1ull) >> 1);
         if (b < 0) F = -F;
     }
     const long long G = F + (long long)oz::kBal;
@@ -92,7 +92,7 @@ __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return lo 
 // shared memory.
 constexpr int kGThreads = 512;
 constexpr int kProducers = kGThreads - 32;
-constexpr int kItemsP = (2 * 16 * kMaxM + kProducers - 1) / kProducers;   // split items per producer (3)
+constexpr int kItemsP = (2 * 4 * (kMaxM / 8) * 32 + kProducers - 1) / kProducers;   // split items per producer (3)
 
 // G = F + kBal for the balanced digits of split7 (64-bit, two registers)
 __device__ __forceinline__ long long balanced(double v, int emax) {
@@ -101,8 +101,8 @@ __device__ __forceinline__ long long balanced(double v, int emax) {
     long long F = 0;
     if (ex != 0 && emax < 2047) {
         const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = emax - ex + 4;
-        if (sh < 64) F = (long long)((mant >> sh) + ((mant >> (sh - 1)) & 1ull));
+        const int sh = emax - ex + 4;   // round half up with one variable shift
+        if (sh <= 64) F = (long long)(((mant >> (sh - 1)) + 1ull) >> 1);
         if (b < 0) F = -F;
     }
     return F + (long long)oz::kBal;
@@ -120,7 +120,7 @@ struct GramGeo {
     size_t tile, buf, acc;
     __host__ __device__ GramGeo(int m, bool w)
         : RP(round16(2 * m)), RA((w ? 2 : 1) * round16(2 * m)), nbuf(2), tile((size_t)RA * 128),
-          buf((size_t)(6 * RA + 128) * 128), acc((size_t)(w ? 2 : 1) * round16(2 * m) * round16(2 * m) * 8) {
+          buf((size_t)(6 * RA + 128) * 128), acc((size_t)(w ? 2 : 1) * round16(2 * m) * (round16(2 * m) + 1) * 8) {
         if (bytes(2) > kSmemMax) nbuf = 1;
     }
     __host__ __device__ size_t bytes(int nb) const { return 1024 + nb * buf + acc + 2 * 128 * sizeof(int) + 64; }
@@ -147,8 +147,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int nmat = hasW ? 2 : 1;
     const GramGeo geo(m, hasW);
     const int RP = geo.RP, nbuf = geo.nbuf;
+    const int RD = RP + 1;   // running-sum row stride (odd: the lanes of a warp, one row each, hit distinct banks)
     unsigned char* dig = sm;                                          // [nbuf][buf]
-    double* D = reinterpret_cast<double*>(dig + nbuf * geo.buf);     // [nmat][RP][RP] FP64 running sums
+    double* D = reinterpret_cast<double*>(dig + nbuf * geo.buf);     // [nmat][RP][RD] FP64 running sums
     int* ea = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(D) + geo.acc);   // [2][128] block exponents
     uint64_t* bars = reinterpret_cast<uint64_t*>(ea + 2 * 128);       // [2] one per digit buffer
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -241,9 +242,22 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int nq = RP / 4, jb = (warp >> 2) * nq;
     const bool vrow = i_row < 2 * m || (hasW && i_row >= RP && i_row < RP + 2 * m);
     const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    double* Drow = D + (size_t)(i_row < RP ? 0 : 1) * RP * RP + (size_t)(i_row < RP ? i_row : i_row - RP) * RP;
+    double* Drow = D + (size_t)(i_row < RP ? 0 : 1) * RP * RD + (size_t)(i_row < RP ? i_row : i_row - RP) * RD;
 
-    const int nitems = nmat * 16 * m;   // split items: (matrix, 4-row group, complex column)
+    // split items (matrix, 4-row group k4, complex column cc): a warp's 32
+    // lanes take 8 consecutive columns (lane & 7) of 4 consecutive groups
+    // (lane >> 3), so that its 8-byte digit stores spread over the banks;
+    // item groups of 32: (matrix, k4 / 4, column octet)
+    const int ncg = (m + 7) / 8;
+    const int nitems = nmat * 4 * ncg * 32;
+    auto item = [&](int it, int& mat, int& k4, int& cc) {
+        const int l = it & 31, grp = it >> 5;
+        const int cg = grp % ncg, rest = grp / ncg;
+        const int k4hi = rest & 3;
+        mat = rest >> 2;
+        k4 = 4 * k4hi + (l >> 3);
+        cc = 8 * cg + (l & 7);
+    };
     long long c = 0;                    // chunks split so far
     long long ncommit = 0;              // chunks whose products were issued
     bool failed = false;
@@ -277,10 +291,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
 #pragma unroll
                 for (int u = 0; u < kItemsP; ++u) {
                     const int it = ptid + u * kProducers;
-                    if (it < nitems) {
-                        const int mat = it / (16 * m);
-                        const int rem = it - mat * 16 * m;
-                        const int k4 = rem / m, cc = rem - k4 * m;
+                    int mat, k4, cc;
+                    item(it, mat, k4, cc);
+                    if (it < nitems && cc < m) {
                         const double2* src = (mat ? W : Y) + (rs0 + 4 * k4) * ld + col0 + cc;
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
@@ -291,9 +304,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 for (int u = 0; u < kItemsP; ++u) {
                     const int it = ptid + u * kProducers;
                     if (it >= nitems) break;
-                    const int mat = it / (16 * m);
-                    const int rem = it - mat * 16 * m;
-                    const int k4 = rem / m, cc = rem - k4 * m;
+                    int mat, k4, cc;
+                    item(it, mat, k4, cc);
+                    if (cc >= m) continue;
                     const int rre = mat * RP + cc, rim = mat * RP + m + cc;
                     const int er = eac[rre], ei = eac[rim];
                     long long gr[4], gi[4];
@@ -385,14 +398,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
         double re, im;
         if (which == 0) {
             const double* Dm = D;
-            re = Dm[i * RP + j] + Dm[(i + m) * RP + j + m];
-            im = Dm[i * RP + j + m] - Dm[(i + m) * RP + j];
+            re = Dm[i * RD + j] + Dm[(i + m) * RD + j + m];
+            im = Dm[i * RD + j + m] - Dm[(i + m) * RD + j];
         } else {
             // S_ij = sum_k conj(Y_ki) W_kj:  with T[a][b] = W_a . Y_b,
             // Re = T[j][i] + T[j+m][i+m], Im = T[j+m][i] - T[j][i+m]
-            const double* T = D + (size_t)RP * RP;
-            re = T[j * RP + i] + T[(j + m) * RP + i + m];
-            im = T[(j + m) * RP + i] - T[j * RP + i + m];
+            const double* T = D + (size_t)RP * RD;
+            re = T[j * RD + i] + T[(j + m) * RD + i + m];
+            im = T[(j + m) * RD + i] - T[j * RD + i + m];
         }
         partial[(size_t)blockIdx.x * E + e] = make_double2(re, im);
     }
