@@ -91,7 +91,15 @@ typedef struct {
  *                 accurate; block_m <= 32, wider blocks use 1); 1 = FP64
  *                 ALU; 2 = the same split-digit products through the
  *                 warp-level mma.sync path.  Zero-initialised options
- *                 select 0. */
+ *                 select 0.
+ *  start          start block when warm_start_dev is NULL: 0 = random
+ *                 (counter-based, from seed); 1 = coarse grid: the lowest
+ *                 block_m states of the grid of every second point at twice
+ *                 the spacing (on-site fields restricted, same material,
+ *                 field and gauge), solved loosely (tolerance max(tol_ev,
+ *                 1e-4) eV, degree 60) and prolongated trilinearly; falls
+ *                 back to 0 when that grid has fewer than 4 (block_m + 8)
+ *                 unknowns or block_m + 8 > 64.  khp_eigensolve only. */
 typedef struct {
     int n_states;
     int block_m;
@@ -104,6 +112,7 @@ typedef struct {
     const void* warm_start_dev;
     int warm_cols;
     int projections;
+    int start;
 } khp_solver_opts;
 
 /* Per-solve statistics (optional output).  The filter timings come from
@@ -145,6 +154,8 @@ typedef struct {
     double bytes_rr;           /* algorithmic HBM bytes of the Gram and rotation passes */
     int n_history;             /* outer iterations recorded (incl. the start)  */
     double res_history[KHP_STATS_HISTORY]; /* max residual [eV] after each (first 64) */
+    double ms_start;           /* wall time of the coarse-grid start [ms]      */
+    int start_iterations;      /* outer iterations of the coarse-grid solve    */
 } khp_stats;
 
 /* Create a grid handle.

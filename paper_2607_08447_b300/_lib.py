@@ -40,7 +40,7 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("tol_ev", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("warm_start_dev", ctypes.c_void_p),
-                ("warm_cols", ctypes.c_int), ("projections", ctypes.c_int)]
+                ("warm_cols", ctypes.c_int), ("projections", ctypes.c_int), ("start", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("autotune_ms", ctypes.c_double),
                 ("ms_gram", ctypes.c_double), ("ms_small", ctypes.c_double), ("ms_rotate", ctypes.c_double),
                 ("ms_between", ctypes.c_double), ("bytes_rr", ctypes.c_double), ("n_history", ctypes.c_int),
-                ("res_history", ctypes.c_double * 64)]
+                ("res_history", ctypes.c_double * 64), ("ms_start", ctypes.c_double),
+                ("start_iterations", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "res_history"}

@@ -498,6 +498,8 @@ khp_status khp_create_grid_h0(khp_handle* out, int nx, int ny, int nz, double h_
 khp_status khp_destroy(khp_handle g) {
     if (!g) return KHP_OK;
     cudaStreamSynchronize(g->stream);
+    if (g->coarse) khp_destroy(g->coarse);
+    if (g->coarse_x) cudaFree(g->coarse_x);
     free_ws(g);
     if (g->onsite64) cudaFree(g->onsite64);
     if (g->onsite32) cudaFree(g->onsite32);
@@ -514,6 +516,65 @@ khp_status khp_destroy(khp_handle g) {
     for (int k = 0; k < 5; ++k)
         if (g->evp[k]) cudaEventDestroy(g->evp[k]);
     delete g;
+    return KHP_OK;
+}
+
+// Gershgorin upper bound of the spectrum once the on-site block is set (and
+// the device flag word of the field set-up, when bad is given)
+static khp_status finish_fields(khp_grid* g, int* bad) {
+    double* partial = g->dvec + 2 * KHP_MAX_M;   // 6*KHP_MAX_M doubles available
+    const int nb = 4 * KHP_MAX_M;
+    CK(launch_onsite_rowmax(g, partial, nb, g->dvec));
+    CK(cudaMemcpyAsync(g->host_pinned, g->dvec, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    if (bad) CK(cudaMemcpyAsync(bad, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (bad && *bad) return KHP_OK;
+    double soz = 0;
+    for (int b = 0; b < 6; ++b) {
+        double s = 0;
+        for (int b2 = 0; b2 < 6; ++b2) s += std::hypot(g->soz_re[b][b2], g->soz_im[b][b2]);
+        soz = std::max(soz, s);
+    }
+    double hops = 0;
+    for (int d = 0; d < 9; ++d) hops += 2.0 * sym_rowsum_max(g->hop[d]);
+    g->onsite_absmax = g->host_pinned[0] + soz + hops;
+    g->fields_set = true;
+    g->bound_valid = false;
+    return KHP_OK;
+}
+
+// The coarse grid of the coarse-grid start: every second point at twice the
+// spacing, the same material, frame, field and gauge (symmetric gauge about
+// the fine grid's centre), on-site block restricted from the fine one.
+static khp_status coarse_prepare(khp_grid* g) {
+    if (!g->coarse) {
+        khp_handle gc = nullptr;
+        CKS(create_grid(&gc, g->nx / 2, g->ny / 2, g->nz / 2, 2.0 * g->h, &g->mat, g->rot, nullptr, g->stream,
+                        g->nb));
+        g->coarse = gc;
+        if (g->mask) CK(cudaMalloc(&gc->mask, gc->np));
+        gc->ctr[0] = 0.5 * (g->nx + 1) * g->h;
+        gc->ctr[1] = 0.5 * (g->ny + 1) * g->h;
+        gc->ctr[2] = 0.5 * (g->nz + 1) * g->h;
+        gc->ctr_set = 1;
+    }
+    if (g->coarse_valid) return KHP_OK;
+    khp_grid* gc = g->coarse;
+    for (int k = 0; k < 3; ++k) gc->B[k] = g->B[k];
+    gc->gauge = g->gauge;
+    gc->has_phase = g->has_phase;
+    gc->phase_mode = g->phase_mode;
+    gc->pair_phase = g->pair_phase;
+    gc->has_strain = g->has_strain;
+    build_operator(gc);
+    if (gc->has_phase && !gc->phase64) {
+        CK(cudaMalloc(&gc->phase64, sizeof(double2) * 18 * gc->np));
+        CK(cudaMalloc(&gc->phase32, sizeof(float2) * 18 * gc->np));
+    }
+    CK(launch_restrict_onsite(g, gc));
+    CK(launch_phase_setup(gc));
+    CKS(finish_fields(gc, nullptr));
+    g->coarse_valid = true;
     return KHP_OK;
 }
 
@@ -548,29 +609,13 @@ khp_status khp_set_potential_strain_field(khp_handle g, const double* V_dev, con
     CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
     g->has_strain = strain_dev != nullptr;
     CK(launch_field_setup(g, V_dev, strain_dev, n_gates ? levers_dev : nullptr, alpha_host, n_gates, g->dflag));
-    // Gershgorin upper bound of the spectrum
-    double* partial = g->dvec + 2 * KHP_MAX_M;   // 6*KHP_MAX_M doubles available
-    const int nb = 4 * KHP_MAX_M;
-    CK(launch_onsite_rowmax(g, partial, nb, g->dvec));
-    CK(cudaMemcpyAsync(g->host_pinned, g->dvec, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    g->coarse_valid = false;
     int bad = 0;
-    CK(cudaMemcpyAsync(&bad, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
+    CKS(finish_fields(g, &bad));
     if (bad) {
         g->fields_set = false;
         return fail(KHP_ERR_INVALID_ARG, "non-finite value in V, strain or levers");
     }
-    double soz = 0;
-    for (int b = 0; b < 6; ++b) {
-        double s = 0;
-        for (int b2 = 0; b2 < 6; ++b2) s += std::hypot(g->soz_re[b][b2], g->soz_im[b][b2]);
-        soz = std::max(soz, s);
-    }
-    double hops = 0;
-    for (int d = 0; d < 9; ++d) hops += 2.0 * sym_rowsum_max(g->hop[d]);
-    g->onsite_absmax = g->host_pinned[0] + soz + hops;
-    g->fields_set = true;
-    g->bound_valid = false;
     return KHP_OK;
 }
 
@@ -832,6 +877,8 @@ struct Solve {
         if (!(opts->tol_ev > 0.0)) return fail(KHP_ERR_INVALID_ARG, "tol_ev must be > 0");
         if (opts->warm_start_dev && (opts->warm_cols < 1 || opts->warm_cols > m))
             return fail(KHP_ERR_INVALID_ARG, "warm_cols must be in 1..block_m");
+        if (opts->start < 0 || opts->start > 1)
+            return fail(KHP_ERR_INVALID_ARG, "start must be 0 (random) or 1 (coarse grid)");
         if (opts->projections < 0 || opts->projections > 2)
             return fail(KHP_ERR_INVALID_ARG,
                         "projections must be 0 (tcgen05 tensor cores), 1 (FP64 ALU) or 2 (mma.sync tensor cores)");
@@ -852,6 +899,64 @@ struct Solve {
         g->launches = 0;
         need_bound = !g->bound_valid;
         if (need_bound) CKS(lanczos_issue(g, (int)std::min<long long>(40, g->n), o.seed));
+        return KHP_OK;
+    }
+
+    // Coarse-grid start: the lowest m states of the 2x coarser grid (a loose
+    // solve: tolerance max(tol, 1e-4 eV), degree 60, block m + 8), prolongated
+    // trilinearly into all m columns of X.  `started` stays false (random
+    // start) when the coarse grid is too small for that block.
+    khp_status coarse_start(double2* X, bool& started) {
+        started = false;
+        const int mc = m + 8;
+        const long long npc = (long long)(g->nx / 2) * (g->ny / 2) * (g->nz / 2);
+        if (mc > KHP_MAX_M || npc < 1 || (long long)g->nb * npc < 4LL * mc) return KHP_OK;
+        const auto tc0 = std::chrono::steady_clock::now();
+        CKS(coarse_prepare(g));
+        khp_grid* gc = g->coarse;
+        if (g->coarse_m < m) {
+            if (g->coarse_x) cudaFree(g->coarse_x);
+            g->coarse_x = nullptr;
+            g->coarse_m = 0;
+            CK(cudaMalloc(&g->coarse_x, sizeof(double2) * gc->n * m));
+            g->coarse_m = m;
+        }
+        khp_solver_opts oc{};
+        oc.n_states = m;
+        oc.block_m = mc;
+        oc.degree = 60;
+        oc.max_iter = 60;
+        oc.precision = o.precision == 0 ? 0 : 2;
+        oc.refine_sweeps = o.refine_sweeps;
+        oc.tol_ev = std::max(o.tol_ev, 1e-4);
+        oc.seed = o.seed;
+        oc.projections = o.projections;
+        std::vector<double> ev(m);
+        khp_stats sc_st{};
+        {
+            Solve sc;
+            sc.timing = false;
+            CKS(sc.begin_a(gc, &oc));
+            CK(cudaStreamSynchronize(gc->stream));
+            CKS(sc.begin_b());
+            CK(cudaStreamSynchronize(gc->stream));
+            CKS(sc.absorb());
+            for (;;) {
+                CKS(sc.decide());
+                if (sc.finished) break;
+                CKS(sc.issue());
+                CK(cudaStreamSynchronize(gc->stream));
+                CKS(sc.absorb());
+            }
+            const khp_status es = sc.end(ev.data(), g->coarse_x, nullptr, &sc_st);
+            if (es != KHP_OK && es != KHP_ERR_NOT_CONVERGED) return es;
+            g_err.clear();
+        }
+        CK(launch_prolong(gc, g->coarse_x, m, g, X, m, m));
+        g->launches += 1 + sc_st.kernel_launches;
+        st.start_iterations = sc_st.iterations;
+        st.ms_start = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
+        started = true;
         return KHP_OK;
     }
 
@@ -882,8 +987,12 @@ struct Solve {
         trace_cols = tr && tr[0] == '2';
         double2** B = g->blk64;
         CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
-        CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, o.seed, g->mask, g->stream, g->nb));
-        g->launches += 1;
+        bool started = false;
+        if (o.start == 1 && !o.warm_start_dev) CKS(coarse_start(B[ib[0]], started));
+        if (!started) {
+            CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, o.seed, g->mask, g->stream, g->nb));
+            g->launches += 1;
+        }
         if (o.warm_start_dev)
             CK(cudaMemcpy2DAsync(B[ib[0]], sizeof(double2) * m, o.warm_start_dev, sizeof(double2) * o.warm_cols,
                                  sizeof(double2) * o.warm_cols, g->n, cudaMemcpyDeviceToDevice, g->stream));
@@ -1261,6 +1370,7 @@ extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, co
     if (!hs || !opts || !evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
     if (count < 1) return fail(KHP_ERR_INVALID_ARG, "count must be >= 1");
     if (opts->warm_start_dev) return fail(KHP_ERR_INVALID_ARG, "warm starts are per problem: not in batched mode");
+    if (opts->start != 0) return fail(KHP_ERR_INVALID_ARG, "the coarse-grid start is for khp_eigensolve");
     khp_solver_opts o = *opts;
     const int n = o.n_states;
     int dev0 = -1;

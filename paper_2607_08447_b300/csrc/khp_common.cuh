@@ -159,6 +159,13 @@ struct khp_grid {
     double lambda_lanczos; // Lanczos upper bound of the spectrum
     double lambda_low;     // Lanczos lower estimate of the spectrum
 
+    double ctr[3];         // symmetric-gauge centre when ctr_set (else the box centre)
+    int ctr_set;
+    khp_grid* coarse;      // coarse-grid start: the handle of the 2x coarser grid, or null
+    double2* coarse_x;     // its start block [n_coarse][coarse_m]
+    int coarse_m;
+    bool coarse_valid;     // coarse fields match the current fine fields
+
     long long launches;    // kernel launches issued (per call accounting)
     cudaEvent_t ev0, ev1;  // filter timing
     cudaEvent_t evp[5];    // phase timing: Gram | small problem | rotation, and the H Y apply

@@ -29,7 +29,17 @@ cudaError_t launch_stencil_plane_group(const StencilArgs<float>* const* a, int c
 cudaError_t prepare_plane();
 cudaError_t launch_field_setup(khp_grid* g, const double* V, const double* strain,
                                const double* levers, const double* alpha, int ng, int* bad);
+cudaError_t launch_phase_setup(khp_grid* g);
 cudaError_t launch_onsite_rowmax(khp_grid* g, double* partial, int nblocks, double* out);
+
+// coarse.cu: the coarse-grid start.  The coarse grid takes every second
+// point (fine index 2j + 1, 0-based) at twice the spacing; its on-site
+// block is the fine one at those points with the fine kinetic diagonal
+// replaced by the coarse one.  The prolongation fills the fine block by
+// trilinear interpolation (zero at the walls and at masked points).
+cudaError_t launch_restrict_onsite(const khp_grid* fine, khp_grid* coarse);
+cudaError_t launch_prolong(const khp_grid* coarse, const double2* Xc, int ldc, const khp_grid* fine, double2* X,
+                           int ld, int ncol);
 
 // dense.cu
 int dense_blocks(long long rows);

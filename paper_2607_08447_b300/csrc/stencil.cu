@@ -1262,13 +1262,23 @@ cudaError_t launch_field_setup(khp_grid* g, const double* V, const double* strai
     const long long blocks = (g->np + threads - 1) / threads;
     onsite_kernel<<<(unsigned)blocks, threads, 0, g->stream>>>(a);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !g->has_phase) return e;
+    if (e != cudaSuccess) return e;
+    return launch_phase_setup(g);
+}
+
+// Peierls phase tables of the handle's field and gauge; the symmetric gauge
+// is taken about the box centre, or about g->ctr when g->ctr_set (a coarse
+// grid whose walls sit half a fine step away keeps the fine grid's centre)
+cudaError_t launch_phase_setup(khp_grid* g) {
+    if (!g->has_phase) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (g->np + threads - 1) / threads;
     PhaseArgs pa;
     pa.nx = g->nx; pa.ny = g->ny; pa.nz = g->nz; pa.h = g->h;
     for (int k = 0; k < 3; ++k) pa.B[k] = g->B[k];
-    pa.c[0] = 0.5 * (g->nx + 1) * g->h;
-    pa.c[1] = 0.5 * (g->ny + 1) * g->h;
-    pa.c[2] = 0.5 * (g->nz + 1) * g->h;
+    pa.c[0] = g->ctr_set ? g->ctr[0] : 0.5 * (g->nx + 1) * g->h;
+    pa.c[1] = g->ctr_set ? g->ctr[1] : 0.5 * (g->ny + 1) * g->h;
+    pa.c[2] = g->ctr_set ? g->ctr[2] : 0.5 * (g->nz + 1) * g->h;
     pa.gauge = g->gauge;
     pa.phase64 = g->phase64; pa.phase32 = g->phase32;
     phase_kernel<<<(unsigned)blocks, threads, 0, g->stream>>>(pa);

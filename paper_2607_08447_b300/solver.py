@@ -194,13 +194,20 @@ class KPGrid:
         return X, HX
 
     def eigensolve(self, n_states, block_m=None, degree=20, max_iter=0, precision=0, refine_sweeps=2,
-                   tol=1e-9, seed=1, warm_start=None, out=None, allow_not_converged=False, projections="tensor"):
+                   tol=1e-9, seed=1, warm_start=None, out=None, allow_not_converged=False, projections="tensor",
+                   start="random"):
+        """Lowest n_states eigenpairs (khp_eigensolve).  start: 'random'
+        (counter-based start block) or 'coarse' (the block of the 2x coarser
+        grid, prolongated); a warm_start block takes precedence."""
         block_m = block_m or max(n_states + 8, 16)
         block_m += block_m % 2
         opts = _lib.SolverOpts()
         opts.n_states, opts.block_m, opts.degree, opts.max_iter = n_states, block_m, degree, max_iter
         opts.precision, opts.refine_sweeps, opts.tol_ev, opts.seed = precision, refine_sweeps, tol, seed
         opts.projections = _projections(projections)
+        if start not in ("random", "coarse", 0, 1):
+            raise ValueError("start must be 'random' or 'coarse'")
+        opts.start = 1 if start in ("coarse", 1) else 0
         ws = None
         if warm_start is not None:
             ws = _dev(warm_start, torch.complex128, self.device)
