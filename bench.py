@@ -41,9 +41,10 @@ MIXED_DEGREE = 200   # defect-corrected FP32 filter (precision 2)
 CROP = (32, 12, 12)
 # DRAM bytes per point-vector of the FP64 fused stencil launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum = 2.463 GB + 0.829 GB over
-# 24 x 368640 point-vectors, one ncu capture of the FP64 stencil at C2).  Valid for the
-# kernel version profiled there; set to None when the kernel changes.
-NCU_TRAFFIC_FP64_PER_PV = (2.462602e9 + 0.828694e9) / (24 * 368640)
+# 24 x 368640 point-vectors, one ncu capture of a full-width FP64 filter
+# launch at C2).  Valid for the kernel version profiled there; set to None
+# when the kernel changes.
+NCU_TRAFFIC_FP64_PER_PV = (2.463422464e9 + 0.829164544e9) / (24 * 368640)
 
 
 def _args():
@@ -65,6 +66,8 @@ def _args():
                     help="sweep points also solved in plain FP64 for the mixed-vs-plain speed-up")
     ap.add_argument("--profile", choices=["plain", "mixed", "dc"], default=None,
                     help="one short C2 solve (6 outer iterations) for profiler captures; prints its stats")
+    ap.add_argument("--profile-start", choices=["random", "coarse"], default="random",
+                    help="start block of the --profile solve (the timed solves use the coarse-grid start)")
     return ap.parse_args()
 
 
@@ -732,8 +735,9 @@ def run_profile(args):
     p = inputs.config2()
     g = khp.KPGrid.from_problem(p)
     prec = {"plain": 0, "mixed": 1, "dc": 2}[args.profile]
-    # random start: the captured launches are the full grid's own
-    kw = dict(SOLVE_KW, max_iter=6, precision=prec, refine_sweeps=0, start="random")
+    # a random start by default: then every captured launch is the full
+    # grid's own; --profile-start coarse gives the timed solves' sequence
+    kw = dict(SOLVE_KW, max_iter=6, precision=prec, refine_sweeps=0, start=args.profile_start)
     if prec == 2:
         kw["degree"] = MIXED_DEGREE
     r = g.eigensolve(**kw, allow_not_converged=True)

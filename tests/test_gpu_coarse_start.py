@@ -90,4 +90,5 @@ def test_coarse_start_spin_independent_h0(khp):
     rc = g.eigensolve(**kw, start="coarse")
     assert rc.stats["start_iterations"] > 0
     assert np.abs(rc.evals - rr.evals).max() <= 1e-10
-    assert rc.stats["res_history"][0] < 0.05 * rr.stats["res_history"][0]
+    # a 14x8x8 coarse grid at 1 nm: a coarser start than on larger grids
+    assert rc.stats["res_history"][0] < 0.2 * rr.stats["res_history"][0]
