@@ -34,10 +34,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged k·p eigenpairs/s at 2.2M unknowns; stencil HBM GB/s vs peak"
 UNIT = "eigenpairs/s"
-WORKLOAD = ("c2: 160x48x48 grid h=0.5nm (2.21M unknowns), FP64, lowest 16 of block 24, degree 120, "
+WORKLOAD = ("c2: 160x48x48 grid h=0.5nm (2.21M unknowns), FP64, lowest 16 of block 24, degree 180, "
             "tol 1e-10 eV, coarse-grid start")
-SOLVE_KW = dict(n_states=16, block_m=24, degree=120, precision=0, tol=1e-10, seed=1, max_iter=600, start="coarse")
-MIXED_DEGREE = 200   # defect-corrected FP32 filter (precision 2)
+# filter degrees measured at C2 (B300): from the coarse-grid start plain
+# FP64 is fastest at degree 180 (4 outer iterations; 120 takes 6) and the
+# defect-corrected FP32 filter at 250 (3; 200 takes 4); from a random start
+# 120 and 200; warm-started solves (SP loop, CI, sweeps) keep 200
+SOLVE_KW = dict(n_states=16, block_m=24, degree=180, precision=0, tol=1e-10, seed=1, max_iter=600, start="coarse")
+RANDOM_START_DEGREE = 120
+MIXED_DEGREE = 250        # defect-corrected FP32 filter (precision 2), coarse-grid start
+MIXED_DEGREE_WARM = 200   # the same filter from warm or random starts
 CROP = (32, 12, 12)
 # DRAM bytes per point-vector of the FP64 fused stencil launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum = 2.463 GB + 0.829 GB over
@@ -350,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
     # the same solve from a random start block (the coarse-grid start's gain)
     er0, er1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     er0.record(stream)
-    rr = grid.eigensolve(**dict(SOLVE_KW, start="random"))
+    rr = grid.eigensolve(**dict(SOLVE_KW, start="random", degree=RANDOM_START_DEGREE))
     er1.record(stream)
     torch.cuda.synchronize()
     ms_random = er0.elapsed_time(er1)
@@ -406,7 +412,9 @@ def run_ours(args, rank, world, local_rank):
     line["random_start"] = {"value": rr.stats["converged"] / (ms_random * 1e-3), "unit": UNIT,
                             "ms_per_solve": ms_random, "iterations": rr.stats["iterations"],
                             "max_abs_dE_vs_coarse_start_ev": float(np.abs(rr.evals - evals_plain).max()),
-                            "note": "the same solve from a random start block instead of the coarse-grid start"}
+                            "degree": RANDOM_START_DEGREE,
+                            "note": "the same solve from a random start block instead of the coarse-grid start, "
+                                    "at the degree that is fastest from a random start"}
     line["warm"] = {"value": rw.stats["converged"] / (ms_warm * 1e-3), "unit": UNIT, "ms_per_solve": ms_warm,
                     "iterations": rw.stats["iterations"],
                     "note": "warm start from the previous solve's eigenvectors, V changed by 0.1 meV smooth noise"}
@@ -528,7 +536,7 @@ def _sp_bench(p, dev, torch, khp):
     gate[:, :, -1] = 1
     g = khp.KPGrid.from_problem(p, device=dev)
     P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V), device=dev)
-    kw = dict(block_m=SOLVE_KW["block_m"], degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1)
+    kw = dict(block_m=SOLVE_KW["block_m"], degree=MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = sp_solve(g, P, p.V, SOLVE_KW["n_states"], 2.0, T=1.5, mix=0.3, iters=12, tol_v=1e-6, strain=p.strain,
@@ -583,7 +591,7 @@ def _ci_bench(p, dev, torch, khp):
     gate[:, :, -1] = 1
     g = khp.KPGrid.from_problem(p, device=dev, bands=3)
     P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V), device=dev)
-    kw = dict(block_m=16, degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1)
+    kw = dict(block_m=16, degree=MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1)
     ci_exchange(g, P, 4, p.material["delta_so"], solve_kw=kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -612,7 +620,7 @@ def _gtensor_bench(p, dev, torch, khp, j_ci):
     from paper_2607_08447_b300 import exchange as ex
     from paper_2607_08447_b300.gtensor import g_tensors
     g = khp.KPGrid.from_problem(p, device=dev)
-    kw = dict(block_m=12, degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1)
+    kw = dict(block_m=12, degree=MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1)
     g_tensors(g, solve_kw=kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -738,8 +746,11 @@ def run_profile(args):
     # a random start by default: then every captured launch is the full
     # grid's own; --profile-start coarse gives the timed solves' sequence
     kw = dict(SOLVE_KW, max_iter=6, precision=prec, refine_sweeps=0, start=args.profile_start)
+    coarse = args.profile_start == "coarse"
     if prec == 2:
-        kw["degree"] = MIXED_DEGREE
+        kw["degree"] = MIXED_DEGREE if coarse else MIXED_DEGREE_WARM
+    elif not coarse:
+        kw["degree"] = RANDOM_START_DEGREE
     r = g.eigensolve(**kw, allow_not_converged=True)
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "stats": r.stats}), flush=True)
@@ -767,7 +778,7 @@ def run_sweep(args):
     allp = inputs.config4()[: args.sweep]
     mine = shard_of([p.n_unknowns for p in allp], rank, world)
     probs = [allp[i] for i in mine]
-    n, kw = 12, dict(degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1)
+    n, kw = 12, dict(degree=MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1)
     unknowns = sum(p.n_unknowns for p in allp)
     # tuned once on the first chunk, reused for the rest
     grids = [khp.KPGrid.from_problem(p) for p in probs[: args.sweep_chunk]]
@@ -826,7 +837,7 @@ def run_sweep(args):
             g.close()
         return ev
 
-    plain_kw = dict(degree=SOLVE_KW["degree"], precision=0, tol=1e-10, seed=1)
+    plain_kw = dict(degree=RANDOM_START_DEGREE, precision=0, tol=1e-10, seed=1)
     ev_dc, t_dc = timed(lambda: batched_sample(kw))
     ev_fp64, t_fp64 = timed(lambda: batched_sample(plain_kw))
     d_plain = max(float(np.abs(a - b).max()) for a, b in zip(ev_dc, ev_fp64)) if sample else 0.0
@@ -834,7 +845,7 @@ def run_sweep(args):
             "unit": "eigenpairs/s", "n_gpus": world, "higher_is_better": True, "scaling": "strong",
             "dtype": "fp32 filter + fp64 RR", "data": "synthetic",
             "config": {"workload": f"config-4 sweep: {len(allp)} points, {unknowns} unknowns in total, "
-                                   f"12 states each, chunks of {args.sweep_chunk}, degree {MIXED_DEGREE}, "
+                                   f"12 states each, chunks of {args.sweep_chunk}, degree {MIXED_DEGREE_WARM}, "
                                    f"block_m autotuned = {bm}", "autotune_ms": tune_ms,
                        "parallelism": f"sweep sharded over {world} rank(s), no collective"},
             "sequential": {"value": n * len(allp) / ts, "unit": "eigenpairs/s", "s": ts},
@@ -846,7 +857,7 @@ def run_sweep(args):
                               "max_abs_dE_ev": d_plain,
                               "note": "same points, block width and tolerance (1e-10 eV); plain FP64 at degree "
                                       f"{SOLVE_KW['degree']}, mixed = defect-corrected FP32 filter at degree "
-                                      f"{MIXED_DEGREE}"}}
+                                      f"{MIXED_DEGREE_WARM}"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -259,7 +259,13 @@ khp_status khp_rotate(khp_handle h, const void* Y_dev, const void* W_dev, const 
  *  resid_host  optional float64 [n_states] residual norms ||H x - theta x||
  *  stats       optional
  * Returns NOT_CONVERGED (with the current Ritz pairs written) when max_iter
- * is reached before every residual is <= tol_ev. */
+ * is reached before every residual is <= tol_ev.
+ * The filter degree of an outer iteration is capped so that the filter
+ * amplifies the bottom of the spectrum at most 1e4 times relative to the
+ * filter interval (1e5 for precision 2), keeping the filtered block well
+ * conditioned.  Environment: KHP_TRACE=1 prints one line per outer
+ * iteration (2 adds every column's Ritz value and residual) to stderr;
+ * KHP_AMP_CAP=<value > 1> replaces the amplification cap (tuning). */
 khp_status khp_eigensolve(khp_handle h, const khp_solver_opts* opts, double* evals_host,
                           void* evecs_dev, double* resid_host, khp_stats* stats);
 

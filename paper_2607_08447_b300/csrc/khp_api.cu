@@ -1112,7 +1112,12 @@ struct Solve {
             // the defect-corrected mode filters the correction Z in FP32, not
             // the amplified block itself, and takes a 1e5 cap (measured at
             // C2: 7 instead of 8 outer iterations, 3 % faster)
-            const double cap = dc ? 1e5 : 1e4;
+            double cap = dc ? 1e5 : 1e4;
+            // KHP_AMP_CAP in the environment overrides the cap (tuning)
+            if (const char* ac = std::getenv("KHP_AMP_CAP")) {
+                const double v = std::atof(ac);
+                if (v > 1.0 && std::isfinite(v)) cap = v;
+            }
             const int dmax = (int)std::floor(std::acosh(cap) / std::acosh(xl));
             deg = std::max(1, std::min(deg, dmax));
         }
