@@ -97,7 +97,9 @@ typedef struct {
  *                 block_m states of the grid of every second point at twice
  *                 the spacing (on-site fields restricted, same material,
  *                 field and gauge), solved loosely (tolerance max(tol_ev,
- *                 1e-4) eV, degree 60) and prolongated trilinearly; falls
+ *                 1e-3) eV, degree 120 plain / 60 otherwise, block_m + 8
+ *                 columns; KHP_COARSE="degree,tol,extra" in the environment
+ *                 replaces these) and prolongated trilinearly; falls
  *                 back to 0 when that grid has fewer than 4 (block_m + 8)
  *                 unknowns or block_m + 8 > 64.  khp_eigensolve only. */
 typedef struct {

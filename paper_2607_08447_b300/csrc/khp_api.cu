@@ -903,12 +903,27 @@ struct Solve {
     }
 
     // Coarse-grid start: the lowest m states of the 2x coarser grid (a loose
-    // solve: tolerance max(tol, 1e-4 eV), degree 60, block m + 8), prolongated
-    // trilinearly into all m columns of X.  `started` stays false (random
+    // solve, see below), prolongated trilinearly into all m columns of X.  `started` stays false (random
     // start) when the coarse grid is too small for that block.
     khp_status coarse_start(double2* X, bool& started) {
         started = false;
-        const int mc = m + 8;
+        // coarse solve: degree 120 (plain) or 60 (defect-corrected FP32),
+        // tolerance 1e-3 eV, block m + 8 (measured at C2: a tighter coarse
+        // tolerance does not improve the fine start, whose residuals are set
+        // by the difference of the two discretisations); KHP_COARSE=
+        // "degree,tol_ev,extra_columns" in the environment replaces them (tuning)
+        int cdeg = o.precision == 0 ? 120 : 60, cextra = 8;
+        double ctol = 1e-3;
+        if (const char* cs = std::getenv("KHP_COARSE")) {
+            int d = 0, x = 0;
+            double t = 0.0;
+            if (std::sscanf(cs, "%d,%lf,%d", &d, &t, &x) == 3 && d >= 1 && t > 0.0 && x >= 2 && (x % 2) == 0) {
+                cdeg = d;
+                ctol = t;
+                cextra = x;
+            }
+        }
+        const int mc = m + cextra;
         const long long npc = (long long)(g->nx / 2) * (g->ny / 2) * (g->nz / 2);
         if (mc > KHP_MAX_M || npc < 1 || (long long)g->nb * npc < 4LL * mc) return KHP_OK;
         const auto tc0 = std::chrono::steady_clock::now();
@@ -924,11 +939,11 @@ struct Solve {
         khp_solver_opts oc{};
         oc.n_states = m;
         oc.block_m = mc;
-        oc.degree = 60;
+        oc.degree = cdeg;
         oc.max_iter = 60;
         oc.precision = o.precision == 0 ? 0 : 2;
         oc.refine_sweeps = o.refine_sweeps;
-        oc.tol_ev = std::max(o.tol_ev, 1e-4);
+        oc.tol_ev = std::max(o.tol_ev, ctol);
         oc.seed = o.seed;
         oc.projections = o.projections;
         std::vector<double> ev(m);
