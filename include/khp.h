@@ -477,7 +477,10 @@ khp_status khp_eigs_backward(khp_handle h, const void* evecs_dev, const double* 
  *  - All calls share the array: calls whose kernels overlap on the GPU
  *    (other streams or unordered host threads) race and must be serialised
  *    by the caller.
- *  - It runs on the handle's stream and synchronises it when n_gates > 0. */
+ *  - It runs on the handle's stream and synchronises it when n_gates > 0
+ *    (it copies dL/dalpha to the host), so such calls cannot be captured
+ *    into a CUDA graph; with n_gates = 0 a call can be captured once a
+ *    first uncaptured call has been made on that device. */
 khp_status khp_eigs_backward_noalloc(khp_handle h, const void* evecs_dev, const double* evals_host,
                                      int n, const double* dLdE_host, double* dLdV_dev,
                                      double* dLdstrain_dev, const double* levers_dev, int n_gates,
