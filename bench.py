@@ -72,6 +72,8 @@ def _args():
                     help="sweep points also solved in plain FP64 for the mixed-vs-plain speed-up")
     ap.add_argument("--profile", choices=["plain", "mixed", "dc"], default=None,
                     help="one short C2 solve (6 outer iterations) for profiler captures; prints its stats")
+    ap.add_argument("--sweep-start", choices=["coarse", "random"], default="coarse",
+                    help="start block of the sweep's solves (coarse-grid start or random)")
     ap.add_argument("--profile-start", choices=["random", "coarse"], default="random",
                     help="start block of the --profile solve (the timed solves use the coarse-grid start)")
     return ap.parse_args()
@@ -797,7 +799,9 @@ def run_sweep(args):
     allp = inputs.config4()[: args.sweep]
     mine = shard_of([p.n_unknowns for p in allp], rank, world)
     probs = [allp[i] for i in mine]
-    n, kw = 12, dict(degree=MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1)
+    coarse = args.sweep_start == "coarse"
+    n, kw = 12, dict(degree=MIXED_DEGREE if coarse else MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1,
+                     start=args.sweep_start)
     unknowns = sum(p.n_unknowns for p in allp)
     # tuned once on the first chunk, reused for the rest
     grids = [khp.KPGrid.from_problem(p) for p in probs[: args.sweep_chunk]]
@@ -841,6 +845,12 @@ def run_sweep(args):
     evals_b, tb = timed(batched)
     evals_u, tu = timed(lambda: batched(grouped=False))
     evals_s, ts = timed(sequential)
+    # the same grouped batches from random start blocks (the coarse start's gain)
+    kw_coarse = kw
+    kw = dict(kw, start="random", degree=MIXED_DEGREE_WARM)
+    evals_r, tr = timed(batched)
+    kw = kw_coarse
+    dgr = max(float(np.abs(a - b).max()) for a, b in zip(evals_b, evals_r)) if probs else 0.0
     dmax = max(float(np.abs(a - b).max()) for a, b in zip(evals_b, evals_s)) if probs else 0.0
     dgu = max(float(np.abs(a - b).max()) for a, b in zip(evals_b, evals_u)) if probs else 0.0
 
@@ -856,7 +866,8 @@ def run_sweep(args):
             g.close()
         return ev
 
-    plain_kw = dict(degree=RANDOM_START_DEGREE, precision=0, tol=1e-10, seed=1)
+    plain_kw = dict(degree=SOLVE_KW["degree"] if coarse else RANDOM_START_DEGREE, precision=0, tol=1e-10, seed=1,
+                    start=args.sweep_start)
     ev_dc, t_dc = timed(lambda: batched_sample(kw))
     ev_fp64, t_fp64 = timed(lambda: batched_sample(plain_kw))
     d_plain = max(float(np.abs(a - b).max()) for a, b in zip(ev_dc, ev_fp64)) if sample else 0.0
@@ -864,19 +875,21 @@ def run_sweep(args):
             "unit": "eigenpairs/s", "n_gpus": world, "higher_is_better": True, "scaling": "strong",
             "dtype": "fp32 filter + fp64 RR", "data": "synthetic",
             "config": {"workload": f"config-4 sweep: {len(allp)} points, {unknowns} unknowns in total, "
-                                   f"12 states each, chunks of {args.sweep_chunk}, degree {MIXED_DEGREE_WARM}, "
-                                   f"block_m autotuned = {bm}", "autotune_ms": tune_ms,
+                                   f"12 states each, chunks of {args.sweep_chunk}, degree {kw['degree']}, "
+                                   f"{args.sweep_start} start, block_m autotuned = {bm}", "autotune_ms": tune_ms,
                        "parallelism": f"sweep sharded over {world} rank(s), no collective"},
             "sequential": {"value": n * len(allp) / ts, "unit": "eigenpairs/s", "s": ts},
             "batched_s": tb, "speedup_vs_sequential": ts / tb, "max_abs_dE_batched_vs_single_ev": dmax,
             "ungrouped": {"s": tu, "speedup_vs_sequential": ts / tu, "max_abs_dE_vs_grouped_ev": dgu,
                           "note": "the same batched rounds with one filter launch per problem and step"},
+            "random_start": {"s": tr, "value": n * len(allp) / tr, "max_abs_dE_vs_grouped_ev": dgr,
+                             "note": f"the same grouped batches from random start blocks at degree {MIXED_DEGREE_WARM}"},
             "vs_plain_fp64": {"points": len(sample), "mixed_batched_s": t_dc, "fp64_batched_s": t_fp64,
                               "speedup": t_fp64 / t_dc if t_dc > 0 else None,
                               "max_abs_dE_ev": d_plain,
-                              "note": "same points, block width and tolerance (1e-10 eV); plain FP64 at degree "
-                                      f"{SOLVE_KW['degree']}, mixed = defect-corrected FP32 filter at degree "
-                                      f"{MIXED_DEGREE_WARM}"}}
+                              "note": "same points, start, block width and tolerance (1e-10 eV); plain FP64 at "
+                                      f"degree {plain_kw['degree']}, mixed = defect-corrected FP32 filter at degree "
+                                      f"{kw['degree']}"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

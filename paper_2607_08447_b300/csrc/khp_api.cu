@@ -498,7 +498,12 @@ khp_status khp_create_grid_h0(khp_handle* out, int nx, int ny, int nz, double h_
 khp_status khp_destroy(khp_handle g) {
     if (!g) return KHP_OK;
     cudaStreamSynchronize(g->stream);
-    if (g->coarse) khp_destroy(g->coarse);
+    if (g->coarse) {
+        // the coarse handle may still name a stream of an earlier call: it
+        // works on the fine handle's stream
+        g->coarse->stream = g->stream;
+        khp_destroy(g->coarse);
+    }
     if (g->coarse_x) cudaFree(g->coarse_x);
     free_ws(g);
     if (g->onsite64) cudaFree(g->onsite64);
@@ -575,6 +580,55 @@ static khp_status coarse_prepare(khp_grid* g) {
     CK(launch_phase_setup(gc));
     CKS(finish_fields(gc, nullptr));
     g->coarse_valid = true;
+    return KHP_OK;
+}
+
+// Whether a block of m columns can start from the coarse grid: the coarse
+// block (m + extra columns) fits the library's width and the coarse grid has
+// at least 4 (m + extra) unknowns.
+static bool coarse_eligible(const khp_grid* g, int m, int extra) {
+    const long long npc = (long long)(g->nx / 2) * (g->ny / 2) * (g->nz / 2);
+    return m + extra <= KHP_MAX_M && npc >= 1 && (long long)g->nb * npc >= 4LL * (m + extra);
+}
+
+// Options of the coarse solve for a fine solve with options o and width m:
+// degree 120 (plain) or 60 (defect-corrected FP32), tolerance max(tol, 1e-3
+// eV), block m + 8 (measured at C2: a tighter coarse tolerance does not
+// improve the fine start, whose residuals are set by the difference of the
+// two discretisations); KHP_COARSE="degree,tol_ev,extra_columns" in the
+// environment replaces them (tuning).
+static khp_solver_opts coarse_opts(const khp_solver_opts& o, int m) {
+    int cdeg = o.precision == 0 ? 120 : 60, cextra = 8;
+    double ctol = 1e-3;
+    if (const char* cs = std::getenv("KHP_COARSE")) {
+        int d = 0, x = 0;
+        double t = 0.0;
+        if (std::sscanf(cs, "%d,%lf,%d", &d, &t, &x) == 3 && d >= 1 && t > 0.0 && x >= 2 && (x % 2) == 0) {
+            cdeg = d;
+            ctol = t;
+            cextra = x;
+        }
+    }
+    khp_solver_opts oc{};
+    oc.n_states = m;
+    oc.block_m = m + cextra;
+    oc.degree = cdeg;
+    oc.max_iter = 60;
+    oc.precision = o.precision == 0 ? 0 : 2;
+    oc.refine_sweeps = o.refine_sweeps;
+    oc.tol_ev = std::max(o.tol_ev, ctol);
+    oc.seed = o.seed;
+    oc.projections = o.projections;
+    return oc;
+}
+
+static khp_status coarse_block(khp_grid* g, int m) {
+    if (g->coarse_m >= m) return KHP_OK;
+    if (g->coarse_x) cudaFree(g->coarse_x);
+    g->coarse_x = nullptr;
+    g->coarse_m = 0;
+    CK(cudaMalloc(&g->coarse_x, sizeof(double2) * g->coarse->n * m));
+    g->coarse_m = m;
     return KHP_OK;
 }
 
@@ -907,45 +961,13 @@ struct Solve {
     // start) when the coarse grid is too small for that block.
     khp_status coarse_start(double2* X, bool& started) {
         started = false;
-        // coarse solve: degree 120 (plain) or 60 (defect-corrected FP32),
-        // tolerance 1e-3 eV, block m + 8 (measured at C2: a tighter coarse
-        // tolerance does not improve the fine start, whose residuals are set
-        // by the difference of the two discretisations); KHP_COARSE=
-        // "degree,tol_ev,extra_columns" in the environment replaces them (tuning)
-        int cdeg = o.precision == 0 ? 120 : 60, cextra = 8;
-        double ctol = 1e-3;
-        if (const char* cs = std::getenv("KHP_COARSE")) {
-            int d = 0, x = 0;
-            double t = 0.0;
-            if (std::sscanf(cs, "%d,%lf,%d", &d, &t, &x) == 3 && d >= 1 && t > 0.0 && x >= 2 && (x % 2) == 0) {
-                cdeg = d;
-                ctol = t;
-                cextra = x;
-            }
-        }
-        const int mc = m + cextra;
-        const long long npc = (long long)(g->nx / 2) * (g->ny / 2) * (g->nz / 2);
-        if (mc > KHP_MAX_M || npc < 1 || (long long)g->nb * npc < 4LL * mc) return KHP_OK;
+        const khp_solver_opts oc = coarse_opts(o, m);
+        if (!coarse_eligible(g, m, oc.block_m - m)) return KHP_OK;
         const auto tc0 = std::chrono::steady_clock::now();
         CKS(coarse_prepare(g));
         khp_grid* gc = g->coarse;
-        if (g->coarse_m < m) {
-            if (g->coarse_x) cudaFree(g->coarse_x);
-            g->coarse_x = nullptr;
-            g->coarse_m = 0;
-            CK(cudaMalloc(&g->coarse_x, sizeof(double2) * gc->n * m));
-            g->coarse_m = m;
-        }
-        khp_solver_opts oc{};
-        oc.n_states = m;
-        oc.block_m = mc;
-        oc.degree = cdeg;
-        oc.max_iter = 60;
-        oc.precision = o.precision == 0 ? 0 : 2;
-        oc.refine_sweeps = o.refine_sweeps;
-        oc.tol_ev = std::max(o.tol_ev, ctol);
-        oc.seed = o.seed;
-        oc.projections = o.projections;
+        gc->stream = g->stream;
+        CKS(coarse_block(g, m));
         std::vector<double> ev(m);
         khp_stats sc_st{};
         {
@@ -975,6 +997,12 @@ struct Solve {
         return KHP_OK;
     }
 
+    // set by the batched solver when it has filled the start block from the
+    // coarse grids (begin_b then keeps it); its coarse statistics
+    bool prefilled = false;
+    int pre_iterations = 0;
+    double pre_ms = 0.0;
+
     // stage b: random / warm start, orthonormalisation and the first
     // Rayleigh-Ritz, issued; the caller synchronises before absorb
     khp_status begin_b() {
@@ -1002,8 +1030,13 @@ struct Solve {
         trace_cols = tr && tr[0] == '2';
         double2** B = g->blk64;
         CK(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 8, g->stream));
-        bool started = false;
-        if (o.start == 1 && !o.warm_start_dev) CKS(coarse_start(B[ib[0]], started));
+        bool started = prefilled;
+        if (prefilled) {
+            st.start_iterations = pre_iterations;
+            st.ms_start = pre_ms;
+        } else if (o.start == 1 && !o.warm_start_dev) {
+            CKS(coarse_start(B[ib[0]], started));
+        }
         if (!started) {
             CK(launch_random_fill(B[ib[0]], g->n, m, 0, m, o.seed, g->mask, g->stream, g->nb));
             g->launches += 1;
@@ -1390,7 +1423,6 @@ extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, co
     if (!hs || !opts || !evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
     if (count < 1) return fail(KHP_ERR_INVALID_ARG, "count must be >= 1");
     if (opts->warm_start_dev) return fail(KHP_ERR_INVALID_ARG, "warm starts are per problem: not in batched mode");
-    if (opts->start != 0) return fail(KHP_ERR_INVALID_ARG, "the coarse-grid start is for khp_eigensolve");
     khp_solver_opts o = *opts;
     const int n = o.n_states;
     int dev0 = -1;
@@ -1464,6 +1496,47 @@ extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, co
         CKS(S[i].begin_a(hs[i], &o));
     }
     for (int i = 0; i < count; ++i) CK(cudaStreamSynchronize(hs[i]->stream));
+    if (o.start == 1) {
+        // coarse-grid start: the coarse grids of the eligible problems solved
+        // together (one batched call), each block prolongated into its
+        // problem's start block; the others start from random blocks
+        const auto tc0 = std::chrono::steady_clock::now();
+        const int m = o.block_m;
+        const khp_solver_opts oc = coarse_opts(o, m);
+        std::vector<int> ci;
+        std::vector<khp_handle> hc;
+        std::vector<void*> xc;
+        for (int i = 0; i < count; ++i) {
+            if (!coarse_eligible(hs[i], m, oc.block_m - m)) continue;
+            CKS(coarse_prepare(hs[i]));
+            hs[i]->coarse->stream = hs[i]->stream;
+            CKS(coarse_block(hs[i], m));
+            ci.push_back(i);
+            hc.push_back(hs[i]->coarse);
+            xc.push_back(hs[i]->coarse_x);
+        }
+        if (!hc.empty()) {
+            std::vector<double> ev(hc.size() * (size_t)m);
+            std::vector<khp_stats> cst(hc.size());
+            const khp_status r = khp_eigensolve_batched(hc.data(), (int)hc.size(), &oc, ev.data(), xc.data(), nullptr,
+                                                        cst.data(), flags & (KHP_BATCH_GRAPH | KHP_BATCH_GROUPED));
+            if (r != KHP_OK && r != KHP_ERR_NOT_CONVERGED) return r;
+            g_err.clear();
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
+            for (size_t k = 0; k < ci.size(); ++k) {
+                const int i = ci[k];
+                khp_grid* g = hs[i];
+                CK(launch_prolong(g->coarse, g->coarse_x, m, g, g->blk64[S[i].ib[0]], m, m));
+                g->launches += 1 + cst[k].kernel_launches;
+                // the batch streams end with this call: the coarse handle goes
+                // back to the fine handle's own stream
+                g->coarse->stream = bs.orig[i];
+                S[i].prefilled = true;
+                S[i].pre_iterations = cst[k].iterations;
+                S[i].pre_ms = ms;
+            }
+        }
+    }
     for (int i = 0; i < count; ++i) CKS(S[i].begin_b());
     for (int i = 0; i < count; ++i) {
         CK(cudaStreamSynchronize(hs[i]->stream));

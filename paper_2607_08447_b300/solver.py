@@ -298,11 +298,12 @@ def _projections(p):
 
 def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precision=0, refine_sweeps=-1,
                   tol=1e-9, seed=1, graph=True, autotune=False, allow_not_converged=False, projections="tensor",
-                  grouped=False):
+                  grouped=False, start="random"):
     """Solve every grid's lowest states in one khp_eigensolve_batched call
     (lock-step rounds, optionally one CUDA graph per round, an autotuned
-    block width, and grouped filter launches across the problems).
-    Returns a list of SolveResult."""
+    block width, and grouped filter launches across the problems).  start
+    'coarse' solves the problems' coarse grids together first and starts
+    each from its prolongated block.  Returns a list of SolveResult."""
     lib = _lib.load()
     count = len(grids)
     opts = _lib.SolverOpts()
@@ -310,6 +311,9 @@ def solve_batched(grids, n_states, block_m=None, degree=80, max_iter=0, precisio
     opts.n_states, opts.block_m, opts.degree, opts.max_iter = n_states, bm + bm % 2, degree, max_iter
     opts.precision, opts.refine_sweeps, opts.tol_ev, opts.seed = precision, refine_sweeps, tol, seed
     opts.projections = _projections(projections)
+    if start not in ("random", "coarse", 0, 1):
+        raise ValueError("start must be 'random' or 'coarse'")
+    opts.start = 1 if start in ("coarse", 1) else 0
     hs = (ctypes.c_void_p * count)(*[g.handle.value for g in grids])
     outs = [torch.empty((g.N, n_states), dtype=torch.complex128, device=g.device) for g in grids]
     ptrs = (ctypes.c_void_p * count)(*[o.data_ptr() for o in outs])

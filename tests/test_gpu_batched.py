@@ -80,3 +80,28 @@ def test_batched_rejects_bad_input(khp):
     grids = [khp.KPGrid.from_problem(p) for p in probs]
     with pytest.raises(khp.KHPError):
         khp.solve_batched([grids[0], grids[0]], 8, block_m=16)
+
+
+def test_batched_coarse_start(khp):
+    """start = 'coarse' in a batched call: the coarse grids of the eligible
+    problems are solved together and prolongated; a grid too small for a
+    coarse block starts from a random one.  Plain and grouped
+    defect-corrected rounds; eigenvalues equal to single random-start solves
+    and to the oracle."""
+    shapes = [(20, 12, 10), (16, 14, 12), (18, 10, 12), (5, 4, 4)]
+    probs = [inputs.small_problem(*sh, h=0.5, seed=60 + k, rot="device", B=(0.3 + 0.1 * k, 0.0, 0.1), strain=True)
+             for k, sh in enumerate(shapes)]
+    grids = [khp.KPGrid.from_problem(p) for p in probs]
+    rc = None
+    for grouped, prec in ((False, 0), (True, 2)):
+        kw = dict(block_m=16, degree=40, precision=prec, tol=1e-10)
+        rc = khp.solve_batched(grids, 8, graph=True, grouped=grouped, start="coarse", **kw)
+        for k, (g, r) in enumerate(zip(grids, rc)):
+            r1 = g.eigensolve(8, start="random", **kw)
+            assert np.abs(r1.evals - r.evals).max() <= 1e-10
+            if k < 3:
+                assert r.stats["start_iterations"] > 0
+            else:
+                assert r.stats["start_iterations"] == 0
+    w, _ = eig.lowest_arpack(kp.assemble(probs[0]), 8)
+    assert np.abs(rc[0].evals - w).max() <= 1e-9
