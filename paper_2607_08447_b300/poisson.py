@@ -126,13 +126,15 @@ class SPResult:
 
 
 def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, tol_v=1e-8, strain=None,
-             B=None, gauge=0, solve_kw=None, anderson_depth=0, relax=False):
+             B=None, gauge=0, solve_kw=None, anderson_depth=0, relax=False, warm=True):
     """Self-consistent loop from V = V_ext: `iters` iterations at most, or
     until max |dV| <= tol_v.  Linear mixing with weight `mix`, or Anderson
     mixing (damping `mix`) over `anderson_depth` > 0 previous iterates.
     relax=True relaxes the occupations within each update
     (khp_sp_relax_occupations) instead of fixing them at the Fermi-Dirac
-    values of the current levels.  Returns SPResult (V on the device)."""
+    values of the current levels.  warm=True starts every eigensolve from
+    the previous iteration's eigenvectors; warm=False takes the start of
+    solve_kw (e.g. start='coarse').  Returns SPResult (V on the device)."""
     kw = dict(block_m=max(n_states + 8, 16), degree=40, tol=1e-11, seed=1)
     kw.update(solve_kw or {})
     V_ext = _dev(V_ext, torch.float64, grid.device).reshape(-1)
@@ -140,13 +142,13 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
     phi = torch.zeros_like(V)
     kT = KB_EV * T
     hist, piters = [], []
-    warm = None
+    prev = None
     if anderson_depth > 0:
         poisson.reset_mixing()
     for _ in range(iters):
         grid.set_fields(V, strain, None, None, B, gauge)
-        r = grid.eigensolve(n_states, warm_start=warm, **kw)
-        warm = r.evecs
+        r = grid.eigensolve(n_states, warm_start=prev, **kw)
+        prev = r.evecs if warm else None
         if relax:
             dens = grid.state_densities(r.evecs)
             _, f, mu = poisson.relax(dens, r.evals, n_holes, kT, V, V_ext, phi)
