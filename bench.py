@@ -575,9 +575,22 @@ def _sp_bench(p, dev, torch, khp):
     P.solve(rho, phi, tol=1e-10)
     torch.cuda.synchronize()
     tp = time.perf_counter() - t1
+    cold_iterations = P.last_iterations
+    # the same solve with the Jacobi preconditioner
+    P.set_preconditioner("jacobi")
+    phi.zero_()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    P.solve(rho, phi, tol=1e-10)
+    torch.cuda.synchronize()
+    tj = time.perf_counter() - t1
+    jacobi_iterations = P.last_iterations
+    P.set_preconditioner("multigrid")
     out = {"iterations": len(r.history), "s_total": t, "s_per_iteration": t / len(r.history),
            "final_max_dV_ev": r.history[-1], "poisson_cg_iterations": r.poisson_iterations,
-           "poisson_ms_cold": 1e3 * tp, "poisson_cold_iterations": P.last_iterations,
+           "poisson_ms_cold": 1e3 * tp, "poisson_cold_iterations": cold_iterations,
+           "poisson_multigrid_levels": P.mg_levels,
+           "poisson_ms_cold_jacobi": 1e3 * tj, "poisson_cold_iterations_jacobi": jacobi_iterations,
            "workload": "C2 grid and fields, grounded gates on both x faces, 2 holes, T 1.5 K, mix 0.3"}
     # Anderson mixing (library history, depth 6, damping 0.5) at 20 K, where
     # kT exceeds the splittings of the random wells and the density responds

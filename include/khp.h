@@ -283,8 +283,18 @@ khp_status khp_eigensolve(khp_handle h, const khp_solver_opts* opts, double* eva
  *     sum over in-box face neighbours n of (phi_p - phi_n) / h^2 = (e / eps) rho_p,
  *     eps = eps0 eps_r,  phi_p = phi_gate(p) at gates.
  * Every connected set of free points must touch a gate.  Solved by
- * Jacobi-preconditioned conjugate gradients on the device. */
+ * preconditioned conjugate gradients on the device (the paper names no
+ * solver): by default with a geometric multigrid V-cycle (cell-centred
+ * 2x2x2 aggregation down to at most 64 cells, coarse cells that hold a gate
+ * point are gates, the 7-point operator rediscretised at each spacing, two
+ * weighted-Jacobi sweeps (0.8) before and after the coarse correction, a
+ * dense solve on the coarsest level; FP32), else with the diagonal (Jacobi)
+ * preconditioner; see khp_poisson_set_preconditioner. */
 typedef struct khp_poisson_s* khp_poisson;
+
+/* Preconditioners of the Poisson CG. */
+#define KHP_POISSON_PRECOND_JACOBI 0
+#define KHP_POISSON_PRECOND_MULTIGRID 1
 
 /*  gate_mask_dev  uint8 [Np] device array, nonzero = gate point (copied)
  *  gate_phi_dev   float64 [Np] device array, gate potentials [V] (read at gates, copied)
@@ -302,6 +312,19 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
  * last iterate) when max_iter is reached. */
 khp_status khp_poisson_solve(khp_poisson p, const double* rho_dev, double* phi_dev, double tol, int max_iter,
                              int* iterations, double* rel_residual);
+
+/* Selects the preconditioner of the handle's later solves
+ * (KHP_POISSON_PRECOND_*; multigrid is the default).  The multigrid
+ * hierarchy is built by khp_poisson_create: three FP32 vectors and a 16-bit
+ * neighbour code per grid point, and about 1/7 of that again for the
+ * coarse levels (the V-cycle runs in FP32; the CG's vectors and dot
+ * products stay FP64).  Where it could not be built
+ * (a grid that does not coarsen to 64 cells in 12 levels, or one without
+ * gates) the solves use the Jacobi preconditioner.
+ *  levels  optional output: the multigrid levels in use (0 = Jacobi)
+ * Synchronises the handle's private stream when the choice changes.
+ * Errors: INVALID_ARG (NULL handle, unknown kind). */
+khp_status khp_poisson_set_preconditioner(khp_poisson p, int kind, int* levels);
 
 /* Potential update of the loop: V = (1 - mix) V + mix (V_ext + phi), all
  * float64 [Np] device arrays (V_ext may be NULL), mix in (0, 1];

@@ -6,10 +6,12 @@
 // nb(p) = face neighbours inside the box.  The gate values move to the
 // right-hand side; the remaining operator on the free points is symmetric
 // positive definite (some gate in every connected part) and is solved by
-// conjugate gradients with the diagonal (Jacobi) preconditioner, matrix-free
-// (7-point stencil), every scalar on the device, the residual read back every
-// 16 iterations, replayed as one captured CUDA graph of 16 iterations.
-// Reductions run in two fixed-order stages (deterministic).
+// preconditioned conjugate gradients, matrix-free (7-point stencil), every
+// scalar on the device; the preconditioner is a geometric multigrid V-cycle
+// (default) or the diagonal (Jacobi).  The residual is read back every 8
+// (multigrid) or 16 (Jacobi) iterations, the iterations between two reads
+// replayed as one captured CUDA graph.  Reductions run in two fixed-order
+// stages (deterministic).
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -27,6 +29,7 @@ struct khp_poisson_s {
     double h, eps_r, coef, h2inv;
     cudaStream_t stream;
     uint8_t* gate;
+    uint16_t* code;        // neighbour codes of the grid's points (see Geo)
     double* gphi;
     double *x, *r, *z, *p, *Ap, *b;
     double* partial;       // [nblk][2]
@@ -51,6 +54,24 @@ struct khp_poisson_s {
     double* r_host;        // pinned copy of r_out
     int r_nmax, r_nq;      // capacity; states whose Q holds a previous solution
     bool r_have_phig;
+    // multigrid preconditioner of the CG (FP32): level 0 is the grid itself
+    // (its right-hand side b is the FP32 copy of the CG residual r; its last
+    // sweep writes the CG's z in FP64), levels 1.. the 2x2x2-aggregated grids
+    struct MGLevel {
+        int nx, ny, nz;
+        long long np;
+        double h2inv;
+        uint8_t* gate;     // level 0: the handle's gate mask
+        uint16_t* code;    // level 0: the handle's codes
+        float *b, *u, *v;  // right-hand side, smoothing scratch, result
+    };
+    static constexpr int kMaxLevels = 12;
+    int mg_n;              // levels; 0 when the hierarchy could not be built
+    MGLevel mg[kMaxLevels];
+    float* mg_cinv;        // inverse of the coarsest operator on its free points [nf][nf]
+    int* mg_cidx;          // coarsest cell -> free index, -1 at gates
+    int mg_nf;
+    int precond;           // KHP_POISSON_PRECOND_*
 };
 
 namespace khp {
@@ -70,7 +91,27 @@ struct Geo {
     long long np;
     double h2inv;
     const uint8_t* gate;
+    const uint16_t* code;   // per point: kCodeGate, the degree << 8, bit d = neighbour d in the box and free
+    float h2f, h2invf;      // h^2 and h^-2 in FP32 (the multigrid levels)
 };
+
+constexpr unsigned kCodeGate = 0x8000u;
+
+__device__ __forceinline__ int code_degree(unsigned c) { return (int)((c >> 8) & 7u); }
+
+// offset of neighbour d (0..5: +x, -x, +y, -y, +z, -z)
+__device__ __forceinline__ long long nbr_offset(const Geo& g, int d) {
+    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
+    return d == 0 ? sx : d == 1 ? -sx : d == 2 ? sy : d == 3 ? -sy : d == 4 ? sz : -sz;
+}
+
+// coordinates by 32-bit division (np <= 2^31)
+__device__ __forceinline__ void coords32(long long p, int nx, int ny, int& ix, int& iy, int& iz) {
+    const unsigned u = (unsigned)p, q = u / (unsigned)nx;
+    ix = (int)(u - q * (unsigned)nx);
+    iy = (int)(q % (unsigned)ny);
+    iz = (int)(q / (unsigned)ny);
+}
 
 // neighbour d of p (0..5: +x, -x, +y, -y, +z, -z) or -1 outside the box
 __device__ __forceinline__ long long nbr(const Geo& g, long long p, int ix, int iy, int iz, int d) {
@@ -132,21 +173,16 @@ __global__ void rhs_kernel(const Geo g, const double* rho, const double* gphi, d
 __global__ void apply_kernel(const Geo g, const double* __restrict__ x, double* __restrict__ y, double* partial) {
     double xy = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
-        if (g.gate[p]) {
+        const unsigned c = g.code[p];
+        if (c & kCodeGate) {
             y[p] = 0.0;
             continue;
         }
-        int ix, iy, iz;
-        coords(p, g.nx, g.ny, ix, iy, iz);
-        int deg = 0;
         double s = 0.0;
-        for (int d = 0; d < 6; ++d) {
-            const long long q = nbr(g, p, ix, iy, iz, d);
-            if (q < 0) continue;
-            ++deg;
-            if (!g.gate[q]) s += x[q];
-        }
-        const double v = g.h2inv * (deg * x[p] - s);
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+            if (c >> d & 1u) s += x[p + nbr_offset(g, d)];
+        const double v = g.h2inv * (code_degree(c) * x[p] - s);
         y[p] = v;
         xy += x[p] * v;
     }
@@ -183,11 +219,9 @@ __global__ void update_kernel(const Geo g, const double* s, const double* pv, co
     const double alpha = s[2];
     double rz = 0.0, rr = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
-        if (g.gate[p]) continue;
-        int ix, iy, iz;
-        coords(p, g.nx, g.ny, ix, iy, iz);
-        int deg = 0;
-        for (int d = 0; d < 6; ++d) deg += nbr(g, p, ix, iy, iz, d) >= 0;
+        const unsigned c = g.code[p];
+        if (c & kCodeGate) continue;
+        const int deg = code_degree(c);
         x[p] += alpha * pv[p];
         const double rv = r[p] - alpha * Ap[p];
         const double zv = rv / (g.h2inv * (deg > 0 ? deg : 1));
@@ -204,6 +238,221 @@ __global__ void direction_kernel(const Geo g, const double* s, const double* z, 
     const double beta = s[3];
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT)
         if (!g.gate[p]) pv[p] = z[p] + beta * pv[p];
+}
+
+// ------------------------------------------------- multigrid preconditioner
+// Cell-centred geometric multigrid V-cycle on the Poisson operator, in
+// FP32 (a preconditioner needs no more: the CG's residual, iterate and dot
+// products stay FP64, and FP32 arithmetic runs at many times B300's FP64
+// rate).  Level l+1 aggregates 2x2x2 cells of level l (the last cell along
+// an odd dimension has one child along it); its spacing doubles and a
+// coarse cell is a gate when any of its children is.  The coarse operator
+// is the same 7-point form rediscretised at the coarse spacing with zero
+// gate values (the levels solve for corrections).  Restriction averages
+// the 8 children, prolongation adds the coarse value to every free child,
+// two weighted-Jacobi sweeps (omega = 0.8) run before and after the coarse
+// correction, and the coarsest level (at most 64 cells) is solved by a
+// dense inverse.  Restriction is 1/8 of the transposed prolongation and
+// the smoothing is symmetric, so the V-cycle is a symmetric preconditioner
+// for the CG.  The rediscretised coarse operator is half the Galerkin one
+// (R A P), so the coarse correction is twice the A-orthogonal projection:
+// the usual remedy for the too-small correction that piecewise-constant
+// prolongation gives on smooth errors.
+//
+// A Jacobi sweep y -> y + w D^-1 (b - A y), D = deg / h^2, is evaluated as
+// (1 - w) y + (w / deg) (sum of the free neighbours' y + h^2 b).
+constexpr float kOmega = 0.8f;
+
+__device__ __forceinline__ long long idx_of(const Geo& g, int ix, int iy, int iz) {
+    return ix + (long long)g.nx * (iy + (long long)g.ny * iz);
+}
+
+// 1 / max(deg, 1) of a point's code
+__device__ __forceinline__ float inv_deg(unsigned c) {
+    const int d = code_degree(c);
+    return d == 6 ? 1.0f / 6.0f : d == 5 ? 0.2f : d == 4 ? 0.25f : d == 3 ? 1.0f / 3.0f : d == 2 ? 0.5f : 1.0f;
+}
+
+// the neighbour code of every point of a level (from its gate mask)
+__global__ void mg_code_kernel(const Geo g, uint16_t* code) {
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        int ix, iy, iz;
+        coords32(p, g.nx, g.ny, ix, iy, iz);
+        const bool in[6] = {ix + 1 < g.nx, ix > 0, iy + 1 < g.ny, iy > 0, iz + 1 < g.nz, iz > 0};
+        unsigned c = g.gate[p] ? kCodeGate : 0u;
+        int deg = 0;
+        for (int d = 0; d < 6; ++d) {
+            if (!in[d]) continue;
+            ++deg;
+            if (!g.gate[p + nbr_offset(g, d)]) c |= 1u << d;
+        }
+        code[p] = (uint16_t)(c | (unsigned)deg << 8);
+    }
+}
+
+// pre-smoothing from a zero start, both sweeps in one pass:
+// u = w D^-1 b, v = u + w D^-1 (b - A u) (u of the neighbours recomputed); 0 at gates
+__global__ void mg_presmooth_kernel(const Geo g, const float* __restrict__ b, float* __restrict__ v) {
+    const float wh2 = kOmega * g.h2f;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        const unsigned c = g.code[p];
+        if (c & kCodeGate) {
+            v[p] = 0.0f;
+            continue;
+        }
+        float s = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+            if (c >> d & 1u) {
+                const long long q = p + nbr_offset(g, d);
+                s = fmaf(b[q], inv_deg(g.code[q]), s);
+            }
+        const float id = inv_deg(c), bp = b[p];
+        const float up = wh2 * bp * id;
+        v[p] = fmaf(1.0f - kOmega, up, kOmega * id * fmaf(g.h2f, bp, wh2 * s));
+    }
+}
+
+// coarse right-hand side: the mean of the residuals b - A v of the 8
+// children (a free coarse cell has only free children); 0 at coarse gates
+__global__ void mg_restrict_kernel(const Geo f, const float* __restrict__ v, const float* __restrict__ b,
+                                   const Geo c, float* __restrict__ bc) {
+    for (long long q = (long long)blockIdx.x * kT + threadIdx.x; q < c.np; q += (long long)gridDim.x * kT) {
+        if (c.code[q] & kCodeGate) {
+            bc[q] = 0.0f;
+            continue;
+        }
+        int jx, jy, jz;
+        coords32(q, c.nx, c.ny, jx, jy, jz);
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int ix = 2 * jx + (k & 1), iy = 2 * jy + ((k >> 1) & 1), iz = 2 * jz + (k >> 2);
+            if (ix >= f.nx || iy >= f.ny || iz >= f.nz) continue;
+            const long long p = idx_of(f, ix, iy, iz);
+            const unsigned cp = f.code[p];
+            if (cp & kCodeGate) continue;
+            float sn = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 6; ++d)
+                if (cp >> d & 1u) sn += v[p + nbr_offset(f, d)];
+            acc += b[p] - f.h2invf * fmaf((float)code_degree(cp), v[p], -sn);
+        }
+        bc[q] = 0.125f * acc;
+    }
+}
+
+// coarsest level: x = A^-1 b on its free points (one CTA, dense inverse of at most 64 x 64)
+__global__ void __launch_bounds__(kT) mg_coarse_kernel(const Geo c, const float* __restrict__ b,
+                                                       float* __restrict__ x, const float* __restrict__ cinv,
+                                                       const int* __restrict__ cidx, int nf) {
+    __shared__ float bf[64];
+    for (int p = threadIdx.x; p < (int)c.np; p += kT)
+        if (cidx[p] >= 0) bf[cidx[p]] = b[p];
+    __syncthreads();
+    for (int p = threadIdx.x; p < (int)c.np; p += kT) {
+        const int i = cidx[p];
+        float s = 0.0f;
+        if (i >= 0)
+            for (int j = 0; j < nf; ++j) s = fmaf(cinv[i * nf + j], bf[j], s);
+        x[p] = s;
+    }
+}
+
+// one weighted-Jacobi sweep xout = y + w D^-1 (b - A y) with y = xin, plus
+// with kCoarse the coarse correction xc of the parent cell (the
+// prolongation fused into the first post-smoothing sweep); 0 at gates.
+// kLast (the last sweep on the grid itself): the result goes to z in FP64,
+// with the block sums of (r.z, r.r) over the FP64 residual r into partial.
+template <bool kCoarse, bool kLast>
+__global__ void mg_smooth_kernel(const Geo g, const float* __restrict__ xin, const Geo c,
+                                 const float* __restrict__ xc, const float* __restrict__ b,
+                                 float* __restrict__ xout, const double* __restrict__ r, double* __restrict__ z,
+                                 double* partial) {
+    double rz = 0.0, rr = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        const unsigned cp = g.code[p];
+        if (cp & kCodeGate) {
+            if constexpr (kLast) z[p] = 0.0;
+            else xout[p] = 0.0f;
+            continue;
+        }
+        float yp = xin[p], s = 0.0f;
+        if constexpr (kCoarse) {
+            int ix, iy, iz;
+            coords32(p, g.nx, g.ny, ix, iy, iz);
+            yp += xc[idx_of(c, ix >> 1, iy >> 1, iz >> 1)];
+#pragma unroll
+            for (int d = 0; d < 6; ++d)
+                if (cp >> d & 1u) {
+                    const int qx = ix + (d == 0) - (d == 1), qy = iy + (d == 2) - (d == 3), qz = iz + (d == 4) - (d == 5);
+                    s += xin[p + nbr_offset(g, d)] + xc[idx_of(c, qx >> 1, qy >> 1, qz >> 1)];
+                }
+        } else {
+#pragma unroll
+            for (int d = 0; d < 6; ++d)
+                if (cp >> d & 1u) s += xin[p + nbr_offset(g, d)];
+        }
+        const float out = fmaf(1.0f - kOmega, yp, kOmega * inv_deg(cp) * fmaf(g.h2f, b[p], s));
+        if constexpr (kLast) {
+            const double zd = (double)out, rd = r[p];
+            z[p] = zd;
+            rz = fma(rd, zd, rz);
+            rr = fma(rd, rd, rr);
+        } else {
+            xout[p] = out;
+        }
+    }
+    if constexpr (kLast) block_sum2(rz, rr, partial);
+}
+
+// z = x (FP32 result of a V-cycle that is the coarsest solve alone) in FP64; partial: (r.z, r.r)
+__global__ void mg_out_kernel(const Geo g, const float* x, const double* r, double* z, double* partial) {
+    double rz = 0.0, rr = 0.0;
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        const double zd = g.gate[p] ? 0.0 : (double)x[p], rd = r[p];
+        z[p] = zd;
+        rz = fma(rd, zd, rz);
+        rr = fma(rd, rd, rr);
+    }
+    block_sum2(rz, rr, partial);
+}
+
+// CG steps around the multigrid preconditioner:
+// r = b - A x (A x in Ax) and its FP32 copy rf, 0 at gates
+__global__ void init_mg_kernel(const Geo g, const double* b, const double* Ax, double* r, float* rf) {
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        const double v = g.gate[p] ? 0.0 : b[p] - Ax[p];
+        r[p] = v;
+        rf[p] = (float)v;
+    }
+}
+
+// x += alpha p, r -= alpha Ap, rf = r in FP32
+__global__ void update_mg_kernel(const Geo g, const double* s, const double* pv, const double* Ap, double* x,
+                                 double* r, float* rf) {
+    const double alpha = s[2];
+    for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
+        if (g.code[p] & kCodeGate) continue;
+        x[p] += alpha * pv[p];
+        const double v = r[p] - alpha * Ap[p];
+        r[p] = v;
+        rf[p] = (float)v;
+    }
+}
+
+// coarse gate mask: a coarse cell is a gate when any child is
+__global__ void mg_gate_kernel(const Geo f, const Geo c, uint8_t* gc) {
+    for (long long q = (long long)blockIdx.x * kT + threadIdx.x; q < c.np; q += (long long)gridDim.x * kT) {
+        int jx, jy, jz;
+        coords(q, c.nx, c.ny, jx, jy, jz);
+        uint8_t gv = 0;
+        for (int k = 0; k < 8; ++k) {
+            const int ix = 2 * jx + (k & 1), iy = 2 * jy + ((k >> 1) & 1), iz = 2 * jz + (k >> 2);
+            if (ix < f.nx && iy < f.ny && iz < f.nz && f.gate[idx_of(f, ix, iy, iz)]) gv = 1;
+        }
+        gc[q] = gv;
+    }
 }
 
 // one block sums the block partials (thread t takes partials t, t + 256, ...
@@ -516,10 +765,43 @@ khp_status pfail(khp_status s, const std::string& m) { return khp_set_error(s, m
 khp::poisson::Geo geo(const khp_poisson_s* P) {
     khp::poisson::Geo g;
     g.nx = P->nx; g.ny = P->ny; g.nz = P->nz; g.np = P->np; g.h2inv = P->h2inv; g.gate = P->gate;
+    g.code = P->code;
+    g.h2f = (float)(1.0 / P->h2inv);
+    g.h2invf = (float)P->h2inv;
     return g;
 }
 
+khp::poisson::Geo mg_geo(const khp_poisson_s* P, int l) {
+    const khp_poisson_s::MGLevel& L = P->mg[l];
+    khp::poisson::Geo g;
+    g.nx = L.nx; g.ny = L.ny; g.nz = L.nz; g.np = L.np; g.h2inv = L.h2inv; g.gate = L.gate;
+    g.code = L.code;
+    g.h2f = (float)(1.0 / L.h2inv);
+    g.h2invf = (float)L.h2inv;
+    return g;
+}
+
+void mg_free(khp_poisson_s* P) {
+    for (int l = 0; l < khp_poisson_s::kMaxLevels; ++l) {
+        khp_poisson_s::MGLevel& L = P->mg[l];
+        if (l > 0) {
+            if (L.gate) cudaFree(L.gate);
+            if (L.code) cudaFree(L.code);
+        }
+        if (L.b) cudaFree(L.b);
+        if (L.u) cudaFree(L.u);
+        if (L.v) cudaFree(L.v);
+        L = khp_poisson_s::MGLevel{};
+    }
+    if (P->mg_cinv) cudaFree(P->mg_cinv);
+    if (P->mg_cidx) cudaFree(P->mg_cidx);
+    P->mg_cinv = nullptr;
+    P->mg_cidx = nullptr;
+    P->mg_n = 0;
+}
+
 void free_all(khp_poisson_s* P) {
+    mg_free(P);
     if (P->have_chunk) cudaGraphExecDestroy(P->chunk);
     if (P->work) cudaStreamDestroy(P->work);
     double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s,
@@ -528,9 +810,159 @@ void free_all(khp_poisson_s* P) {
     for (double* b : bufs)
         if (b) cudaFree(b);
     if (P->gate) cudaFree(P->gate);
+    if (P->code) cudaFree(P->code);
     if (P->host_pinned) cudaFreeHost(P->host_pinned);
     if (P->a_host) cudaFreeHost(P->a_host);
     if (P->r_host) cudaFreeHost(P->r_host);
+}
+
+int mg_blocks(long long np, int nblk) { return (int)std::min<long long>((np + kT - 1) / kT, nblk); }
+
+// Builds the multigrid hierarchy of the handle's grid and gate mask on the
+// handle's stream (synchronous).  Leaves mg_n = 0 (Jacobi preconditioner
+// only) when the grid does not coarsen to at most 64 cells within
+// kMaxLevels levels, or when the coarsest operator is not positive definite
+// (a grid without gates, whose Poisson operator is singular).
+khp_status mg_build(khp_poisson_s* P) {
+    using namespace khp::poisson;
+    using MGLevel = khp_poisson_s::MGLevel;
+    constexpr int kMaxL = khp_poisson_s::kMaxLevels;
+    int dims[kMaxL][3] = {{P->nx, P->ny, P->nz}};
+    auto npl = [&](int l) { return (long long)dims[l][0] * dims[l][1] * dims[l][2]; };
+    int L = 1;
+    while (npl(L - 1) > 64 && L < kMaxL) {
+        for (int a = 0; a < 3; ++a) dims[L][a] = (dims[L - 1][a] + 1) / 2;
+        ++L;
+    }
+    if (npl(L - 1) > 64) return KHP_OK;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < L && e == cudaSuccess; ++l) {
+        MGLevel& M = P->mg[l];
+        M.nx = dims[l][0]; M.ny = dims[l][1]; M.nz = dims[l][2];
+        M.np = npl(l);
+        M.h2inv = std::ldexp(P->h2inv, -2 * l);
+        const size_t vb = sizeof(float) * M.np;
+        if (l == 0) {
+            M.gate = P->gate;
+            M.code = P->code;
+        } else if ((e = cudaMalloc(&M.gate, M.np)) == cudaSuccess) {
+            e = cudaMalloc(&M.code, sizeof(uint16_t) * M.np);
+        }
+        if (e == cudaSuccess && (e = cudaMalloc(&M.b, vb)) == cudaSuccess && (e = cudaMalloc(&M.u, vb)) == cudaSuccess)
+            e = cudaMalloc(&M.v, vb);
+    }
+    if (e != cudaSuccess) {
+        mg_free(P);
+        return pfail(KHP_ERR_OOM, std::string("multigrid levels: ") + cudaGetErrorString(e));
+    }
+    for (int l = 1; l < L; ++l) {
+        const int nb = mg_blocks(P->mg[l].np, P->nblk);
+        mg_gate_kernel<<<nb, kT, 0, P->stream>>>(mg_geo(P, l - 1), mg_geo(P, l), P->mg[l].gate);
+        mg_code_kernel<<<nb, kT, 0, P->stream>>>(mg_geo(P, l), P->mg[l].code);
+    }
+    const MGLevel& C = P->mg[L - 1];
+    const int nc = (int)C.np;
+    std::vector<uint8_t> gh(nc);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(gh.data(), C.gate, nc, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(P->stream)) != cudaSuccess) {
+        mg_free(P);
+        return pfail(KHP_ERR_CUDA, std::string("multigrid gate masks: ") + cudaGetErrorString(e));
+    }
+    // the coarsest operator on its free cells, the same 7-point rule as the kernels
+    std::vector<int> idx(nc, -1);
+    int nf = 0;
+    for (int q = 0; q < nc; ++q)
+        if (!gh[q]) idx[q] = nf++;
+    std::vector<double> A((size_t)nf * nf, 0.0);
+    std::vector<float> inv((size_t)std::max(nf, 1) * std::max(nf, 1), 0.0f);
+    for (int q = 0; q < nc; ++q) {
+        if (idx[q] < 0) continue;
+        const int ix = q % C.nx, iy = (q / C.nx) % C.ny, iz = q / (C.nx * C.ny);
+        const int nb[6][3] = {{ix + 1, iy, iz}, {ix - 1, iy, iz}, {ix, iy + 1, iz},
+                              {ix, iy - 1, iz}, {ix, iy, iz + 1}, {ix, iy, iz - 1}};
+        int deg = 0;
+        for (const auto& n : nb) {
+            if (n[0] < 0 || n[0] >= C.nx || n[1] < 0 || n[1] >= C.ny || n[2] < 0 || n[2] >= C.nz) continue;
+            ++deg;
+            const int j = idx[n[0] + C.nx * (n[1] + C.ny * n[2])];
+            if (j >= 0) A[(size_t)idx[q] * nf + j] -= C.h2inv;
+        }
+        A[(size_t)idx[q] * nf + idx[q]] += C.h2inv * deg;
+    }
+    // Cholesky A = G G^T (lower G in place), then the inverse column by column
+    for (int j = 0; j < nf; ++j) {
+        double d = A[(size_t)j * nf + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * nf + k] * A[(size_t)j * nf + k];
+        if (!(d > 1e-12 * C.h2inv)) {
+            mg_free(P);
+            return KHP_OK;
+        }
+        const double gjj = std::sqrt(d);
+        A[(size_t)j * nf + j] = gjj;
+        for (int i = j + 1; i < nf; ++i) {
+            double v = A[(size_t)i * nf + j];
+            for (int k = 0; k < j; ++k) v -= A[(size_t)i * nf + k] * A[(size_t)j * nf + k];
+            A[(size_t)i * nf + j] = v / gjj;
+        }
+    }
+    std::vector<double> y(nf);
+    for (int c = 0; c < nf; ++c) {
+        for (int i = 0; i < nf; ++i) {       // G y = e_c
+            double v = i == c ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= A[(size_t)i * nf + k] * y[k];
+            y[i] = v / A[(size_t)i * nf + i];
+        }
+        for (int i = nf - 1; i >= 0; --i) {  // G^T x = y
+            double v = y[i];
+            for (int k = i + 1; k < nf; ++k) v -= A[(size_t)k * nf + i] * y[k];
+            y[i] = v / A[(size_t)i * nf + i];
+        }
+        for (int i = 0; i < nf; ++i) inv[(size_t)i * nf + c] = (float)y[i];
+    }
+    if ((e = cudaMalloc(&P->mg_cinv, sizeof(float) * inv.size())) != cudaSuccess ||
+        (e = cudaMalloc(&P->mg_cidx, sizeof(int) * nc)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->mg_cinv, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice,
+                             P->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->mg_cidx, idx.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, P->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(P->stream)) != cudaSuccess) {
+        mg_free(P);
+        return pfail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
+                     std::string("multigrid coarsest level: ") + cudaGetErrorString(e));
+    }
+    P->mg_nf = nf;
+    P->mg_n = L;
+    return KHP_OK;
+}
+
+bool mg_active(const khp_poisson_s* P) { return P->precond == KHP_POISSON_PRECOND_MULTIGRID && P->mg_n > 0; }
+
+// the V-cycle z = M^-1 r (from r's FP32 copy, level 0's b) with the block partials of (r.z, r.r)
+void mg_vcycle(khp_poisson_s* P, cudaStream_t st) {
+    using namespace khp::poisson;
+    const int L = P->mg_n;
+    for (int l = 0; l + 1 < L; ++l) {
+        const Geo f = mg_geo(P, l), c = mg_geo(P, l + 1);
+        mg_presmooth_kernel<<<mg_blocks(f.np, P->nblk), kT, 0, st>>>(f, P->mg[l].b, P->mg[l].v);
+        mg_restrict_kernel<<<mg_blocks(c.np, P->nblk), kT, 0, st>>>(f, P->mg[l].v, P->mg[l].b, c,
+                                                                    P->mg[l + 1].b);
+    }
+    const khp_poisson_s::MGLevel& C = P->mg[L - 1];
+    mg_coarse_kernel<<<1, kT, 0, st>>>(mg_geo(P, L - 1), C.b, C.v, P->mg_cinv, P->mg_cidx, P->mg_nf);
+    for (int l = L - 2; l >= 0; --l) {
+        const Geo f = mg_geo(P, l), c = mg_geo(P, l + 1);
+        const khp_poisson_s::MGLevel& M = P->mg[l];
+        const int nb = mg_blocks(f.np, P->nblk);
+        mg_smooth_kernel<true, false>
+            <<<nb, kT, 0, st>>>(f, M.v, c, P->mg[l + 1].v, M.b, M.u, nullptr, nullptr, nullptr);
+        if (l == 0)
+            mg_smooth_kernel<false, true>
+                <<<nb, kT, 0, st>>>(f, M.u, c, nullptr, M.b, nullptr, P->r, P->z, P->partial);
+        else
+            mg_smooth_kernel<false, false><<<nb, kT, 0, st>>>(f, M.u, c, nullptr, M.b, M.v, nullptr, nullptr, nullptr);
+    }
+    if (L == 1) mg_out_kernel<<<P->nblk, kT, 0, st>>>(geo(P), C.v, P->r, P->z, P->partial);
 }
 
 // Host side of the tall-skinny QR: fold the blocks' factors into one
@@ -646,7 +1078,8 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
     P->nblk = (int)std::min<long long>((np + kT - 1) / kT, 1184);
     cudaError_t e = cudaSuccess;
     const size_t vb = sizeof(double) * np;
-    if ((e = cudaMalloc(&P->gate, np)) != cudaSuccess || (e = cudaMalloc(&P->gphi, vb)) != cudaSuccess ||
+    if ((e = cudaMalloc(&P->gate, np)) != cudaSuccess || (e = cudaMalloc(&P->code, sizeof(uint16_t) * np)) != cudaSuccess ||
+        (e = cudaMalloc(&P->gphi, vb)) != cudaSuccess ||
         (e = cudaMalloc(&P->x, vb)) != cudaSuccess || (e = cudaMalloc(&P->r, vb)) != cudaSuccess ||
         (e = cudaMalloc(&P->z, vb)) != cudaSuccess || (e = cudaMalloc(&P->p, vb)) != cudaSuccess ||
         (e = cudaMalloc(&P->Ap, vb)) != cudaSuccess || (e = cudaMalloc(&P->b, vb)) != cudaSuccess ||
@@ -665,22 +1098,36 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
         return pfail(KHP_ERR_CUDA, std::string("gate copy: ") + cudaGetErrorString(e));
     }
     khp::poisson::copy_gate_values_kernel<<<P->nblk, kT, 0, P->stream>>>(np, P->gate, gate_phi_dev, P->gphi);
+    khp::poisson::mg_code_kernel<<<P->nblk, kT, 0, P->stream>>>(geo(P), P->code);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(P->stream)) != cudaSuccess) {
         free_all(P);
         delete P;
         return pfail(KHP_ERR_CUDA, std::string("gate set-up: ") + cudaGetErrorString(e));
     }
+    P->precond = KHP_POISSON_PRECOND_MULTIGRID;
+    const khp_status ms = mg_build(P);
+    if (ms != KHP_OK) {
+        free_all(P);
+        delete P;
+        return ms;
+    }
     *out = P;
     return KHP_OK;
 }
 
-// the 5 launches of one CG iteration
+// one CG iteration: 5 launches with the Jacobi preconditioner, the
+// V-cycle's in place of the z = r / diag step with the multigrid one
 static void cg_iteration(khp_poisson_s* P, const khp::poisson::Geo& g, cudaStream_t st) {
     using namespace khp::poisson;
     const int nb = P->nblk;
     apply_kernel<<<nb, kT, 0, st>>>(g, P->p, P->Ap, P->partial);
     finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 2, P->s);
-    update_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->z, P->partial);
+    if (mg_active(P)) {
+        update_mg_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->mg[0].b);
+        mg_vcycle(P, st);
+    } else {
+        update_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->z, P->partial);
+    }
     finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 3, P->s);
     direction_kernel<<<nb, kT, 0, st>>>(g, P->s, P->z, P->p);
 }
@@ -700,22 +1147,32 @@ static khp_status cg_solve(khp_poisson P, const double* rho_dev, double rho_scal
     rhs_kernel<<<nb, kT, 0, st>>>(g, rho_dev, gphi, P->coef * rho_scale, phi_dev, P->b, P->x, P->partial);
     finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 0, P->s);
     apply_kernel<<<nb, kT, 0, st>>>(g, P->x, P->Ap, P->partial);
-    init_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->z, P->p, P->partial);
+    const bool mg = mg_active(P);
+    if (mg) {
+        init_mg_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->mg[0].b);
+        mg_vcycle(P, st);
+    } else {
+        init_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->z, P->p, P->partial);
+    }
     finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 1, P->s);
     PCKL("CG set-up launches");
+    if (mg) PCK(cudaMemcpyAsync(P->p, P->z, sizeof(double) * P->np, cudaMemcpyDeviceToDevice, st));
     PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
     const double bb = hp[5];
     double rel = bb > 0.0 ? std::sqrt(hp[4] / bb) : std::sqrt(hp[4]);
     int it = 0;
     // a zero right-hand side with a zero start is already solved
+    // residual check every 16 Jacobi-preconditioned iterations or every 8
+    // multigrid ones (the graph holds the iterations between two checks)
+    const int per_check = mg ? 8 : 16;
     while (rel > tol && it < max_iter) {
-        const int chunk = std::min(16, max_iter - it);
-        if (chunk == 16) {
+        const int chunk = std::min(per_check, max_iter - it);
+        if (chunk == per_check) {
             if (!P->have_chunk) {
                 cudaGraph_t graph;
                 PCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                for (int k = 0; k < 16; ++k) cg_iteration(P, g, st);
+                for (int k = 0; k < per_check; ++k) cg_iteration(P, g, st);
                 PCK(cudaStreamEndCapture(st, &graph));
                 const cudaError_t e = cudaGraphInstantiate(&P->chunk, graph, 0);
                 cudaGraphDestroy(graph);
@@ -1070,6 +1527,21 @@ khp_status khp_sp_relax_occupations(khp_poisson P, const double* dens_dev, const
     if (occ_host)
         for (int j = 0; j < n; ++j) occ_host[j] = f[j];
     if (mu_out) *mu_out = mu;
+    return KHP_OK;
+}
+
+khp_status khp_poisson_set_preconditioner(khp_poisson P, int kind, int* levels) {
+    khp_set_error(KHP_OK, "");
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (kind != KHP_POISSON_PRECOND_JACOBI && kind != KHP_POISSON_PRECOND_MULTIGRID)
+        return pfail(KHP_ERR_INVALID_ARG, "unknown preconditioner");
+    if (kind != P->precond && P->have_chunk) {
+        PCK(cudaStreamSynchronize(P->work));
+        cudaGraphExecDestroy(P->chunk);
+        P->have_chunk = false;
+    }
+    P->precond = kind;
+    if (levels) *levels = mg_active(P) ? P->mg_n : 0;
     return KHP_OK;
 }
 

@@ -26,7 +26,10 @@ EPS_SI = 11.7
 class Poisson:
     """FD Poisson operator on a grid with gate (Dirichlet) points."""
 
-    def __init__(self, nx, ny, nz, h, gate_mask, gate_phi, eps_r=EPS_SI, device="cuda", stream=None):
+    PRECONDITIONERS = {"jacobi": 0, "multigrid": 1}
+
+    def __init__(self, nx, ny, nz, h, gate_mask, gate_phi, eps_r=EPS_SI, device="cuda", stream=None,
+                 preconditioner="multigrid"):
         self.lib = _lib.load()
         self.device = torch.device(device)
         self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
@@ -42,6 +45,19 @@ class Poisson:
                                                    float(eps_r), _ptr(self._gate), _ptr(self._gphi),
                                                    ctypes.c_void_p(self.stream.cuda_stream)))
         self.handle = h_
+        self.set_preconditioner(preconditioner)
+
+    def set_preconditioner(self, kind):
+        """'multigrid' (geometric V-cycle, the default) or 'jacobi' for the
+        later solves; sets and returns `mg_levels`, the multigrid levels in
+        use (0: the Jacobi preconditioner, also where the hierarchy could
+        not be built)."""
+        if kind not in self.PRECONDITIONERS:
+            raise ValueError(f"preconditioner must be one of {sorted(self.PRECONDITIONERS)}")
+        lv = ctypes.c_int(0)
+        _lib.check(self.lib.khp_poisson_set_preconditioner(self.handle, self.PRECONDITIONERS[kind], ctypes.byref(lv)))
+        self.preconditioner, self.mg_levels = kind, lv.value
+        return lv.value
 
     def solve(self, rho, phi=None, tol=1e-12, max_iter=20000):
         """phi [Np] (V) for the hole density rho [Np] (nm^-3); `phi` (if

@@ -79,6 +79,7 @@ def test_host_side_validation_of_the_next_rows(lib):
     assert lib.khp_sp_anderson(None, None, buf, 0.5, 4, buf, ctypes.byref(ch)) == 1
     assert b"NULL" in lib.khp_last_error()
     assert lib.khp_sp_anderson_reset(None) == 1
+    assert lib.khp_poisson_set_preconditioner(None, 1, None) == 1
     assert lib.khp_poisson_destroy(None) == 0
 
 

@@ -41,6 +41,57 @@ def test_poisson_matches_oracle(khp, shape):
     P.close()
 
 
+@pytest.mark.parametrize("shape", [(9, 7, 5), (33, 17, 12), (80, 24, 24), (50, 1, 1), (3, 40, 1), (4, 4, 4)])
+def test_poisson_preconditioners_agree(khp, shape):
+    """The multigrid and the Jacobi preconditioned CG reach the same
+    solution as the oracle's direct solve; the multigrid levels are those
+    of halving every dimension down to at most 64 cells, the V-cycle of a
+    grid of at most 64 cells is the exact inverse (one CG step), and the
+    multigrid takes fewer CG iterations."""
+    from paper_2607_08447_b300.poisson import Poisson
+    nx, ny, nz = shape
+    h = 0.5
+    rng = np.random.default_rng(7 + sum(shape))
+    gate = _end_gates(nx, ny, nz)
+    if nx * ny * nz > 64:
+        gate |= (rng.random((nz, ny, nx)) < 0.03).astype(np.uint8)
+    gphi = rng.uniform(-0.5, 0.8, (nz, ny, nx))
+    rho = rng.random(nx * ny * nz) * 1e-3
+    ref = po.solve(nx, ny, nz, h, gate, gphi, rho)
+    P = Poisson(nx, ny, nz, h, gate, gphi)
+    levels, d = 1, [nx, ny, nz]
+    while d[0] * d[1] * d[2] > 64:
+        d = [(v + 1) // 2 for v in d]
+        levels += 1
+    assert P.mg_levels == levels
+    out = {}
+    for kind in ("multigrid", "jacobi"):
+        P.set_preconditioner(kind)
+        phi = P.solve(torch.from_numpy(rho).cuda(), tol=1e-13, max_iter=50000).cpu().numpy()
+        assert P.last_residual <= 1e-13
+        assert np.abs(phi - ref).max() <= 1e-10 * np.abs(ref).max(), kind
+        out[kind] = P.last_iterations
+    if levels == 1:
+        assert out["multigrid"] == 8          # converged in the first of the 8 iterations between checks
+    if nx * ny * nz >= 5000:
+        assert 4 * out["multigrid"] <= out["jacobi"]
+    P.close()
+
+
+def test_poisson_multigrid_unavailable_without_gates(khp):
+    """A grid without gates has a singular operator: no multigrid hierarchy
+    (the coarsest level has no Cholesky factor), the handle reports the
+    Jacobi preconditioner."""
+    from paper_2607_08447_b300.poisson import Poisson
+    g = np.zeros((10, 10, 10), dtype=np.uint8)
+    P = Poisson(10, 10, 10, 0.5, g, np.zeros((10, 10, 10)))
+    assert P.mg_levels == 0
+    assert P.set_preconditioner("jacobi") == 0
+    with pytest.raises(ValueError):
+        P.set_preconditioner("ilu")
+    P.close()
+
+
 def test_poisson_linear_between_gates(khp):
     from paper_2607_08447_b300.poisson import Poisson
     nx, ny, nz, U = 40, 6, 5, 0.9
