@@ -70,8 +70,9 @@ def _args():
     ap.add_argument("--sweep-chunk", type=int, default=8)
     ap.add_argument("--sweep-plain", type=int, default=4,
                     help="sweep points also solved in plain FP64 for the mixed-vs-plain speed-up")
-    ap.add_argument("--profile", choices=["plain", "mixed", "dc"], default=None,
-                    help="one short C2 solve (6 outer iterations) for profiler captures; prints its stats")
+    ap.add_argument("--profile", choices=["plain", "mixed", "dc", "poisson"], default=None,
+                    help="one short C2 solve (6 outer iterations; 'poisson': one Poisson solve from zero on the "
+                         "C2 grid with gates on the x faces) for profiler captures; prints its stats")
     ap.add_argument("--sweep-start", choices=["coarse", "random"], default="coarse",
                     help="start block of the sweep's solves (coarse-grid start or random)")
     ap.add_argument("--profile-start", choices=["random", "coarse"], default="random",
@@ -777,6 +778,19 @@ def run_profile(args):
     import inputs
     import paper_2607_08447_b300 as khp
     p = inputs.config2()
+    if args.profile == "poisson":
+        from paper_2607_08447_b300.poisson import Poisson
+        gate = np.zeros((p.nz, p.ny, p.nx), dtype=np.uint8)
+        gate[:, :, 0] = 1
+        gate[:, :, -1] = 1
+        P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V))
+        rho = torch.from_numpy(np.random.default_rng(5).random(p.n_points) * 1e-3).cuda()
+        phi = P.solve(rho, tol=1e-10)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "poisson", "multigrid_levels": P.mg_levels, "iterations": P.last_iterations,
+                          "rel_residual": P.last_residual, "phi_max": float(phi.abs().max())}), flush=True)
+        P.close()
+        return
     g = khp.KPGrid.from_problem(p)
     prec = {"plain": 0, "mixed": 1, "dc": 2}[args.profile]
     # a random start by default: then every captured launch is the full
