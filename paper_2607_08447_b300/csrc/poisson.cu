@@ -314,31 +314,39 @@ __global__ void mg_presmooth_kernel(const Geo g, const float* __restrict__ b, fl
 }
 
 // coarse right-hand side: the mean of the residuals b - A v of the 8
-// children (a free coarse cell has only free children); 0 at coarse gates
+// children (a free coarse cell has only free children); 0 at coarse gates.
+// Eight consecutive lanes per coarse cell, one child each, summed by
+// shuffles in a fixed order.
 __global__ void mg_restrict_kernel(const Geo f, const float* __restrict__ v, const float* __restrict__ b,
                                    const Geo c, float* __restrict__ bc) {
-    for (long long q = (long long)blockIdx.x * kT + threadIdx.x; q < c.np; q += (long long)gridDim.x * kT) {
-        if (c.code[q] & kCodeGate) {
-            bc[q] = 0.0f;
-            continue;
-        }
-        int jx, jy, jz;
-        coords32(q, c.nx, c.ny, jx, jy, jz);
-        float acc = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
+    const long long n8 = 8 * c.np;
+    // n8 and the stride are multiples of 8: the 8 lanes of a cell run every iteration together
+    for (long long t = (long long)blockIdx.x * kT + threadIdx.x; t < n8; t += (long long)gridDim.x * kT) {
+        const long long q = t >> 3;
+        const int k = (int)(t & 7);
+        const bool cgate = (c.code[q] & kCodeGate) != 0;
+        float res = 0.0f;
+        if (!cgate) {
+            int jx, jy, jz;
+            coords32(q, c.nx, c.ny, jx, jy, jz);
             const int ix = 2 * jx + (k & 1), iy = 2 * jy + ((k >> 1) & 1), iz = 2 * jz + (k >> 2);
-            if (ix >= f.nx || iy >= f.ny || iz >= f.nz) continue;
-            const long long p = idx_of(f, ix, iy, iz);
-            const unsigned cp = f.code[p];
-            if (cp & kCodeGate) continue;
-            float sn = 0.0f;
+            if (ix < f.nx && iy < f.ny && iz < f.nz) {
+                const long long p = idx_of(f, ix, iy, iz);
+                const unsigned cp = f.code[p];
+                if (!(cp & kCodeGate)) {
+                    float sn = 0.0f;
 #pragma unroll
-            for (int d = 0; d < 6; ++d)
-                if (cp >> d & 1u) sn += v[p + nbr_offset(f, d)];
-            acc += b[p] - f.h2invf * fmaf((float)code_degree(cp), v[p], -sn);
+                    for (int d = 0; d < 6; ++d)
+                        if (cp >> d & 1u) sn += v[p + nbr_offset(f, d)];
+                    res = b[p] - f.h2invf * fmaf((float)code_degree(cp), v[p], -sn);
+                }
+            }
         }
-        bc[q] = 0.125f * acc;
+        const unsigned mask = 0xFFu << (threadIdx.x & 24u);
+        res += __shfl_xor_sync(mask, res, 1);
+        res += __shfl_xor_sync(mask, res, 2);
+        res += __shfl_xor_sync(mask, res, 4);
+        if (k == 0) bc[q] = cgate ? 0.0f : 0.125f * res;
     }
 }
 
@@ -945,8 +953,8 @@ void mg_vcycle(khp_poisson_s* P, cudaStream_t st) {
     for (int l = 0; l + 1 < L; ++l) {
         const Geo f = mg_geo(P, l), c = mg_geo(P, l + 1);
         mg_presmooth_kernel<<<mg_blocks(f.np, P->nblk), kT, 0, st>>>(f, P->mg[l].b, P->mg[l].v);
-        mg_restrict_kernel<<<mg_blocks(c.np, P->nblk), kT, 0, st>>>(f, P->mg[l].v, P->mg[l].b, c,
-                                                                    P->mg[l + 1].b);
+        mg_restrict_kernel<<<mg_blocks(8 * c.np, P->nblk), kT, 0, st>>>(f, P->mg[l].v, P->mg[l].b, c,
+                                                                        P->mg[l + 1].b);
     }
     const khp_poisson_s::MGLevel& C = P->mg[L - 1];
     mg_coarse_kernel<<<1, kT, 0, st>>>(mg_geo(P, L - 1), C.b, C.v, P->mg_cinv, P->mg_cidx, P->mg_nf);
