@@ -43,6 +43,11 @@ WORKLOAD = ("c2: 160x48x48 grid h=0.5nm (2.21M unknowns), FP64, lowest 16 of blo
 SOLVE_KW = dict(n_states=16, block_m=24, degree=180, precision=0, tol=1e-10, seed=1, max_iter=600, start="coarse")
 RANDOM_START_DEGREE = 120
 MIXED_DEGREE = 250        # defect-corrected FP32 filter (precision 2), coarse-grid start
+# block width of the relaxed-occupation SP loops: their solves need 5-6
+# outer iterations at 24 columns; measured over 24 iterations at C2 (B300,
+# s per SP iteration): 24 cols 0.683, 28 cols 0.594, 32 cols 0.685
+# (degree 200: 0.623), with identical iterates
+RELAXED_BLOCK_M = 28
 MIXED_DEGREE_WARM = 200   # the same filter from warm or random starts
 CROP = (32, 12, 12)
 # DRAM bytes per point-vector of the FP64 fused stencil launch, from ncu
@@ -601,12 +606,14 @@ def _sp_bench(p, dev, torch, khp):
             ("relaxed_1p5k_linear", 1.5, dict(mix=0.5, relax=True)),
             ("relaxed_1p5k_anderson", 1.5, dict(mix=0.8, anderson_depth=4, relax=True)))
     for name, T, opt in runs:
+        kw_run = dict(kw, block_m=RELAXED_BLOCK_M) if opt.get("relax") else kw
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ra = sp_solve(g, P, p.V, SOLVE_KW["n_states"], 2.0, T=T, iters=24, tol_v=1e-6, strain=p.strain,
-                      B=p.B, gauge=p.gauge, solve_kw=kw, warm=False, **opt)
+                      B=p.B, gauge=p.gauge, solve_kw=kw_run, warm=False, **opt)
         torch.cuda.synchronize()
         out[name] = {"T_K": T, "iterations": len(ra.history), "s_total": time.perf_counter() - t0,
+                     "block_m": kw_run["block_m"],
                      "converged": ra.history[-1] <= 1e-6,
                      "max_dV_last_ev": [float(f"{x:.3g}") for x in ra.history[-4:]]}
         if ra.occupations is not None:
