@@ -313,6 +313,24 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
 khp_status khp_poisson_solve(khp_poisson p, const double* rho_dev, double* phi_dev, double tol, int max_iter,
                              int* iterations, double* rel_residual);
 
+/* Solves of nrhs right-hand sides at once (the Coulomb potentials of the
+ * CI's pair densities, the unit-occupation potentials of the relaxed SP
+ * update): the CG runs them side by side in batches of up to 32, every
+ * kernel launch covering the batch, until the largest relative residual of
+ * the batch is at most tol.
+ *  rho_dev   float64 [nrhs][Np] densities [nm^-3] (device)
+ *  phi_dev   float64 [nrhs][Np] (device): in = starting guesses, out = phi [V]
+ *  grounded  nonzero: gate potentials zero (the potential of the density
+ *            alone); 0: the handle's gate potentials
+ *  iterations      optional: the most CG iterations a batch took
+ *  max_rel_residual optional: the largest relative residual
+ * Synchronises the handle's stream.  Errors: INVALID_ARG (NULL arrays,
+ * nrhs < 1, tol <= 0, max_iter < 1), OOM (the batch's vectors: about
+ * 62 bytes per point and right-hand side, allocated on first use),
+ * NOT_CONVERGED as khp_poisson_solve. */
+khp_status khp_poisson_solve_many(khp_poisson p, const double* rho_dev, double* phi_dev, int nrhs, int grounded,
+                                  double tol, int max_iter, int* iterations, double* max_rel_residual);
+
 /* Selects the preconditioner of the handle's later solves
  * (KHP_POISSON_PRECOND_*; multigrid is the default).  The multigrid
  * hierarchy is built by khp_poisson_create: three FP32 vectors and a 16-bit

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "KHP_OK", 1: "KHP_ERR_INVALID_ARG", 2: "KHP_ERR_CUDA", 3: "KH
                 4: "KHP_ERR_NOT_CONVERGED", 5: "KHP_ERR_BREAKDOWN", 6: "KHP_ERR_STATE",
                 7: "KHP_ERR_DEGENERATE"}
 
-EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_position_moments", "khp_create_grid_h0", "khp_poisson_create", "khp_poisson_solve", "khp_poisson_set_preconditioner", "khp_sp_update",
+EXPORTED = ["khp_create_grid", "khp_project_rows", "khp_pair_densities", "khp_position_moments", "khp_create_grid_h0", "khp_poisson_create", "khp_poisson_solve", "khp_poisson_solve_many", "khp_poisson_set_preconditioner", "khp_sp_update",
             "khp_poisson_destroy", "khp_set_potential_strain_field", "khp_apply", "khp_project", "khp_rotate",
             "khp_eigensolve",
             "khp_eigensolve_batched",
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.khp_poisson_create.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, vp, vp, vp]
     lib.khp_poisson_solve.argtypes = [vp, vp, vp, d, i, ctypes.POINTER(i), dp]
     lib.khp_poisson_set_preconditioner.argtypes = [vp, i, ctypes.POINTER(i)]
+    lib.khp_poisson_solve_many.argtypes = [vp, vp, vp, i, i, d, i, ctypes.POINTER(i), dp]
     lib.khp_sp_update.argtypes = [vp, vp, vp, d, vp, dp]
     lib.khp_sp_anderson.argtypes = [vp, vp, vp, d, i, vp, dp]
     lib.khp_sp_anderson_reset.argtypes = [vp]

@@ -146,11 +146,11 @@ def ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=None, method=0, e_c=Non
     # Coulomb: potentials of every pair density (real and imaginary parts),
     # contracted against the pair densities on the tensor cores
     R = grid.pair_densities(psi)                                # [Np][n n], rho_jl at j n + l
-    V = torch.empty_like(R)
-    for k in range(n * n):
-        re = poisson.solve(R[:, k].real.contiguous(), tol=1e-13)
-        im = poisson.solve(R[:, k].imag.contiguous(), tol=1e-13)
-        V[:, k] = torch.complex(re, im)
+    # the real and imaginary parts of all n^2 pair densities, solved side by
+    # side with grounded gates
+    rho = torch.cat([R.real.t(), R.imag.t()]).contiguous()     # [2 n^2][Np]
+    phi = poisson.solve_many(rho, grounded=True, tol=1e-13)
+    V = torch.complex(phi[:n * n].t(), phi[n * n:].t()).contiguous()
     _, S = grid.project_rows(R, V, method=m_cb)
     # S[(k i), (j l)] = sum_p conj(rho_ki) V_jl = sum_p rho_ik V_jl; the
     # potentials were solved for rho (per point), hence the 1 / h^3

@@ -31,14 +31,8 @@ struct khp_poisson_s {
     uint8_t* gate;
     uint16_t* code;        // neighbour codes of the grid's points (see Geo)
     double* gphi;
-    double *x, *r, *z, *p, *Ap, *b;
-    double* partial;       // [nblk][2]
     int nblk;
-    double* s;             // device scalars: 0 rz, 1 pAp, 2 alpha, 3 beta, 4 rr, 5 bb, 6 max change
-    double* host_pinned;   // [8]
-    cudaStream_t work;     // private stream: the CG chunk is captured and replayed on it
-    cudaGraphExec_t chunk; // 16 CG iterations, instantiated on first use
-    bool have_chunk;
+    cudaStream_t work;     // private stream: the CG chunks are captured and replayed on it
     // Anderson mixing of the SP loop (allocated on first use)
     double *a_dv, *a_df;   // [kMaxDepth][np] rings of iterate / residual differences
     double *a_vprev, *a_fprev, *a_f;   // [np]
@@ -55,7 +49,7 @@ struct khp_poisson_s {
     int r_nmax, r_nq;      // capacity; states whose Q holds a previous solution
     bool r_have_phig;
     // multigrid preconditioner of the CG (FP32): level 0 is the grid itself
-    // (its right-hand side b is the FP32 copy of the CG residual r; its last
+    // (its right-hand side is the FP32 copy of the CG residual r; its last
     // sweep writes the CG's z in FP64), levels 1.. the 2x2x2-aggregated grids
     struct MGLevel {
         int nx, ny, nz;
@@ -63,11 +57,28 @@ struct khp_poisson_s {
         double h2inv;
         uint8_t* gate;     // level 0: the handle's gate mask
         uint16_t* code;    // level 0: the handle's codes
-        float *b, *u, *v;  // right-hand side, smoothing scratch, result
     };
     static constexpr int kMaxLevels = 12;
+    static constexpr int kMaxRhs = 32;
     int mg_n;              // levels; 0 when the hierarchy could not be built
     MGLevel mg[kMaxLevels];
+    // the vectors of a CG run over up to cap right-hand sides: [cap][np]
+    // (the FP32 multigrid vectors [cap][np_l]), scalars [cap][8] (0 rz,
+    // 1 pAp, 2 alpha, 3 beta, 4 rr, 5 bb, 6 max change), block partials
+    // [cap][nblk][2]
+    struct CGSpace {
+        int cap;
+        double *x, *r, *z, *p, *Ap, *b, *partial, *s;
+        double* host;                      // pinned [cap][8]
+        float* mb[kMaxLevels];             // level right-hand sides (level 0: r in FP32)
+        float* mu[kMaxLevels];             // smoothing scratch
+        float* mv[kMaxLevels];             // level results
+        cudaGraphExec_t chunk;             // the iterations between two residual checks
+        bool have_chunk;
+        int chunk_n;                       // right-hand sides the chunk was captured for
+    };
+    CGSpace one;           // one right-hand side (its partials and scalars also serve the SP updates)
+    CGSpace many;          // up to kMaxRhs right-hand sides, allocated on first use
     float* mg_cinv;        // inverse of the coarsest operator on its free points [nf][nf]
     int* mg_cidx;          // coarsest cell -> free index, -1 at gates
     int mg_nf;
@@ -144,10 +155,21 @@ __device__ __forceinline__ void block_sum2(double va, double vb, double* partial
     }
 }
 
+// Every CG and multigrid kernel runs the right-hand side blockIdx.y of a
+// batch: its vectors follow each other at the stride of their level's
+// point count (rho and phi at the caller's strides), its scalars at a
+// stride of 8, its block partials at a stride of 2 x the launch's blocks.
+
 // b = (e/eps) rho + h^-2 sum_{gate nbrs} phi_gate at free points, 0 at gates;
 // x = initial guess at free points, 0 at gates; partial: (b.b, 0)
-__global__ void rhs_kernel(const Geo g, const double* rho, const double* gphi, double coef, const double* phi_in,
-                           double* b, double* x, double* partial) {
+__global__ void rhs_kernel(const Geo g, const double* rho, long long ld_rho, const double* gphi, double coef,
+                           const double* phi_in, long long ld_phi, double* b, double* x, double* partial) {
+    const long long k = blockIdx.y;
+    rho += k * ld_rho;
+    if (phi_in) phi_in += k * ld_phi;
+    b += k * g.np;
+    x += k * g.np;
+    partial += 2 * gridDim.x * k;
     double bb = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         if (g.gate[p]) {
@@ -171,6 +193,10 @@ __global__ void rhs_kernel(const Geo g, const double* rho, const double* gphi, d
 
 // y = A x on free points (0 at gates); partial: (x.y, 0)
 __global__ void apply_kernel(const Geo g, const double* __restrict__ x, double* __restrict__ y, double* partial) {
+    const long long k = blockIdx.y;
+    x += k * g.np;
+    y += k * g.np;
+    partial += 2 * gridDim.x * k;
     double xy = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         const unsigned c = g.code[p];
@@ -192,6 +218,13 @@ __global__ void apply_kernel(const Geo g, const double* __restrict__ x, double* 
 // r = b - A x (A x in y), z = r / diag, p = z; partial: (r.z, r.r)
 __global__ void init_kernel(const Geo g, const double* b, const double* Ax, double* r, double* z, double* pv,
                             double* partial) {
+    const long long k = blockIdx.y;
+    b += k * g.np;
+    Ax += k * g.np;
+    r += k * g.np;
+    z += k * g.np;
+    pv += k * g.np;
+    partial += 2 * gridDim.x * k;
     double rz = 0.0, rr = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         if (g.gate[p]) {
@@ -216,7 +249,14 @@ __global__ void init_kernel(const Geo g, const double* b, const double* Ax, doub
 // x += alpha p, r -= alpha Ap, z = r / diag; partial: (r.z, r.r)
 __global__ void update_kernel(const Geo g, const double* s, const double* pv, const double* Ap, double* x, double* r,
                               double* z, double* partial) {
-    const double alpha = s[2];
+    const long long k = blockIdx.y;
+    pv += k * g.np;
+    Ap += k * g.np;
+    x += k * g.np;
+    r += k * g.np;
+    z += k * g.np;
+    partial += 2 * gridDim.x * k;
+    const double alpha = s[8 * k + 2];
     double rz = 0.0, rr = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         const unsigned c = g.code[p];
@@ -235,7 +275,10 @@ __global__ void update_kernel(const Geo g, const double* s, const double* pv, co
 
 // p = z + beta p
 __global__ void direction_kernel(const Geo g, const double* s, const double* z, double* pv) {
-    const double beta = s[3];
+    const long long k = blockIdx.y;
+    z += k * g.np;
+    pv += k * g.np;
+    const double beta = s[8 * k + 3];
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT)
         if (!g.gate[p]) pv[p] = z[p] + beta * pv[p];
 }
@@ -293,6 +336,8 @@ __global__ void mg_code_kernel(const Geo g, uint16_t* code) {
 // pre-smoothing from a zero start, both sweeps in one pass:
 // u = w D^-1 b, v = u + w D^-1 (b - A u) (u of the neighbours recomputed); 0 at gates
 __global__ void mg_presmooth_kernel(const Geo g, const float* __restrict__ b, float* __restrict__ v) {
+    b += blockIdx.y * g.np;
+    v += blockIdx.y * g.np;
     const float wh2 = kOmega * g.h2f;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         const unsigned c = g.code[p];
@@ -319,6 +364,9 @@ __global__ void mg_presmooth_kernel(const Geo g, const float* __restrict__ b, fl
 // shuffles in a fixed order.
 __global__ void mg_restrict_kernel(const Geo f, const float* __restrict__ v, const float* __restrict__ b,
                                    const Geo c, float* __restrict__ bc) {
+    v += blockIdx.y * f.np;
+    b += blockIdx.y * f.np;
+    bc += blockIdx.y * c.np;
     const long long n8 = 8 * c.np;
     // n8 and the stride are multiples of 8: the 8 lanes of a cell run every iteration together
     for (long long t = (long long)blockIdx.x * kT + threadIdx.x; t < n8; t += (long long)gridDim.x * kT) {
@@ -354,6 +402,8 @@ __global__ void mg_restrict_kernel(const Geo f, const float* __restrict__ v, con
 __global__ void __launch_bounds__(kT) mg_coarse_kernel(const Geo c, const float* __restrict__ b,
                                                        float* __restrict__ x, const float* __restrict__ cinv,
                                                        const int* __restrict__ cidx, int nf) {
+    b += blockIdx.x * c.np;     // one CTA per right-hand side
+    x += blockIdx.x * c.np;
     __shared__ float bf[64];
     for (int p = threadIdx.x; p < (int)c.np; p += kT)
         if (cidx[p] >= 0) bf[cidx[p]] = b[p];
@@ -377,6 +427,17 @@ __global__ void mg_smooth_kernel(const Geo g, const float* __restrict__ xin, con
                                  const float* __restrict__ xc, const float* __restrict__ b,
                                  float* __restrict__ xout, const double* __restrict__ r, double* __restrict__ z,
                                  double* partial) {
+    const long long k = blockIdx.y;
+    xin += k * g.np;
+    b += k * g.np;
+    if constexpr (kCoarse) xc += k * c.np;
+    if constexpr (kLast) {
+        r += k * g.np;
+        z += k * g.np;
+        partial += 2 * gridDim.x * k;
+    } else {
+        xout += k * g.np;
+    }
     double rz = 0.0, rr = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         const unsigned cp = g.code[p];
@@ -416,6 +477,11 @@ __global__ void mg_smooth_kernel(const Geo g, const float* __restrict__ xin, con
 
 // z = x (FP32 result of a V-cycle that is the coarsest solve alone) in FP64; partial: (r.z, r.r)
 __global__ void mg_out_kernel(const Geo g, const float* x, const double* r, double* z, double* partial) {
+    const long long k = blockIdx.y;
+    x += k * g.np;
+    r += k * g.np;
+    z += k * g.np;
+    partial += 2 * gridDim.x * k;
     double rz = 0.0, rr = 0.0;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         const double zd = g.gate[p] ? 0.0 : (double)x[p], rd = r[p];
@@ -429,6 +495,11 @@ __global__ void mg_out_kernel(const Geo g, const float* x, const double* r, doub
 // CG steps around the multigrid preconditioner:
 // r = b - A x (A x in Ax) and its FP32 copy rf, 0 at gates
 __global__ void init_mg_kernel(const Geo g, const double* b, const double* Ax, double* r, float* rf) {
+    const long long k = blockIdx.y;
+    b += k * g.np;
+    Ax += k * g.np;
+    r += k * g.np;
+    rf += k * g.np;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         const double v = g.gate[p] ? 0.0 : b[p] - Ax[p];
         r[p] = v;
@@ -439,7 +510,13 @@ __global__ void init_mg_kernel(const Geo g, const double* b, const double* Ax, d
 // x += alpha p, r -= alpha Ap, rf = r in FP32
 __global__ void update_mg_kernel(const Geo g, const double* s, const double* pv, const double* Ap, double* x,
                                  double* r, float* rf) {
-    const double alpha = s[2];
+    const long long k = blockIdx.y;
+    pv += k * g.np;
+    Ap += k * g.np;
+    x += k * g.np;
+    r += k * g.np;
+    rf += k * g.np;
+    const double alpha = s[8 * k + 2];
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT) {
         if (g.code[p] & kCodeGate) continue;
         x[p] += alpha * pv[p];
@@ -471,6 +548,8 @@ __global__ void mg_gate_kernel(const Geo f, const Geo c, uint8_t* gc) {
 //  2: s[1] = pAp, s[2] = rz / pAp    (after apply_kernel on p)
 //  3: s[3] = rz_new / rz, s[0] = rz_new, s[4] = rr   (after update_kernel)
 __global__ void __launch_bounds__(kT) finish_kernel(const double* partial, int nblk, int mode, double* s) {
+    partial += 2 * (long long)nblk * blockIdx.x;   // one CTA per right-hand side
+    s += 8 * blockIdx.x;
     __shared__ double sa[kT], sb[kT];
     double a = 0.0, b = 0.0;
     for (int k = threadIdx.x; k < nblk; k += kT) {
@@ -497,7 +576,9 @@ __global__ void __launch_bounds__(kT) finish_kernel(const double* partial, int n
 }
 
 // phi = x at free points, phi_gate at gates
-__global__ void output_kernel(const Geo g, const double* x, const double* gphi, double* phi) {
+__global__ void output_kernel(const Geo g, const double* x, const double* gphi, double* phi, long long ld_phi) {
+    x += blockIdx.y * g.np;
+    phi += blockIdx.y * ld_phi;
     for (long long p = (long long)blockIdx.x * kT + threadIdx.x; p < g.np; p += (long long)gridDim.x * kT)
         phi[p] = g.gate[p] ? gphi[p] : x[p];
 }
@@ -790,17 +871,12 @@ khp::poisson::Geo mg_geo(const khp_poisson_s* P, int l) {
 }
 
 void mg_free(khp_poisson_s* P) {
-    for (int l = 0; l < khp_poisson_s::kMaxLevels; ++l) {
+    for (int l = 1; l < khp_poisson_s::kMaxLevels; ++l) {
         khp_poisson_s::MGLevel& L = P->mg[l];
-        if (l > 0) {
-            if (L.gate) cudaFree(L.gate);
-            if (L.code) cudaFree(L.code);
-        }
-        if (L.b) cudaFree(L.b);
-        if (L.u) cudaFree(L.u);
-        if (L.v) cudaFree(L.v);
-        L = khp_poisson_s::MGLevel{};
+        if (L.gate) cudaFree(L.gate);
+        if (L.code) cudaFree(L.code);
     }
+    for (auto& L : P->mg) L = khp_poisson_s::MGLevel{};
     if (P->mg_cinv) cudaFree(P->mg_cinv);
     if (P->mg_cidx) cudaFree(P->mg_cidx);
     P->mg_cinv = nullptr;
@@ -808,26 +884,62 @@ void mg_free(khp_poisson_s* P) {
     P->mg_n = 0;
 }
 
+void space_free(khp_poisson_s::CGSpace& w) {
+    if (w.have_chunk) cudaGraphExecDestroy(w.chunk);
+    double* bufs[] = {w.x, w.r, w.z, w.p, w.Ap, w.b, w.partial, w.s};
+    for (double* b : bufs)
+        if (b) cudaFree(b);
+    if (w.host) cudaFreeHost(w.host);
+    for (int l = 0; l < khp_poisson_s::kMaxLevels; ++l) {
+        if (w.mb[l]) cudaFree(w.mb[l]);
+        if (w.mu[l]) cudaFree(w.mu[l]);
+        if (w.mv[l]) cudaFree(w.mv[l]);
+    }
+    w = khp_poisson_s::CGSpace{};
+}
+
+// the vectors of cap right-hand sides (the multigrid ones for the levels built)
+cudaError_t space_alloc(khp_poisson_s* P, khp_poisson_s::CGSpace& w, int cap) {
+    space_free(w);
+    w.cap = cap;
+    const size_t vb = sizeof(double) * (size_t)P->np * cap;
+    cudaError_t e;
+    if ((e = cudaMalloc(&w.x, vb)) != cudaSuccess || (e = cudaMalloc(&w.r, vb)) != cudaSuccess ||
+        (e = cudaMalloc(&w.z, vb)) != cudaSuccess || (e = cudaMalloc(&w.p, vb)) != cudaSuccess ||
+        (e = cudaMalloc(&w.Ap, vb)) != cudaSuccess || (e = cudaMalloc(&w.b, vb)) != cudaSuccess ||
+        (e = cudaMalloc(&w.partial, sizeof(double) * 2 * P->nblk * cap)) != cudaSuccess ||
+        (e = cudaMalloc(&w.s, sizeof(double) * 8 * cap)) != cudaSuccess ||
+        (e = cudaMallocHost(&w.host, sizeof(double) * 8 * cap)) != cudaSuccess)
+        return e;
+    for (int l = 0; l < P->mg_n; ++l) {
+        const size_t fb = sizeof(float) * (size_t)P->mg[l].np * cap;
+        if ((e = cudaMalloc(&w.mb[l], fb)) != cudaSuccess || (e = cudaMalloc(&w.mu[l], fb)) != cudaSuccess ||
+            (e = cudaMalloc(&w.mv[l], fb)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
 void free_all(khp_poisson_s* P) {
+    space_free(P->one);
+    space_free(P->many);
     mg_free(P);
-    if (P->have_chunk) cudaGraphExecDestroy(P->chunk);
     if (P->work) cudaStreamDestroy(P->work);
-    double* bufs[] = {P->gphi, P->x, P->r, P->z, P->p, P->Ap, P->b, P->partial, P->s,
-                      P->a_dv, P->a_df, P->a_vprev, P->a_fprev, P->a_f, P->a_partial,
+    double* bufs[] = {P->gphi, P->a_dv, P->a_df, P->a_vprev, P->a_fprev, P->a_f, P->a_partial,
                       P->r_Q, P->r_phig, P->r_zero, P->r_partial, P->r_out};
     for (double* b : bufs)
         if (b) cudaFree(b);
     if (P->gate) cudaFree(P->gate);
     if (P->code) cudaFree(P->code);
-    if (P->host_pinned) cudaFreeHost(P->host_pinned);
     if (P->a_host) cudaFreeHost(P->a_host);
     if (P->r_host) cudaFreeHost(P->r_host);
 }
 
 int mg_blocks(long long np, int nblk) { return (int)std::min<long long>((np + kT - 1) / kT, nblk); }
 
-// Builds the multigrid hierarchy of the handle's grid and gate mask on the
-// handle's stream (synchronous).  Leaves mg_n = 0 (Jacobi preconditioner
+// Builds the multigrid hierarchy (geometry, gate masks, codes, coarsest
+// inverse; the vectors belong to the CG spaces) of the handle's grid and
+// gate mask on the handle's stream (synchronous).  Leaves mg_n = 0 (Jacobi preconditioner
 // only) when the grid does not coarsen to at most 64 cells within
 // kMaxLevels levels, or when the coarsest operator is not positive definite
 // (a grid without gates, whose Poisson operator is singular).
@@ -849,15 +961,12 @@ khp_status mg_build(khp_poisson_s* P) {
         M.nx = dims[l][0]; M.ny = dims[l][1]; M.nz = dims[l][2];
         M.np = npl(l);
         M.h2inv = std::ldexp(P->h2inv, -2 * l);
-        const size_t vb = sizeof(float) * M.np;
         if (l == 0) {
             M.gate = P->gate;
             M.code = P->code;
         } else if ((e = cudaMalloc(&M.gate, M.np)) == cudaSuccess) {
             e = cudaMalloc(&M.code, sizeof(uint16_t) * M.np);
         }
-        if (e == cudaSuccess && (e = cudaMalloc(&M.b, vb)) == cudaSuccess && (e = cudaMalloc(&M.u, vb)) == cudaSuccess)
-            e = cudaMalloc(&M.v, vb);
     }
     if (e != cudaSuccess) {
         mg_free(P);
@@ -946,31 +1055,32 @@ khp_status mg_build(khp_poisson_s* P) {
 
 bool mg_active(const khp_poisson_s* P) { return P->precond == KHP_POISSON_PRECOND_MULTIGRID && P->mg_n > 0; }
 
-// the V-cycle z = M^-1 r (from r's FP32 copy, level 0's b) with the block partials of (r.z, r.r)
-void mg_vcycle(khp_poisson_s* P, cudaStream_t st) {
+// the V-cycle z = M^-1 r of n right-hand sides (from r's FP32 copy, level
+// 0's b) with the block partials of (r.z, r.r)
+void mg_vcycle(khp_poisson_s* P, const khp_poisson_s::CGSpace& w, cudaStream_t st, int n) {
     using namespace khp::poisson;
     const int L = P->mg_n;
     for (int l = 0; l + 1 < L; ++l) {
         const Geo f = mg_geo(P, l), c = mg_geo(P, l + 1);
-        mg_presmooth_kernel<<<mg_blocks(f.np, P->nblk), kT, 0, st>>>(f, P->mg[l].b, P->mg[l].v);
-        mg_restrict_kernel<<<mg_blocks(8 * c.np, P->nblk), kT, 0, st>>>(f, P->mg[l].v, P->mg[l].b, c,
-                                                                        P->mg[l + 1].b);
+        mg_presmooth_kernel<<<dim3(mg_blocks(f.np, P->nblk), n), kT, 0, st>>>(f, w.mb[l], w.mv[l]);
+        mg_restrict_kernel<<<dim3(mg_blocks(8 * c.np, P->nblk), n), kT, 0, st>>>(f, w.mv[l], w.mb[l], c,
+                                                                                 w.mb[l + 1]);
     }
-    const khp_poisson_s::MGLevel& C = P->mg[L - 1];
-    mg_coarse_kernel<<<1, kT, 0, st>>>(mg_geo(P, L - 1), C.b, C.v, P->mg_cinv, P->mg_cidx, P->mg_nf);
+    mg_coarse_kernel<<<n, kT, 0, st>>>(mg_geo(P, L - 1), w.mb[L - 1], w.mv[L - 1], P->mg_cinv, P->mg_cidx,
+                                       P->mg_nf);
     for (int l = L - 2; l >= 0; --l) {
         const Geo f = mg_geo(P, l), c = mg_geo(P, l + 1);
-        const khp_poisson_s::MGLevel& M = P->mg[l];
-        const int nb = mg_blocks(f.np, P->nblk);
+        const dim3 grid(mg_blocks(f.np, P->nblk), n);
         mg_smooth_kernel<true, false>
-            <<<nb, kT, 0, st>>>(f, M.v, c, P->mg[l + 1].v, M.b, M.u, nullptr, nullptr, nullptr);
+            <<<grid, kT, 0, st>>>(f, w.mv[l], c, w.mv[l + 1], w.mb[l], w.mu[l], nullptr, nullptr, nullptr);
         if (l == 0)
             mg_smooth_kernel<false, true>
-                <<<nb, kT, 0, st>>>(f, M.u, c, nullptr, M.b, nullptr, P->r, P->z, P->partial);
+                <<<grid, kT, 0, st>>>(f, w.mu[0], c, nullptr, w.mb[0], nullptr, w.r, w.z, w.partial);
         else
-            mg_smooth_kernel<false, false><<<nb, kT, 0, st>>>(f, M.u, c, nullptr, M.b, M.v, nullptr, nullptr, nullptr);
+            mg_smooth_kernel<false, false>
+                <<<grid, kT, 0, st>>>(f, w.mu[l], c, nullptr, w.mb[l], w.mv[l], nullptr, nullptr, nullptr);
     }
-    if (L == 1) mg_out_kernel<<<P->nblk, kT, 0, st>>>(geo(P), C.v, P->r, P->z, P->partial);
+    if (L == 1) mg_out_kernel<<<dim3(P->nblk, n), kT, 0, st>>>(geo(P), w.mv[0], w.r, w.z, w.partial);
 }
 
 // Host side of the tall-skinny QR: fold the blocks' factors into one
@@ -1088,12 +1198,6 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
     const size_t vb = sizeof(double) * np;
     if ((e = cudaMalloc(&P->gate, np)) != cudaSuccess || (e = cudaMalloc(&P->code, sizeof(uint16_t) * np)) != cudaSuccess ||
         (e = cudaMalloc(&P->gphi, vb)) != cudaSuccess ||
-        (e = cudaMalloc(&P->x, vb)) != cudaSuccess || (e = cudaMalloc(&P->r, vb)) != cudaSuccess ||
-        (e = cudaMalloc(&P->z, vb)) != cudaSuccess || (e = cudaMalloc(&P->p, vb)) != cudaSuccess ||
-        (e = cudaMalloc(&P->Ap, vb)) != cudaSuccess || (e = cudaMalloc(&P->b, vb)) != cudaSuccess ||
-        (e = cudaMalloc(&P->partial, sizeof(double) * 2 * P->nblk)) != cudaSuccess ||
-        (e = cudaMalloc(&P->s, sizeof(double) * 8)) != cudaSuccess ||
-        (e = cudaMallocHost(&P->host_pinned, sizeof(double) * 8)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&P->work, cudaStreamNonBlocking)) != cudaSuccess) {
         free_all(P);
         delete P;
@@ -1119,86 +1223,117 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
         delete P;
         return ms;
     }
+    if ((e = space_alloc(P, P->one, 1)) != cudaSuccess) {
+        free_all(P);
+        delete P;
+        return pfail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
+                     std::string("CG vectors: ") + cudaGetErrorString(e));
+    }
     *out = P;
     return KHP_OK;
 }
 
-// one CG iteration: 5 launches with the Jacobi preconditioner, the
-// V-cycle's in place of the z = r / diag step with the multigrid one
-static void cg_iteration(khp_poisson_s* P, const khp::poisson::Geo& g, cudaStream_t st) {
+// one CG iteration of n right-hand sides: 5 launches with the Jacobi
+// preconditioner, the V-cycle's in place of the z = r / diag step with the
+// multigrid one
+static void cg_iteration(khp_poisson_s* P, const khp_poisson_s::CGSpace& w, const khp::poisson::Geo& g,
+                         cudaStream_t st, int n) {
     using namespace khp::poisson;
     const int nb = P->nblk;
-    apply_kernel<<<nb, kT, 0, st>>>(g, P->p, P->Ap, P->partial);
-    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 2, P->s);
+    const dim3 grid(nb, n);
+    apply_kernel<<<grid, kT, 0, st>>>(g, w.p, w.Ap, w.partial);
+    finish_kernel<<<n, kT, 0, st>>>(w.partial, nb, 2, w.s);
     if (mg_active(P)) {
-        update_mg_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->mg[0].b);
-        mg_vcycle(P, st);
+        update_mg_kernel<<<grid, kT, 0, st>>>(g, w.s, w.p, w.Ap, w.x, w.r, w.mb[0]);
+        mg_vcycle(P, w, st, n);
     } else {
-        update_kernel<<<nb, kT, 0, st>>>(g, P->s, P->p, P->Ap, P->x, P->r, P->z, P->partial);
+        update_kernel<<<grid, kT, 0, st>>>(g, w.s, w.p, w.Ap, w.x, w.r, w.z, w.partial);
     }
-    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 3, P->s);
-    direction_kernel<<<nb, kT, 0, st>>>(g, P->s, P->z, P->p);
+    finish_kernel<<<n, kT, 0, st>>>(w.partial, nb, 3, w.s);
+    direction_kernel<<<grid, kT, 0, st>>>(g, w.s, w.z, w.p);
 }
 
-// CG solve of A phi = coef * rho_scale * rho (free points) with the gate
-// potentials gphi (the handle's, or zeros for grounded gates); phi is the
-// start at the free points and the solution on return.  Synchronous.
-static khp_status cg_solve(khp_poisson P, const double* rho_dev, double rho_scale, const double* gphi,
-                           double* phi_dev, double tol, int max_iter, int* iterations, double* rel_residual) {
+// CG solves of A phi_k = coef * rho_scale * rho_k (free points) for the n
+// right-hand sides of w (rho_k at rho_dev + k ld_rho, phi_k at phi_dev +
+// k ld_phi) with the gate potentials gphi (the handle's, or zeros for
+// grounded gates); phi_k is the start at the free points and the solution
+// on return.  All right-hand sides iterate until the largest relative
+// residual is at most tol.  Synchronous.
+static khp_status cg_solve(khp_poisson P, khp_poisson_s::CGSpace& w, int n, const double* rho_dev,
+                           long long ld_rho, double rho_scale, const double* gphi, double* phi_dev,
+                           long long ld_phi, double tol, int max_iter, int* iterations, double* rel_residual) {
     using namespace khp::poisson;
     const Geo g = geo(P);
     const int nb = P->nblk;
+    const dim3 grid(nb, n);
     // the caller's work (rho, phi) is complete before the private stream starts
     PCK(cudaStreamSynchronize(P->stream));
     cudaStream_t st = P->work;
-    double* hp = P->host_pinned;
-    rhs_kernel<<<nb, kT, 0, st>>>(g, rho_dev, gphi, P->coef * rho_scale, phi_dev, P->b, P->x, P->partial);
-    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 0, P->s);
-    apply_kernel<<<nb, kT, 0, st>>>(g, P->x, P->Ap, P->partial);
+    double* hp = w.host;
+    rhs_kernel<<<grid, kT, 0, st>>>(g, rho_dev, ld_rho, gphi, P->coef * rho_scale, phi_dev, ld_phi, w.b, w.x,
+                                    w.partial);
+    finish_kernel<<<n, kT, 0, st>>>(w.partial, nb, 0, w.s);
+    apply_kernel<<<grid, kT, 0, st>>>(g, w.x, w.Ap, w.partial);
     const bool mg = mg_active(P);
     if (mg) {
-        init_mg_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->mg[0].b);
-        mg_vcycle(P, st);
+        init_mg_kernel<<<grid, kT, 0, st>>>(g, w.b, w.Ap, w.r, w.mb[0]);
+        mg_vcycle(P, w, st, n);
     } else {
-        init_kernel<<<nb, kT, 0, st>>>(g, P->b, P->Ap, P->r, P->z, P->p, P->partial);
+        init_kernel<<<grid, kT, 0, st>>>(g, w.b, w.Ap, w.r, w.z, w.p, w.partial);
     }
-    finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, 1, P->s);
+    finish_kernel<<<n, kT, 0, st>>>(w.partial, nb, 1, w.s);
     PCKL("CG set-up launches");
-    if (mg) PCK(cudaMemcpyAsync(P->p, P->z, sizeof(double) * P->np, cudaMemcpyDeviceToDevice, st));
-    PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+    if (mg) PCK(cudaMemcpyAsync(w.p, w.z, sizeof(double) * P->np * n, cudaMemcpyDeviceToDevice, st));
+    // the largest relative residual over the right-hand sides (a zero
+    // right-hand side counts its absolute residual, zero from a zero start)
+    auto worst = [&]() {
+        double m = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double bb = hp[8 * k + 5], rr = hp[8 * k + 4];
+            const double rel = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+            m = std::isnan(rel) ? rel : std::max(m, rel);
+            if (std::isnan(m)) break;
+        }
+        return m;
+    };
+    PCK(cudaMemcpyAsync(hp, w.s, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
-    const double bb = hp[5];
-    double rel = bb > 0.0 ? std::sqrt(hp[4] / bb) : std::sqrt(hp[4]);
+    double rel = worst();
+    if (!std::isfinite(rel)) return pfail(KHP_ERR_BREAKDOWN, "Poisson CG: non-finite initial residual");
     int it = 0;
-    // a zero right-hand side with a zero start is already solved
     // residual check every 16 Jacobi-preconditioned iterations or every 8
     // multigrid ones (the graph holds the iterations between two checks)
     const int per_check = mg ? 8 : 16;
     while (rel > tol && it < max_iter) {
         const int chunk = std::min(per_check, max_iter - it);
         if (chunk == per_check) {
-            if (!P->have_chunk) {
+            if (w.have_chunk && w.chunk_n != n) {
+                cudaGraphExecDestroy(w.chunk);
+                w.have_chunk = false;
+            }
+            if (!w.have_chunk) {
                 cudaGraph_t graph;
                 PCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                for (int k = 0; k < per_check; ++k) cg_iteration(P, g, st);
+                for (int k = 0; k < per_check; ++k) cg_iteration(P, w, g, st, n);
                 PCK(cudaStreamEndCapture(st, &graph));
-                const cudaError_t e = cudaGraphInstantiate(&P->chunk, graph, 0);
+                const cudaError_t e = cudaGraphInstantiate(&w.chunk, graph, 0);
                 cudaGraphDestroy(graph);
                 PCK(e);
-                P->have_chunk = true;
+                w.have_chunk = true;
+                w.chunk_n = n;
             }
-            PCK(cudaGraphLaunch(P->chunk, st));
+            PCK(cudaGraphLaunch(w.chunk, st));
         } else {
-            for (int k = 0; k < chunk; ++k) cg_iteration(P, g, st);
+            for (int k = 0; k < chunk; ++k) cg_iteration(P, w, g, st, n);
         }
         PCKL("CG iterations");
         it += chunk;
-        PCK(cudaMemcpyAsync(hp, P->s, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+        PCK(cudaMemcpyAsync(hp, w.s, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, st));
         PCK(cudaStreamSynchronize(st));
-        rel = bb > 0.0 ? std::sqrt(hp[4] / bb) : std::sqrt(hp[4]);
+        rel = worst();
         if (!std::isfinite(rel)) return pfail(KHP_ERR_BREAKDOWN, "Poisson CG produced a non-finite residual");
     }
-    output_kernel<<<nb, kT, 0, st>>>(g, P->x, gphi, phi_dev);
+    output_kernel<<<grid, kT, 0, st>>>(g, w.x, gphi, phi_dev, ld_phi);
     PCKL("CG output");
     PCK(cudaStreamSynchronize(st));
     if (iterations) *iterations = it;
@@ -1207,13 +1342,68 @@ static khp_status cg_solve(khp_poisson P, const double* rho_dev, double rho_scal
     return KHP_OK;
 }
 
+static khp_status ensure_zeros(khp_poisson P) {
+    if (P->r_zero) return KHP_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&P->r_zero, sizeof(double) * P->np)) != cudaSuccess)
+        return pfail(KHP_ERR_OOM, std::string("zero gate potentials: ") + cudaGetErrorString(e));
+    PCK(cudaMemsetAsync(P->r_zero, 0, sizeof(double) * P->np, P->work));
+    PCK(cudaStreamSynchronize(P->work));
+    return KHP_OK;
+}
+
+// nrhs solves (contiguous [nrhs][Np] rho and phi, rho scaled by rho_scale)
+// in batches of at most kMaxRhs right-hand sides on the handle's second CG
+// space; iterations = the most any batch took, rel = the largest residual
+static khp_status cg_solve_batches(khp_poisson P, const double* rho_dev, double rho_scale, const double* gphi,
+                                   double* phi_dev, int nrhs, double tol, int max_iter, int* iterations,
+                                   double* rel_residual) {
+    const int cap = std::min(nrhs, khp_poisson_s::kMaxRhs);
+    if (P->many.cap < cap) {
+        const cudaError_t e = space_alloc(P, P->many, cap);
+        if (e != cudaSuccess) {
+            space_free(P->many);
+            return pfail(e == cudaErrorMemoryAllocation ? KHP_ERR_OOM : KHP_ERR_CUDA,
+                         std::string("CG vectors of a batch: ") + cudaGetErrorString(e));
+        }
+    }
+    int it_max = 0;
+    double rel_max = 0.0;
+    khp_status st = KHP_OK;
+    for (int k0 = 0; k0 < nrhs && st == KHP_OK; k0 += cap) {
+        const int n = std::min(cap, nrhs - k0);
+        int it = 0;
+        double rel = 0.0;
+        st = cg_solve(P, P->many, n, rho_dev + (size_t)k0 * P->np, P->np, rho_scale, gphi,
+                      phi_dev + (size_t)k0 * P->np, P->np, tol, max_iter, &it, &rel);
+        it_max = std::max(it_max, it);
+        rel_max = std::max(rel_max, rel);
+    }
+    if (iterations) *iterations = it_max;
+    if (rel_residual) *rel_residual = rel_max;
+    return st;
+}
+
 khp_status khp_poisson_solve(khp_poisson P, const double* rho_dev, double* phi_dev, double tol, int max_iter,
                              int* iterations, double* rel_residual) {
     khp_set_error(KHP_OK, "");
     if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
     if (!rho_dev || !phi_dev) return pfail(KHP_ERR_INVALID_ARG, "rho or phi is NULL");
     if (!(tol > 0.0) || max_iter < 1) return pfail(KHP_ERR_INVALID_ARG, "need tol > 0 and max_iter >= 1");
-    return cg_solve(P, rho_dev, 1.0, P->gphi, phi_dev, tol, max_iter, iterations, rel_residual);
+    return cg_solve(P, P->one, 1, rho_dev, P->np, 1.0, P->gphi, phi_dev, P->np, tol, max_iter, iterations,
+                    rel_residual);
+}
+
+khp_status khp_poisson_solve_many(khp_poisson P, const double* rho_dev, double* phi_dev, int nrhs, int grounded,
+                                  double tol, int max_iter, int* iterations, double* max_rel_residual) {
+    khp_set_error(KHP_OK, "");
+    if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
+    if (!rho_dev || !phi_dev) return pfail(KHP_ERR_INVALID_ARG, "rho or phi is NULL");
+    if (nrhs < 1) return pfail(KHP_ERR_INVALID_ARG, "nrhs must be >= 1");
+    if (!(tol > 0.0) || max_iter < 1) return pfail(KHP_ERR_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+    if (grounded) CKSP(ensure_zeros(P));
+    return cg_solve_batches(P, rho_dev, 1.0, grounded ? P->r_zero : P->gphi, phi_dev, nrhs, tol, max_iter,
+                            iterations, max_rel_residual);
 }
 
 khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* phi_dev, double mix, double* V_dev,
@@ -1224,12 +1414,12 @@ khp_status khp_sp_update(khp_poisson P, const double* V_ext_dev, const double* p
     if (!(mix > 0.0 && mix <= 1.0)) return pfail(KHP_ERR_INVALID_ARG, "mix must be in (0, 1]");
     using namespace khp::poisson;
     PCK(cudaStreamSynchronize(P->stream));
-    mix_kernel<<<P->nblk, kT, 0, P->work>>>(P->np, V_ext_dev, phi_dev, mix, V_dev, P->partial);
-    max_finish_kernel<<<1, kT, 0, P->work>>>(P->partial, P->nblk, P->s + 6);
+    mix_kernel<<<P->nblk, kT, 0, P->work>>>(P->np, V_ext_dev, phi_dev, mix, V_dev, P->one.partial);
+    max_finish_kernel<<<1, kT, 0, P->work>>>(P->one.partial, P->nblk, P->one.s + 6);
     PCKL("linear update");
-    PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->work));
+    PCK(cudaMemcpyAsync(P->one.host + 6, P->one.s + 6, sizeof(double), cudaMemcpyDeviceToHost, P->work));
     PCK(cudaStreamSynchronize(P->work));
-    if (max_change) *max_change = P->host_pinned[6];
+    if (max_change) *max_change = P->one.host[6];
     return KHP_OK;
 }
 
@@ -1287,13 +1477,13 @@ khp_status khp_sp_anderson(khp_poisson P, const double* V_ext_dev, const double*
         PCK(cudaStreamSynchronize(st));
         anderson_solve(P->a_host, nb, m, np, c.gamma);
     }
-    anderson_update_kernel<<<nb, kT, 0, st>>>(np, m, beta, c, V_dev, P->a_f, P->a_dv, P->a_df, P->partial);
-    max_finish_kernel<<<1, kT, 0, st>>>(P->partial, nb, P->s + 6);
+    anderson_update_kernel<<<nb, kT, 0, st>>>(np, m, beta, c, V_dev, P->a_f, P->a_dv, P->a_df, P->one.partial);
+    max_finish_kernel<<<1, kT, 0, st>>>(P->one.partial, nb, P->one.s + 6);
     PCKL("Anderson update");
-    PCK(cudaMemcpyAsync(P->host_pinned + 6, P->s + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCK(cudaMemcpyAsync(P->one.host + 6, P->one.s + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     PCK(cudaStreamSynchronize(st));
     P->a_count += 1;
-    if (max_change) *max_change = P->host_pinned[6];
+    if (max_change) *max_change = P->one.host[6];
     return KHP_OK;
 }
 
@@ -1480,32 +1670,29 @@ khp_status khp_sp_relax_occupations(khp_poisson P, const double* dens_dev, const
     if (!P->r_phig) {
         const int rows = KHP_MAX_M * ((KHP_MAX_M + kRJ - 1) / kRJ);
         cudaError_t e;
+        CKSP(ensure_zeros(P));
         if ((e = cudaMalloc(&P->r_phig, sizeof(double) * np)) != cudaSuccess ||
-            (e = cudaMalloc(&P->r_zero, sizeof(double) * np)) != cudaSuccess ||
             (e = cudaMalloc(&P->r_partial, sizeof(double) * (size_t)rows * nb * (kRJ + 1))) != cudaSuccess ||
             (e = cudaMalloc(&P->r_out, sizeof(double) * (size_t)rows * (kRJ + 1))) != cudaSuccess ||
             (e = cudaMallocHost(&P->r_host, sizeof(double) * (size_t)rows * (kRJ + 1))) != cudaSuccess)
             return pfail(KHP_ERR_OOM, std::string("relaxed step buffers: ") + cudaGetErrorString(e));
-        PCK(cudaMemsetAsync(P->r_zero, 0, sizeof(double) * np, P->work));
         PCK(cudaMemsetAsync(P->r_phig, 0, sizeof(double) * np, P->work));
         PCK(cudaStreamSynchronize(P->work));
         P->r_have_phig = false;
     }
     const int max_iter = 100000;
     if (!P->r_have_phig) {
-        CKSP(cg_solve(P, P->r_zero, 1.0, P->gphi, P->r_phig, tol, max_iter, nullptr, nullptr));
+        CKSP(cg_solve(P, P->one, 1, P->r_zero, np, 1.0, P->gphi, P->r_phig, np, tol, max_iter, nullptr, nullptr));
         P->r_have_phig = true;
     }
-    // unit-occupation potentials (grounded gates), each started from the
-    // previous call's solution for the same state index
+    // unit-occupation potentials (grounded gates), solved together, each
+    // started from the previous call's solution for the same state index
     if (P->r_nq < n) {
         PCK(cudaMemsetAsync(P->r_Q + (size_t)P->r_nq * np, 0, sizeof(double) * (size_t)(n - P->r_nq) * np, P->work));
         PCK(cudaStreamSynchronize(P->work));
     }
     const double h3inv = 1.0 / (P->h * P->h * P->h);
-    for (int j = 0; j < n; ++j)
-        CKSP(cg_solve(P, dens_dev + (size_t)j * np, h3inv, P->r_zero, P->r_Q + (size_t)j * np, tol, max_iter,
-                      nullptr, nullptr));
+    CKSP(cg_solve_batches(P, dens_dev, h3inv, P->r_zero, P->r_Q, n, tol, max_iter, nullptr, nullptr));
     P->r_nq = std::max(P->r_nq, n);
     cudaStream_t st = P->work;
     relax_dots_kernel<<<dim3(nb, n, nch), kT, 0, st>>>(np, n, dens_dev, P->r_Q, P->r_phig, V_dev, V_ext_dev,
@@ -1543,10 +1730,13 @@ khp_status khp_poisson_set_preconditioner(khp_poisson P, int kind, int* levels) 
     if (!P) return pfail(KHP_ERR_INVALID_ARG, "handle is NULL");
     if (kind != KHP_POISSON_PRECOND_JACOBI && kind != KHP_POISSON_PRECOND_MULTIGRID)
         return pfail(KHP_ERR_INVALID_ARG, "unknown preconditioner");
-    if (kind != P->precond && P->have_chunk) {
+    if (kind != P->precond) {
         PCK(cudaStreamSynchronize(P->work));
-        cudaGraphExecDestroy(P->chunk);
-        P->have_chunk = false;
+        for (khp_poisson_s::CGSpace* w : {&P->one, &P->many})
+            if (w->have_chunk) {
+                cudaGraphExecDestroy(w->chunk);
+                w->have_chunk = false;
+            }
     }
     P->precond = kind;
     if (levels) *levels = mg_active(P) ? P->mg_n : 0;

@@ -72,6 +72,24 @@ class Poisson:
         self.last_iterations, self.last_residual = it.value, rel.value
         return phi
 
+    def solve_many(self, rho, phi=None, grounded=False, tol=1e-12, max_iter=20000):
+        """phi [nrhs, Np] (V) of the densities rho [nrhs, Np] (nm^-3),
+        solved side by side (khp_poisson_solve_many); grounded=True sets the
+        gate potentials to zero.  `phi` (if given) holds the starting
+        guesses and is overwritten."""
+        rho = _dev(rho, torch.float64, self.device).reshape(-1, self.np_).contiguous()
+        nrhs = rho.shape[0]
+        if phi is None:
+            phi = torch.zeros(nrhs, self.np_, dtype=torch.float64, device=self.device)
+        if phi.shape != (nrhs, self.np_) or not phi.is_contiguous():
+            raise ValueError("phi must be a contiguous [nrhs, Np] tensor")
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        _lib.check(self.lib.khp_poisson_solve_many(self.handle, _ptr(rho), _ptr(phi), int(nrhs), int(bool(grounded)),
+                                                   float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(rel)))
+        self.last_iterations, self.last_residual = it.value, rel.value
+        return phi
+
     def update(self, V, phi, mix, V_ext=None):
         """V <- (1 - mix) V + mix (V_ext + phi) in place; returns max |dV|."""
         ch = ctypes.c_double(0.0)

@@ -80,6 +80,7 @@ def test_host_side_validation_of_the_next_rows(lib):
     assert b"NULL" in lib.khp_last_error()
     assert lib.khp_sp_anderson_reset(None) == 1
     assert lib.khp_poisson_set_preconditioner(None, 1, None) == 1
+    assert lib.khp_poisson_solve_many(None, buf, buf, 2, 1, 1e-10, 100, None, None) == 1
     assert lib.khp_poisson_destroy(None) == 0
 
 

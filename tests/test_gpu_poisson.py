@@ -109,6 +109,38 @@ def test_poisson_manufactured_potential_at_1p5m_points(khp):
     P.close()
 
 
+@pytest.mark.parametrize("kind", ["multigrid", "jacobi"])
+def test_poisson_solve_many_matches_the_oracle(khp, kind):
+    """khp_poisson_solve_many: 37 right-hand sides (a batch of 32 and one of
+    5) with grounded gates against the oracle's direct solves, and 3 with
+    the handle's gate potentials against single solves."""
+    from paper_2607_08447_b300.poisson import Poisson
+    nx, ny, nz, h = 33, 17, 12, 0.5
+    rng = np.random.default_rng(21)
+    gate = _end_gates(nx, ny, nz)
+    gate |= (rng.random((nz, ny, nx)) < 0.04).astype(np.uint8)
+    gphi = rng.uniform(-0.5, 0.8, (nz, ny, nx))
+    Np = nx * ny * nz
+    rho = rng.random((37, Np)) * 1e-3
+    rho[5] = 0.0                                   # a zero right-hand side
+    P = Poisson(nx, ny, nz, h, gate, gphi, preconditioner=kind)
+    phi = P.solve_many(torch.from_numpy(rho).cuda(), grounded=True, tol=1e-13, max_iter=50000).cpu().numpy()
+    assert P.last_residual <= 1e-13
+    zero = np.zeros((nz, ny, nx))
+    for k in range(37):
+        ref = po.solve(nx, ny, nz, h, gate, zero, rho[k])
+        assert np.abs(phi[k] - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300), k
+    assert np.abs(phi[5]).max() == 0.0
+    sub = torch.from_numpy(rho[:3]).cuda()
+    many = P.solve_many(sub, tol=1e-13, max_iter=50000).cpu().numpy()
+    for k in range(3):
+        one = P.solve(sub[k].clone(), tol=1e-13, max_iter=50000).cpu().numpy()
+        ref = po.solve(nx, ny, nz, h, gate, gphi, rho[k])
+        assert np.abs(many[k] - ref).max() <= 1e-10 * np.abs(ref).max()
+        assert np.abs(many[k] - one).max() <= 1e-10 * np.abs(ref).max()
+    P.close()
+
+
 def test_poisson_multigrid_unavailable_without_gates(khp):
     """A grid without gates has a singular operator: no multigrid hierarchy
     (the coarsest level has no Cholesky factor), the handle reports the
