@@ -402,7 +402,8 @@ khp_status khp_state_densities(khp_handle h, const void* evecs_dev, int n, doubl
  * states of H(V) held fixed:
  *   Q_j   potential of a unit occupation of state j (density dens_j / h^3,
  *         gates grounded), phi_g the potential of the gates alone (CG on
- *         the device, each Q_j started from the previous call's);
+ *         the device, the Q_j solved side by side as in
+ *         khp_poisson_solve_many, each started from the previous call's);
  *   K_ij  = sum_p dens_i(p) Q_j(p),  e0_i = E_i + sum_p dens_i(p) (phi_g - (V - V_ext))(p);
  *   f     the Fermi-Dirac occupations of the levels eps = e0 + K f at the
  *         Fermi level holding n_holes (Newton's method on eps, host);
@@ -418,7 +419,8 @@ khp_status khp_state_densities(khp_handle h, const void* evecs_dev, int n, doubl
  *  occ_host   optional float64 [n] output, the occupations; mu_out optional
  * Synchronous.  Errors: INVALID_ARG (NULL, n outside 1..64, kT <= 0,
  * n_holes outside (0, n), non-finite level), OOM (2 + n Np doubles on the
- * handle), NOT_CONVERGED (a CG solve), BREAKDOWN (singular Newton system). */
+ * handle, and the batch vectors of khp_poisson_solve_many), NOT_CONVERGED
+ * (a CG solve), BREAKDOWN (singular Newton system). */
 khp_status khp_sp_relax_occupations(khp_poisson p, const double* dens_dev, const double* E_host, int n,
                                     double n_holes, double kT, const double* V_dev, const double* V_ext_dev,
                                     double* phi_dev, double tol, double* occ_host, double* mu_out);
