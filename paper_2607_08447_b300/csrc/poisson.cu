@@ -31,7 +31,9 @@ struct khp_poisson_s {
     uint8_t* gate;
     uint16_t* code;        // neighbour codes of the grid's points (see Geo)
     double* gphi;
-    int nblk;
+    int nblk;              // blocks of the kernels with block partials (2 per SM: each thread
+                           // takes several points, so the block reductions stay cheap)
+    int sblk;              // blocks of the streaming multigrid kernels (8 per SM)
     cudaStream_t work;     // private stream: the CG chunks are captured and replayed on it
     // Anderson mixing of the SP loop (allocated on first use)
     double *a_dv, *a_df;   // [kMaxDepth][np] rings of iterate / residual differences
@@ -136,22 +138,30 @@ __device__ __forceinline__ long long nbr(const Geo& g, long long p, int ix, int 
     }
 }
 
-// block-partial sums of (a . b) and (c . d) into partial[block][0..1]
+// block-partial sums of (a . b) and (c . d) into partial[block][0..1]:
+// warp shuffles, then the warps' sums in order (every thread of the block
+// calls it)
 __device__ __forceinline__ void block_sum2(double va, double vb, double* partial) {
-    __shared__ double sa[kT], sb[kT];
-    sa[threadIdx.x] = va;
-    sb[threadIdx.x] = vb;
-    __syncthreads();
-    for (int st = kT / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) {
-            sa[threadIdx.x] += sa[threadIdx.x + st];
-            sb[threadIdx.x] += sb[threadIdx.x + st];
-        }
-        __syncthreads();
+    __shared__ double sa[kT / 32], sb[kT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        va += __shfl_down_sync(0xffffffffu, va, o);
+        vb += __shfl_down_sync(0xffffffffu, vb, o);
     }
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = va;
+        sb[threadIdx.x >> 5] = vb;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = sa[0];
-        partial[2 * blockIdx.x + 1] = sb[0];
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int w = 0; w < kT / 32; ++w) {
+            a += sa[w];
+            b += sb[w];
+        }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
     }
 }
 
@@ -973,7 +983,7 @@ khp_status mg_build(khp_poisson_s* P) {
         return pfail(KHP_ERR_OOM, std::string("multigrid levels: ") + cudaGetErrorString(e));
     }
     for (int l = 1; l < L; ++l) {
-        const int nb = mg_blocks(P->mg[l].np, P->nblk);
+        const int nb = mg_blocks(P->mg[l].np, P->sblk);
         mg_gate_kernel<<<nb, kT, 0, P->stream>>>(mg_geo(P, l - 1), mg_geo(P, l), P->mg[l].gate);
         mg_code_kernel<<<nb, kT, 0, P->stream>>>(mg_geo(P, l), P->mg[l].code);
     }
@@ -1062,20 +1072,20 @@ void mg_vcycle(khp_poisson_s* P, const khp_poisson_s::CGSpace& w, cudaStream_t s
     const int L = P->mg_n;
     for (int l = 0; l + 1 < L; ++l) {
         const Geo f = mg_geo(P, l), c = mg_geo(P, l + 1);
-        mg_presmooth_kernel<<<dim3(mg_blocks(f.np, P->nblk), n), kT, 0, st>>>(f, w.mb[l], w.mv[l]);
-        mg_restrict_kernel<<<dim3(mg_blocks(8 * c.np, P->nblk), n), kT, 0, st>>>(f, w.mv[l], w.mb[l], c,
+        mg_presmooth_kernel<<<dim3(mg_blocks(f.np, P->sblk), n), kT, 0, st>>>(f, w.mb[l], w.mv[l]);
+        mg_restrict_kernel<<<dim3(mg_blocks(8 * c.np, P->sblk), n), kT, 0, st>>>(f, w.mv[l], w.mb[l], c,
                                                                                  w.mb[l + 1]);
     }
     mg_coarse_kernel<<<n, kT, 0, st>>>(mg_geo(P, L - 1), w.mb[L - 1], w.mv[L - 1], P->mg_cinv, P->mg_cidx,
                                        P->mg_nf);
     for (int l = L - 2; l >= 0; --l) {
         const Geo f = mg_geo(P, l), c = mg_geo(P, l + 1);
-        const dim3 grid(mg_blocks(f.np, P->nblk), n);
+        const dim3 grid(mg_blocks(f.np, P->sblk), n);
         mg_smooth_kernel<true, false>
             <<<grid, kT, 0, st>>>(f, w.mv[l], c, w.mv[l + 1], w.mb[l], w.mu[l], nullptr, nullptr, nullptr);
-        if (l == 0)
+        if (l == 0)      // block partials: the CG's block count
             mg_smooth_kernel<false, true>
-                <<<grid, kT, 0, st>>>(f, w.mu[0], c, nullptr, w.mb[0], nullptr, w.r, w.z, w.partial);
+                <<<dim3(P->nblk, n), kT, 0, st>>>(f, w.mu[0], c, nullptr, w.mb[0], nullptr, w.r, w.z, w.partial);
         else
             mg_smooth_kernel<false, false>
                 <<<grid, kT, 0, st>>>(f, w.mu[l], c, nullptr, w.mb[l], w.mv[l], nullptr, nullptr, nullptr);
@@ -1193,7 +1203,14 @@ khp_status khp_poisson_create(khp_poisson* out, int nx, int ny, int nz, double h
     P->coef = 1.602176634e-19 / (8.8541878128e-21 * eps_r);
     P->h2inv = 1.0 / (h_nm * h_nm);
     P->stream = (cudaStream_t)stream;
-    P->nblk = (int)std::min<long long>((np + kT - 1) / kT, 1184);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        delete P;
+        return pfail(KHP_ERR_CUDA, "no CUDA device");
+    }
+    P->nblk = (int)std::min<long long>((np + kT - 1) / kT, 2LL * sms);
+    P->sblk = (int)std::min<long long>((np + kT - 1) / kT, 8LL * sms);
     cudaError_t e = cudaSuccess;
     const size_t vb = sizeof(double) * np;
     if ((e = cudaMalloc(&P->gate, np)) != cudaSuccess || (e = cudaMalloc(&P->code, sizeof(uint16_t) * np)) != cudaSuccess ||
