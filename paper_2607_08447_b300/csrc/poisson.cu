@@ -1257,17 +1257,18 @@ static void cg_iteration(khp_poisson_s* P, const khp_poisson_s::CGSpace& w, cons
                          cudaStream_t st, int n) {
     using namespace khp::poisson;
     const int nb = P->nblk;
-    const dim3 grid(nb, n);
+    const dim3 grid(nb, n);              // kernels with block partials
+    const dim3 sgrid(P->sblk, n);        // streaming kernels
     apply_kernel<<<grid, kT, 0, st>>>(g, w.p, w.Ap, w.partial);
     finish_kernel<<<n, kT, 0, st>>>(w.partial, nb, 2, w.s);
     if (mg_active(P)) {
-        update_mg_kernel<<<grid, kT, 0, st>>>(g, w.s, w.p, w.Ap, w.x, w.r, w.mb[0]);
+        update_mg_kernel<<<sgrid, kT, 0, st>>>(g, w.s, w.p, w.Ap, w.x, w.r, w.mb[0]);
         mg_vcycle(P, w, st, n);
     } else {
         update_kernel<<<grid, kT, 0, st>>>(g, w.s, w.p, w.Ap, w.x, w.r, w.z, w.partial);
     }
     finish_kernel<<<n, kT, 0, st>>>(w.partial, nb, 3, w.s);
-    direction_kernel<<<grid, kT, 0, st>>>(g, w.s, w.z, w.p);
+    direction_kernel<<<sgrid, kT, 0, st>>>(g, w.s, w.z, w.p);
 }
 
 // CG solves of A phi_k = coef * rho_scale * rho_k (free points) for the n
@@ -1293,7 +1294,7 @@ static khp_status cg_solve(khp_poisson P, khp_poisson_s::CGSpace& w, int n, cons
     apply_kernel<<<grid, kT, 0, st>>>(g, w.x, w.Ap, w.partial);
     const bool mg = mg_active(P);
     if (mg) {
-        init_mg_kernel<<<grid, kT, 0, st>>>(g, w.b, w.Ap, w.r, w.mb[0]);
+        init_mg_kernel<<<dim3(P->sblk, n), kT, 0, st>>>(g, w.b, w.Ap, w.r, w.mb[0]);
         mg_vcycle(P, w, st, n);
     } else {
         init_kernel<<<grid, kT, 0, st>>>(g, w.b, w.Ap, w.r, w.z, w.p, w.partial);
@@ -1350,7 +1351,7 @@ static khp_status cg_solve(khp_poisson P, khp_poisson_s::CGSpace& w, int n, cons
         rel = worst();
         if (!std::isfinite(rel)) return pfail(KHP_ERR_BREAKDOWN, "Poisson CG produced a non-finite residual");
     }
-    output_kernel<<<grid, kT, 0, st>>>(g, w.x, gphi, phi_dev, ld_phi);
+    output_kernel<<<dim3(P->sblk, n), kT, 0, st>>>(g, w.x, gphi, phi_dev, ld_phi);
     PCKL("CG output");
     PCK(cudaStreamSynchronize(st));
     if (iterations) *iterations = it;
