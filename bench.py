@@ -43,11 +43,17 @@ WORKLOAD = ("c2: 160x48x48 grid h=0.5nm (2.21M unknowns), FP64, lowest 16 of blo
 SOLVE_KW = dict(n_states=16, block_m=24, degree=180, precision=0, tol=1e-10, seed=1, max_iter=600, start="coarse")
 RANDOM_START_DEGREE = 120
 MIXED_DEGREE = 250        # defect-corrected FP32 filter (precision 2), coarse-grid start
-# block width of the relaxed-occupation SP loops: their solves need 5-6
-# outer iterations at 24 columns; measured over 24 iterations at C2 (B300,
-# s per SP iteration): 24 cols 0.683, 28 cols 0.594, 32 cols 0.685
-# (degree 200: 0.623), with identical iterates
-RELAXED_BLOCK_M = 28
+# SP loops: every solve after the first starts from the previous
+# iteration's whole Ritz block (eigenvectors and guard columns); measured
+# over 24 relaxed-occupation iterations at C2 (B300, s per SP iteration,
+# identical iterates): coarse-grid start at 24 columns 0.683, at 28
+# columns 0.562 (32: 0.685); block start at 28 columns degree 250 0.398,
+# degree 160 0.391, degree 100 0.422; at 24 columns degree 160 0.516.
+# The linear-mixing loop at 1.5 K oscillates (max |dV| ~1e-2 eV per
+# iteration): there the previous block is a poor start (0.578 against
+# 0.471 s per iteration from the coarse grid at 24 columns, degree 250)
+SP_BLOCK_M = 28
+SP_DEGREE = 160
 MIXED_DEGREE_WARM = 200   # the same filter from warm or random starts
 CROP = (32, 12, 12)
 # DRAM bytes per point-vector of the FP64 fused stencil launch, from ncu
@@ -554,22 +560,22 @@ def _h0_bench(p, dev, torch, khp):
 def _sp_bench(p, dev, torch, khp):
     """Schroedinger-Poisson loop on the C2 grid and fields: grounded gates on
     the two x faces, 2 holes at 1.5 K, linear mixing 0.3, defect-corrected
-    solves from the coarse-grid start (measured faster than starting from
-    the previous iteration's eigenvectors: 1.18 against 1.34 s per
-    relaxed-occupation iteration, identical iterates), up to 12 iterations
-    or max |dV| <= 1e-6 eV; then Anderson mixing at 20 K and the loop with
-    relaxed occupations at 1.5 K."""
+    solves from the coarse-grid start, up to 12 iterations or max |dV| <=
+    1e-6 eV; then Anderson mixing at 20 K and the loop with relaxed
+    occupations at 1.5 K, whose solves after the first start from the
+    previous iteration's whole Ritz block."""
     from paper_2607_08447_b300.poisson import Poisson, sp_solve
     gate = np.zeros((p.nz, p.ny, p.nx), dtype=np.uint8)
     gate[:, :, 0] = 1
     gate[:, :, -1] = 1
     g = khp.KPGrid.from_problem(p, device=dev)
     P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V), device=dev)
-    kw = dict(block_m=SOLVE_KW["block_m"], degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1, start="coarse")
+    kw_lin = dict(block_m=SOLVE_KW["block_m"], degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1, start="coarse")
+    kw = dict(block_m=SP_BLOCK_M, degree=SP_DEGREE, precision=2, tol=1e-10, seed=1, start="coarse")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = sp_solve(g, P, p.V, SOLVE_KW["n_states"], 2.0, T=1.5, mix=0.3, iters=12, tol_v=1e-6, strain=p.strain,
-                 B=p.B, gauge=p.gauge, solve_kw=kw, warm=False)
+                 B=p.B, gauge=p.gauge, solve_kw=kw_lin, warm=False)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     # the Poisson solve alone, from zero, on the final density
@@ -597,7 +603,10 @@ def _sp_bench(p, dev, torch, khp):
            "poisson_ms_cold": 1e3 * tp, "poisson_cold_iterations": cold_iterations,
            "poisson_multigrid_levels": P.mg_levels,
            "poisson_ms_cold_jacobi": 1e3 * tj, "poisson_cold_iterations_jacobi": jacobi_iterations,
-           "workload": "C2 grid and fields, grounded gates on both x faces, 2 holes, T 1.5 K, mix 0.3"}
+           "workload": "C2 grid and fields, grounded gates on both x faces, 2 holes, T 1.5 K, mix 0.3",
+           "solves": f"defect-corrected, {SOLVE_KW['block_m']} columns, degree {MIXED_DEGREE}, coarse-grid start; "
+                     f"the runs below: {SP_BLOCK_M} columns, degree {SP_DEGREE}, coarse-grid start then the "
+                     "previous iteration's Ritz block"}
     # Anderson mixing (library history, depth 6, damping 0.5) at 20 K, where
     # kT exceeds the splittings of the random wells and the density responds
     # smoothly to V; then the loop with relaxed occupations at 1.5 K, with
@@ -606,14 +615,12 @@ def _sp_bench(p, dev, torch, khp):
             ("relaxed_1p5k_linear", 1.5, dict(mix=0.5, relax=True)),
             ("relaxed_1p5k_anderson", 1.5, dict(mix=0.8, anderson_depth=4, relax=True)))
     for name, T, opt in runs:
-        kw_run = dict(kw, block_m=RELAXED_BLOCK_M) if opt.get("relax") else kw
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ra = sp_solve(g, P, p.V, SOLVE_KW["n_states"], 2.0, T=T, iters=24, tol_v=1e-6, strain=p.strain,
-                      B=p.B, gauge=p.gauge, solve_kw=kw_run, warm=False, **opt)
+                      B=p.B, gauge=p.gauge, solve_kw=kw, warm="block", **opt)
         torch.cuda.synchronize()
         out[name] = {"T_K": T, "iterations": len(ra.history), "s_total": time.perf_counter() - t0,
-                     "block_m": kw_run["block_m"],
                      "converged": ra.history[-1] <= 1e-6,
                      "max_dV_last_ev": [float(f"{x:.3g}") for x in ra.history[-4:]]}
         if ra.occupations is not None:

@@ -101,7 +101,12 @@ typedef struct {
  *                 columns; KHP_COARSE="degree,tol,extra" in the environment
  *                 replaces these) and prolongated trilinearly; falls
  *                 back to 0 when that grid has fewer than 4 (block_m + 8)
- *                 unknowns or block_m + 8 > 64.  khp_eigensolve only. */
+ *                 unknowns or block_m + 8 > 64.  khp_eigensolve only.
+ *  block_out_dev  optional complex128 [N][block_m] output (row-major): the
+ *                 final orthonormal Ritz block, all block_m columns (the
+ *                 n_states eigenvectors first, then the guard columns), a
+ *                 start block for a solve of a nearby Hamiltonian through
+ *                 warm_start_dev.  NULL: not written.  khp_eigensolve only. */
 typedef struct {
     int n_states;
     int block_m;
@@ -115,6 +120,7 @@ typedef struct {
     int warm_cols;
     int projections;
     int start;
+    void* block_out_dev;
 } khp_solver_opts;
 
 /* Per-solve statistics (optional output).  The filter timings come from

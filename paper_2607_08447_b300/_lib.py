@@ -40,7 +40,8 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_sweeps", ctypes.c_int), ("tol_ev", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("warm_start_dev", ctypes.c_void_p),
-                ("warm_cols", ctypes.c_int), ("projections", ctypes.c_int), ("start", ctypes.c_int)]
+                ("warm_cols", ctypes.c_int), ("projections", ctypes.c_int), ("start", ctypes.c_int),
+                ("block_out_dev", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):

@@ -1341,6 +1341,9 @@ struct Solve {
         CKS(S.orth(B[ib[0]]));
         CK(cudaMemcpy2DAsync(evecs_dev, sizeof(double2) * n, B[ib[0]], sizeof(double2) * m, sizeof(double2) * n,
                              g->n, cudaMemcpyDeviceToDevice, g->stream));
+        if (o.block_out_dev)
+            CK(cudaMemcpyAsync(o.block_out_dev, B[ib[0]], sizeof(double2) * g->n * m, cudaMemcpyDeviceToDevice,
+                               g->stream));
         CK(cudaStreamSynchronize(g->stream));
         for (int i = 0; i < n; ++i) evals_host[i] = th[i];
         double rmax = 0;
@@ -1423,6 +1426,7 @@ extern "C" khp_status khp_eigensolve_batched(const khp_handle* hs, int count, co
     if (!hs || !opts || !evals_host || !evecs_dev) return fail(KHP_ERR_INVALID_ARG, "NULL argument");
     if (count < 1) return fail(KHP_ERR_INVALID_ARG, "count must be >= 1");
     if (opts->warm_start_dev) return fail(KHP_ERR_INVALID_ARG, "warm starts are per problem: not in batched mode");
+    if (opts->block_out_dev) return fail(KHP_ERR_INVALID_ARG, "block output is per problem: not in batched mode");
     khp_solver_opts o = *opts;
     const int n = o.n_states;
     int dev0 = -1;

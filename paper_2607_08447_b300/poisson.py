@@ -167,7 +167,9 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
     relax=True relaxes the occupations within each update
     (khp_sp_relax_occupations) instead of fixing them at the Fermi-Dirac
     values of the current levels.  warm=True starts every eigensolve from
-    the previous iteration's eigenvectors; warm=False takes the start of
+    the previous iteration's eigenvectors; warm='block' from the previous
+    iteration's whole Ritz block (eigenvectors and guard columns; the first
+    solve takes the start of solve_kw); warm=False takes the start of
     solve_kw (e.g. start='coarse').  Returns SPResult (V on the device)."""
     kw = dict(block_m=max(n_states + 8, 16), degree=40, tol=1e-11, seed=1)
     kw.update(solve_kw or {})
@@ -177,12 +179,22 @@ def sp_solve(grid, poisson, V_ext, n_states, n_holes, T=1.5, mix=0.3, iters=20, 
     kT = KB_EV * T
     hist, piters = [], []
     prev = None
+    block = None
+    if warm == "block":
+        bm = kw["block_m"] + kw["block_m"] % 2
+        kw["block_m"] = bm
+        block = [torch.empty((grid.N, bm), dtype=torch.complex128, device=grid.device) for _ in range(2)]
     if anderson_depth > 0:
         poisson.reset_mixing()
-    for _ in range(iters):
+    for it in range(iters):
         grid.set_fields(V, strain, None, None, B, gauge)
-        r = grid.eigensolve(n_states, warm_start=prev, **kw)
-        prev = r.evecs if warm else None
+        if block is not None:
+            # the previous block starts this solve while the other receives its block
+            r = grid.eigensolve(n_states, warm_start=prev, block_out=block[it % 2], **kw)
+            prev = block[it % 2]
+        else:
+            r = grid.eigensolve(n_states, warm_start=prev, **kw)
+            prev = r.evecs if warm else None
         if relax:
             dens = grid.state_densities(r.evecs)
             _, f, mu = poisson.relax(dens, r.evals, n_holes, kT, V, V_ext, phi)

@@ -195,10 +195,12 @@ class KPGrid:
 
     def eigensolve(self, n_states, block_m=None, degree=20, max_iter=0, precision=0, refine_sweeps=2,
                    tol=1e-9, seed=1, warm_start=None, out=None, allow_not_converged=False, projections="tensor",
-                   start="random"):
+                   start="random", block_out=None):
         """Lowest n_states eigenpairs (khp_eigensolve).  start: 'random'
         (counter-based start block) or 'coarse' (the block of the 2x coarser
-        grid, prolongated); a warm_start block takes precedence."""
+        grid, prolongated); a warm_start block takes precedence.
+        block_out: a contiguous complex128 [N, block_m] device tensor that
+        receives the final Ritz block (all block_m columns)."""
         block_m = block_m or max(n_states + 8, 16)
         block_m += block_m % 2
         opts = _lib.SolverOpts()
@@ -213,6 +215,11 @@ class KPGrid:
             ws = _dev(warm_start, torch.complex128, self.device)
             opts.warm_start_dev = ctypes.c_void_p(ws.data_ptr())
             opts.warm_cols = ws.shape[1]
+        if block_out is not None:
+            if (block_out.dtype != torch.complex128 or tuple(block_out.shape) != (self.N, block_m)
+                    or not block_out.is_contiguous() or not block_out.is_cuda):
+                raise ValueError("block_out must be a contiguous complex128 [N, block_m] CUDA tensor")
+            opts.block_out_dev = ctypes.c_void_p(block_out.data_ptr())
         evals = np.zeros(n_states)
         res = np.zeros(n_states)
         evecs = out if out is not None else torch.empty((self.N, n_states), dtype=torch.complex128, device=self.device)

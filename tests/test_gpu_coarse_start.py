@@ -92,3 +92,32 @@ def test_coarse_start_spin_independent_h0(khp):
     assert np.abs(rc.evals - rr.evals).max() <= 1e-10
     # a 14x8x8 coarse grid at 1 nm: a coarser start than on larger grids
     assert rc.stats["res_history"][0] < 0.2 * rr.stats["res_history"][0]
+
+
+def test_block_output_restarts_a_solve(khp):
+    """block_out receives the final orthonormal Ritz block: its first
+    n_states columns are the returned eigenvectors; a solve of a slightly
+    changed potential warm-started from the whole block needs fewer outer
+    iterations than one from the coarse grid and finds the same levels as a
+    cold solve (both vs the dense oracle)."""
+    import torch
+    p = inputs.small_problem(12, 8, 6, h=0.5, seed=3, strain=True)
+    g = khp.KPGrid.from_problem(p)
+    n, m = 8, 16
+    blk = torch.empty((g.N, m), dtype=torch.complex128, device="cuda")
+    kw = dict(block_m=m, degree=30, tol=1e-11, seed=2)
+    r = g.eigensolve(n, block_out=blk, start="coarse", **kw)
+    X = blk.cpu().numpy()
+    assert np.abs(X[:, :n] - r.evecs.cpu().numpy()).max() == 0.0
+    assert np.abs(X.conj().T @ X - np.eye(m)).max() <= 1e-12
+    V2 = p.V + 1e-3 * inputs.smooth_noise(np.random.default_rng(8), p.V.shape)
+    g.set_fields(V2, p.strain, None, None, p.B, p.gauge)
+    warm = g.eigensolve(n, warm_start=blk.clone(), **kw)
+    cold = g.eigensolve(n, start="coarse", **kw)
+    ref, _ = eig.lowest_dense(kp.assemble(p.with_(V=V2)), n)
+    assert np.abs(warm.evals - ref).max() <= 1e-10
+    assert np.abs(cold.evals - ref).max() <= 1e-10
+    assert warm.stats["iterations"] < cold.stats["iterations"]
+    with pytest.raises(ValueError):
+        g.eigensolve(n, block_out=torch.empty((g.N, m - 2), dtype=torch.complex128, device="cuda"), **kw)
+    g.close()

@@ -276,8 +276,8 @@ def test_sp_loop_anderson_matches_oracle(khp, bands):
     g.close()
 
 
-@pytest.mark.parametrize("bands,depth", [(6, 0), (6, 3), (3, 0)])
-def test_sp_loop_relaxed_matches_oracle(khp, bands, depth):
+@pytest.mark.parametrize("bands,depth,warm", [(6, 0, True), (6, 3, True), (3, 0, True), (6, 3, "block")])
+def test_sp_loop_relaxed_matches_oracle(khp, bands, depth, warm):
     """Four iterations with relaxed occupations (2 holes, T = 1.5 K; linear
     mixing 0.5 or Anderson depth 3) from the same start: potential, levels,
     occupations and the max |dV| history agree with the oracle's loop
@@ -292,7 +292,7 @@ def test_sp_loop_relaxed_matches_oracle(khp, bands, depth):
     g = khp.KPGrid.from_problem(p, bands=bands)
     P = Poisson(p.nx, p.ny, p.nz, p.h, gate, gphi)
     r = sp_solve(g, P, p.V, n, nh, T=1.5, mix=0.5, iters=iters, tol_v=0.0, strain=p.strain,
-                 solve_kw=dict(block_m=16, degree=16, tol=1e-12), anderson_depth=depth, relax=True)
+                 solve_kw=dict(block_m=16, degree=16, tol=1e-12), anderson_depth=depth, relax=True, warm=warm)
     assert np.abs(np.array(r.history) - np.array(hist_or)).max() <= 1e-9
     assert np.abs(r.V.cpu().numpy() - V_or).max() <= 1e-10
     assert np.abs(r.evals - E_or).max() <= 1e-10
