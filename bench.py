@@ -642,7 +642,11 @@ def _ci_bench(p, dev, torch, khp):
     gate[:, :, -1] = 1
     g = khp.KPGrid.from_problem(p, device=dev, bands=3)
     P = Poisson(p.nx, p.ny, p.nz, p.h, gate, np.zeros_like(p.V), device=dev)
-    kw = dict(block_m=16, degree=MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1)
+    # H0 solve from the coarse grid at 12 columns, degree 250; measured on
+    # B300 (s per CI, the same J to 1e-12 eV): random start 16 columns
+    # degree 200 0.206, 12 columns 0.168; coarse start 16 columns degree
+    # 250 0.182, 160 0.204; 12 columns degree 250 0.149
+    kw = dict(block_m=12, degree=MIXED_DEGREE, precision=2, tol=1e-10, seed=1, start="coarse")
     ci_exchange(g, P, 4, p.material["delta_so"], solve_kw=kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -671,7 +675,9 @@ def _gtensor_bench(p, dev, torch, khp, j_ci):
     from paper_2607_08447_b300 import exchange as ex
     from paper_2607_08447_b300.gtensor import g_tensors
     g = khp.KPGrid.from_problem(p, device=dev)
-    kw = dict(block_m=12, degree=MIXED_DEGREE_WARM, precision=2, tol=1e-10, seed=1)
+    # measured on B300 (s per call, the same t to 1e-17 eV): random start
+    # degree 200 0.259; coarse start degree 250 0.231, degree 160 0.218
+    kw = dict(block_m=12, degree=160, precision=2, tol=1e-10, seed=1, start="coarse")
     g_tensors(g, solve_kw=kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
