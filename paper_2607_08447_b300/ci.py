@@ -167,16 +167,19 @@ def ci_detuning_sweep(grid, poisson, potentials, n_orb, delta_so, strain=None, s
                       e_c=None, T_c=1.0):
     """The CI at every potential of a detuning sweep (Fig. 2(f): the CI
     matrix is rebuilt for each gate configuration).  `potentials` is a
-    sequence of V fields for the H0 handle `grid`; each H0 solve starts
-    from the previous point's orbitals.  Returns the list of CIResult."""
+    sequence of V fields for the H0 handle `grid`; each H0 solve after the
+    first starts from the previous point's whole Ritz block (orbitals and
+    guard columns).  Returns the list of CIResult."""
     out = []
-    warm = None
-    for V in potentials:
+    kw0 = dict(solve_kw or {})
+    bm = kw0.get("block_m") or max(int(n_orb) + 8, 16)
+    kw0["block_m"] = bm + bm % 2
+    blocks = [torch.empty((grid.N, kw0["block_m"]), dtype=torch.complex128, device=grid.device) for _ in range(2)]
+    for i, V in enumerate(potentials):
         grid.set_fields(V, strain)
-        kw = dict(solve_kw or {})
-        if warm is not None and warm.shape[1] == int(n_orb):
-            kw["warm_start"] = warm
+        kw = dict(kw0, block_out=blocks[i % 2])
+        if i > 0:
+            kw["warm_start"] = blocks[(i - 1) % 2]
         r = ci_exchange(grid, poisson, n_orb, delta_so, solve_kw=kw, method=method, e_c=e_c, T_c=T_c)
-        warm = r.orbitals if r.orbitals.shape[1] == int(n_orb) else None
         out.append(r)
     return out
